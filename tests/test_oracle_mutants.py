@@ -1,0 +1,56 @@
+"""The oracle's pins must catch plausible mistakes in the oracle itself.
+
+Each case copies oracle/adpar_oracle.c to a temporary directory, plants one
+mistake (a dropped term, a wrong sign, index or tie rule, a transposed
+operand), builds it with the oracle's own flags and runs the pin suite
+against that build in a subprocess.  The suite must fail for every mutant.
+Nothing here touches the committed oracle or any GPU.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "adpar_oracle.c")
+
+MUTANTS = {
+    "max_tie_to_later": ("case O_MAX: return (t >= a) ? 1.0 : 0.0;",
+                         "case O_MAX: return (t > a) ? 1.0 : 0.0;"),
+    "min_tie_to_later": ("case O_MIN: return (t <= a) ? 1.0 : 0.0;",
+                         "case O_MIN: return (t < a) ? 1.0 : 0.0;"),
+    "mul_wrong_operand": ("case O_MUL: return t;\n", "case O_MUL: return a;\n"),
+    "linrec_jright_transposed": ("Jr->v[1][0] = prev[1];", "Jr->v[0][1] = prev[1];"),
+    "linrec_jleft_dropped_term": ("Jl->v[1][1] = x[0];", "Jl->v[1][1] = 1.0;"),
+    "scan_first_element_dropped": ("for (int c = 0; c < w; ++c) asb[c][0] += rsbar[c];",
+                                   "for (int c = 0; c < w; ++c) asb[c][0] += 0.0 * rsbar[c];"),
+    "scan_overwrites_adjoint": ("asb[c][i] += dr[c];", "asb[c][i] = dr[c];"),
+    "xd_exponent_dropped": ("r.e = a.e + b.e + e;", "r.e = a.e + b.e;"),
+    "hist_chain_wrong_factor": ("g[b] = ft * g[b];", "g[b] = fa * g[b];"),
+    "scatter_wrong_index": ("vsbar[j] += ysbar_inout[k];", "vsbar[j] += ysbar_inout[j];"),
+    "sqdist_sign": ("asbar[i * width + k] += -2.0 * diff * xb;",
+                    "asbar[i * width + k] += 2.0 * diff * xb;"),
+    "kmeans_sign": ("ybar * (-2.0) * (X[i * d + j] - C[arg * d + j]);",
+                    "ybar * (2.0) * (X[i * d + j] - C[arg * d + j]);"),
+    "prod_zero_count_off": ("if (first < 0) first = i;\n            ++nz;",
+                            "if (first < 0) first = i + 1;\n            ++nz;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(tmp_path, name):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, "mutation site not found exactly once: %s" % name
+    msrc = tmp_path / "mutant.c"
+    msrc.write_text(src.replace(old, new))
+    lib = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared",
+                           "-ffp-contract=off", "-fno-fast-math", "-o", str(lib),
+                           str(msrc), "-lm"])
+    env = dict(os.environ, ADPAR_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, "pins did not catch mutant %s:\n%s" % (name, r.stdout[-2000:])

@@ -1,0 +1,446 @@
+"""Pins of the FP64 oracle against what arXiv 2202.10297 and mathematics fix.
+
+The oracle computes every adjoint by a sequential tape sweep.  These tests
+check it against independent statements of the same numbers: the paper's
+fixed cases (tests/golden/fixed_cases.json), closed forms, brute force on
+tiny inputs, central finite differences of multilinear functions (exact up
+to rounding), forward-mode dual numbers (Sec. 3) and library routines.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2202_10297_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "fixed_cases.json")
+
+
+@pytest.fixture(scope="module")
+def golden():
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+# ---------------------------------------------------------------- fixed cases
+def test_golden_prod_reduce(oracle, golden):
+    for c in golden["prod_reduce"]:
+        r = oracle.prod_reduce_vjp(c["a"], c["ybar"])
+        np.testing.assert_array_equal(r["abar"], c["abar"], err_msg=c["cite"])
+        assert r["nzero"] == c["nzero"] and r["first_zero"] == c["first_zero"]
+
+
+def test_golden_minmax_reduce(oracle, golden):
+    for c in golden["minmax_reduce"]:
+        y, ab, arg = oracle.reduce_vjp(c["op"], c["a"], c["ybar"])
+        assert y == c["y"] and arg == c["argidx"], c["cite"]
+        np.testing.assert_array_equal(ab, c["abar"])
+
+
+def test_golden_scan(oracle, golden):
+    for c in golden["scan"]:
+        if c["op"] == "linrec":
+            ab, bb, ya, yb = oracle.scan_vjp("linrec", c["a"], c["ybar_a"], c["b"], c["ybar_b"])
+            np.testing.assert_array_equal(ab, c["abar"], err_msg=c["cite"])
+            np.testing.assert_array_equal(bb, c["bbar"])
+            np.testing.assert_array_equal(ya, c["ys_a"])
+            np.testing.assert_array_equal(yb, c["ys_b"])
+        else:
+            ab, _, _, _ = oracle.scan_vjp(c["op"], c["a"], c["ybar"])
+            np.testing.assert_array_equal(ab, c["abar"], err_msg=c["cite"])
+
+
+def test_golden_hist(oracle, golden):
+    for c in golden["hist"]:
+        vb, hs, arg = oracle.hist_vjp(c["op"], c["vals"], c["inds"], c["m"], c["hsbar"])
+        np.testing.assert_array_equal(vb, c["valsbar"], err_msg=c["cite"])
+        if "argidx" in c:
+            np.testing.assert_array_equal(arg, c["argidx"])
+
+
+def test_golden_scatter(oracle, golden):
+    for c in golden["scatter"]:
+        xb, vb, yr = oracle.scatter_vjp(c["n"], c["is"], c["ysbar"], ys=c["ys"],
+                                        xs_saved=c["xs_saved"])
+        np.testing.assert_array_equal(vb, c["vsbar"], err_msg=c["cite"])
+        np.testing.assert_array_equal(xb, c["xsbar"])
+        np.testing.assert_array_equal(yr, c["ys_restored"])
+
+
+def test_golden_map_acc(oracle, golden):
+    for c in golden["map_acc"]:
+        ab, _ = oracle.map_acc_vjp(c["g"], c["as"], c["is"], c["xsbar"])
+        np.testing.assert_array_equal(ab, c["asbar"], err_msg=c["cite"])
+
+
+# ------------------------------------------------------------- product reduce
+def _prod_brute(a, ybar):
+    """d(prod a)/d a_i = product of all other elements (O(n^2))."""
+    n = len(a)
+    return np.array([ybar * np.prod(np.delete(a, i)) for i in range(n)])
+
+
+@pytest.mark.parametrize("nz", [0, 1, 2, 3])
+def test_prod_reduce_brute_force(oracle, nz):
+    g = synth.rng(11 + nz)
+    for n in (1, 2, 7, 33, 64):
+        a = g.uniform(0.5, 1.5, n)
+        if nz:
+            a[g.choice(n, size=min(nz, n), replace=False)] = 0.0
+        ybar = g.normal()
+        r = oracle.prod_reduce_vjp(a, ybar)
+        np.testing.assert_allclose(r["abar"], _prod_brute(a, ybar), rtol=1e-13, atol=0)
+        assert r["nzero"] == int((a == 0).sum())
+        zs = np.flatnonzero(a == 0)
+        assert r["first_zero"] == (int(zs[0]) if zs.size else -1)
+
+
+def test_prod_reduce_finite_differences(oracle):
+    """The product is linear in each a_i, so a central difference is exact up to rounding."""
+    g = synth.rng(5)
+    a = g.uniform(0.5, 1.5, 24)
+    a[7] = 0.0
+    r = oracle.prod_reduce_vjp(a, 1.0)
+    h = 0.25
+    fd = np.empty_like(a)
+    for i in range(a.size):
+        ap, am = a.copy(), a.copy()
+        ap[i] += h
+        am[i] -= h
+        fd[i] = (np.prod(ap) - np.prod(am)) / (2 * h)
+    np.testing.assert_allclose(r["abar"], fd, rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("nz", [0, 1, 2])
+def test_prod_reduce_log_domain_closed_form(oracle, nz):
+    """n = 65536 underflows FP64; ln|abar_i| = sum_{j != i} ln|a_j| + ln|ybar| (math.fsum)."""
+    a, zpos = synth.prod_reduce(65536, nz)
+    ybar = -1.5
+    r = oracle.prod_reduce_vjp(a, ybar)
+    la = np.log(np.abs(np.where(a == 0, 1.0, a)))
+    total = math.fsum(la[a != 0])
+    assert abs(r["lognz"] - total) <= 1e-12 * abs(total)
+    assert r["y"] == 0.0  # the full product (about 1e-1287) rounds to zero
+    np.testing.assert_array_equal(r["abar"], np.zeros_like(a))  # correctly rounded values
+    if nz == 0:
+        expect = total - la + math.log(1.5)
+        np.testing.assert_allclose(r["log"], expect, rtol=1e-12)
+        np.testing.assert_array_equal(r["sign"], -np.sign(a).astype(np.int8))
+    elif nz == 1:
+        i0 = zpos[0]
+        assert abs(r["log"][i0] - (total + math.log(1.5))) <= 1e-12 * abs(total)
+        assert r["sign"][i0] == -1
+        assert np.all(np.isneginf(np.delete(r["log"], i0)))
+    else:
+        assert np.all(np.isneginf(r["log"])) and np.all(r["sign"] == 0)
+
+
+def test_prod_reduce_representable_value_mode(oracle):
+    """A representable case: values scaled so the product stays in range."""
+    a, _ = synth.prod_reduce(1024, 0)
+    a = a * math.exp(0.04523)
+    r = oracle.prod_reduce_vjp(a, 1.0)
+    y = np.prod(a)
+    assert 1e-30 < abs(y) < 1e30
+    np.testing.assert_allclose(r["abar"], y / a, rtol=1e-12)
+
+
+def test_prod_reduce_equals_hist_with_one_bin(oracle):
+    g = synth.rng(9)
+    a = g.uniform(0.5, 1.5, 300)
+    a[17] = 0
+    r = oracle.prod_reduce_vjp(a, 0.75)
+    h = oracle.hist_prod_vjp(a, np.zeros(300, np.int64), 1, [0.75])
+    np.testing.assert_array_equal(r["abar"], h["valsbar"])
+    np.testing.assert_array_equal(r["log"], h["log"])
+    assert h["nzero"][0] == 1 and h["first_zero"][0] == 17
+
+
+# ------------------------------------------------------------ min/max reduce
+@pytest.mark.parametrize("op", ["min", "max"])
+def test_minmax_reduce_first_index_ties(oracle, op):
+    g = synth.rng(3)
+    for n in (1, 2, 5, 64, 1000):
+        a = np.round(g.normal(size=n) * 2) / 8  # quantised: many exact ties
+        y, ab, arg = oracle.reduce_vjp(op, a, 2.5)
+        ref = int(np.argmax(a) if op == "max" else np.argmin(a))  # numpy: first occurrence
+        assert arg == ref and y == a[ref]
+        e = np.zeros(n)
+        e[ref] = 2.5
+        np.testing.assert_array_equal(ab, e)
+
+
+def test_add_reduce_broadcast(oracle):
+    a = synth.normal(100, np.float64, seed=1)
+    y, ab, _ = oracle.reduce_vjp("add", a, 0.5)
+    assert abs(y - math.fsum(a)) < 1e-12
+    np.testing.assert_array_equal(ab, np.full(100, 0.5))
+
+
+# ---------------------------------------------------------------------- scans
+def test_add_scan_suffix_sums(oracle):
+    yb = synth.normal(5000, np.float64, seed=2)
+    a = synth.normal(5000, np.float64, seed=3)
+    ab, _, ys, _ = oracle.scan_vjp("add", a, yb)
+    np.testing.assert_allclose(ab, np.cumsum(yb[::-1])[::-1], rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(ys, np.cumsum(a), rtol=1e-10, atol=1e-10)
+
+
+@pytest.mark.parametrize("op", ["min", "max"])
+def test_minmax_scan_brute_force(oracle, op):
+    """abar: each ybar_i goes to the first arg-extremum of a[0..i]."""
+    g = synth.rng(4)
+    for n in (1, 2, 3, 17, 64):
+        a = np.round(g.normal(size=n) * 2) / 4
+        yb = g.normal(size=n)
+        ab, _, _, _ = oracle.scan_vjp(op, a, yb)
+        ref = np.zeros(n)
+        for i in range(n):
+            k = int(np.argmax(a[: i + 1]) if op == "max" else np.argmin(a[: i + 1]))
+            ref[k] += yb[i]
+        np.testing.assert_allclose(ab, ref, rtol=1e-13, atol=1e-13)
+
+
+def test_mul_scan_brute_force(oracle):
+    """d rs_i / d a_k = prod_{j <= i, j != k} a_j, so abar_k = sum_{i >= k} ybar_i * that."""
+    g = synth.rng(6)
+    for n in (1, 2, 9, 32):
+        a = g.uniform(0.5, 1.5, n)
+        if n > 4:
+            a[3] = 0.0
+        yb = g.normal(size=n)
+        ab, _, ys, _ = oracle.scan_vjp("mul", a, yb)
+        ref = np.zeros(n)
+        for k in range(n):
+            for i in range(k, n):
+                ref[k] += yb[i] * np.prod(np.delete(a[: i + 1], k))
+        np.testing.assert_allclose(ab, ref, rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(ys, np.cumprod(a), rtol=1e-13)
+
+
+def _linrec_forward(a, b):
+    A = np.cumprod(a)
+    B = np.empty_like(b)
+    acc = 0.0
+    for i in range(b.size):
+        acc = a[i] * acc + b[i]
+        B[i] = acc
+    return A, B
+
+
+def test_linrec_scan_forward_mode_dual_numbers(oracle):
+    """Full Jacobian by 2n JVPs (dual numbers, Sec. 3), then J^T ybar."""
+    g = synth.rng(7)
+    for n in (1, 2, 5, 40):
+        a = g.uniform(0.9, 1.0, n)
+        b = g.normal(size=n)
+        ya = g.normal(size=n)
+        yb = g.normal(size=n)
+        # tangent seeds: columns 0..n-1 perturb a, n..2n-1 perturb b
+        da = np.zeros((n, 2 * n))
+        db = np.zeros((n, 2 * n))
+        da[np.arange(n), np.arange(n)] = 1.0
+        db[np.arange(n), n + np.arange(n)] = 1.0
+        A = B = None
+        dA = dB = None
+        JA = np.zeros((n, 2 * n))
+        JB = np.zeros((n, 2 * n))
+        for i in range(n):
+            if i == 0:
+                A, B, dA, dB = a[0], b[0], da[0].copy(), db[0].copy()
+            else:
+                dA = da[i] * A + a[i] * dA
+                dB = da[i] * B + a[i] * dB + db[i]
+                A, B = a[i] * A, a[i] * B + b[i]
+            JA[i], JB[i] = dA, dB
+        vjp = ya @ JA + yb @ JB
+        ab, bb, ys_a, ys_b = oracle.scan_vjp("linrec", a, ya, b, yb)
+        np.testing.assert_allclose(ab, vjp[:n], rtol=1e-12, atol=1e-13)
+        np.testing.assert_allclose(bb, vjp[n:], rtol=1e-12, atol=1e-13)
+        A_ref, B_ref = _linrec_forward(a, b)
+        np.testing.assert_allclose(ys_a, A_ref, rtol=1e-13)
+        np.testing.assert_allclose(ys_b, B_ref, rtol=1e-12, atol=1e-14)
+
+
+def test_linrec_scan_finite_differences(oracle):
+    """A and B are multilinear in (a, b): central differences are exact up to rounding."""
+    g = synth.rng(8)
+    n = 30
+    a = g.uniform(0.9, 1.0, n)
+    b = g.normal(size=n)
+    ya = g.normal(size=n)
+    yb = g.normal(size=n)
+
+    def L(a_, b_):
+        A, B = _linrec_forward(a_, b_)
+        return float(ya @ A + yb @ B)
+
+    ab, bb, _, _ = oracle.scan_vjp("linrec", a, ya, b, yb)
+    h = 0.125
+    for k in range(n):
+        e = np.zeros(n)
+        e[k] = h
+        fa = (L(a + e, b) - L(a - e, b)) / (2 * h)
+        fb = (L(a, b + e) - L(a, b - e)) / (2 * h)
+        assert abs(fa - ab[k]) <= 1e-10 * (1 + abs(fa))
+        assert abs(fb - bb[k]) <= 1e-10 * (1 + abs(fb))
+
+
+def test_linrec_closed_form(oracle):
+    """b_bar_k = sum_{i >= k} ybar_B_i prod_{j=k+1..i} a_j (explicit O(n^2))."""
+    g = synth.rng(12)
+    n = 50
+    a = g.uniform(0.9, 1.0, n)
+    b = g.normal(size=n)
+    ya = g.normal(size=n)
+    yb = g.normal(size=n)
+    _, bb, _, _ = oracle.scan_vjp("linrec", a, ya, b, yb)
+    ref = np.array([sum(yb[i] * np.prod(a[k + 1: i + 1]) for i in range(k, n)) for k in range(n)])
+    np.testing.assert_allclose(bb, ref, rtol=1e-12)
+
+
+def test_scan_accumulates(oracle):
+    """Adjoints are added into the given arrays (Eq. rewrite-adj, +=)."""
+    yb = np.array([1.0, 2.0, 3.0])
+    ab, _, _, _ = oracle.scan_vjp("add", [0.0, 0.0, 0.0], yb, abar=[100.0, 0.0, -1.0])
+    np.testing.assert_array_equal(ab, [106.0, 5.0, 2.0])
+
+
+# --------------------------------------------------------------- histograms
+def test_hist_add_is_gather(oracle):
+    vals, inds, hsbar = synth.hist(20000, 97, "zipf", seed=1)
+    vb, hs, _ = oracle.hist_vjp("add", vals, inds, 97, hsbar)
+    ok = (inds >= 0) & (inds < 97)
+    ref = np.where(ok, hsbar.astype(np.float64)[np.clip(inds, 0, 96)], 0.0)
+    np.testing.assert_array_equal(vb, ref)
+    ref_hs = np.zeros(97)
+    np.add.at(ref_hs, inds[ok], vals[ok].astype(np.float64))
+    np.testing.assert_allclose(hs, ref_hs, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("op", ["min", "max"])
+def test_hist_minmax_brute_force(oracle, op):
+    g = synth.rng(13)
+    n, m = 3000, 37
+    vals = np.round(g.normal(size=n) * 4) / 4  # ties
+    inds = g.integers(-3, m + 3, size=n)
+    hsbar = g.normal(size=m)
+    vb, hs, arg = oracle.hist_vjp(op, vals, inds, m, hsbar)
+    ref = np.zeros(n)
+    for b in range(m):
+        members = np.flatnonzero(inds == b)
+        if members.size == 0:
+            assert arg[b] == -1
+            continue
+        v = vals[members]
+        k = members[int(np.argmax(v) if op == "max" else np.argmin(v))]
+        assert arg[b] == k and hs[b] == vals[k]
+        ref[k] += hsbar[b]
+    np.testing.assert_array_equal(vb, ref)
+
+
+def test_hist_prod_brute_force(oracle):
+    g = synth.rng(14)
+    n, m = 200, 6
+    vals = g.uniform(0.5, 1.5, n) * np.where(g.random(n) < 0.5, -1, 1)
+    inds = g.integers(-1, m + 1, size=n)
+    vals[np.flatnonzero(inds == 2)[:1]] = 0.0  # bin 2: one zero
+    vals[np.flatnonzero(inds == 3)[:2]] = 0.0  # bin 3: two zeros
+    hsbar = g.normal(size=m)
+    r = oracle.hist_prod_vjp(vals, inds, m, hsbar)
+    ref = np.zeros(n)
+    for i in range(n):
+        b = inds[i]
+        if 0 <= b < m:
+            members = np.flatnonzero(inds == b)
+            ref[i] = hsbar[b] * np.prod(vals[members[members != i]])
+    np.testing.assert_allclose(r["valsbar"], ref, rtol=1e-12, atol=1e-300)
+    assert r["nzero"][2] == 1 and r["nzero"][3] == 2
+    assert r["first_zero"][2] == np.flatnonzero(inds == 2)[0]
+
+
+def test_hist_minmax_equal_reduce_with_one_bin(oracle):
+    a = np.round(synth.normal(500, np.float64, seed=5) * 3) / 3
+    for op in ("min", "max"):
+        y, ab, arg = oracle.reduce_vjp(op, a, 1.25)
+        vb, hs, harg = oracle.hist_vjp(op, a, np.zeros(500, np.int64), 1, [1.25])
+        assert arg == harg[0] and y == hs[0]
+        np.testing.assert_array_equal(ab, vb)
+
+
+# ------------------------------------------------------------------- scatter
+def test_scatter_closed_form(oracle):
+    n, m = 4096, 1000
+    is_, ysbar, xs_saved = synth.scatter(n, m, seed=3)
+    ys = synth.normal(n, np.float64, seed=4)
+    xb, vb, yr = oracle.scatter_vjp(n, is_, ysbar, ys=ys, xs_saved=xs_saved)
+    assert np.unique(is_).size == m
+    np.testing.assert_array_equal(vb, ysbar.astype(np.float64)[is_])
+    ref = ysbar.astype(np.float64).copy()
+    ref[is_] = 0.0
+    np.testing.assert_array_equal(xb, ref)
+    ref_y = ys.copy()
+    ref_y[is_] = xs_saved
+    np.testing.assert_array_equal(yr, ref_y)
+
+
+# ------------------------------------------------------------------- map_acc
+def test_map_acc_gather_add_at(oracle):
+    as_, is_, ws, xsbar = synth.map_acc(5000, 300)
+    ab, _ = oracle.map_acc_vjp("gather", as_, is_, xsbar)
+    ref = np.zeros(300)
+    np.add.at(ref, is_, xsbar.astype(np.float64))
+    np.testing.assert_allclose(ab, ref, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("g,width", [("scale", 1), ("sqdist_row", 4)])
+def test_map_acc_finite_differences(oracle, g, width):
+    """sum_j xsbar_j g(as[is_j], ws_j) is quadratic at most: central differences are exact."""
+    as_, is_, ws, xsbar = synth.map_acc(40, 7, width=width, seed=21)
+    as_ = as_.astype(np.float64)
+    ws = ws.astype(np.float64)
+
+    def L(a_, w_):
+        A = a_.reshape(-1, width)[is_]
+        W = w_.reshape(-1, width)
+        x = (A * W)[:, 0] if g == "scale" else ((W - A) ** 2).sum(1)
+        return float(xsbar.astype(np.float64) @ x)
+
+    ab, wb = oracle.map_acc_vjp(g, as_, is_, xsbar, ws=ws, width=width)
+    h = 0.5
+    for k in range(as_.size):
+        e = np.zeros(as_.size)
+        e[k] = h
+        assert abs((L(as_ + e, ws) - L(as_ - e, ws)) / (2 * h) - ab[k]) < 1e-11
+    for k in range(ws.size):
+        e = np.zeros(ws.size)
+        e[k] = h
+        assert abs((L(as_, ws + e) - L(as_, ws - e)) / (2 * h) - wb[k]) < 1e-11
+
+
+# ------------------------------------------------------------------- k-means
+def test_kmeans_closed_form_and_fd(oracle):
+    X, Cm = synth.kmeans(300, 5, 8, seed=2)
+    X = X.astype(np.float64)
+    Cm = Cm.astype(np.float64)
+    loss, arg, mind, cb = oracle.kmeans(X, Cm, 1.5)
+    D = ((X[:, None, :] - Cm[None, :, :]) ** 2).sum(-1)
+    np.testing.assert_array_equal(arg, np.argmin(D, axis=1))
+    assert abs(loss - D.min(1).sum()) < 1e-9
+    ref = np.zeros_like(Cm)
+    for k in range(8):
+        sel = arg == k
+        ref[k] = 2 * 1.5 * (sel.sum() * Cm[k] - X[sel].sum(0))
+    np.testing.assert_allclose(cb, ref, rtol=1e-11, atol=1e-11)
+    # finite differences (no argmin changes for a small step away from ties)
+    gap = np.sort(D, 1)[:, 1] - D.min(1)
+    assert gap.min() > 1e-4
+    h = 1e-6
+    for (k, j) in [(0, 0), (3, 2), (7, 4)]:
+        Cp, Cn = Cm.copy(), Cm.copy()
+        Cp[k, j] += h
+        Cn[k, j] -= h
+        fd = 1.5 * (oracle.kmeans(X, Cp)[0] - oracle.kmeans(X, Cn)[0]) / (2 * h)
+        assert abs(fd - cb[k, j]) < 1e-5 * (1 + abs(fd))

@@ -1,0 +1,172 @@
+/*
+ * adpar.h -- C ABI of libadpar: tape-free reverse-mode adjoints (VJPs) of
+ * bulk-parallel operators, after "AD for an Array Language with Nested
+ * Parallelism" (arXiv 2202.10297), as hand-written CUDA kernels for GB300
+ * (sm_103a).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Memory.    Every array argument is a DEVICE pointer unless it is marked
+ *            "host".  The caller allocates and owns every buffer; the
+ *            library allocates nothing.  Arrays are dense and contiguous
+ *            (structure of arrays for multi-component elements) and must
+ *            start on a 16-byte boundary (ADPAR_ERR_ALIGN otherwise).
+ * Streams.   `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *            default stream).  Every call only enqueues work on it and
+ *            returns; nothing synchronises the host.
+ * Workspace. Calls that take (work, work_bytes) need scratch device memory
+ *            of at least adpar_workspace_size(...) bytes, 256-byte aligned.
+ *            Its contents need no initialisation and are clobbered; two
+ *            calls in flight at once must not share one workspace.
+ * Adjoints.  Output adjoints are overwritten (x_bar = contribution) unless
+ *            flags has ADPAR_ACCUMULATE, in which case the contribution is
+ *            added (x_bar += contribution), as in Eq. rewrite-adj (Sec. 2).
+ * Recompute. Every rule re-executes the primal from its inputs (Sec. 4's
+ *            redundant execution); no tape or saved intermediate is read.
+ * Errors.    Argument errors are detected on the host and returned before
+ *            anything is enqueued.  Device-side give-ups (a bounded wait
+ *            that ran out) are recorded in the workspace and read back with
+ *            adpar_workspace_status().  Kernel launch failures return
+ *            ADPAR_ERR_CUDA.
+ * NaN/inf.   Inputs holding NaN or infinities are outside the contract:
+ *            results are unspecified, but no kernel faults or hangs.
+ */
+#ifndef ADPAR_H
+#define ADPAR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* element types of values and of indices */
+typedef enum { ADPAR_F32 = 0, ADPAR_F64 = 1 } adpar_dtype;
+typedef enum { ADPAR_I32 = 0, ADPAR_I64 = 1 } adpar_itype;
+
+/* associative operators (Sec. 5.1 and 5.2).  LINREC is the pair operator
+ * (a1,b1) (.) (a2,b2) = (a2*a1, a2*b1 + b2) of a first-order linear
+ * recurrence; its elements are two arrays a, b (width 2). */
+typedef enum {
+    ADPAR_OP_ADD = 0,
+    ADPAR_OP_MUL = 1,
+    ADPAR_OP_MIN = 2,
+    ADPAR_OP_MAX = 3,
+    ADPAR_OP_LINREC = 4
+} adpar_op;
+
+/* map bodies g for adpar_vjp_map_acc (Sec. 5.4) */
+typedef enum {
+    ADPAR_G_GATHER = 0,     /* x_j = as[is_j]                               */
+    ADPAR_G_SCALE = 1,      /* x_j = as[is_j] * ws_j                        */
+    ADPAR_G_SQDIST_ROW = 2  /* x_j = sum_k (ws[j,k] - as[is_j,k])^2, rows of width */
+} adpar_gfun;
+
+/* rules, for adpar_workspace_size */
+typedef enum {
+    ADPAR_RULE_REDUCE = 0,
+    ADPAR_RULE_SCAN = 1,
+    ADPAR_RULE_HIST = 2,
+    ADPAR_RULE_SCATTER = 3,
+    ADPAR_RULE_MAP_ACC = 4,
+    ADPAR_RULE_KMEANS = 5
+} adpar_rule;
+
+typedef enum {
+    ADPAR_OK = 0,
+    ADPAR_ERR_INVALID = 1,     /* null pointer, negative size, bad enum value   */
+    ADPAR_ERR_UNSUPPORTED = 2, /* valid combination this library does not do    */
+    ADPAR_ERR_ALIGN = 3,       /* an array does not start on a 16-byte boundary */
+    ADPAR_ERR_WORKSPACE = 4,   /* work is NULL, misaligned or too small         */
+    ADPAR_ERR_CUDA = 5,        /* a CUDA call or kernel launch failed           */
+    ADPAR_ERR_TIMEOUT = 6      /* a bounded device-side wait gave up            */
+} adpar_status;
+
+/* flags */
+#define ADPAR_ACCUMULATE      0x1u /* x_bar += contribution (else x_bar = contribution) */
+#define ADPAR_PROD_LOGDOMAIN  0x4u /* * rules: write ln|contribution| and its sign      */
+#define ADPAR_SCATTER_RESTORE 0x8u /* scatter: also restore ys[is_j] = xs_saved[j]      */
+
+/* operator descriptor: op (adpar_op), dtype (adpar_dtype) of the values,
+ * width = number of arrays per element (1, or 2 for ADPAR_OP_LINREC). */
+typedef struct {
+    int32_t op;
+    int32_t dtype;
+    int32_t width;
+} adpar_opdesc;
+
+/* Result of the recomputed product forward sweep of Sec. 5.1.1: the
+ * number of zeros, the lowest zero index, and the product of the nonzero
+ * elements in scaled form  p_nz = mant * 2^exp2  (0.5 <= |mant| < 1, or
+ * mant = 0 when there are no elements), with ln|p_nz| and sign(p_nz). */
+typedef struct {
+    int64_t nzero;
+    int64_t first_zero;  /* -1 when there is no zero */
+    int64_t exp2;
+    double mant;
+    double log_abs_nz;
+    int32_t sign;        /* -1, 0 or +1 */
+    int32_t reserved;
+} adpar_prod_aux;
+
+/* ------------------------------------------------------------------ */
+/* Library                                                             */
+/* ------------------------------------------------------------------ */
+
+/* Human-readable name of a status code (static storage, never NULL). */
+const char *adpar_status_string(int status);
+
+/* Version string of the library (static storage). */
+const char *adpar_version(void);
+
+/* Bytes of workspace needed by `rule` for an operator `desc` over n
+ * elements (m = number of bins for HIST, of destination elements for
+ * SCATTER, of accumulator rows for MAP_ACC; for KMEANS n = points, m =
+ * centroids).  Returns 0 when the rule needs none, and (size_t)-1 for an
+ * invalid request. */
+size_t adpar_workspace_size(int rule, adpar_opdesc desc, int64_t n, int64_t m);
+
+/* Waits for `stream`, then reads the device-side status word that the
+ * last call using `work` left there (ADPAR_OK, or ADPAR_ERR_TIMEOUT when
+ * a bounded wait inside a kernel gave up).  *device_status receives it
+ * (host pointer).  Returns ADPAR_ERR_CUDA if the read itself fails. */
+int adpar_workspace_status(const void *work, void *stream, int *device_status);
+
+/* ------------------------------------------------------------------ */
+/* scan (Sec. 5.2)                                                     */
+/* ------------------------------------------------------------------ */
+/* Inclusive scan rs_i = rs_{i-1} (.) as_i and its adjoint, for op = ADD,
+ * MUL, MIN, MAX (width 1) and LINREC (width 2: arrays a, b), dtype F32 or
+ * F64.  The return sweep is the one of Sec. 5.2: with
+ *   J_left(i) = d(rs_{i-1} (.) as_i)/d rs_{i-1}   and
+ *   J_right(i) = d(rs_{i-1} (.) as_i)/d as_i,
+ * rs_bar_i = ys_bar_i + J_left(i+1)^T rs_bar_{i+1} (a backward linear
+ * recurrence solved by a scan with the lin_o operator of Sec. 5.2) and
+ * as_bar_i = J_right(i)^T rs_bar_i, as_bar_0 = rs_bar_0.  MAX/MIN keep the
+ * gradient with the earlier element on ties.
+ * Arguments:
+ *   n            number of elements (0 allowed: nothing is written).
+ *   a, b         [n] inputs (b only for LINREC, else NULL).
+ *   ybar_a/_b    [n] cotangents of the outputs (ybar_b only for LINREC).
+ *   abar, bbar   [n] output adjoints (bbar only for LINREC).
+ *   ys_a, ys_b   nullable [n]: the recomputed primal outputs.
+ * Flags: ADPAR_ACCUMULATE.
+ * Workspace: adpar_workspace_size(ADPAR_RULE_SCAN, desc, n, 0). */
+int adpar_vjp_scan(adpar_opdesc desc, int64_t n, const void *a, const void *b,
+                   const void *ybar_a, const void *ybar_b, void *abar, void *bbar,
+                   void *ys_a, void *ys_b, uint32_t flags, void *work,
+                   size_t work_bytes, void *stream);
+
+/* The primal forward scan ys = scan (.) as (Sec. 5.2's forward sweep), on
+ * its own.  It is the baseline of the AD overhead ratio (VJP time / primal
+ * time, Sec. 7).  Arguments as for adpar_vjp_scan; ys_a (and ys_b for
+ * LINREC) are required outputs.  Workspace: as for adpar_vjp_scan. */
+int adpar_scan(adpar_opdesc desc, int64_t n, const void *a, const void *b, void *ys_a,
+               void *ys_b, void *work, size_t work_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADPAR_H */

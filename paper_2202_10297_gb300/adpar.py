@@ -1,0 +1,208 @@
+"""Python binding of the libadpar C ABI (argument marshalling only).
+
+Each ``adpar_*`` function here has the name of the C entry point it calls
+(declared in include/adpar.h).  It takes torch CUDA tensors, checks dtypes
+and shapes, passes raw device pointers, the current CUDA stream and a
+workspace to the library, and raises :class:`AdparError` on a non-zero
+status.  PyTorch only provides device memory and streams; every step of
+every rule runs in the library's kernels.  There is no CPU fallback: if
+libadpar.so is missing, loading fails loudly.
+"""
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libadpar.so")
+
+F32, F64 = 0, 1
+I32, I64 = 0, 1
+OP_ADD, OP_MUL, OP_MIN, OP_MAX, OP_LINREC = 0, 1, 2, 3, 4
+OPS = {"add": OP_ADD, "mul": OP_MUL, "min": OP_MIN, "max": OP_MAX, "linrec": OP_LINREC}
+G_GATHER, G_SCALE, G_SQDIST_ROW = 0, 1, 2
+GFUNS = {"gather": G_GATHER, "scale": G_SCALE, "sqdist_row": G_SQDIST_ROW}
+RULE_REDUCE, RULE_SCAN, RULE_HIST, RULE_SCATTER, RULE_MAP_ACC, RULE_KMEANS = range(6)
+ACCUMULATE, PROD_LOGDOMAIN, SCATTER_RESTORE = 0x1, 0x4, 0x8
+OK, ERR_TIMEOUT = 0, 6
+
+
+class AdparError(RuntimeError):
+    def __init__(self, fn, status):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (fn, status_string(status), status))
+
+
+class OpDesc(C.Structure):
+    _fields_ = [("op", C.c_int32), ("dtype", C.c_int32), ("width", C.c_int32)]
+
+
+class ProdAux(C.Structure):
+    _fields_ = [("nzero", C.c_int64), ("first_zero", C.c_int64), ("exp2", C.c_int64),
+                ("mant", C.c_double), ("log_abs_nz", C.c_double), ("sign", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+PROD_AUX_BYTES = C.sizeof(ProdAux)
+
+_lib = None
+_VP = C.c_void_p
+
+
+def lib():
+    """The loaded libadpar (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libadpar.so not found at %s: run paper_2202_10297_gb300.build.build() "
+                               "(or __graft_entry__.build()) first" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        L.adpar_status_string.restype = C.c_char_p
+        L.adpar_status_string.argtypes = [C.c_int]
+        L.adpar_version.restype = C.c_char_p
+        L.adpar_workspace_size.restype = C.c_size_t
+        L.adpar_workspace_size.argtypes = [C.c_int, OpDesc, C.c_int64, C.c_int64]
+        L.adpar_workspace_status.restype = C.c_int
+        L.adpar_workspace_status.argtypes = [_VP, _VP, C.POINTER(C.c_int)]
+        L.adpar_vjp_scan.restype = C.c_int
+        L.adpar_vjp_scan.argtypes = [OpDesc, C.c_int64] + [_VP] * 8 + [C.c_uint32, _VP, C.c_size_t, _VP]
+        L.adpar_scan.restype = C.c_int
+        L.adpar_scan.argtypes = [OpDesc, C.c_int64] + [_VP] * 4 + [_VP, C.c_size_t, _VP]
+        _bind_optional(L)
+        _lib = L
+    return _lib
+
+
+def _bind_optional(L):
+    """Signatures of the entry points other than the scan."""
+    sigs = {
+        "adpar_vjp_reduce": [OpDesc, C.c_int64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, C.c_uint32, _VP,
+                             C.c_size_t, _VP],
+        "adpar_vjp_hist": [OpDesc, C.c_int64, C.c_int64, _VP, _VP, C.c_int, _VP, _VP, _VP, _VP, _VP,
+                           _VP, C.c_uint32, _VP, C.c_size_t, _VP],
+        "adpar_vjp_scatter": [C.c_int, C.c_int64, C.c_int64, _VP, C.c_int, _VP, _VP, _VP, _VP,
+                              C.c_uint32, _VP],
+        "adpar_vjp_map_acc": [C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int, _VP, _VP, C.c_int, _VP,
+                              _VP, _VP, _VP, C.c_uint32, _VP, C.c_size_t, _VP],
+    }
+    for name, argt in sigs.items():
+        if hasattr(L, name):
+            f = getattr(L, name)
+            f.restype = C.c_int
+            f.argtypes = argt
+
+
+def status_string(status):
+    return lib().adpar_status_string(int(status)).decode()
+
+
+def version():
+    return lib().adpar_version().decode()
+
+
+def _dtype_code(t):
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.float64:
+        return F64
+    raise TypeError("values must be float32 or float64, got %s" % t.dtype)
+
+
+def _itype_code(t):
+    if t.dtype == torch.int32:
+        return I32
+    if t.dtype == torch.int64:
+        return I64
+    raise TypeError("indices must be int32 or int64, got %s" % t.dtype)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("tensor must live on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def _check(fn, status):
+    if status != OK:
+        raise AdparError(fn, status)
+
+
+def adpar_workspace_size(rule, op, dtype, n, m=0, width=None):
+    """Bytes of workspace a call needs (C: adpar_workspace_size)."""
+    if width is None:
+        width = 2 if op == OP_LINREC else 1
+    sz = lib().adpar_workspace_size(rule, OpDesc(op, dtype, width), n, m)
+    if sz == C.c_size_t(-1).value:
+        raise ValueError("invalid workspace request")
+    return sz
+
+
+def workspace(nbytes, device=None):
+    """A workspace buffer (256-byte aligned by the CUDA caching allocator)."""
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device or "cuda")
+
+
+def adpar_workspace_status(work, stream=None):
+    """Device status word left in ``work`` by the last call (synchronises)."""
+    st = C.c_int(0)
+    _check("adpar_workspace_status",
+           lib().adpar_workspace_status(_ptr(work), _stream(stream), C.byref(st)))
+    return st.value
+
+
+def adpar_vjp_scan(op, a, ybar_a, b=None, ybar_b=None, abar=None, bbar=None, ys_a=None, ys_b=None,
+                   accumulate=False, work=None, stream=None):
+    """VJP of an inclusive scan (C: adpar_vjp_scan).  Returns (abar, bbar, work).
+
+    ``op`` is a name ("add", "mul", "min", "max", "linrec") or code.
+    Missing outputs are allocated; ``ys_a``/``ys_b`` are filled when given.
+    """
+    opc = OPS[op] if isinstance(op, str) else int(op)
+    ref = ybar_a
+    n = ref.numel()
+    dt = _dtype_code(ref)
+    w = 2 if opc == OP_LINREC else 1
+    if abar is None:
+        abar = torch.empty_like(ref) if not accumulate else torch.zeros_like(ref)
+    if w == 2 and bbar is None:
+        bbar = torch.empty_like(ref) if not accumulate else torch.zeros_like(ref)
+    need = adpar_workspace_size(RULE_SCAN, opc, dt, n)
+    if work is None or work.numel() < need:
+        work = workspace(need, ref.device)
+    for t in (a, b, ybar_b, abar, bbar, ys_a, ys_b):
+        if t is not None and (t.dtype != ref.dtype or t.numel() != n):
+            raise ValueError("all scan arrays must share dtype and length")
+    st = lib().adpar_vjp_scan(OpDesc(opc, dt, w), n, _ptr(a), _ptr(b), _ptr(ybar_a), _ptr(ybar_b),
+                              _ptr(abar), _ptr(bbar), _ptr(ys_a), _ptr(ys_b),
+                              ACCUMULATE if accumulate else 0, _ptr(work), work.numel(),
+                              _stream(stream))
+    _check("adpar_vjp_scan", st)
+    return abar, bbar, work
+
+
+def adpar_scan(op, a, b=None, ys_a=None, ys_b=None, work=None, stream=None):
+    """Primal inclusive scan (C: adpar_scan).  Returns (ys_a, ys_b, work)."""
+    opc = OPS[op] if isinstance(op, str) else int(op)
+    n = a.numel()
+    dt = _dtype_code(a)
+    w = 2 if opc == OP_LINREC else 1
+    if ys_a is None:
+        ys_a = torch.empty_like(a)
+    if w == 2 and ys_b is None:
+        ys_b = torch.empty_like(a)
+    need = adpar_workspace_size(RULE_SCAN, opc, dt, n)
+    if work is None or work.numel() < need:
+        work = workspace(need, a.device)
+    st = lib().adpar_scan(OpDesc(opc, dt, w), n, _ptr(a), _ptr(b), _ptr(ys_a), _ptr(ys_b),
+                          _ptr(work), work.numel(), _stream(stream))
+    _check("adpar_scan", st)
+    return ys_a, ys_b, work

@@ -1,0 +1,40 @@
+// Library-wide entry points of the adpar C ABI: status strings, version,
+// workspace sizing and the device status word.
+#include "common.cuh"
+
+namespace adpar {
+size_t scan_workspace_size(adpar_opdesc d, int64_t n);
+}
+
+extern "C" const char* adpar_status_string(int status) {
+    switch (status) {
+    case ADPAR_OK: return "ok";
+    case ADPAR_ERR_INVALID: return "invalid argument";
+    case ADPAR_ERR_UNSUPPORTED: return "unsupported combination";
+    case ADPAR_ERR_ALIGN: return "array not 16-byte aligned";
+    case ADPAR_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case ADPAR_ERR_CUDA: return "CUDA error";
+    case ADPAR_ERR_TIMEOUT: return "device-side wait timed out";
+    }
+    return "unknown status";
+}
+
+extern "C" const char* adpar_version(void) { return "adpar 0.1 (sm_103a)"; }
+
+extern "C" size_t adpar_workspace_size(int rule, adpar_opdesc d, int64_t n, int64_t m) {
+    (void)m;
+    switch (rule) {
+    case ADPAR_RULE_SCAN: return adpar::scan_workspace_size(d, n);
+    }
+    return (size_t)-1;
+}
+
+extern "C" int adpar_workspace_status(const void* work, void* stream, int* device_status) {
+    if (!work || !device_status) return ADPAR_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return ADPAR_ERR_CUDA;
+    uint32_t v = 0;
+    if (cudaMemcpy(&v, work, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return ADPAR_ERR_CUDA;
+    *device_status = (int)v;
+    return ADPAR_OK;
+}

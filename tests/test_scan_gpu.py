@@ -1,0 +1,163 @@
+"""GPU parity of the scan VJP (Sec. 5.2) against the FP64 oracle, through the C ABI.
+
+Tolerances (relative L2 against the FP64 oracle on the same inputs):
+FP32 1e-4 (1e-3 for scans longer than 2^24 elements), FP64 1e-12.
+Record positions of max/min scans (where the adjoint is nonzero) must
+match exactly.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2202_10297_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TILE_F32 = 4 * 256 * 4  # elements per tile of the width-1 FP32 scan
+SIZES = [1, 2, 3, 5, 17, 1000, TILE_F32 - 1, TILE_F32, TILE_F32 + 1, 3 * TILE_F32 + 5, 65536 + 7,
+         200003]
+
+
+def rel_l2(x, ref):
+    x = np.asarray(x, np.float64)
+    ref = np.asarray(ref, np.float64)
+    d = np.linalg.norm(ref)
+    return float(np.linalg.norm(x - ref) / (d if d > 0 else 1.0))
+
+
+def tol(dt, n):
+    if dt == np.float64:
+        return 1e-12
+    return 1e-3 if n > (1 << 24) else 1e-4
+
+
+@pytest.fixture(scope="module")
+def A():
+    from paper_2202_10297_gb300 import adpar
+    adpar.lib()
+    return adpar
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def inputs(op, n, dt, seed):
+    g = synth.rng(seed)
+    if op == "mul":
+        a = g.uniform(0.5, 1.5, n).astype(dt)
+        if n > 10:
+            a[g.choice(n, size=2, replace=False)] = 0  # zeros are safe: no division
+    elif op in ("min", "max"):
+        a = (np.round(g.standard_normal(n) * 8) / 8).astype(dt)  # forced ties
+    else:
+        a = g.standard_normal(n).astype(dt)
+    y = g.standard_normal(n).astype(dt)
+    return a, y
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+@pytest.mark.parametrize("op", ["add", "mul", "min", "max"])
+@pytest.mark.parametrize("n", SIZES)
+def test_scan_vjp_width1(A, oracle, op, dt, n):
+    a, y = inputs(op, n, dt, seed=n * 7 + len(op))
+    ys = torch.empty(n, dtype=torch.float32 if dt == np.float32 else torch.float64, device="cuda")
+    ab, _, work = A.adpar_vjp_scan(op, dev(a), dev(y), ys_a=ys)
+    torch.cuda.synchronize()
+    assert A.adpar_workspace_status(work) == A.OK
+    ref, _, rys, _ = oracle.scan_vjp(op, a, y)
+    got = ab.cpu().numpy()
+    assert rel_l2(got, ref) < tol(dt, n), (op, n, rel_l2(got, ref))
+    assert rel_l2(ys.cpu().numpy(), rys) < tol(dt, n)
+    if op in ("min", "max"):
+        np.testing.assert_array_equal(got != 0, ref != 0)  # record positions, bit-exact
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+@pytest.mark.parametrize("n", [1, 2, 7, 2047, 2048, 2049, 8192 + 3, 100001])
+def test_scan_vjp_linrec(A, oracle, dt, n):
+    a, b, ya, yb = synth.linrec(n, dt, seed=n)
+    ysa = torch.empty(n, dtype=torch.float32 if dt == np.float32 else torch.float64, device="cuda")
+    ysb = torch.empty_like(ysa)
+    ab, bb, _ = A.adpar_vjp_scan("linrec", dev(a), dev(ya), b=dev(b), ybar_b=dev(yb), ys_a=ysa, ys_b=ysb)
+    rab, rbb, rya, ryb = oracle.scan_vjp("linrec", a, ya, b, yb)
+    assert rel_l2(ab.cpu().numpy(), rab) < tol(dt, n)
+    assert rel_l2(bb.cpu().numpy(), rbb) < tol(dt, n)
+    assert rel_l2(ysa.cpu().numpy(), rya) < tol(dt, n)
+    assert rel_l2(ysb.cpu().numpy(), ryb) < tol(dt, n)
+
+
+@pytest.mark.parametrize("op", ["add", "max", "linrec"])
+def test_scan_vjp_accumulate(A, oracle, op):
+    n = 50000
+    dt = np.float64
+    a, y = inputs(op, n, dt, seed=3)
+    base = synth.normal(n, dt, seed=4)
+    if op == "linrec":
+        a, b, ya, yb = synth.linrec(n, dt, seed=5)
+        ab0, bb0 = dev(base), dev(base[::-1].copy())
+        A.adpar_vjp_scan(op, dev(a), dev(ya), b=dev(b), ybar_b=dev(yb), abar=ab0, bbar=bb0, accumulate=True)
+        rab, rbb, _, _ = oracle.scan_vjp(op, a, ya, b, yb, abar=base, bbar=base[::-1].copy())
+        assert rel_l2(ab0.cpu().numpy(), rab) < 1e-12
+        assert rel_l2(bb0.cpu().numpy(), rbb) < 1e-12
+    else:
+        ab0 = dev(base)
+        A.adpar_vjp_scan(op, dev(a), dev(y), abar=ab0, accumulate=True)
+        ref, _, _, _ = oracle.scan_vjp(op, a, y, abar=base)
+        assert rel_l2(ab0.cpu().numpy(), ref) < 1e-12
+
+
+@pytest.mark.parametrize("op", ["add", "mul", "max", "linrec"])
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+def test_primal_scan(A, oracle, op, dt):
+    n = 123457
+    if op == "linrec":
+        a, b, _, _ = synth.linrec(n, dt, seed=6)
+        ya, yb, _ = A.adpar_scan(op, dev(a), b=dev(b))
+        _, _, rya, ryb = oracle.scan_vjp(op, a, np.zeros(n), b, np.zeros(n))
+        assert rel_l2(ya.cpu().numpy(), rya) < tol(dt, n)
+        assert rel_l2(yb.cpu().numpy(), ryb) < tol(dt, n)
+    else:
+        a, _ = inputs(op, n, dt, seed=8)
+        ya, _, _ = A.adpar_scan(op, dev(a))
+        _, _, rya, _ = oracle.scan_vjp(op, a, np.zeros(n))
+        assert rel_l2(ya.cpu().numpy(), rya) < tol(dt, n)
+
+
+def test_scan_zero_length_and_errors(A):
+    e = torch.empty(0, device="cuda")
+    ab, _, _ = A.adpar_vjp_scan("add", e, e)
+    assert ab.numel() == 0
+    x = torch.zeros(9, device="cuda")
+    with pytest.raises(A.AdparError):
+        A.adpar_vjp_scan("add", x[1:], x[1:])  # 4-byte offset: not 16-byte aligned
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+def test_linrec_full_size(A, oracle, dt):
+    """n = 2^26 pairs (the benchmark size), full comparison with the oracle."""
+    n = 1 << 26
+    a, b, ya, yb = synth.linrec(n, dt, seed=synth.SEED_BASE + 1)
+    ab, bb, work = A.adpar_vjp_scan("linrec", dev(a), dev(ya), b=dev(b), ybar_b=dev(yb))
+    assert A.adpar_workspace_status(work) == A.OK
+    rab, rbb, _, _ = oracle.scan_vjp("linrec", a, ya, b, yb)
+    assert rel_l2(ab.cpu().numpy(), rab) < tol(dt, n)
+    assert rel_l2(bb.cpu().numpy(), rbb) < tol(dt, n)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("op", ["add", "max"])
+def test_add_max_scan_full_size(A, oracle, op):
+    """n = 2^28 FP32 (the benchmark size): full comparison with the oracle."""
+    n = 1 << 28
+    x = synth.normal(n, np.float32, seed=synth.SEED_BASE + 1)
+    y = synth.normal(n, np.float32, seed=synth.SEED_BASE + 11)
+    ab, _, work = A.adpar_vjp_scan(op, dev(x), dev(y))
+    assert A.adpar_workspace_status(work) == A.OK
+    got = ab.cpu().numpy()
+    del ab
+    ref, _, _, _ = oracle.scan_vjp(op, x, y)
+    assert rel_l2(got, ref) < 1e-3
+    if op == "max":
+        np.testing.assert_array_equal(np.flatnonzero(got), np.flatnonzero(ref))

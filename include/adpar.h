@@ -80,7 +80,8 @@ typedef enum {
     ADPAR_ERR_ALIGN = 3,       /* an array does not start on a 16-byte boundary */
     ADPAR_ERR_WORKSPACE = 4,   /* work is NULL, misaligned or too small         */
     ADPAR_ERR_CUDA = 5,        /* a CUDA call or kernel launch failed           */
-    ADPAR_ERR_TIMEOUT = 6      /* a bounded device-side wait gave up            */
+    ADPAR_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up            */
+    ADPAR_ERR_TOO_LARGE = 7    /* needs more than the static no-allocation scratch */
 } adpar_status;
 
 /* flags */
@@ -164,6 +165,37 @@ int adpar_vjp_scan(adpar_opdesc desc, int64_t n, const void *a, const void *b,
  * LINREC) are required outputs.  Workspace: as for adpar_vjp_scan. */
 int adpar_scan(adpar_opdesc desc, int64_t n, const void *a, const void *b, void *ys_a,
                void *ys_b, void *work, size_t work_bytes, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* scan VJP without any allocation                                     */
+/* ------------------------------------------------------------------ */
+/* The paper has no counterpart of this entry point; it serves callers
+ * that cannot allocate device memory when they need the gradient (code
+ * inside an allocator or memory-manager hook that must not re-enter it,
+ * loops that forbid allocation after start-up, hosts that hand over fixed
+ * buffers only).  It computes exactly what adpar_vjp_scan computes, with
+ * the same arguments minus (work, work_bytes): its scratch is one static
+ * device array of adpar_noalloc_scratch_bytes() bytes (8 MiB), which every
+ * GPU that loads the library holds until the process exits.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *   - Sizes whose scan workspace exceeds the array are refused with
+ *     ADPAR_ERR_TOO_LARGE before anything is enqueued (up to 2^28 FP32
+ *     elements of a width-1 operator and 2^26 FP64 LINREC pairs fit).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current) and caches it; make
+ *     that first call before any stream capture on the device.
+ *   - All calls on one device share the array.  Each call clears the parts
+ *     that must start at zero, but two calls that overlap on the GPU (on
+ *     different streams, or from different threads) race on it and give
+ *     wrong results: serialise them.
+ *   - The device status word of adpar_workspace_status lives in the same
+ *     array and is not exposed here. */
+int adpar_vjp_scan_noalloc(adpar_opdesc desc, int64_t n, const void *a, const void *b,
+                           const void *ybar_a, const void *ybar_b, void *abar, void *bbar,
+                           void *ys_a, void *ys_b, uint32_t flags, void *stream);
+
+/* Size in bytes of the static scratch array of adpar_vjp_scan_noalloc. */
+size_t adpar_noalloc_scratch_bytes(void);
 
 #ifdef __cplusplus
 }

@@ -24,7 +24,7 @@ G_GATHER, G_SCALE, G_SQDIST_ROW = 0, 1, 2
 GFUNS = {"gather": G_GATHER, "scale": G_SCALE, "sqdist_row": G_SQDIST_ROW}
 RULE_REDUCE, RULE_SCAN, RULE_HIST, RULE_SCATTER, RULE_MAP_ACC, RULE_KMEANS = range(6)
 ACCUMULATE, PROD_LOGDOMAIN, SCATTER_RESTORE = 0x1, 0x4, 0x8
-OK, ERR_TIMEOUT = 0, 6
+OK, ERR_TIMEOUT, ERR_TOO_LARGE = 0, 6, 7
 
 
 class AdparError(RuntimeError):
@@ -66,6 +66,10 @@ def lib():
         L.adpar_workspace_status.argtypes = [_VP, _VP, C.POINTER(C.c_int)]
         L.adpar_vjp_scan.restype = C.c_int
         L.adpar_vjp_scan.argtypes = [OpDesc, C.c_int64] + [_VP] * 8 + [C.c_uint32, _VP, C.c_size_t, _VP]
+        L.adpar_vjp_scan_noalloc.restype = C.c_int
+        L.adpar_vjp_scan_noalloc.argtypes = [OpDesc, C.c_int64] + [_VP] * 8 + [C.c_uint32, _VP]
+        L.adpar_noalloc_scratch_bytes.restype = C.c_size_t
+        L.adpar_noalloc_scratch_bytes.argtypes = []
         L.adpar_scan.restype = C.c_int
         L.adpar_scan.argtypes = [OpDesc, C.c_int64] + [_VP] * 4 + [_VP, C.c_size_t, _VP]
         _bind_optional(L)
@@ -206,3 +210,30 @@ def adpar_scan(op, a, b=None, ys_a=None, ys_b=None, work=None, stream=None):
                           _ptr(work), work.numel(), _stream(stream))
     _check("adpar_scan", st)
     return ys_a, ys_b, work
+
+
+def adpar_vjp_scan_noalloc(op, a, ybar_a, b=None, ybar_b=None, abar=None, bbar=None, ys_a=None,
+                           ys_b=None, accumulate=False, stream=None):
+    """Scan VJP that allocates nothing in the library (C: adpar_vjp_scan_noalloc).
+
+    For callers that cannot allocate device memory at the call site: the
+    library uses its static device scratch instead of a workspace.  Output
+    tensors must be passed in (none is allocated here either).  Returns
+    (abar, bbar).  Calls that overlap on the GPU race on the shared scratch.
+    """
+    opc = OPS[op] if isinstance(op, str) else int(op)
+    w = 2 if opc == OP_LINREC else 1
+    if abar is None or (w == 2 and bbar is None):
+        raise ValueError("pass the output adjoint tensors: this entry point allocates nothing")
+    n = ybar_a.numel()
+    dt = _dtype_code(ybar_a)
+    st = lib().adpar_vjp_scan_noalloc(OpDesc(opc, dt, w), n, _ptr(a), _ptr(b), _ptr(ybar_a),
+                                      _ptr(ybar_b), _ptr(abar), _ptr(bbar), _ptr(ys_a), _ptr(ys_b),
+                                      ACCUMULATE if accumulate else 0, _stream(stream))
+    _check("adpar_vjp_scan_noalloc", st)
+    return abar, bbar
+
+
+def adpar_noalloc_scratch_bytes():
+    """Bytes of the static scratch behind adpar_vjp_scan_noalloc."""
+    return lib().adpar_noalloc_scratch_bytes()

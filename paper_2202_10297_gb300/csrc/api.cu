@@ -15,6 +15,7 @@ extern "C" const char* adpar_status_string(int status) {
     case ADPAR_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
     case ADPAR_ERR_CUDA: return "CUDA error";
     case ADPAR_ERR_TIMEOUT: return "device-side wait timed out";
+    case ADPAR_ERR_TOO_LARGE: return "problem needs more than the static no-allocation scratch";
     }
     return "unknown status";
 }

@@ -27,12 +27,17 @@ namespace {
 
 constexpr int kScanBlock = 256;
 
+// Tile shape: K chunks of kScanBlock * E elements; in each chunk a thread
+// owns E consecutive elements (kept in registers).  Larger E amortises the
+// warp-shuffle scans over more elements, which matters where arithmetic,
+// not memory, bounds the kernel (FP64 on GB300).
 template <class Op, class T>
 struct ScanCfg {
-    // chunks per tile: keeps the per-thread inputs in registers
-    static constexpr int K = (Op::kWidth == 2) ? 2 : 4;
-    static constexpr int V = Vec16<T>::N;
-    static constexpr int TILE = K * kScanBlock * V;
+    static constexpr bool kF64 = sizeof(T) == 8;
+    static constexpr int E = kF64 ? (Op::kWidth == 2 ? 8 : 4) : 4;
+    static constexpr int K = kF64 ? (Op::kWidth == 2 ? 1 : 4) : (Op::kWidth == 2 ? 4 : 8);
+    static constexpr int V = E;
+    static constexpr int TILE = K * kScanBlock * E;
 };
 
 struct ScanArgs {
@@ -49,59 +54,66 @@ struct ScanArgs {
     int64_t tiles;
     WsHeader* hdr;
     void* carry;  // [tiles] P
-    LookbackState<char> lbP;  // typed in the kernels
-    LookbackState<char> lbR;
+    unsigned long long* lbP_agg;  // look-back slots of the primal pass
+    unsigned long long* lbP_incl;
+    unsigned long long* lbR_agg;  // look-back slots of the adjoint pass
+    unsigned long long* lbR_incl;
 };
 
-template <class T>
-__device__ __forceinline__ void load_chunk(const T* p, int64_t e, int64_t n, T pad, T (&out)[Vec16<T>::N]) {
-    constexpr int V = Vec16<T>::N;
-    if (e + V <= n) {
-        Vec16<T> x = ld_vec_stream(p + e);
+// A thread's E consecutive elements of a chunk, as E / (16 / sizeof(T))
+// 16-byte vectors; a partial chunk at the end of the data is read element
+// by element and padded with `pad`.
+template <int E, bool STREAM, class T>
+__device__ __forceinline__ void load_chunk_e(const T* p, int64_t e, int64_t n, T pad, T (&out)[E]) {
+    constexpr int VV = Vec16<T>::N;
+    static_assert(E % VV == 0, "whole vectors");
+    if (e + E <= n) {
 #pragma unroll
-        for (int j = 0; j < V; ++j) out[j] = x.v[j];
+        for (int q = 0; q < E / VV; ++q) {
+            Vec16<T> x = STREAM ? ld_vec_stream(p + e + q * VV) : ld_vec(p + e + q * VV);
+#pragma unroll
+            for (int j = 0; j < VV; ++j) out[q * VV + j] = x.v[j];
+        }
     } else {
 #pragma unroll
-        for (int j = 0; j < V; ++j) out[j] = (e + j < n) ? p[e + j] : pad;
+        for (int j = 0; j < E; ++j) out[j] = (e + j < n) ? p[e + j] : pad;
     }
 }
 
-template <class T>
-__device__ __forceinline__ void load_chunk_keep(const T* p, int64_t e, int64_t n, T pad, T (&out)[Vec16<T>::N]) {
-    constexpr int V = Vec16<T>::N;
-    if (e + V <= n) {
-        Vec16<T> x = ld_vec(p + e);
-#pragma unroll
-        for (int j = 0; j < V; ++j) out[j] = x.v[j];
-    } else {
-#pragma unroll
-        for (int j = 0; j < V; ++j) out[j] = (e + j < n) ? p[e + j] : pad;
-    }
+template <int E, class T>
+__device__ __forceinline__ void load_chunk(const T* p, int64_t e, int64_t n, T pad, T (&out)[E]) {
+    load_chunk_e<E, true>(p, e, n, pad, out);
 }
 
-template <class T>
-__device__ __forceinline__ void store_chunk(T* p, int64_t e, int64_t n, const T (&v)[Vec16<T>::N]) {
-    constexpr int V = Vec16<T>::N;
-    if (e + V <= n) {
-        Vec16<T> x;
+template <int E, class T>
+__device__ __forceinline__ void load_chunk_keep(const T* p, int64_t e, int64_t n, T pad, T (&out)[E]) {
+    load_chunk_e<E, false>(p, e, n, pad, out);
+}
+
+template <int E, class T>
+__device__ __forceinline__ void store_chunk(T* p, int64_t e, int64_t n, const T (&v)[E]) {
+    constexpr int VV = Vec16<T>::N;
+    if (e + E <= n) {
 #pragma unroll
-        for (int j = 0; j < V; ++j) x.v[j] = v[j];
-        st_vec(p + e, x);
+        for (int q = 0; q < E / VV; ++q) {
+            Vec16<T> x;
+#pragma unroll
+            for (int j = 0; j < VV; ++j) x.v[j] = v[q * VV + j];
+            st_vec(p + e + q * VV, x);
+        }
     } else {
 #pragma unroll
-        for (int j = 0; j < V; ++j)
+        for (int j = 0; j < E; ++j)
             if (e + j < n) p[e + j] = v[j];
     }
 }
 
-__global__ void scan_init_kernel(WsHeader* hdr, uint32_t* fP, uint32_t* fR, int64_t tiles) {
+// Zeroes the header and the look-back slots (one contiguous region).
+__global__ void scan_init_kernel(WsHeader* hdr, unsigned long long* slots, int64_t nwords) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     if (i < 64) reinterpret_cast<uint32_t*>(hdr)[i] = 0u;
-    for (int64_t t = i; t < tiles; t += stride) {
-        if (fP) fP[t] = 0u;
-        fR[t] = 0u;
-    }
+    for (int64_t t = i; t < nwords; t += stride) slots[t] = 0ull;
 }
 
 // ---------------------------------------------------------------- pass P
@@ -140,14 +152,14 @@ __global__ void __launch_bounds__(kScanBlock) scan_primal_kernel(ScanArgs A) {
     P wex[K];
     P total = block_scan_part1<P, false, K, NW>(agg, wex, s_tot, Op::pid(), comb);
     if ((threadIdx.x >> 5) == 0) {
-        LookbackState<P> st{A.lbP.flag, reinterpret_cast<P*>(A.lbP.agg), reinterpret_cast<P*>(A.lbP.incl)};
+        LookbackState<P> st{A.lbP_agg, A.lbP_incl};
         P prefix = lookback(tile, st, total, Op::pid(), comb, A.hdr);
         if ((threadIdx.x & 31) == 0) static_cast<P*>(A.carry)[tile] = prefix;
     }
 }
 
 // ---------------------------------------------------------------- pass R
-template <class Op, class T>
+template <class Op, class T, bool WYS>
 __global__ void __launch_bounds__(kScanBlock) scan_adjoint_kernel(ScanArgs A) {
     using Cfg = ScanCfg<Op, T>;
     using P = typename Op::P;
@@ -166,8 +178,8 @@ __global__ void __launch_bounds__(kScanBlock) scan_adjoint_kernel(ScanArgs A) {
     const int64_t t_log = s_tile;             // logical tile in reverse scan order
     const int64_t tile = A.tiles - 1 - t_log;  // data tile
     const int64_t base = tile * Cfg::TILE;
-    const bool write_ys = A.ys_a != nullptr;
-    const bool need_primal = kPrimal || write_ys;
+    constexpr bool write_ys = WYS;
+    constexpr bool need_primal = kPrimal || WYS;
 
     const T* a = static_cast<const T*>(A.a);
     const T* b = static_cast<const T*>(A.b);
@@ -180,7 +192,7 @@ __global__ void __launch_bounds__(kScanBlock) scan_adjoint_kernel(ScanArgs A) {
         const int64_t e = base + (int64_t)k * kScanBlock * V + threadIdx.x * V;
         load_chunk(ya, e, A.n, T(0), yav[k]);
         if constexpr (W == 2) load_chunk(yb, e, A.n, T(0), ybv[k]);
-        if (need_primal || !Op::kCoefOne) {
+        if constexpr (need_primal || !Op::kCoefOne) {
             load_chunk(a, e, A.n, Op::pad_a(), av[k]);
             if constexpr (W == 2) load_chunk(b, e, A.n, T(0), bv[k]);
         }
@@ -188,7 +200,7 @@ __global__ void __launch_bounds__(kScanBlock) scan_adjoint_kernel(ScanArgs A) {
 
     // ---- primal: exclusive prefix of every element (forward), from the carry
     P pex[K];  // thread's exclusive primal prefix per chunk
-    if (need_primal) {
+    if constexpr (need_primal) {
         if (threadIdx.x == 0) s_carry = static_cast<const P*>(A.carry)[tile];
         P agg[K];
 #pragma unroll
@@ -238,7 +250,7 @@ __global__ void __launch_bounds__(kScanBlock) scan_adjoint_kernel(ScanArgs A) {
     L wexR[K];
     L totR = block_scan_part1<L, true, K, NW>(aggR, wexR, s_totR, L::id(), lc);
     if ((threadIdx.x >> 5) == 0) {
-        LookbackState<L> st{A.lbR.flag, reinterpret_cast<L*>(A.lbR.agg), reinterpret_cast<L*>(A.lbR.incl)};
+        LookbackState<L> st{A.lbR_agg, A.lbR_incl};
         L pre = lookback(t_log, st, totR, L::id(), lc, A.hdr);
         if ((threadIdx.x & 31) == 0) s_prefR = pre;
     }
@@ -288,7 +300,7 @@ __global__ void __launch_bounds__(kScanBlock) scan_adjoint_kernel(ScanArgs A) {
         }
         store_chunk(abar, e, A.n, oa);
         if constexpr (W == 2) store_chunk(bbar, e, A.n, ob);
-        if (write_ys) {
+        if constexpr (write_ys) {
             T y1[V], y2[V];
 #pragma unroll
             for (int j = 0; j < V; ++j) {
@@ -337,7 +349,7 @@ __global__ void __launch_bounds__(kScanBlock) scan_forward_kernel(ScanArgs A) {
     P wex[K];
     P total = block_scan_part1<P, false, K, NW>(agg, wex, s_tot, Op::pid(), comb);
     if ((threadIdx.x >> 5) == 0) {
-        LookbackState<P> st{A.lbP.flag, reinterpret_cast<P*>(A.lbP.agg), reinterpret_cast<P*>(A.lbP.incl)};
+        LookbackState<P> st{A.lbP_agg, A.lbP_incl};
         P pre = lookback(tile, st, total, Op::pid(), comb, A.hdr);
         if ((threadIdx.x & 31) == 0) s_pref = pre;
     }
@@ -361,26 +373,44 @@ __global__ void __launch_bounds__(kScanBlock) scan_forward_kernel(ScanArgs A) {
 
 // ------------------------------------------------------------ host side
 struct ScanLayout {
-    size_t off_fP, off_aggP, off_inclP, off_carry, off_fR, off_aggR, off_inclR, total;
+    size_t off_carry, off_slots, off_pA, off_pI, off_rA, off_rI, slot_words, total;
 };
 
+// header | carry[tiles] | look-back slots (primal agg, primal incl,
+// adjoint agg, adjoint incl), the slots contiguous so one kernel zeroes them
 template <class Op, class T>
 ScanLayout scan_layout(int64_t n) {
     using Cfg = ScanCfg<Op, T>;
     using P = typename Op::P;
     using L = Lin<T, Op::kWidth, !Op::kCoefOne>;
     const size_t tiles = (size_t)((n + Cfg::TILE - 1) / Cfg::TILE);
+    const size_t wp = tiles * (size_t)lb_words<P>(), wr = tiles * (size_t)lb_words<L>();
     ScanLayout s;
     size_t o = sizeof(WsHeader);
-    s.off_fP = o;    o = round_up(o + tiles * 4, 256);
-    s.off_aggP = o;  o = round_up(o + tiles * sizeof(P), 256);
-    s.off_inclP = o; o = round_up(o + tiles * sizeof(P), 256);
     s.off_carry = o; o = round_up(o + tiles * sizeof(P), 256);
-    s.off_fR = o;    o = round_up(o + tiles * 4, 256);
-    s.off_aggR = o;  o = round_up(o + tiles * sizeof(L), 256);
-    s.off_inclR = o; o = round_up(o + tiles * sizeof(L), 256);
-    s.total = o;
+    s.off_slots = o;
+    s.off_pA = o; o += wp * 8;
+    s.off_pI = o; o += wp * 8;
+    s.off_rA = o; o += wr * 8;
+    s.off_rI = o; o += wr * 8;
+    s.slot_words = (o - s.off_slots) / 8;
+    s.total = round_up(o, 256);
     return s;
+}
+
+inline void set_slots(ScanArgs& A, char* w, const ScanLayout& L) {
+    A.carry = w + L.off_carry;
+    A.lbP_agg = reinterpret_cast<unsigned long long*>(w + L.off_pA);
+    A.lbP_incl = reinterpret_cast<unsigned long long*>(w + L.off_pI);
+    A.lbR_agg = reinterpret_cast<unsigned long long*>(w + L.off_rA);
+    A.lbR_incl = reinterpret_cast<unsigned long long*>(w + L.off_rI);
+}
+
+inline void launch_init(const ScanArgs& A, char* w, const ScanLayout& L, cudaStream_t stream) {
+    const int64_t words = (int64_t)L.slot_words;
+    const int blocks = (int)std::min<int64_t>((words + 255) / 256 + 1, 2048);
+    scan_init_kernel<<<blocks, 256, 0, stream>>>(A.hdr, reinterpret_cast<unsigned long long*>(w + L.off_slots),
+                                                 words);
 }
 
 template <class Op, class T>
@@ -400,16 +430,12 @@ int run_scan(int64_t n, const void* a, const void* b, const void* ya, const void
     A.accumulate = (flags & ADPAR_ACCUMULATE) ? 1 : 0;
     A.tiles = (n + Cfg::TILE - 1) / Cfg::TILE;
     A.hdr = reinterpret_cast<WsHeader*>(w);
-    A.carry = w + L.off_carry;
-    A.lbP = {reinterpret_cast<uint32_t*>(w + L.off_fP), w + L.off_aggP, w + L.off_inclP};
-    A.lbR = {reinterpret_cast<uint32_t*>(w + L.off_fR), w + L.off_aggR, w + L.off_inclR};
+    set_slots(A, w, L);
     const bool need_primal = Op::kNeedPrimal || Op::kCoefNeedsPrimal || ys_a != nullptr;
-
-    const int init_blocks = (int)std::min<int64_t>((A.tiles + 255) / 256 + 1, 1024);
-    scan_init_kernel<<<init_blocks, 256, 0, stream>>>(A.hdr, need_primal ? A.lbP.flag : nullptr,
-                                                      A.lbR.flag, A.tiles);
+    launch_init(A, w, L, stream);
     if (need_primal) scan_primal_kernel<Op, T><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
-    scan_adjoint_kernel<Op, T><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
+    if (ys_a) scan_adjoint_kernel<Op, T, true><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
+    else scan_adjoint_kernel<Op, T, false><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
     return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
 }
 
@@ -458,10 +484,8 @@ int run_scan_forward(int64_t n, const void* a, const void* b, void* ys_a, void* 
     A.a = a; A.b = b; A.ys_a = ys_a; A.ys_b = ys_b;
     A.tiles = (n + Cfg::TILE - 1) / Cfg::TILE;
     A.hdr = reinterpret_cast<WsHeader*>(w);
-    A.lbP = {reinterpret_cast<uint32_t*>(w + L.off_fP), w + L.off_aggP, w + L.off_inclP};
-    A.lbR = {reinterpret_cast<uint32_t*>(w + L.off_fR), w + L.off_aggR, w + L.off_inclR};
-    const int init_blocks = (int)std::min<int64_t>((A.tiles + 255) / 256 + 1, 1024);
-    scan_init_kernel<<<init_blocks, 256, 0, stream>>>(A.hdr, A.lbP.flag, A.lbR.flag, A.tiles);
+    set_slots(A, w, L);
+    launch_init(A, w, L, stream);
     scan_forward_kernel<Op, T><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
     return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
 }

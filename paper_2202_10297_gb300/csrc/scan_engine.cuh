@@ -24,12 +24,14 @@ __device__ __forceinline__ int chunk_warp_pos(int k, int w) {
 //   wex[k]        the warp-exclusive prefix of the thread for chunk k,
 //   s_tot[q]      the block-exclusive prefix of (chunk, warp) q,
 //   return value  (in warp 0) the aggregate of the whole tile.
-// Requires K * NW <= 32.  Warp 0 writes s_tot after the internal barrier,
-// so callers must __syncthreads() before block_scan_excl reads it.
+// Warp 0 scans the K*NW per-warp totals with R = ceil(K*NW/32) of them per
+// lane.  Warp 0 writes s_tot after the internal barrier, so callers must
+// __syncthreads() before block_scan_excl reads it.
 template <class S, bool REV, int K, int NW, class Comb>
 __device__ __forceinline__ S block_scan_part1(const S (&agg)[K], S (&wex)[K], S* s_tot,
                                               const S& ident, Comb comb) {
-    static_assert(K * NW <= 32, "one warp scans the per-warp totals");
+    constexpr int Q = K * NW;
+    constexpr int R = (Q + 31) / 32;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
 #pragma unroll
@@ -49,9 +51,15 @@ __device__ __forceinline__ S block_scan_part1(const S (&agg)[K], S (&wex)[K], S*
     __syncthreads();
     S total = ident;
     if (warp == 0) {
-        constexpr int Q = K * NW;
-        S v = lane < Q ? s_tot[lane] : ident;
-        S inc = v;
+        S v[R];
+        S run = ident;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int q = lane * R + r;
+            v[r] = q < Q ? s_tot[q] : ident;
+            run = comb(run, v[r]);
+        }
+        S inc = run;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             S o = shfl_up_s(inc, off);
@@ -60,8 +68,13 @@ __device__ __forceinline__ S block_scan_part1(const S (&agg)[K], S (&wex)[K], S*
         S ex = shfl_up_s(inc, 1);
         if (lane == 0) ex = ident;
         __syncwarp();
-        if (lane < Q) s_tot[lane] = ex;
-        total = shfl_idx_s(inc, Q - 1);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int q = lane * R + r;
+            if (q < Q) s_tot[q] = ex;
+            ex = comb(ex, v[r]);
+        }
+        total = shfl_idx_s(inc, 31);
     }
     return total;
 }
@@ -75,13 +88,75 @@ __device__ __forceinline__ S block_scan_excl(int k, const S (&wex)[K], const S* 
     return comb(tile_prefix, comb(s_tot[chunk_warp_pos<REV, K, NW>(k, warp)], wex[k]));
 }
 
-// Tile status arrays of one single-pass scan.
+// Look-back slots of one single-pass scan.  Every tile has an aggregate
+// slot and an inclusive-prefix slot; a slot holds the state S as 64-bit
+// words whose high half is a status tag (1 = aggregate, 2 = inclusive)
+// and whose low half is 32 bits of S.  Each word is written and read as
+// one single-copy-atomic 64-bit access, so a reader that sees the tag in
+// every word of a slot has the whole value: no fence on either side and
+// one memory round trip per look-back window.  Slots start zeroed.
 template <class S>
 struct LookbackState {
-    uint32_t* flag;  // 0: nothing yet, 1: aggregate published, 2: inclusive prefix published
-    S* agg;
-    S* incl;
+    unsigned long long* agg;   // [tiles * words]
+    unsigned long long* incl;  // [tiles * words]
 };
+
+template <class S>
+constexpr int lb_words() {
+    static_assert(sizeof(S) % 4 == 0, "4-byte granules");
+    return (int)(sizeof(S) / 4);
+}
+
+template <class S>
+__device__ __forceinline__ void lb_publish(unsigned long long* slot, const S& v, uint32_t tag) {
+    constexpr int W = lb_words<S>();
+    union { S s; uint32_t w[W]; } u;
+    u.s = v;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        const unsigned long long word = ((unsigned long long)tag << 32) | u.w[i];
+        asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(slot + i), "l"(word) : "memory");
+    }
+}
+
+// Reads a slot; returns true (and the value) if every word carries `tag`.
+template <class S>
+__device__ __forceinline__ bool lb_read(const unsigned long long* slot, uint32_t tag, S& out) {
+    constexpr int W = lb_words<S>();
+    union { S s; uint32_t w[W]; } u;
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        unsigned long long word;
+        asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(word) : "l"(slot + i) : "memory");
+        ok = ok && (uint32_t)(word >> 32) == tag;
+        u.w[i] = (uint32_t)word;
+    }
+    out = u.s;
+    return ok;
+}
+
+// Polls tile idx until its inclusive prefix (returns 2) or aggregate
+// (returns 1) is out; returns 0 after a timeout (status recorded).
+template <class S>
+__device__ __forceinline__ uint32_t lb_wait(const LookbackState<S>& st, int64_t idx, S& out,
+                                            WsHeader* hdr) {
+    constexpr int W = lb_words<S>();
+    uint32_t it = 0;
+    while (true) {
+        S vi, va;
+        const bool inc = lb_read(st.incl + idx * W, 2u, vi);
+        const bool ag = lb_read(st.agg + idx * W, 1u, va);
+        if (inc) { out = vi; return 2u; }
+        if (ag) { out = va; return 1u; }
+        ++it;
+        if (it > kSpinLimit || ((it & 255u) == 0 && gave_up(hdr))) {
+            record_status(hdr, ADPAR_ERR_TIMEOUT);
+            return 0u;
+        }
+        __nanosleep(it < 32 ? 0 : 100);
+    }
+}
 
 // Decoupled look-back, run by one whole warp for logical tile t.
 // Publishes the tile's aggregate, walks back over the predecessors in
@@ -91,31 +166,23 @@ struct LookbackState {
 template <class S, class Comb>
 __device__ __forceinline__ S lookback(int64_t t, LookbackState<S> st, const S& tile_total,
                                       const S& ident, Comb comb, WsHeader* hdr) {
+    constexpr int W = lb_words<S>();
     const int lane = threadIdx.x & 31;
     if (t == 0) {
-        if (lane == 0) {
-            st.incl[0] = tile_total;
-            st_release_u32(&st.flag[0], 2u);
-        }
+        if (lane == 0) lb_publish(st.incl, tile_total, 2u);
         return ident;
     }
-    if (lane == 0) {
-        st.agg[t] = tile_total;
-        st_release_u32(&st.flag[t], 1u);
-    }
+    if (lane == 0) lb_publish(st.agg + t * W, tile_total, 1u);
     S prefix = ident;
     int64_t base = t - 1;
     while (true) {
         const int64_t idx = base - lane;
         uint32_t f = 2u;  // before tile 0: a virtual inclusive identity
-        if (idx >= 0) f = wait_flag(&st.flag[idx], hdr);  // 0 only after a timeout
+        S v = ident;
+        if (idx >= 0) f = lb_wait(st, idx, v, hdr);  // 0 only after a timeout
         const uint32_t stop_mask = __ballot_sync(0xffffffffu, f != 1u);
         const int stop = stop_mask ? __ffs(stop_mask) - 1 : 31;
-        S v = ident;
-        if (lane <= stop && idx >= 0) {
-            if (f == 2u) v = ld_cg(&st.incl[idx]);
-            else if (f == 1u) v = ld_cg(&st.agg[idx]);
-        }
+        if (lane > stop || idx < 0 || f == 0u) v = ident;
         // lanes hold tiles in decreasing order: higher lane = earlier tile
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -127,10 +194,7 @@ __device__ __forceinline__ S lookback(int64_t t, LookbackState<S> st, const S& t
         base -= 32;
     }
     prefix = shfl_idx_s(prefix, 0);
-    if (lane == 0) {
-        st.incl[t] = comb(prefix, tile_total);
-        st_release_u32(&st.flag[t], 2u);
-    }
+    if (lane == 0) lb_publish(st.incl + t * W, comb(prefix, tile_total), 2u);
     return prefix;
 }
 

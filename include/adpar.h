@@ -135,6 +135,39 @@ size_t adpar_workspace_size(int rule, adpar_opdesc desc, int64_t n, int64_t m);
 int adpar_workspace_status(const void *work, void *stream, int *device_status);
 
 /* ------------------------------------------------------------------ */
+/* reduce (Sec. 5.1 and 5.1.1)                                         */
+/* ------------------------------------------------------------------ */
+/* y = a_0 (.) a_1 (.) ... (.) a_{n-1} and its adjoint a_bar, for
+ * op = ADD, MUL, MIN, MAX (width 1), dtype F32 or F64.
+ *   ADD:  a_bar_i = y_bar                                   (Sec. 5.1.1)
+ *   MUL:  the three cases of Sec. 5.1.1 on the zero count z:
+ *         z = 0: a_bar_i = p_nz / a_i * y_bar;  z = 1: a_bar_{i0} = p_nz *
+ *         y_bar (p_nz = product of the nonzero elements), all others 0;
+ *         z >= 2: all 0.  The forward sweep is re-executed as a map-reduce
+ *         of (zero count, lowest zero index, scaled nonzero product), so
+ *         no intermediate underflows.
+ *   MIN/MAX: (y, i_y) = argmin/argmax with the LOWEST index on ties
+ *         (Sec. 5.1.1, "(first) index"); a_bar_{i_y} = y_bar, others 0.
+ * Arguments:
+ *   n          number of elements (0 allowed: y = neutral element).
+ *   a          [n] input values, dtype.
+ *   ybar       device scalar (dtype): the cotangent of y.
+ *   abar       [n] output adjoint, dtype.  With ADPAR_PROD_LOGDOMAIN (MUL
+ *              only) it receives ln|contribution| (-inf where it is 0).
+ *   y_out      nullable device scalar (dtype): the recomputed y (MUL: the
+ *              product rounded to dtype, 0 or subnormal on underflow).
+ *   argidx_out nullable device int64 scalar: i_y (MIN/MAX; -1 if n == 0).
+ *   aux_out    nullable device adpar_prod_aux (MUL only).
+ *   abar_sign  nullable device int8 [n]: sign of each contribution
+ *              (MUL with ADPAR_PROD_LOGDOMAIN only).
+ * Flags: ADPAR_ACCUMULATE (not with LOGDOMAIN), ADPAR_PROD_LOGDOMAIN.
+ * Workspace: adpar_workspace_size(ADPAR_RULE_REDUCE, desc, n, 0). */
+int adpar_vjp_reduce(adpar_opdesc desc, int64_t n, const void *a, const void *ybar,
+                     void *abar, void *y_out, int64_t *argidx_out,
+                     adpar_prod_aux *aux_out, int8_t *abar_sign, uint32_t flags,
+                     void *work, size_t work_bytes, void *stream);
+
+/* ------------------------------------------------------------------ */
 /* scan (Sec. 5.2)                                                     */
 /* ------------------------------------------------------------------ */
 /* Inclusive scan rs_i = rs_{i-1} (.) as_i and its adjoint, for op = ADD,
@@ -165,6 +198,74 @@ int adpar_vjp_scan(adpar_opdesc desc, int64_t n, const void *a, const void *b,
  * LINREC) are required outputs.  Workspace: as for adpar_vjp_scan. */
 int adpar_scan(adpar_opdesc desc, int64_t n, const void *a, const void *b, void *ys_a,
                void *ys_b, void *work, size_t work_bytes, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* reduce_by_index (Sec. 5.1.2)                                        */
+/* ------------------------------------------------------------------ */
+/* hs = reduce_by_index (.) e inds vals, i.e. the loop
+ *   hs = replicate m e;  for i: hs[inds_i] = hs[inds_i] (.) vals_i,
+ * with indices outside [0, m) ignored, and its adjoint valsbar given hsbar:
+ * the reduce rule of Sec. 5.1.1 per bin with ybar replaced by hsbar[inds_i].
+ *   ADD      valsbar_i = hsbar[inds_i] (in range), else 0.
+ *   MIN/MAX  per bin the extremum and its LOWEST index; that element gets
+ *            hsbar_b, every other element 0.
+ *   MUL      per bin (zero count, lowest zero index, scaled product of the
+ *            nonzeros); the three cases of Sec. 5.1.1 per element.
+ * Out-of-range elements get 0 (overwrite) or keep their value (accumulate).
+ * Arguments:
+ *   n, m         elements and bins.
+ *   vals         [n] values, dtype (may be NULL for ADD without hs_out).
+ *   inds         [n] bin indices, itype (adpar_itype).
+ *   hsbar        [m] cotangent of hs, dtype.
+ *   valsbar      [n] output adjoint, dtype (ln|contribution| with
+ *                ADPAR_PROD_LOGDOMAIN, MUL only).
+ *   hs_out       nullable [m]: the recomputed histogram (ADD: sums; MIN/MAX:
+ *                extremum, +-inf for an empty bin; MUL: product rounded to
+ *                dtype).
+ *   argidx_out   nullable [m] int64 (MIN/MAX): the lowest index of the
+ *                extremum of each bin, -1 for an empty bin.
+ *   bin_aux_out  nullable [m] adpar_prod_aux (MUL).
+ *   valsbar_sign nullable [n] int8 (MUL with ADPAR_PROD_LOGDOMAIN).
+ * Limits: FP32 MIN/MAX keep 32-bit element indices (n <= 2^32).
+ * Workspace: adpar_workspace_size(ADPAR_RULE_HIST, desc, n, m). */
+int adpar_vjp_hist(adpar_opdesc desc, int64_t n, int64_t m, const void *vals, const void *inds,
+                   int itype, const void *hsbar, void *valsbar, void *hs_out, int64_t *argidx_out,
+                   adpar_prod_aux *bin_aux_out, int8_t *valsbar_sign, uint32_t flags, void *work,
+                   size_t work_bytes, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* scatter (Sec. 5.3)                                                  */
+/* ------------------------------------------------------------------ */
+/* ys = scatter xs is vs with `is` free of duplicates (a duplicate is a
+ * caller error, not detected).  Return sweep of Sec. 5.3, O(m) work:
+ *   vsbar[j] += ysbar[is_j];  ysbar[is_j] = 0 (ysbar becomes xsbar in
+ *   place);  with ADPAR_SCATTER_RESTORE also ys[is_j] = xs_saved[j].
+ * Indices outside [0, n) are skipped (vsbar_j gets 0, or keeps its value
+ * with ADPAR_ACCUMULATE).
+ * Arguments: dtype (adpar_dtype); n destination length; m = |is|; is [m]
+ * (itype); ysbar_inout [n]; vsbar [m]; ys_restore [n] and xs_saved [m]
+ * (only with ADPAR_SCATTER_RESTORE).  No workspace. */
+int adpar_vjp_scatter(int dtype, int64_t n, int64_t m, const void *is, int itype, void *ysbar_inout,
+                      void *vsbar, void *ys_restore, const void *xs_saved, uint32_t flags, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* map with a free array (Sec. 5.4)                                    */
+/* ------------------------------------------------------------------ */
+/* xs[j] = g(as[is_j, :], ws[j, :]) for j < nj, with as a free array of na
+ * rows of `width` values.  Each read of as becomes an accumulation into
+ * asbar at the same index (Sec. 5.4's accumulators):
+ *   GATHER      (width 1)  asbar[is_j] += xsbar_j
+ *   SCALE       (width 1)  asbar[is_j] += ws_j xsbar_j;  wsbar_j = as[is_j] xsbar_j
+ *   SQDIST_ROW  (width d)  asbar[is_j,k] += -2 (ws[j,k] - as[is_j,k]) xsbar_j;
+ *                          wsbar[j,k] = 2 (ws[j,k] - as[is_j,k]) xsbar_j
+ * Indices outside [0, na) are skipped.  asbar starts from zero unless
+ * ADPAR_ACCUMULATE; wsbar (nullable) is overwritten or accumulated likewise.
+ * Arguments: gfun (adpar_gfun), dtype, nj, na, width; as [na*width]; is
+ * [nj] (itype); ws [nj*width] (not for GATHER); xsbar [nj]; asbar
+ * [na*width]; wsbar [nj*width].  work/work_bytes: unused (may be NULL). */
+int adpar_vjp_map_acc(int gfun, int dtype, int64_t nj, int64_t na, int width, const void *as,
+                      const void *is, int itype, const void *ws, const void *xsbar, void *asbar,
+                      void *wsbar, uint32_t flags, void *work, size_t work_bytes, void *stream);
 
 /* ------------------------------------------------------------------ */
 /* scan VJP without any allocation                                     */

@@ -237,3 +237,128 @@ def adpar_vjp_scan_noalloc(op, a, ybar_a, b=None, ybar_b=None, abar=None, bbar=N
 def adpar_noalloc_scratch_bytes():
     """Bytes of the static scratch behind adpar_vjp_scan_noalloc."""
     return lib().adpar_noalloc_scratch_bytes()
+
+
+def _scalar_dev(x, like):
+    if isinstance(x, torch.Tensor):
+        return x.reshape(1).to(device=like.device, dtype=like.dtype).contiguous()
+    return torch.tensor([float(x)], dtype=like.dtype, device=like.device)
+
+
+def adpar_vjp_reduce(op, a, ybar=1.0, abar=None, want_y=False, want_argidx=False, want_aux=False,
+                     logdomain=False, want_sign=False, accumulate=False, work=None, stream=None):
+    """VJP of reduce (C: adpar_vjp_reduce).
+
+    Returns a dict with ``abar`` and, when asked for, ``y`` (device scalar),
+    ``argidx`` (int64 device scalar), ``aux`` (ProdAux, read back to the
+    host) and ``sign`` (int8 [n]).
+    """
+    opc = OPS[op] if isinstance(op, str) else int(op)
+    n = a.numel()
+    dt = _dtype_code(a)
+    yb = _scalar_dev(ybar, a)
+    if abar is None:
+        abar = torch.zeros_like(a) if accumulate else torch.empty_like(a)
+    y = torch.empty(1, dtype=a.dtype, device=a.device) if want_y else None
+    arg = torch.empty(1, dtype=torch.int64, device=a.device) if want_argidx else None
+    aux = torch.empty(PROD_AUX_BYTES, dtype=torch.uint8, device=a.device) if want_aux else None
+    sg = torch.empty(n, dtype=torch.int8, device=a.device) if want_sign else None
+    need = adpar_workspace_size(RULE_REDUCE, opc, dt, n)
+    if work is None or work.numel() < need:
+        work = workspace(need, a.device)
+    flags = (ACCUMULATE if accumulate else 0) | (PROD_LOGDOMAIN if logdomain else 0)
+    st = lib().adpar_vjp_reduce(OpDesc(opc, dt, 1), n, _ptr(a), _ptr(yb), _ptr(abar), _ptr(y), _ptr(arg),
+                                _ptr(aux), _ptr(sg), flags, _ptr(work), work.numel(), _stream(stream))
+    _check("adpar_vjp_reduce", st)
+    out = {"abar": abar, "work": work}
+    if want_y:
+        out["y"] = y
+    if want_argidx:
+        out["argidx"] = arg
+    if want_sign:
+        out["sign"] = sg
+    if want_aux:
+        raw = aux.cpu().numpy().tobytes()
+        out["aux"] = ProdAux.from_buffer_copy(raw)
+    return out
+
+
+def adpar_vjp_hist(op, inds, m, hsbar, vals=None, valsbar=None, want_hs=False, want_argidx=False,
+                   want_aux=False, logdomain=False, want_sign=False, accumulate=False, work=None,
+                   stream=None):
+    """VJP of reduce_by_index (C: adpar_vjp_hist).
+
+    Returns a dict with ``valsbar`` and, when asked for, ``hs`` [m],
+    ``argidx`` [m] int64, ``aux`` (structured numpy array of ProdAux, [m])
+    and ``sign`` [n] int8.
+    """
+    opc = OPS[op] if isinstance(op, str) else int(op)
+    n = inds.numel()
+    ref = hsbar
+    dt = _dtype_code(ref)
+    it = _itype_code(inds)
+    if valsbar is None:
+        valsbar = (torch.zeros if accumulate else torch.empty)(n, dtype=ref.dtype, device=ref.device)
+    hs = torch.empty(m, dtype=ref.dtype, device=ref.device) if want_hs else None
+    arg = torch.empty(m, dtype=torch.int64, device=ref.device) if want_argidx else None
+    aux = torch.empty(max(m, 1) * PROD_AUX_BYTES, dtype=torch.uint8, device=ref.device) if want_aux else None
+    sg = torch.empty(n, dtype=torch.int8, device=ref.device) if want_sign else None
+    need = adpar_workspace_size(RULE_HIST, opc, dt, n, m)
+    if work is None or work.numel() < need:
+        work = workspace(need, ref.device)
+    flags = (ACCUMULATE if accumulate else 0) | (PROD_LOGDOMAIN if logdomain else 0)
+    st = lib().adpar_vjp_hist(OpDesc(opc, dt, 1), n, m, _ptr(vals), _ptr(inds), it, _ptr(hsbar), _ptr(valsbar),
+                              _ptr(hs), _ptr(arg), _ptr(aux), _ptr(sg), flags, _ptr(work), work.numel(),
+                              _stream(stream))
+    _check("adpar_vjp_hist", st)
+    out = {"valsbar": valsbar, "work": work}
+    if want_hs:
+        out["hs"] = hs
+    if want_argidx:
+        out["argidx"] = arg
+    if want_sign:
+        out["sign"] = sg
+    if want_aux:
+        import numpy as np
+        dtype = np.dtype([("nzero", "<i8"), ("first_zero", "<i8"), ("exp2", "<i8"), ("mant", "<f8"),
+                          ("log_abs_nz", "<f8"), ("sign", "<i4"), ("reserved", "<i4")])
+        out["aux"] = np.frombuffer(aux.cpu().numpy().tobytes(), dtype=dtype)[:m]
+    return out
+
+
+def adpar_vjp_scatter(is_, ysbar, vsbar=None, ys=None, xs_saved=None, accumulate=False, stream=None):
+    """VJP of scatter (C: adpar_vjp_scatter).  ``ysbar`` becomes xsbar in place.
+
+    Returns (xsbar, vsbar).  With ``ys`` and ``xs_saved`` the scattered
+    positions of ``ys`` are restored too.
+    """
+    m = is_.numel()
+    n = ysbar.numel()
+    dt = _dtype_code(ysbar)
+    it = _itype_code(is_)
+    if vsbar is None:
+        vsbar = (torch.zeros if accumulate else torch.empty)(m, dtype=ysbar.dtype, device=ysbar.device)
+    flags = (ACCUMULATE if accumulate else 0) | (SCATTER_RESTORE if ys is not None else 0)
+    st = lib().adpar_vjp_scatter(dt, n, m, _ptr(is_), it, _ptr(ysbar), _ptr(vsbar), _ptr(ys), _ptr(xs_saved),
+                                 flags, _stream(stream))
+    _check("adpar_vjp_scatter", st)
+    return ysbar, vsbar
+
+
+def adpar_vjp_map_acc(g, as_, is_, xsbar, ws=None, width=1, asbar=None, wsbar=None, want_wsbar=False,
+                      accumulate=False, stream=None):
+    """VJP of map with a free array (C: adpar_vjp_map_acc).  Returns (asbar, wsbar)."""
+    gc = GFUNS[g] if isinstance(g, str) else int(g)
+    nj = is_.numel()
+    na = as_.numel() // width
+    dt = _dtype_code(as_)
+    it = _itype_code(is_)
+    if asbar is None:
+        asbar = torch.zeros_like(as_) if accumulate else torch.empty_like(as_)
+    if want_wsbar and wsbar is None and ws is not None:
+        wsbar = torch.zeros_like(ws) if accumulate else torch.empty_like(ws)
+    st = lib().adpar_vjp_map_acc(gc, dt, nj, na, width, _ptr(as_), _ptr(is_), it, _ptr(ws), _ptr(xsbar),
+                                 _ptr(asbar), _ptr(wsbar), ACCUMULATE if accumulate else 0, None, 0,
+                                 _stream(stream))
+    _check("adpar_vjp_map_acc", st)
+    return asbar, wsbar

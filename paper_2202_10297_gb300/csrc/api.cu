@@ -4,6 +4,8 @@
 
 namespace adpar {
 size_t scan_workspace_size(adpar_opdesc d, int64_t n);
+size_t reduce_workspace_size(adpar_opdesc d);
+size_t hist_workspace_size(adpar_opdesc d, int64_t m);
 }
 
 extern "C" const char* adpar_status_string(int status) {
@@ -26,6 +28,8 @@ extern "C" size_t adpar_workspace_size(int rule, adpar_opdesc d, int64_t n, int6
     (void)m;
     switch (rule) {
     case ADPAR_RULE_SCAN: return adpar::scan_workspace_size(d, n);
+    case ADPAR_RULE_REDUCE: return n < 0 ? (size_t)-1 : adpar::reduce_workspace_size(d);
+    case ADPAR_RULE_HIST: return n < 0 ? (size_t)-1 : adpar::hist_workspace_size(d, m);
     }
     return (size_t)-1;
 }

@@ -1,0 +1,587 @@
+// VJP of reduce_by_index (Sec. 5.1.2) for +, min, max and *.
+//
+// The primal is the semantic loop  hs[inds_i] (.)= vals_i  with indices
+// outside [0, m) ignored.  Following Sec. 5.1.2, the return sweep is the
+// reduce rule of Sec. 5.1.1 per bin with ybar replaced by hsbar[inds_i]:
+//   +        valsbar_i = hsbar[inds_i]: one gather pass, no recompute.
+//   min/max  recompute per bin the extremum and its LOWEST index, then
+//            valsbar[argidx_b] = hsbar_b and 0 elsewhere.
+//   *        recompute per bin (zero count, lowest zero index, scaled
+//            product of the nonzeros), then the three cases per element.
+//
+// Recompute pass (min/max/*): a grid-stride loop whose per-block bin state
+// for the bin range [0, H) lives in shared memory (H = min(m, capacity));
+// bins at or above H go straight to global atomics (L2).  Low bin ids are
+// the hot ones of rank-ordered skewed data such as Zipf, so their
+// contention stays on-chip.  The extremum of a bin is one 64-bit word:
+//   max: (orderkey(v) << 32) | ~i   under atomicMax,
+//   min: (orderkey(v) << 32) |  i   under atomicMin,
+// where orderkey maps FP32 bits monotonically to unsigned (+0 and -0 equal),
+// so ties resolve to the lowest index exactly.  FP64 values take two
+// passes: the extremum key (64-bit atomic), then the lowest index holding it.
+#include <algorithm>
+#include <math_constants.h>
+
+#include "common.cuh"
+#include "prod.cuh"
+#include "scan_ops.cuh"
+
+namespace adpar {
+namespace {
+
+constexpr int kHistBlock = 512;
+constexpr int kHistSmemKeys = 8192;  // 64 KB of 64-bit bin words per block
+constexpr int kHistSmemProd = 2048;  // bins of the * state per block (40 B each)
+
+__device__ __forceinline__ uint32_t orderkey_f32(float f) {
+    uint32_t u = __float_as_uint(f);
+    if (u == 0x80000000u) u = 0u;  // -0 == +0
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float from_orderkey_f32(uint32_t k) {
+    const uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+    return __uint_as_float(u);
+}
+__device__ __forceinline__ unsigned long long orderkey_f64(double d) {
+    unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    if (u == 0x8000000000000000ull) u = 0ull;
+    return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double from_orderkey_f64(unsigned long long k) {
+    const unsigned long long u = (k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k;
+    return __longlong_as_double((long long)u);
+}
+
+template <class I>
+__device__ __forceinline__ int64_t ld_index(const I* p, int64_t i) {
+    return (int64_t)__ldcs(p + i);
+}
+
+struct HistArgs {
+    int op;
+    int64_t n, m;
+    const void* vals;
+    const void* inds;
+    const void* hsbar;
+    void* valsbar;
+    void* hs_out;
+    int64_t* argidx_out;
+    adpar_prod_aux* bin_aux;
+    int8_t* vsign;
+    int accumulate;
+    int logdomain;
+    WsHeader* hdr;
+    unsigned long long* key;  // [m] extremum words (min/max), FP64 pass-1 keys
+    unsigned long long* idx;  // [m] lowest index (FP64 min/max pass 2)
+    double* pm;               // [m] * : mantissa of the nonzero product
+    long long* pe;            // [m] * : its exponent
+    unsigned int* pz;         // [m] * : zero count
+    long long* pf;            // [m] * : lowest zero index
+};
+
+__global__ void hist_init_kernel(HistArgs A, unsigned long long key_empty) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t0 < 64) reinterpret_cast<uint32_t*>(A.hdr)[t0] = 0u;
+    for (int64_t b = t0; b < A.m; b += stride) {
+        if (A.key) A.key[b] = key_empty;
+        if (A.idx) A.idx[b] = 0xffffffffffffffffull;
+        if (A.pm) {
+            A.pm[b] = 0.5;
+            A.pe[b] = 1;
+            A.pz[b] = 0u;
+            A.pf[b] = INT64_MAX;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ +
+// valsbar_i = hsbar[inds_i] (in range) -- the whole VJP is this gather.
+template <class T, class I>
+__global__ void __launch_bounds__(kHistBlock) hist_add_vjp_kernel(HistArgs A) {
+    const I* inds = static_cast<const I*>(A.inds);
+    const T* hsbar = static_cast<const T*>(A.hsbar);
+    T* vb = static_cast<T*>(A.valsbar);
+    constexpr int V = 4;  // 4 elements per thread step
+    const int64_t nv = A.n / V;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += stride) {
+        T o[V];
+        int64_t b[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) b[j] = ld_index(inds, v * V + j);
+#pragma unroll
+        for (int j = 0; j < V; ++j) o[j] = (b[j] >= 0 && b[j] < A.m) ? __ldg(hsbar + b[j]) : T(0);
+        if (A.accumulate) {
+#pragma unroll
+            for (int j = 0; j < V; ++j) o[j] += vb[v * V + j];
+        }
+        if constexpr (sizeof(T) == 4) {
+            __stcs(reinterpret_cast<float4*>(vb + v * V), make_float4(o[0], o[1], o[2], o[3]));
+        } else {
+            __stcs(reinterpret_cast<double2*>(vb + v * V), make_double2(o[0], o[1]));
+            __stcs(reinterpret_cast<double2*>(vb + v * V + 2), make_double2(o[2], o[3]));
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x < A.n - nv * V) {
+        const int64_t i = nv * V + threadIdx.x;
+        const int64_t b = ld_index(inds, i);
+        const T o = (b >= 0 && b < A.m) ? hsbar[b] : T(0);
+        vb[i] = A.accumulate ? vb[i] + o : o;
+    }
+}
+
+// primal of + (only when hs_out is asked for): hs[b] += vals_i
+template <class T, class I>
+__global__ void __launch_bounds__(kHistBlock) hist_add_primal_kernel(HistArgs A) {
+    extern __shared__ unsigned char smem_raw[];
+    T* sh = reinterpret_cast<T*>(smem_raw);
+    const int H = (int)std::min<int64_t>(A.m, kHistSmemKeys);
+    for (int b = threadIdx.x; b < H; b += blockDim.x) sh[b] = T(0);
+    __syncthreads();
+    const I* inds = static_cast<const I*>(A.inds);
+    const T* vals = static_cast<const T*>(A.vals);
+    T* hs = static_cast<T*>(A.hs_out);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += stride) {
+        const int64_t b = ld_index(inds, i);
+        if (b < 0 || b >= A.m) continue;
+        const T v = __ldcs(vals + i);
+        if (b < H) atomicAdd(sh + b, v);
+        else atomicAdd(hs + b, v);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < H; b += blockDim.x)
+        if (sh[b] != T(0)) atomicAdd(hs + b, sh[b]);
+}
+
+__global__ void fill_zero_kernel(void* p, int64_t nbytes) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t nv = nbytes / 16;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += stride)
+        reinterpret_cast<uint4*>(p)[v] = make_uint4(0, 0, 0, 0);
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < nbytes - nv * 16) static_cast<unsigned char*>(p)[nv * 16 + t] = 0;
+}
+
+// ------------------------------------------------------------ min / max
+// FP32: one recompute pass with packed words; fuses the zero fill of valsbar.
+template <class I, bool MAX>
+__global__ void __launch_bounds__(kHistBlock) hist_arg_f32_kernel(HistArgs A) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned long long* sh = reinterpret_cast<unsigned long long*>(smem_raw);
+    const unsigned long long empty = MAX ? 0ull : 0xffffffffffffffffull;
+    const int H = (int)std::min<int64_t>(A.m, kHistSmemKeys);
+    for (int b = threadIdx.x; b < H; b += blockDim.x) sh[b] = empty;
+    __syncthreads();
+    const I* inds = static_cast<const I*>(A.inds);
+    const float* vals = static_cast<const float*>(A.vals);
+    float* vb = static_cast<float*>(A.valsbar);
+    const bool fill = !A.accumulate;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += stride) {
+        const int64_t b = ld_index(inds, i);
+        if (fill) __stcs(vb + i, 0.0f);
+        if (b < 0 || b >= A.m) continue;
+        const uint32_t k = orderkey_f32(__ldcs(vals + i));
+        const unsigned long long w = ((unsigned long long)k << 32) |
+                                     (MAX ? (unsigned long long)(~(uint32_t)i) : (unsigned long long)(uint32_t)i);
+        if (b < H) {
+            if (MAX) atomicMax(sh + b, w); else atomicMin(sh + b, w);
+        } else {
+            if (MAX) atomicMax(A.key + b, w); else atomicMin(A.key + b, w);
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < H; b += blockDim.x) {
+        const unsigned long long w = sh[b];
+        if (w != empty) {
+            if (MAX) atomicMax(A.key + b, w); else atomicMin(A.key + b, w);
+        }
+    }
+}
+
+// FP64, pass 1: extremum key per bin (+ zero fill of valsbar)
+template <class I, bool MAX>
+__global__ void __launch_bounds__(kHistBlock) hist_arg_f64_key_kernel(HistArgs A) {
+    const I* inds = static_cast<const I*>(A.inds);
+    const double* vals = static_cast<const double*>(A.vals);
+    double* vb = static_cast<double*>(A.valsbar);
+    const bool fill = !A.accumulate;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += stride) {
+        const int64_t b = ld_index(inds, i);
+        if (fill) vb[i] = 0.0;
+        if (b < 0 || b >= A.m) continue;
+        const unsigned long long k = orderkey_f64(vals[i]);
+        if (MAX) atomicMax(A.key + b, k); else atomicMin(A.key + b, k);
+    }
+}
+// FP64, pass 2: lowest index whose value equals the bin's extremum
+template <class I>
+__global__ void __launch_bounds__(kHistBlock) hist_arg_f64_idx_kernel(HistArgs A) {
+    const I* inds = static_cast<const I*>(A.inds);
+    const double* vals = static_cast<const double*>(A.vals);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += stride) {
+        const int64_t b = ld_index(inds, i);
+        if (b < 0 || b >= A.m) continue;
+        if (orderkey_f64(vals[i]) == A.key[b]) atomicMin(A.idx + b, (unsigned long long)i);
+    }
+}
+
+// per bin: valsbar[argidx_b] (+)= hsbar_b; hs_out, argidx_out
+template <class T, bool MAX>
+__global__ void hist_arg_finish_kernel(HistArgs A) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const T* hsbar = static_cast<const T*>(A.hsbar);
+    T* vb = static_cast<T*>(A.valsbar);
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < A.m; b += stride) {
+        int64_t arg = -1;
+        T val = MAX ? -pos_inf<T>() : pos_inf<T>();
+        if constexpr (sizeof(T) == 4) {
+            const unsigned long long w = A.key[b];
+            const unsigned long long empty = MAX ? 0ull : 0xffffffffffffffffull;
+            if (w != empty) {
+                const uint32_t lo = (uint32_t)w;
+                arg = (int64_t)(MAX ? (uint32_t)~lo : lo);
+                val = (T)from_orderkey_f32((uint32_t)(w >> 32));
+            }
+        } else {
+            const unsigned long long ix = A.idx[b];
+            if (ix != 0xffffffffffffffffull) {
+                arg = (int64_t)ix;
+                val = (T)from_orderkey_f64(A.key[b]);
+            }
+        }
+        if (arg >= 0) vb[arg] = A.accumulate ? vb[arg] + hsbar[b] : hsbar[b];
+        if (A.hs_out) static_cast<T*>(A.hs_out)[b] = val;
+        if (A.argidx_out) A.argidx_out[b] = arg;
+    }
+}
+
+// ------------------------------------------------------------------ *
+__device__ __forceinline__ void mul_into(double* pm, long long* pe, double mi, long long ei) {
+    // pm *= mi under a CAS loop; when the mantissa gets small it is scaled
+    // back up by 2^900 and the exponent counter takes -900 (both exact)
+    atomicAdd(reinterpret_cast<unsigned long long*>(pe), (unsigned long long)ei);
+    unsigned long long* p = reinterpret_cast<unsigned long long*>(pm);
+    unsigned long long old = *reinterpret_cast<volatile unsigned long long*>(p), assumed;
+    long long shift;
+    do {
+        assumed = old;
+        double nv = __longlong_as_double((long long)assumed) * mi;
+        shift = 0;
+        if (fabs(nv) < 1e-250) {
+            nv *= 8.45271249817064e+270;  // 2^900
+            shift = -900;
+        }
+        old = atomicCAS(p, assumed, (unsigned long long)__double_as_longlong(nv));
+    } while (old != assumed);
+    if (shift) atomicAdd(reinterpret_cast<unsigned long long*>(pe), (unsigned long long)shift);
+}
+
+template <class T, class I>
+__global__ void __launch_bounds__(kHistBlock) hist_prod_kernel(HistArgs A) {
+    extern __shared__ unsigned char smem_raw[];
+    const int H = (int)std::min<int64_t>(A.m, kHistSmemProd);
+    double* sm = reinterpret_cast<double*>(smem_raw);
+    long long* se = reinterpret_cast<long long*>(sm + H);
+    long long* sf = se + H;
+    unsigned int* sz = reinterpret_cast<unsigned int*>(sf + H);
+    for (int b = threadIdx.x; b < H; b += blockDim.x) {
+        sm[b] = 0.5;
+        se[b] = 1;
+        sf[b] = INT64_MAX;
+        sz[b] = 0u;
+    }
+    __syncthreads();
+    const I* inds = static_cast<const I*>(A.inds);
+    const T* vals = static_cast<const T*>(A.vals);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += stride) {
+        const int64_t b = ld_index(inds, i);
+        if (b < 0 || b >= A.m) continue;
+        const double v = (double)__ldcs(vals + i);
+        if (v == 0.0) {
+            if (b < H) {
+                atomicAdd(sz + b, 1u);
+                atomicMin(sf + b, (long long)i);
+            } else {
+                atomicAdd(A.pz + b, 1u);
+                atomicMin(A.pf + b, (long long)i);
+            }
+        } else {
+            double mi;
+            int64_t ei;
+            split_pow2(v, mi, ei);
+            if (b < H) mul_into(sm + b, se + b, mi, ei);
+            else mul_into(A.pm + b, A.pe + b, mi, ei);
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < H; b += blockDim.x) {
+        if (sz[b]) {
+            atomicAdd(A.pz + b, sz[b]);
+            atomicMin(A.pf + b, sf[b]);
+        }
+        double mb = sm[b];
+        long long eb = se[b];
+        if (!(mb == 0.5 && eb == 1)) {
+            double mm;
+            int64_t ee;
+            split_pow2(mb, mm, ee);
+            mul_into(A.pm + b, A.pe + b, mm, (long long)(eb + ee));
+        }
+    }
+}
+
+// per bin outputs of *: hs_out (product rounded to T) and aux
+template <class T>
+__global__ void hist_prod_bins_kernel(HistArgs A) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < A.m; b += stride) {
+        double mm;
+        int64_t ee;
+        split_pow2(A.pm[b], mm, ee);
+        const int64_t e = A.pe[b] + ee;
+        const int64_t nz = A.pz[b];
+        if (A.hs_out) static_cast<T*>(A.hs_out)[b] = nz ? T(0) : (T)ldexp_clamped(mm, e);
+        if (A.bin_aux) {
+            adpar_prod_aux x;
+            x.nzero = nz;
+            x.first_zero = nz ? A.pf[b] : -1;
+            x.exp2 = e;
+            x.mant = mm;
+            x.log_abs_nz = log(fabs(mm)) + (double)e * 0.69314718055994530942;
+            x.sign = mm > 0 ? 1 : -1;
+            x.reserved = 0;
+            A.bin_aux[b] = x;
+        }
+    }
+}
+
+// per element: the cases of Sec. 5.1.1 with ybar = hsbar[inds_i]
+template <class T, class I>
+__global__ void __launch_bounds__(kHistBlock) hist_prod_vjp_kernel(HistArgs A) {
+    const I* inds = static_cast<const I*>(A.inds);
+    const T* vals = static_cast<const T*>(A.vals);
+    const T* hsbar = static_cast<const T*>(A.hsbar);
+    T* vb = static_cast<T*>(A.valsbar);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += stride) {
+        const int64_t b = ld_index(inds, i);
+        const bool in = b >= 0 && b < A.m;
+        double c = 0.0, lg = -CUDART_INF;
+        int sg = 0;
+        if (in) {
+            const double yb = (double)hsbar[b];
+            const unsigned int nz = A.pz[b];
+            if (yb != 0.0 && (nz == 0 || (nz == 1 && A.pf[b] == i))) {
+                double mm;
+                int64_t ee;
+                split_pow2(A.pm[b], mm, ee);
+                const int64_t e = A.pe[b] + ee;
+                double ym;
+                int64_t ye;
+                split_pow2(yb, ym, ye);
+                const int spy = (mm > 0 ? 1 : -1) * (yb > 0 ? 1 : -1);
+                if (nz == 0) {
+                    const double v = (double)vals[i];
+                    if (A.logdomain) {
+                        lg = log(fabs(mm)) + (double)e * 0.69314718055994530942 - log(fabs(v)) + log(fabs(yb));
+                        sg = spy * (v > 0 ? 1 : -1);
+                    } else {
+                        double mi;
+                        int64_t ei;
+                        split_pow2(v, mi, ei);
+                        c = ldexp_clamped(mm * ym / mi, e + ye - ei);
+                    }
+                } else {
+                    if (A.logdomain) {
+                        lg = log(fabs(mm)) + (double)e * 0.69314718055994530942 + log(fabs(yb));
+                        sg = spy;
+                    } else {
+                        c = ldexp_clamped(mm * ym, e + ye);
+                    }
+                }
+            }
+        }
+        if (A.logdomain) {
+            vb[i] = (T)lg;
+            if (A.vsign) A.vsign[i] = (int8_t)sg;
+        } else if (A.accumulate) {
+            if (in) vb[i] = (T)((double)vb[i] + c);
+        } else {
+            vb[i] = (T)c;
+        }
+    }
+}
+
+// ------------------------------------------------------------ host side
+struct HistLayout {
+    size_t off_key, off_idx, off_pm, off_pe, off_pz, off_pf, total;
+};
+
+HistLayout hist_layout(int op, int dtype, int64_t m) {
+    HistLayout L{};
+    size_t o = sizeof(WsHeader);
+    const size_t mm = (size_t)std::max<int64_t>(m, 1);
+    if (op == ADPAR_OP_MIN || op == ADPAR_OP_MAX) {
+        L.off_key = o; o = round_up(o + mm * 8, 256);
+        if (dtype == ADPAR_F64) { L.off_idx = o; o = round_up(o + mm * 8, 256); }
+    } else if (op == ADPAR_OP_MUL) {
+        L.off_pm = o; o = round_up(o + mm * 8, 256);
+        L.off_pe = o; o = round_up(o + mm * 8, 256);
+        L.off_pf = o; o = round_up(o + mm * 8, 256);
+        L.off_pz = o; o = round_up(o + mm * 4, 256);
+    }
+    L.total = o;
+    return L;
+}
+
+int num_sms() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 132;
+}
+
+template <class T, class I>
+int run_hist(HistArgs A, cudaStream_t s) {
+    const int sms = num_sms();
+    const int gridN = (int)std::max<int64_t>(1, std::min<int64_t>((A.n + kHistBlock - 1) / kHistBlock, (int64_t)sms * 4));
+    const int gridM = (int)std::max<int64_t>(1, std::min<int64_t>((A.m + 255) / 256, (int64_t)sms * 8));
+    const int op = A.op;
+    if (op != ADPAR_OP_ADD) {
+        const unsigned long long empty = op == ADPAR_OP_MAX ? 0ull : 0xffffffffffffffffull;
+        hist_init_kernel<<<gridM, 256, 0, s>>>(A, empty);
+    }
+    switch (op) {
+    case ADPAR_OP_ADD: {
+        if (A.hs_out) {
+            fill_zero_kernel<<<gridM, 256, 0, s>>>(A.hs_out, A.m * (int64_t)sizeof(T));
+            const size_t sh = (size_t)std::min<int64_t>(A.m, kHistSmemKeys) * sizeof(T);
+            hist_add_primal_kernel<T, I><<<gridN, kHistBlock, sh, s>>>(A);
+        }
+        const int g = (int)std::max<int64_t>(1, std::min<int64_t>((A.n / 4 + kHistBlock - 1) / kHistBlock, (int64_t)sms * 8));
+        hist_add_vjp_kernel<T, I><<<g, kHistBlock, 0, s>>>(A);
+        break;
+    }
+    case ADPAR_OP_MIN:
+    case ADPAR_OP_MAX: {
+        const bool mx = op == ADPAR_OP_MAX;
+        if constexpr (sizeof(T) == 4) {
+            const size_t sh = (size_t)std::min<int64_t>(A.m, kHistSmemKeys) * 8;
+            if (mx) hist_arg_f32_kernel<I, true><<<gridN, kHistBlock, sh, s>>>(A);
+            else hist_arg_f32_kernel<I, false><<<gridN, kHistBlock, sh, s>>>(A);
+        } else {
+            if (mx) hist_arg_f64_key_kernel<I, true><<<gridN, kHistBlock, 0, s>>>(A);
+            else hist_arg_f64_key_kernel<I, false><<<gridN, kHistBlock, 0, s>>>(A);
+            hist_arg_f64_idx_kernel<I><<<gridN, kHistBlock, 0, s>>>(A);
+        }
+        if (mx) hist_arg_finish_kernel<T, true><<<gridM, 256, 0, s>>>(A);
+        else hist_arg_finish_kernel<T, false><<<gridM, 256, 0, s>>>(A);
+        break;
+    }
+    case ADPAR_OP_MUL: {
+        const size_t sh = (size_t)std::min<int64_t>(A.m, kHistSmemProd) * 28;
+        hist_prod_kernel<T, I><<<gridN, kHistBlock, sh, s>>>(A);
+        if (A.hs_out || A.bin_aux) hist_prod_bins_kernel<T><<<gridM, 256, 0, s>>>(A);
+        hist_prod_vjp_kernel<T, I><<<gridN, kHistBlock, 0, s>>>(A);
+        break;
+    }
+    default:
+        return ADPAR_ERR_INVALID;
+    }
+    return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
+}
+
+constexpr int kMaxDev = 64;
+bool smem_configured[kMaxDev] = {};
+
+template <class T, class I>
+void configure_smem() {
+    // the recompute kernels use up to 64 KB of dynamic shared memory
+    cudaFuncSetAttribute(hist_add_primal_kernel<T, I>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(hist_prod_kernel<T, I>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    if constexpr (sizeof(T) == 4) {
+        cudaFuncSetAttribute(hist_arg_f32_kernel<I, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+        cudaFuncSetAttribute(hist_arg_f32_kernel<I, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    }
+}
+
+}  // namespace
+
+size_t hist_workspace_size(adpar_opdesc d, int64_t m) {
+    if (m < 0 || (d.dtype != ADPAR_F32 && d.dtype != ADPAR_F64)) return (size_t)-1;
+    if (d.op != ADPAR_OP_ADD && d.op != ADPAR_OP_MUL && d.op != ADPAR_OP_MIN && d.op != ADPAR_OP_MAX)
+        return (size_t)-1;
+    return hist_layout(d.op, d.dtype, m).total;
+}
+
+}  // namespace adpar
+
+extern "C" int adpar_vjp_hist(adpar_opdesc d, int64_t n, int64_t m, const void* vals, const void* inds,
+                              int itype, const void* hsbar, void* valsbar, void* hs_out,
+                              int64_t* argidx_out, adpar_prod_aux* bin_aux_out, int8_t* valsbar_sign,
+                              uint32_t flags, void* work, size_t work_bytes, void* stream) {
+    using namespace adpar;
+    if (n < 0 || m < 0 || d.width != 1) return ADPAR_ERR_INVALID;
+    if (d.op != ADPAR_OP_ADD && d.op != ADPAR_OP_MUL && d.op != ADPAR_OP_MIN && d.op != ADPAR_OP_MAX)
+        return ADPAR_ERR_INVALID;
+    if (d.dtype != ADPAR_F32 && d.dtype != ADPAR_F64) return ADPAR_ERR_INVALID;
+    if (itype != ADPAR_I32 && itype != ADPAR_I64) return ADPAR_ERR_INVALID;
+    if (flags & ~(uint32_t)(ADPAR_ACCUMULATE | ADPAR_PROD_LOGDOMAIN)) return ADPAR_ERR_UNSUPPORTED;
+    const bool logd = (flags & ADPAR_PROD_LOGDOMAIN) != 0;
+    if (logd && (d.op != ADPAR_OP_MUL || (flags & ADPAR_ACCUMULATE))) return ADPAR_ERR_UNSUPPORTED;
+    if (valsbar_sign && !logd) return ADPAR_ERR_INVALID;
+    if ((d.op == ADPAR_OP_MIN || d.op == ADPAR_OP_MAX) && d.dtype == ADPAR_F32 && n > 0xffffffffLL)
+        return ADPAR_ERR_UNSUPPORTED;  // the packed word holds a 32-bit index
+    if (n > 0 && (!inds || !valsbar)) return ADPAR_ERR_INVALID;
+    if (n > 0 && m > 0 && !hsbar) return ADPAR_ERR_INVALID;
+    if (n > 0 && !vals && (d.op != ADPAR_OP_ADD || hs_out)) return ADPAR_ERR_INVALID;
+    const void* ptrs[] = {vals, inds, hsbar, valsbar, hs_out};
+    for (const void* p : ptrs)
+        if (p && !aligned16(p)) return ADPAR_ERR_ALIGN;
+    const HistLayout L = hist_layout(d.op, d.dtype, m);
+    if (!work || work_bytes < L.total || (reinterpret_cast<uintptr_t>(work) & 255u)) return ADPAR_ERR_WORKSPACE;
+    if (n == 0 && m == 0) return ADPAR_OK;
+    HistArgs A{};
+    A.op = d.op;
+    A.n = n;
+    A.m = m;
+    A.vals = vals;
+    A.inds = inds;
+    A.hsbar = hsbar;
+    A.valsbar = valsbar;
+    A.hs_out = hs_out;
+    A.argidx_out = argidx_out;
+    A.bin_aux = bin_aux_out;
+    A.vsign = valsbar_sign;
+    A.accumulate = (flags & ADPAR_ACCUMULATE) ? 1 : 0;
+    A.logdomain = logd ? 1 : 0;
+    char* w = static_cast<char*>(work);
+    A.hdr = reinterpret_cast<WsHeader*>(w);
+    if (L.off_key) A.key = reinterpret_cast<unsigned long long*>(w + L.off_key);
+    if (L.off_idx) A.idx = reinterpret_cast<unsigned long long*>(w + L.off_idx);
+    if (L.off_pm) {
+        A.pm = reinterpret_cast<double*>(w + L.off_pm);
+        A.pe = reinterpret_cast<long long*>(w + L.off_pe);
+        A.pz = reinterpret_cast<unsigned int*>(w + L.off_pz);
+        A.pf = reinterpret_cast<long long*>(w + L.off_pf);
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return ADPAR_ERR_CUDA;
+    if (!smem_configured[dev]) {  // once per device (idempotent if two threads race here)
+        configure_smem<float, int32_t>();
+        configure_smem<float, int64_t>();
+        configure_smem<double, int32_t>();
+        configure_smem<double, int64_t>();
+        smem_configured[dev] = true;
+    }
+    if (d.dtype == ADPAR_F32)
+        return itype == ADPAR_I32 ? run_hist<float, int32_t>(A, s) : run_hist<float, int64_t>(A, s);
+    return itype == ADPAR_I32 ? run_hist<double, int32_t>(A, s) : run_hist<double, int64_t>(A, s);
+}

@@ -268,6 +268,31 @@ int adpar_vjp_map_acc(int gfun, int dtype, int64_t nj, int64_t na, int width, co
                       void *wsbar, uint32_t flags, void *work, size_t work_bytes, void *stream);
 
 /* ------------------------------------------------------------------ */
+/* k-means cost and its gradient (Sec. 7.3)                            */
+/* ------------------------------------------------------------------ */
+/* loss = sum_i min_k ||x_i - c_k||^2 over N points x_i (rows of X, d = 32
+ * FP32) and k centroids (rows of C), and its VJP in C:
+ *   Cbar[k] = 2 ybar (cnt_k c_k - sum_{i: argmin_i = k} x_i),
+ * the min-reduce rule of Sec. 5.1.1 followed by the accumulator of
+ * Sec. 5.4 on the free array C.  Distances come from a TF32 tensor-core
+ * GEMM X C^T; the argmin is certified (every centroid within the TF32 error
+ * bound of the minimum is recomputed exactly, FP64 breaking what FP32
+ * cannot), so it equals the FP64 argmin with the lowest k on ties, and the
+ * loss sums the exactly recomputed distances.
+ * Arguments:
+ *   N, d, k      points, dimension (32) and centroids (multiple of 32, <= 256).
+ *   X [N*32], C [k*32]   row-major FP32 inputs.
+ *   ybar         device FP32 scalar, required when Cbar is given.
+ *   loss_out     nullable device FP32 scalar.
+ *   argmin_out   nullable device int32 [N].
+ *   Cbar         nullable [k*32] FP32: the gradient (forward only if NULL).
+ * Flags: ADPAR_ACCUMULATE (Cbar += ...).
+ * Workspace: adpar_workspace_size(ADPAR_RULE_KMEANS, desc, N, k). */
+int adpar_kmeans_vjp(int64_t N, int d, int k, const float *X, const float *C, const float *ybar,
+                     float *loss_out, int32_t *argmin_out, float *Cbar, uint32_t flags, void *work,
+                     size_t work_bytes, void *stream);
+
+/* ------------------------------------------------------------------ */
 /* scan VJP without any allocation                                     */
 /* ------------------------------------------------------------------ */
 /* The paper has no counterpart of this entry point; it serves callers

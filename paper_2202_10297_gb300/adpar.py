@@ -88,6 +88,8 @@ def _bind_optional(L):
                               C.c_uint32, _VP],
         "adpar_vjp_map_acc": [C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int, _VP, _VP, C.c_int, _VP,
                               _VP, _VP, _VP, C.c_uint32, _VP, C.c_size_t, _VP],
+        "adpar_kmeans_vjp": [C.c_int64, C.c_int, C.c_int, _VP, _VP, _VP, _VP, _VP, _VP, C.c_uint32, _VP,
+                             C.c_size_t, _VP],
     }
     for name, argt in sigs.items():
         if hasattr(L, name):
@@ -362,3 +364,37 @@ def adpar_vjp_map_acc(g, as_, is_, xsbar, ws=None, width=1, asbar=None, wsbar=No
                                  _stream(stream))
     _check("adpar_vjp_map_acc", st)
     return asbar, wsbar
+
+
+def adpar_kmeans_vjp(X, C, ybar=None, want_grad=True, want_argmin=False, Cbar=None, accumulate=False,
+                     work=None, stream=None):
+    """k-means loss and its gradient in C (C: adpar_kmeans_vjp).
+
+    Returns a dict with ``loss`` (device FP32 scalar), ``Cbar`` [k, d] when
+    ``want_grad`` and ``argmin`` [N] int32 when asked for.
+    """
+    N, d = X.shape
+    k = C.shape[0]
+    if X.dtype != torch.float32 or C.dtype != torch.float32:
+        raise TypeError("k-means takes FP32 X and C")
+    loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    arg = torch.empty(N, dtype=torch.int32, device=X.device) if want_argmin else None
+    yb = None
+    if want_grad:
+        yb = _scalar_dev(1.0 if ybar is None else ybar, X)
+        if Cbar is None:
+            Cbar = torch.zeros_like(C) if accumulate else torch.empty_like(C)
+    else:
+        Cbar = None
+    need = adpar_workspace_size(RULE_KMEANS, 0, F32, N, k)
+    if work is None or work.numel() < need:
+        work = workspace(need, X.device)
+    st = lib().adpar_kmeans_vjp(N, d, k, _ptr(X), _ptr(C), _ptr(yb), _ptr(loss), _ptr(arg), _ptr(Cbar),
+                                ACCUMULATE if accumulate else 0, _ptr(work), work.numel(), _stream(stream))
+    _check("adpar_kmeans_vjp", st)
+    out = {"loss": loss, "work": work}
+    if want_grad:
+        out["Cbar"] = Cbar
+    if want_argmin:
+        out["argmin"] = arg
+    return out

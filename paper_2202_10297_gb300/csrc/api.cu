@@ -6,6 +6,7 @@ namespace adpar {
 size_t scan_workspace_size(adpar_opdesc d, int64_t n);
 size_t reduce_workspace_size(adpar_opdesc d);
 size_t hist_workspace_size(adpar_opdesc d, int64_t m);
+size_t kmeans_workspace_size(int64_t k);
 }
 
 extern "C" const char* adpar_status_string(int status) {
@@ -30,6 +31,7 @@ extern "C" size_t adpar_workspace_size(int rule, adpar_opdesc d, int64_t n, int6
     case ADPAR_RULE_SCAN: return adpar::scan_workspace_size(d, n);
     case ADPAR_RULE_REDUCE: return n < 0 ? (size_t)-1 : adpar::reduce_workspace_size(d);
     case ADPAR_RULE_HIST: return n < 0 ? (size_t)-1 : adpar::hist_workspace_size(d, m);
+    case ADPAR_RULE_KMEANS: return n < 0 ? (size_t)-1 : adpar::kmeans_workspace_size(m);
     }
     return (size_t)-1;
 }

@@ -1,0 +1,493 @@
+// k-means cost and its gradient in C, the nested-parallel program of
+// Sec. 7.3 with squared distances:
+//   loss = sum_i min_k ||x_i - c_k||^2,
+//   Cbar[k] = 2 ybar (cnt_k c_k - sum_{i: argmin_i = k} x_i).
+// Its VJP is the min-reduce rule of Sec. 5.1.1 (the adjoint goes to the
+// argmin only) followed by the accumulator of Sec. 5.4 on the free array C,
+// which Sec. 6.1 turns into a reduction; here that reduction is a per-block
+// histogram of rows (counts and row sums per centroid) in shared memory.
+//
+// One persistent kernel, one CTA per SM, 8 warps:
+//   warp 0     TMA producer: X tiles of 128 rows x 32 FP32 (128-byte rows,
+//              128-byte swizzle) into a 4-stage ring; C (k x 32) once.
+//   warp 1     MMA issuer: S = X_tile C^T with tcgen05.mma kind::tf32
+//              (M = 128, N = k, K = 32 in four steps of 8) into one of two
+//              TMEM accumulators (2 x 256 columns).
+//   warp 2     TMEM allocation and release.
+//   warps 4-7  epilogue, one thread per row: tcgen05.ld of the k
+//              distances  v_k = |c_k|^2 - 2 x.c_k, the minimum, and a
+//              certified argmin: every centroid within the TF32 error
+//              bound of the minimum is recomputed exactly in FP32; if two
+//              remain within the FP32 bound, FP64 (the oracle's own
+//              arithmetic) decides, ties to the lowest k.  Then the loss
+//              term (exact distance of the argmin) and, for the gradient,
+//              warp-cooperative row sums into shared memory.
+// Every mbarrier wait is bounded; a timeout is recorded in the workspace
+// and the kernel drains its copies and MMAs, frees TMEM and returns.
+#include <cuda.h>
+#include <math_constants.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "tc.cuh"
+
+namespace adpar {
+namespace {
+
+constexpr int KM_THREADS = 256;
+constexpr int KM_STAGES = 4;
+constexpr int KM_D = 32;
+constexpr int KM_KMAX = 256;
+constexpr int KM_TILE = 128;
+constexpr uint32_t KM_X_BYTES = KM_TILE * KM_D * 4;  // 16 KB
+constexpr int KM_MAXCAND = 8;
+
+// shared memory layout (offsets from a 1024-aligned base)
+constexpr uint32_t OFF_C = 0;                                           // 32 KB
+constexpr uint32_t OFF_X = OFF_C + KM_KMAX * KM_D * 4;                  // 4 x 16 KB
+constexpr uint32_t OFF_SUM = OFF_X + KM_STAGES * KM_X_BYTES;            // 32 KB
+constexpr uint32_t OFF_CNT = OFF_SUM + KM_KMAX * KM_D * 4;              // 1 KB
+constexpr uint32_t OFF_CN2 = OFF_CNT + KM_KMAX * 4;                     // 1 KB
+constexpr uint32_t OFF_CAND = OFF_CN2 + KM_KMAX * 4;                    // 4 KB
+constexpr uint32_t OFF_ARG = OFF_CAND + KM_TILE * KM_MAXCAND * 4;       // 512 B
+constexpr uint32_t OFF_BAR = OFF_ARG + KM_TILE * 4;                     // barriers
+constexpr uint32_t NBAR = 2 * KM_STAGES + 5;
+constexpr uint32_t OFF_MISC = OFF_BAR + NBAR * 8;
+constexpr uint32_t KM_SMEM = OFF_MISC + 64 + 1024;  // + alignment slack
+static_assert(OFF_X % 1024 == 0 && KM_X_BYTES % 1024 == 0, "swizzled tiles need 1024-byte alignment");
+
+struct KmArgs {
+    int64_t N;
+    int k;
+    const float* X;
+    const float* C;
+    const float* ybar;
+    float* loss_out;
+    int32_t* argmin_out;
+    float* Cbar;
+    int accumulate;
+    int64_t ntiles;
+    WsHeader* hdr;
+    double* loss_acc;
+    float* gsum;  // [k * 32]
+    float* gcnt;  // [k]
+};
+
+// element j of row r of a 128-byte-swizzled tile (rows of 32 FP32)
+__device__ __forceinline__ float sw_elem(const float* tile, int r, int j) {
+    const int chunk = (j >> 2) ^ (r & 7);
+    return tile[r * 32 + chunk * 4 + (j & 3)];
+}
+__device__ __forceinline__ void sw_row(const float* tile, int r, float (&x)[32]) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const float4 v = *reinterpret_cast<const float4*>(tile + r * 32 + ((c ^ (r & 7)) * 4));
+        x[4 * c + 0] = v.x;
+        x[4 * c + 1] = v.y;
+        x[4 * c + 2] = v.z;
+        x[4 * c + 3] = v.w;
+    }
+}
+
+// ||x_r - c_kc||^2 in FP32, sequential over the 32 coordinates (row r of
+// the X tile and row kc of the C tile, both swizzled in shared memory)
+__device__ __noinline__ float exact_f32(const float* xt, int r, const float* sC, int kc) {
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const float d = sw_elem(xt, r, j) - sw_elem(sC, kc, j);
+        s = fmaf(d, d, s);
+    }
+    return s;
+}
+// the oracle's FP64 arithmetic: s += (x - c)^2 with no fused multiply-add
+__device__ __noinline__ double exact_f64(const float* xt, int r, const float* sC, int kc) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const double d = __dsub_rn((double)sw_elem(xt, r, j), (double)sw_elem(sC, kc, j));
+        s = __dadd_rn(s, __dmul_rn(d, d));
+    }
+    return s;
+}
+
+// N == 0: the empty sum
+__global__ void km_empty_kernel(float* loss_out, float* Cbar, int kd, int accumulate) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0 && loss_out) *loss_out = 0.f;
+    if (Cbar && !accumulate)
+        for (int q = t; q < kd; q += gridDim.x * blockDim.x) Cbar[q] = 0.f;
+}
+
+__global__ void km_init_kernel(KmArgs A) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < 64) reinterpret_cast<uint32_t*>(A.hdr)[t] = 0u;
+    if (t == 0) *A.loss_acc = 0.0;
+    for (int q = t; q < A.k * KM_D; q += gridDim.x * blockDim.x) A.gsum[q] = 0.f;
+    for (int q = t; q < A.k; q += gridDim.x * blockDim.x) A.gcnt[q] = 0.f;
+}
+
+__global__ void __launch_bounds__(KM_THREADS, 1)
+    kmeans_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmC, KmArgs A) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    float* sC = reinterpret_cast<float*>(base + OFF_C);
+    float* sX = reinterpret_cast<float*>(base + OFF_X);
+    float* s_sum = reinterpret_cast<float*>(base + OFF_SUM);
+    float* s_cnt = reinterpret_cast<float*>(base + OFF_CNT);
+    float* s_cn2 = reinterpret_cast<float*>(base + OFF_CN2);
+    int* s_cand = reinterpret_cast<int*>(base + OFF_CAND);
+    int* s_arg = reinterpret_cast<int*>(base + OFF_ARG);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + OFF_BAR);
+    uint64_t* x_full = bars;
+    uint64_t* x_empty = bars + KM_STAGES;
+    uint64_t* t_full = bars + 2 * KM_STAGES;
+    uint64_t* t_empty = bars + 2 * KM_STAGES + 2;
+    uint64_t* c_bar = bars + 2 * KM_STAGES + 4;
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(base + OFF_MISC);
+    volatile int* s_abort = reinterpret_cast<volatile int*>(base + OFF_MISC + 4);
+    volatile int* s_never = reinterpret_cast<volatile int*>(base + OFF_MISC + 12);  // stays 0
+    float* s_cmax = reinterpret_cast<float*>(base + OFF_MISC + 8);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k = A.k;
+    const bool want_grad = A.Cbar != nullptr;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < KM_STAGES; ++s) {
+            tc::mbar_init(&x_full[s], 1);
+            tc::mbar_init(&x_empty[s], 128);
+        }
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&t_full[b], 1);
+            tc::mbar_init(&t_empty[b], 128);
+        }
+        tc::mbar_init(c_bar, 1);
+        *s_abort = 0;
+        *s_never = 0;
+        tc::fence_mbar_init();
+        tc::tma_prefetch_desc(&tmX);
+        tc::tma_prefetch_desc(&tmC);
+    }
+    for (int q = threadIdx.x; q < k * KM_D; q += KM_THREADS) s_sum[q] = 0.f;
+    float cm = 0.f;
+    for (int c = threadIdx.x; c < k; c += KM_THREADS) {
+        float s = 0.f;
+        for (int j = 0; j < KM_D; ++j) {
+            const float v = __ldg(A.C + c * KM_D + j);
+            s = fmaf(v, v, s);
+        }
+        s_cn2[c] = s;
+        s_cnt[c] = 0.f;
+        cm = fmaxf(cm, s);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) cm = fmaxf(cm, __shfl_xor_sync(0xffffffffu, cm, off));
+    if (threadIdx.x == 0) *s_cmax = 0.f;
+    if (warp == 2) {
+        tc::tmem_alloc(s_tmem, 512);
+        tc::fence_before_sync();
+    }
+    __syncthreads();
+    if (lane == 0) atomicMax(reinterpret_cast<int*>(s_cmax), __float_as_int(cm));  // cm >= 0
+    tc::fence_after_sync();
+    __syncthreads();
+    const uint32_t tmem = *s_tmem;
+    const float cmax = sqrtf(*s_cmax);
+
+    int issued = 0, committed = 0;
+    if (warp == 0) {
+        if (lane == 0) {
+            tc::mbar_arrive_expect_tx(c_bar, (uint32_t)(k * KM_D * 4));
+            tc::tma_load_2d(sC, &tmC, 0, 0, c_bar);
+            int i = 0;
+            for (int64_t t = blockIdx.x; t < A.ntiles; t += gridDim.x, ++i) {
+                const int s = i % KM_STAGES;
+                if (i >= KM_STAGES && !tc::mbar_wait(&x_empty[s], ((i / KM_STAGES) - 1) & 1, s_abort)) {
+                    *s_abort = 1;
+                    break;
+                }
+                tc::mbar_arrive_expect_tx(&x_full[s], KM_X_BYTES);
+                tc::tma_load_2d(sX + s * (KM_X_BYTES / 4), &tmX, 0, (int)(t * KM_TILE), &x_full[s]);
+                issued = i + 1;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_tf32_m128((uint32_t)k);
+            const uint64_t bdesc = tc::desc_sw128_kmajor(tc::smem_u32(sC));
+            if (!tc::mbar_wait(c_bar, 0, s_abort)) *s_abort = 1;
+            int i = 0;
+            for (int64_t t = blockIdx.x; t < A.ntiles && !*s_abort; t += gridDim.x, ++i) {
+                const int s = i % KM_STAGES, b = i & 1;
+                if (!tc::mbar_wait(&x_full[s], (i / KM_STAGES) & 1, s_abort)) { *s_abort = 1; break; }
+                if (i >= 2 && !tc::mbar_wait(&t_empty[b], ((i >> 1) - 1) & 1, s_abort)) { *s_abort = 1; break; }
+                tc::fence_after_sync();
+                const uint64_t adesc = tc::desc_sw128_kmajor(tc::smem_u32(sX + s * (KM_X_BYTES / 4)));
+#pragma unroll
+                for (int kk = 0; kk < KM_D / 8; ++kk)  // K step of 8 TF32 = 32 bytes = +2 in the address field
+                    tc::mma_tf32(tmem + (uint32_t)(b * 256), adesc + 2 * kk, bdesc + 2 * kk, idesc, kk > 0);
+                tc::mma_commit(&t_full[b]);
+                committed = i + 1;
+            }
+        }
+    } else if (warp >= 4) {
+        const int r = (warp - 4) * 32 + lane;  // row of the tile == TMEM lane
+        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+        double loss_local = 0.0;
+        if (!tc::mbar_wait(c_bar, 0, s_abort)) *s_abort = 1;
+        int i = 0;
+        for (int64_t t = blockIdx.x; t < A.ntiles && !*s_abort; t += gridDim.x, ++i) {
+            const int s = i % KM_STAGES, b = i & 1;
+            if (!tc::mbar_wait(&t_full[b], (i >> 1) & 1, s_abort)) { *s_abort = 1; break; }
+            if (!tc::mbar_wait(&x_full[s], (i / KM_STAGES) & 1, s_abort)) { *s_abort = 1; break; }
+            tc::fence_after_sync();
+            const float* xt = sX + s * (KM_X_BYTES / 4);
+            const int64_t row = t * KM_TILE + r;
+            const bool valid = row < A.N;
+            float x[32];
+            sw_row(xt, r, x);
+            float xn2 = 0.f;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) xn2 = fmaf(x[j], x[j], xn2);
+            const float xn = sqrtf(xn2);
+            // |v~_k - v_k| <= 2 |S~ - S| + rounding <= 2^-8 |x| |c_k| (TF32 keeps 10
+            // mantissa bits of each operand) plus FP32 terms; 2x margin
+            const float tol = 8.0e-3f * xn * cmax + 1.0e-5f * (cmax * cmax + xn * cmax) + 1e-20f;
+            const uint32_t tb = tmem + lane_base + (uint32_t)(b * 256);
+            float m1 = CUDART_INF_F;
+            for (int q = 0; q < k / 32; ++q) {
+                uint32_t v[32];
+                __syncwarp();
+                tc::tmem_ld32(tb + (uint32_t)(q * 32), v);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int c = 0; c < 32; ++c) m1 = fminf(m1, fmaf(-2.f, __uint_as_float(v[c]), s_cn2[q * 32 + c]));
+            }
+            const float thr = m1 + 2.f * tol;
+            int nc = 0;
+            for (int q = 0; q < k / 32; ++q) {
+                uint32_t v[32];
+                __syncwarp();
+                tc::tmem_ld32(tb + (uint32_t)(q * 32), v);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    if (fmaf(-2.f, __uint_as_float(v[c]), s_cn2[q * 32 + c]) <= thr) {
+                        if (nc < KM_MAXCAND) s_cand[r * KM_MAXCAND + nc] = q * 32 + c;
+                        ++nc;
+                    }
+                }
+            }
+            tc::fence_before_sync();
+            tc::mbar_arrive(&t_empty[b]);  // the accumulator may be overwritten now
+
+            // certify the argmin among the candidates (ascending k)
+            int best = 0;
+            double dist = 0.0;
+            if (nc == 1) {
+                best = s_cand[r * KM_MAXCAND];
+                dist = (double)exact_f32(xt, r, sC, best);
+            } else {
+                const int ncc = nc <= KM_MAXCAND ? nc : 0;  // 0: fall back to all k
+                float u32 = CUDART_INF_F;
+                for (int c = 0; c < ncc; ++c) {
+                    const float e = exact_f32(xt, r, sC, s_cand[r * KM_MAXCAND + c]);
+                    u32 = fminf(u32, e + 4.0e-6f * e + 1e-30f);
+                }
+                int n2 = 0, only = -1;
+                float only_e = 0.f;
+                for (int c = 0; c < ncc; ++c) {
+                    const int kc = s_cand[r * KM_MAXCAND + c];
+                    const float e = exact_f32(xt, r, sC, kc);
+                    if (e - 4.0e-6f * e <= u32) {
+                        ++n2;
+                        if (only < 0) { only = kc; only_e = e; }
+                    }
+                }
+                if (ncc > 0 && n2 == 1) {
+                    best = only;
+                    dist = (double)only_e;
+                } else {
+                    double bd = CUDART_INF;
+                    const int lim = ncc > 0 ? ncc : k;
+                    for (int c = 0; c < lim; ++c) {
+                        const int kc = ncc > 0 ? s_cand[r * KM_MAXCAND + c] : c;
+                        if (ncc > 0) {
+                            const float e = exact_f32(xt, r, sC, kc);
+                            if (!(e - 4.0e-6f * e <= u32)) continue;
+                        }
+                        const double d = exact_f64(xt, r, sC, kc);
+                        if (d < bd) { bd = d; best = kc; }
+                    }
+                    dist = bd;
+                }
+            }
+            if (valid) {
+                loss_local += dist;
+                if (A.argmin_out) A.argmin_out[row] = best;
+            }
+            if (want_grad) {
+                s_arg[r] = valid ? best : -1;
+                __syncwarp();
+                const int r0 = (warp - 4) * 32;
+                for (int rr = 0; rr < 32; ++rr) {
+                    const int kc = s_arg[r0 + rr];
+                    if (kc >= 0) {
+                        atomicAdd(&s_sum[kc * KM_D + lane], sw_elem(xt, r0 + rr, lane));
+                        if (lane == 0) atomicAdd(&s_cnt[kc], 1.f);
+                    }
+                }
+                __syncwarp();
+            }
+            tc::mbar_arrive(&x_empty[s]);  // the X stage may be refilled now
+        }
+        // loss: warp reduce, then one double atomic per warp
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) loss_local += __shfl_xor_sync(0xffffffffu, loss_local, off);
+        if (lane == 0) atomicAdd(A.loss_acc, loss_local);
+    }
+
+    // drain: no TMA copy or MMA may be in flight when the CTA leaves
+    if (warp == 0 && lane == 0) {
+        for (int j = std::max(0, issued - KM_STAGES); j < issued; ++j)
+            tc::mbar_wait(&x_full[j % KM_STAGES], (j / KM_STAGES) & 1, s_never, 1u << 20);
+        tc::mbar_wait(c_bar, 0, s_never, 1u << 20);
+    }
+    if (warp == 1 && lane == 0) {
+        for (int j = std::max(0, committed - 2); j < committed; ++j)
+            tc::mbar_wait(&t_full[j & 1], (j >> 1) & 1, s_never, 1u << 20);
+    }
+    __syncthreads();
+    if (*s_abort && threadIdx.x == 0) record_status(A.hdr, ADPAR_ERR_TIMEOUT);
+
+    if (want_grad) {
+        for (int q = threadIdx.x; q < k * KM_D; q += KM_THREADS)
+            if (s_sum[q] != 0.f) atomicAdd(&A.gsum[q], s_sum[q]);
+        for (int q = threadIdx.x; q < k; q += KM_THREADS)
+            if (s_cnt[q] != 0.f) atomicAdd(&A.gcnt[q], s_cnt[q]);
+    }
+    // the last CTA to finish writes the loss and Cbar
+    __shared__ bool s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&A.hdr->done[0], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        if (threadIdx.x == 0 && A.loss_out) *A.loss_out = (float)ld_cg(A.loss_acc);
+        if (want_grad) {
+            const float yb2 = 2.f * (A.ybar ? *A.ybar : 1.f);
+            for (int q = threadIdx.x; q < k * KM_D; q += KM_THREADS) {
+                const int kc = q / KM_D;
+                const float g = yb2 * (ld_cg(&A.gcnt[kc]) * __ldg(A.C + q) - ld_cg(&A.gsum[q]));
+                A.Cbar[q] = A.accumulate ? A.Cbar[q] + g : g;
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 2) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, 512);
+    }
+}
+
+// ------------------------------------------------------------ host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// rows x 32 FP32, row stride 128 bytes, box of box_rows rows, 128-byte swizzle
+bool make_map(CUtensorMap* m, const float* ptr, int64_t rows, uint32_t box_rows) {
+    EncodeTiledFn f = encode_fn();
+    if (!f) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)KM_D, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(KM_D * 4)};
+    cuuint32_t box[2] = {(cuuint32_t)KM_D, box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return f(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(ptr), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+constexpr int kMaxDev = 64;
+bool km_configured[kMaxDev] = {};
+
+}  // namespace
+
+size_t kmeans_workspace_size(int64_t k) {
+    if (k <= 0 || k > KM_KMAX) return (size_t)-1;
+    return sizeof(WsHeader) + 256 + round_up((size_t)k * KM_D * 4, 256) + round_up((size_t)k * 4, 256);
+}
+
+}  // namespace adpar
+
+extern "C" int adpar_kmeans_vjp(int64_t N, int d, int k, const float* X, const float* C, const float* ybar,
+                                float* loss_out, int32_t* argmin_out, float* Cbar, uint32_t flags, void* work,
+                                size_t work_bytes, void* stream) {
+    using namespace adpar;
+    if (N < 0 || d <= 0 || k <= 0) return ADPAR_ERR_INVALID;
+    if (d != KM_D || k > KM_KMAX || k % 32 != 0) return ADPAR_ERR_UNSUPPORTED;
+    if (N > 0 && (!X || !C)) return ADPAR_ERR_INVALID;
+    if (Cbar && !ybar) return ADPAR_ERR_INVALID;
+    if (flags & ~(uint32_t)ADPAR_ACCUMULATE) return ADPAR_ERR_UNSUPPORTED;
+    const void* ptrs[] = {X, C, Cbar, argmin_out};
+    for (const void* p : ptrs)
+        if (p && !aligned16(p)) return ADPAR_ERR_ALIGN;
+    const size_t need = kmeans_workspace_size(k);
+    if (!work || work_bytes < need || (reinterpret_cast<uintptr_t>(work) & 255u)) return ADPAR_ERR_WORKSPACE;
+    if (N >= (int64_t(1) << 31) - KM_TILE) return ADPAR_ERR_UNSUPPORTED;  // 32-bit TMA row coordinate
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return ADPAR_ERR_CUDA;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (!km_configured[dev]) {
+        if (cudaFuncSetAttribute(kmeans_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)KM_SMEM) !=
+            cudaSuccess)
+            return ADPAR_ERR_CUDA;
+        km_configured[dev] = true;
+    }
+    KmArgs A{};
+    A.N = N;
+    A.k = k;
+    A.X = X;
+    A.C = C;
+    A.ybar = ybar;
+    A.loss_out = loss_out;
+    A.argmin_out = argmin_out;
+    A.Cbar = Cbar;
+    A.accumulate = (flags & ADPAR_ACCUMULATE) ? 1 : 0;
+    A.ntiles = (N + KM_TILE - 1) / KM_TILE;
+    char* w = static_cast<char*>(work);
+    A.hdr = reinterpret_cast<WsHeader*>(w);
+    A.loss_acc = reinterpret_cast<double*>(w + sizeof(WsHeader));
+    A.gsum = reinterpret_cast<float*>(w + sizeof(WsHeader) + 256);
+    A.gcnt = reinterpret_cast<float*>(w + sizeof(WsHeader) + 256 + round_up((size_t)k * KM_D * 4, 256));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    km_init_kernel<<<8, 256, 0, s>>>(A);
+    if (N == 0) {
+        // empty sum: loss 0, Cbar = 2 ybar (0 * c - 0) = 0 (accumulate: unchanged)
+        km_empty_kernel<<<1, 256, 0, s>>>(loss_out, Cbar, k * KM_D, A.accumulate);
+        return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
+    }
+    CUtensorMap tmX, tmC;
+    if (!make_map(&tmX, X, N, KM_TILE) || !make_map(&tmC, C, k, (uint32_t)k)) return ADPAR_ERR_CUDA;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(A.ntiles, sms));
+    kmeans_kernel<<<grid, KM_THREADS, KM_SMEM, s>>>(tmX, tmC, A);
+    return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
+}

@@ -293,6 +293,35 @@ int adpar_kmeans_vjp(int64_t N, int d, int k, const float *X, const float *C, co
                      size_t work_bytes, void *stream);
 
 /* ------------------------------------------------------------------ */
+/* primal forward operators                                            */
+/* ------------------------------------------------------------------ */
+/* The forward operators on their own: the forward sweeps of Sec. 5 without
+ * any adjoint.  They serve the autograd forward pass and are the baseline
+ * of the AD overhead ratio (VJP time / primal time, Sec. 7).  Arguments,
+ * layouts and workspaces are those of the matching VJP entry point. */
+
+/* y = reduce (.) a; argidx_out (MIN/MAX) and aux_out (MUL) as for
+ * adpar_vjp_reduce.  y_out is required. */
+int adpar_reduce(adpar_opdesc desc, int64_t n, const void *a, void *y_out, int64_t *argidx_out,
+                 adpar_prod_aux *aux_out, void *work, size_t work_bytes, void *stream);
+
+/* hs = reduce_by_index (.) inds vals into hs_out [m] (required);
+ * argidx_out and bin_aux_out as for adpar_vjp_hist. */
+int adpar_hist(adpar_opdesc desc, int64_t n, int64_t m, const void *vals, const void *inds, int itype,
+               void *hs_out, int64_t *argidx_out, adpar_prod_aux *bin_aux_out, void *work,
+               size_t work_bytes, void *stream);
+
+/* ys = scatter ys is vs in place (ys_inout [n] holds xs on entry), saving
+ * the overwritten values xs_saved_out[j] = xs[is_j] first (nullable), the
+ * forward sweep of Sec. 5.3.  Out-of-range indices are skipped. */
+int adpar_scatter(int dtype, int64_t n, int64_t m, const void *is, int itype, const void *vs,
+                  void *ys_inout, void *xs_saved_out, void *stream);
+
+/* xs[j] = g(as[is_j, :], ws[j, :]) (0 for an index out of range). */
+int adpar_map_acc(int gfun, int dtype, int64_t nj, int64_t na, int width, const void *as, const void *is,
+                  int itype, const void *ws, void *xs_out, void *stream);
+
+/* ------------------------------------------------------------------ */
 /* scan VJP without any allocation                                     */
 /* ------------------------------------------------------------------ */
 /* The paper has no counterpart of this entry point; it serves callers

@@ -90,6 +90,10 @@ def _bind_optional(L):
                               _VP, _VP, _VP, C.c_uint32, _VP, C.c_size_t, _VP],
         "adpar_kmeans_vjp": [C.c_int64, C.c_int, C.c_int, _VP, _VP, _VP, _VP, _VP, _VP, C.c_uint32, _VP,
                              C.c_size_t, _VP],
+        "adpar_reduce": [OpDesc, C.c_int64, _VP, _VP, _VP, _VP, _VP, C.c_size_t, _VP],
+        "adpar_hist": [OpDesc, C.c_int64, C.c_int64, _VP, _VP, C.c_int, _VP, _VP, _VP, _VP, C.c_size_t, _VP],
+        "adpar_scatter": [C.c_int, C.c_int64, C.c_int64, _VP, C.c_int, _VP, _VP, _VP, _VP],
+        "adpar_map_acc": [C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int, _VP, _VP, C.c_int, _VP, _VP, _VP],
     }
     for name, argt in sigs.items():
         if hasattr(L, name):
@@ -398,3 +402,52 @@ def adpar_kmeans_vjp(X, C, ybar=None, want_grad=True, want_argmin=False, Cbar=No
     if want_argmin:
         out["argmin"] = arg
     return out
+
+
+def adpar_reduce(op, a, want_argidx=False, work=None, stream=None):
+    """Primal reduce (C: adpar_reduce).  Returns (y [1], argidx [1] or None)."""
+    opc = OPS[op] if isinstance(op, str) else int(op)
+    n = a.numel()
+    dt = _dtype_code(a)
+    y = torch.empty(1, dtype=a.dtype, device=a.device)
+    arg = torch.empty(1, dtype=torch.int64, device=a.device) if want_argidx else None
+    need = adpar_workspace_size(RULE_REDUCE, opc, dt, n)
+    if work is None or work.numel() < need:
+        work = workspace(need, a.device)
+    _check("adpar_reduce", lib().adpar_reduce(OpDesc(opc, dt, 1), n, _ptr(a), _ptr(y), _ptr(arg), None,
+                                              _ptr(work), work.numel(), _stream(stream)))
+    return y, arg
+
+
+def adpar_hist(op, vals, inds, m, want_argidx=False, work=None, stream=None):
+    """Primal reduce_by_index (C: adpar_hist).  Returns (hs [m], argidx [m] or None)."""
+    opc = OPS[op] if isinstance(op, str) else int(op)
+    n = inds.numel()
+    dt = _dtype_code(vals)
+    hs = torch.empty(m, dtype=vals.dtype, device=vals.device)
+    arg = torch.empty(m, dtype=torch.int64, device=vals.device) if want_argidx else None
+    need = adpar_workspace_size(RULE_HIST, opc, dt, n, m)
+    if work is None or work.numel() < need:
+        work = workspace(need, vals.device)
+    _check("adpar_hist", lib().adpar_hist(OpDesc(opc, dt, 1), n, m, _ptr(vals), _ptr(inds), _itype_code(inds),
+                                          _ptr(hs), _ptr(arg), None, _ptr(work), work.numel(), _stream(stream)))
+    return hs, arg
+
+
+def adpar_scatter(is_, vs, ys_inout, xs_saved=None, stream=None):
+    """Primal scatter in place (C: adpar_scatter).  Returns ys_inout."""
+    _check("adpar_scatter", lib().adpar_scatter(_dtype_code(vs), ys_inout.numel(), is_.numel(), _ptr(is_),
+                                                _itype_code(is_), _ptr(vs), _ptr(ys_inout), _ptr(xs_saved),
+                                                _stream(stream)))
+    return ys_inout
+
+
+def adpar_map_acc(g, as_, is_, ws=None, width=1, stream=None):
+    """Primal map with a free array (C: adpar_map_acc).  Returns xs [nj]."""
+    gc = GFUNS[g] if isinstance(g, str) else int(g)
+    nj = is_.numel()
+    xs = torch.empty(nj, dtype=as_.dtype, device=as_.device)
+    _check("adpar_map_acc", lib().adpar_map_acc(gc, _dtype_code(as_), nj, as_.numel() // width, width, _ptr(as_),
+                                                _ptr(is_), _itype_code(is_), _ptr(ws), _ptr(xs),
+                                                _stream(stream)))
+    return xs

@@ -1,0 +1,149 @@
+"""torch.autograd.Function wrappers of the adpar rules.
+
+Every forward runs the primal operator in the library's kernels and saves
+only its INPUTS; every backward re-executes the primal inside the VJP
+kernels (the redundant-execution policy of Sec. 4: no tape, no stored
+intermediate) and returns the adjoints the paper's rule gives.
+
+    scan(op, a, b=None)           inclusive scan; LINREC returns (A, B)
+    reduce(op, a)                 0-dim result
+    reduce_by_index(op, vals, inds, m)
+    scatter(xs, is_, vs)          out of place: xs is not modified
+    map_acc(g, as_, is_, ws=None, width=1)
+    kmeans_loss(X, C)             gradient with respect to C only
+"""
+import torch
+
+from . import adpar as A
+
+
+def _c(t):
+    return None if t is None else t.contiguous()
+
+
+class _Scan(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, op, a, b):
+        ya, yb, _ = A.adpar_scan(op, a, b=b)
+        ctx.op = op
+        ctx.save_for_backward(a, b)
+        return (ya, yb) if op == "linrec" else ya
+
+    @staticmethod
+    def backward(ctx, ga, gb=None):
+        a, b = ctx.saved_tensors
+        if ctx.op == "linrec":
+            ga = torch.zeros_like(a) if ga is None else ga
+            gb = torch.zeros_like(a) if gb is None else gb
+            abar, bbar, _ = A.adpar_vjp_scan("linrec", a, _c(ga), b=b, ybar_b=_c(gb))
+            return None, abar, bbar
+        abar, _, _ = A.adpar_vjp_scan(ctx.op, a, _c(ga))
+        return None, abar, None
+
+
+def scan(op, a, b=None):
+    """Inclusive scan with op in {add, mul, min, max, linrec} (Sec. 5.2)."""
+    return _Scan.apply(op, _c(a), _c(b))
+
+
+class _Reduce(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, op, a):
+        y, _ = A.adpar_reduce(op, a)
+        ctx.op = op
+        ctx.save_for_backward(a)
+        return y.reshape(())
+
+    @staticmethod
+    def backward(ctx, g):
+        (a,) = ctx.saved_tensors
+        out = A.adpar_vjp_reduce(ctx.op, a, g.reshape(1))
+        return None, out["abar"]
+
+
+def reduce(op, a):
+    """reduce with op in {add, mul, min, max} (Sec. 5.1)."""
+    return _Reduce.apply(op, _c(a))
+
+
+class _Hist(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, op, vals, inds, m):
+        hs, _ = A.adpar_hist(op, vals, inds, m)
+        ctx.op, ctx.m = op, m
+        ctx.save_for_backward(vals, inds)
+        return hs
+
+    @staticmethod
+    def backward(ctx, g):
+        vals, inds = ctx.saved_tensors
+        out = A.adpar_vjp_hist(ctx.op, inds, ctx.m, _c(g), vals=vals)
+        return None, out["valsbar"], None, None
+
+
+def reduce_by_index(op, vals, inds, m):
+    """reduce_by_index with op in {add, mul, min, max} (Sec. 5.1.2)."""
+    return _Hist.apply(op, _c(vals), _c(inds), int(m))
+
+
+class _Scatter(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, xs, is_, vs):
+        ys = xs.clone()  # the functional form consumes a copy of xs
+        A.adpar_scatter(is_, vs, ys)
+        ctx.save_for_backward(is_)
+        return ys
+
+    @staticmethod
+    def backward(ctx, g):
+        (is_,) = ctx.saved_tensors
+        xsbar = g.clone()  # becomes xs_bar in place
+        xsbar, vsbar = A.adpar_vjp_scatter(is_, xsbar)
+        return xsbar, None, vsbar
+
+
+def scatter(xs, is_, vs):
+    """ys = scatter xs is vs with duplicate-free is (Sec. 5.3)."""
+    return _Scatter.apply(_c(xs), _c(is_), _c(vs))
+
+
+class _MapAcc(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, g, as_, is_, ws, width):
+        xs = A.adpar_map_acc(g, as_, is_, ws=ws, width=width)
+        ctx.g, ctx.width = g, width
+        ctx.save_for_backward(as_, is_, ws)
+        return xs
+
+    @staticmethod
+    def backward(ctx, gx):
+        as_, is_, ws = ctx.saved_tensors
+        asbar, wsbar = A.adpar_vjp_map_acc(ctx.g, as_, is_, _c(gx), ws=ws, width=ctx.width,
+                                           want_wsbar=ws is not None)
+        return None, asbar, None, wsbar, None
+
+
+def map_acc(g, as_, is_, ws=None, width=1):
+    """xs[j] = g(as[is_j], ws_j) with g in {gather, scale, sqdist_row} (Sec. 5.4)."""
+    return _MapAcc.apply(g, _c(as_), _c(is_), _c(ws), int(width))
+
+
+class _KMeans(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, X, C):
+        out = A.adpar_kmeans_vjp(X, C, want_grad=False)
+        ctx.save_for_backward(X, C)
+        return out["loss"].reshape(())
+
+    @staticmethod
+    def backward(ctx, g):
+        X, C = ctx.saved_tensors
+        if ctx.needs_input_grad[0]:
+            raise NotImplementedError("kmeans_loss differentiates with respect to the centroids only")
+        out = A.adpar_kmeans_vjp(X, C, ybar=g.reshape(1).to(torch.float32))
+        return None, out["Cbar"]
+
+
+def kmeans_loss(X, C):
+    """sum_i min_k ||x_i - c_k||^2 (Sec. 7.3, squared distances); gradient in C."""
+    return _KMeans.apply(_c(X), _c(C))

@@ -70,6 +70,7 @@ struct HistArgs {
     int8_t* vsign;
     int accumulate;
     int logdomain;
+    int primal_only;  // forward operator only: valsbar is not touched
     WsHeader* hdr;
     unsigned long long* key;  // [m] extremum words (min/max), FP64 pass-1 keys
     unsigned long long* idx;  // [m] lowest index (FP64 min/max pass 2)
@@ -177,7 +178,7 @@ __global__ void __launch_bounds__(kHistBlock) hist_arg_f32_kernel(HistArgs A) {
     const I* inds = static_cast<const I*>(A.inds);
     const float* vals = static_cast<const float*>(A.vals);
     float* vb = static_cast<float*>(A.valsbar);
-    const bool fill = !A.accumulate;
+    const bool fill = !A.accumulate && !A.primal_only;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += stride) {
         const int64_t b = ld_index(inds, i);
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(kHistBlock) hist_arg_f64_key_kernel(HistArgs A
     const I* inds = static_cast<const I*>(A.inds);
     const double* vals = static_cast<const double*>(A.vals);
     double* vb = static_cast<double*>(A.valsbar);
-    const bool fill = !A.accumulate;
+    const bool fill = !A.accumulate && !A.primal_only;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += stride) {
         const int64_t b = ld_index(inds, i);
@@ -254,7 +255,7 @@ __global__ void hist_arg_finish_kernel(HistArgs A) {
                 val = (T)from_orderkey_f64(A.key[b]);
             }
         }
-        if (arg >= 0) vb[arg] = A.accumulate ? vb[arg] + hsbar[b] : hsbar[b];
+        if (arg >= 0 && !A.primal_only) vb[arg] = A.accumulate ? vb[arg] + hsbar[b] : hsbar[b];
         if (A.hs_out) static_cast<T*>(A.hs_out)[b] = val;
         if (A.argidx_out) A.argidx_out[b] = arg;
     }
@@ -464,6 +465,7 @@ int run_hist(HistArgs A, cudaStream_t s) {
             const size_t sh = (size_t)std::min<int64_t>(A.m, kHistSmemKeys) * sizeof(T);
             hist_add_primal_kernel<T, I><<<gridN, kHistBlock, sh, s>>>(A);
         }
+        if (A.primal_only) break;
         const int g = (int)std::max<int64_t>(1, std::min<int64_t>((A.n / 4 + kHistBlock - 1) / kHistBlock, (int64_t)sms * 8));
         hist_add_vjp_kernel<T, I><<<g, kHistBlock, 0, s>>>(A);
         break;
@@ -488,7 +490,7 @@ int run_hist(HistArgs A, cudaStream_t s) {
         const size_t sh = (size_t)std::min<int64_t>(A.m, kHistSmemProd) * 28;
         hist_prod_kernel<T, I><<<gridN, kHistBlock, sh, s>>>(A);
         if (A.hs_out || A.bin_aux) hist_prod_bins_kernel<T><<<gridM, 256, 0, s>>>(A);
-        hist_prod_vjp_kernel<T, I><<<gridN, kHistBlock, 0, s>>>(A);
+        if (!A.primal_only) hist_prod_vjp_kernel<T, I><<<gridN, kHistBlock, 0, s>>>(A);
         break;
     }
     default:
@@ -522,11 +524,12 @@ size_t hist_workspace_size(adpar_opdesc d, int64_t m) {
 
 }  // namespace adpar
 
-extern "C" int adpar_vjp_hist(adpar_opdesc d, int64_t n, int64_t m, const void* vals, const void* inds,
-                              int itype, const void* hsbar, void* valsbar, void* hs_out,
-                              int64_t* argidx_out, adpar_prod_aux* bin_aux_out, int8_t* valsbar_sign,
-                              uint32_t flags, void* work, size_t work_bytes, void* stream) {
-    using namespace adpar;
+namespace adpar {
+namespace {
+int hist_impl(adpar_opdesc d, int64_t n, int64_t m, const void* vals, const void* inds, int itype,
+              const void* hsbar, void* valsbar, void* hs_out, int64_t* argidx_out, adpar_prod_aux* bin_aux_out,
+              int8_t* valsbar_sign, uint32_t flags, void* work, size_t work_bytes, void* stream,
+              bool primal_only) {
     if (n < 0 || m < 0 || d.width != 1) return ADPAR_ERR_INVALID;
     if (d.op != ADPAR_OP_ADD && d.op != ADPAR_OP_MUL && d.op != ADPAR_OP_MIN && d.op != ADPAR_OP_MAX)
         return ADPAR_ERR_INVALID;
@@ -538,8 +541,9 @@ extern "C" int adpar_vjp_hist(adpar_opdesc d, int64_t n, int64_t m, const void* 
     if (valsbar_sign && !logd) return ADPAR_ERR_INVALID;
     if ((d.op == ADPAR_OP_MIN || d.op == ADPAR_OP_MAX) && d.dtype == ADPAR_F32 && n > 0xffffffffLL)
         return ADPAR_ERR_UNSUPPORTED;  // the packed word holds a 32-bit index
-    if (n > 0 && (!inds || !valsbar)) return ADPAR_ERR_INVALID;
-    if (n > 0 && m > 0 && !hsbar) return ADPAR_ERR_INVALID;
+    if (n > 0 && (!inds || (!valsbar && !primal_only))) return ADPAR_ERR_INVALID;
+    if (n > 0 && m > 0 && !hsbar && !primal_only) return ADPAR_ERR_INVALID;
+    if (primal_only && m > 0 && !hs_out) return ADPAR_ERR_INVALID;
     if (n > 0 && !vals && (d.op != ADPAR_OP_ADD || hs_out)) return ADPAR_ERR_INVALID;
     const void* ptrs[] = {vals, inds, hsbar, valsbar, hs_out};
     for (const void* p : ptrs)
@@ -561,6 +565,7 @@ extern "C" int adpar_vjp_hist(adpar_opdesc d, int64_t n, int64_t m, const void* 
     A.vsign = valsbar_sign;
     A.accumulate = (flags & ADPAR_ACCUMULATE) ? 1 : 0;
     A.logdomain = logd ? 1 : 0;
+    A.primal_only = primal_only ? 1 : 0;
     char* w = static_cast<char*>(work);
     A.hdr = reinterpret_cast<WsHeader*>(w);
     if (L.off_key) A.key = reinterpret_cast<unsigned long long*>(w + L.off_key);
@@ -584,4 +589,21 @@ extern "C" int adpar_vjp_hist(adpar_opdesc d, int64_t n, int64_t m, const void* 
     if (d.dtype == ADPAR_F32)
         return itype == ADPAR_I32 ? run_hist<float, int32_t>(A, s) : run_hist<float, int64_t>(A, s);
     return itype == ADPAR_I32 ? run_hist<double, int32_t>(A, s) : run_hist<double, int64_t>(A, s);
+}
+}  // namespace
+}  // namespace adpar
+
+extern "C" int adpar_vjp_hist(adpar_opdesc d, int64_t n, int64_t m, const void* vals, const void* inds,
+                              int itype, const void* hsbar, void* valsbar, void* hs_out,
+                              int64_t* argidx_out, adpar_prod_aux* bin_aux_out, int8_t* valsbar_sign,
+                              uint32_t flags, void* work, size_t work_bytes, void* stream) {
+    return adpar::hist_impl(d, n, m, vals, inds, itype, hsbar, valsbar, hs_out, argidx_out, bin_aux_out,
+                            valsbar_sign, flags, work, work_bytes, stream, false);
+}
+
+extern "C" int adpar_hist(adpar_opdesc d, int64_t n, int64_t m, const void* vals, const void* inds, int itype,
+                          void* hs_out, int64_t* argidx_out, adpar_prod_aux* bin_aux_out, void* work,
+                          size_t work_bytes, void* stream) {
+    return adpar::hist_impl(d, n, m, vals, inds, itype, nullptr, nullptr, hs_out, argidx_out, bin_aux_out,
+                            nullptr, 0u, work, work_bytes, stream, true);
 }

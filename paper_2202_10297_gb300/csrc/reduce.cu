@@ -52,6 +52,7 @@ struct ReduceArgs {
     int8_t* abar_sign;
     int accumulate;
     int logdomain;
+    int primal_only;  // forward operator only: no adjoint is written
     WsHeader* hdr;
     void* partials;  // [gridDim.x] states
     void* final_state;
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(kRedBlock) reduce_add_kernel(ReduceArgs A) {
     __shared__ T s_warp[kRedBlock / 32];
     const T* a = static_cast<const T*>(A.a);
     T* abar = static_cast<T*>(A.abar);
-    const T yb = *static_cast<const T*>(A.ybar);
+    const T yb = A.primal_only ? T(0) : *static_cast<const T*>(A.ybar);
     constexpr int V = Vec16<T>::N;
     const int64_t nvec = A.n / V;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -116,6 +117,7 @@ __global__ void __launch_bounds__(kRedBlock) reduce_add_kernel(ReduceArgs A) {
 #pragma unroll
             for (int j = 0; j < V; ++j) acc += x.v[j];
         }
+        if (A.primal_only) continue;
         Vec16<T> o;
         if (A.accumulate) {
             o = ld_vec(abar + v * V);
@@ -130,7 +132,7 @@ __global__ void __launch_bounds__(kRedBlock) reduce_add_kernel(ReduceArgs A) {
     if (blockIdx.x == 0 && threadIdx.x < A.n - nvec * V) {
         const int64_t i = nvec * V + threadIdx.x;
         if (want_y) acc += a[i];
-        abar[i] = A.accumulate ? abar[i] + yb : yb;
+        if (!A.primal_only) abar[i] = A.accumulate ? abar[i] + yb : yb;
     }
     if (!want_y) return;
     auto add = [](T x, T y) { return x + y; };
@@ -157,7 +159,7 @@ __global__ void __launch_bounds__(kRedBlock) reduce_arg_kernel(ReduceArgs A) {
     constexpr int V = Vec16<T>::N;
     const int64_t nvec = A.n / V;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const bool fill = !A.accumulate;
+    const bool fill = !A.accumulate && !A.primal_only;
     S st{MAX ? -pos_inf<T>() : pos_inf<T>(), INT64_MAX};
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nvec; v += stride) {
         Vec16<T> x = ld_vec_stream(a + v * V);
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(kRedBlock) reduce_arg_kernel(ReduceArgs A) {
         const bool any = A.n > 0;
         if (A.y_out) *static_cast<T*>(A.y_out) = tot.v;
         if (A.argidx_out) *A.argidx_out = any ? tot.i : -1;
-        if (any) {
+        if (any && !A.primal_only) {
             const T yb = *static_cast<const T*>(A.ybar);
             abar[tot.i] = A.accumulate ? abar[tot.i] + yb : yb;
         }
@@ -337,6 +339,7 @@ int run_reduce(ReduceArgs A, int op, cudaStream_t s) {
         break;
     case ADPAR_OP_MUL: {
         reduce_prod_kernel<T><<<grid, kRedBlock, 0, s>>>(A);
+        if (A.primal_only) break;
         const int g2 = (int)std::max<int64_t>(1, std::min<int64_t>((A.n + 1023) / 1024, 4 * 152));
         prod_adjoint_kernel<T><<<g2, kRedBlock, 0, s>>>(A);
         break;
@@ -395,6 +398,35 @@ extern "C" int adpar_vjp_reduce(adpar_opdesc d, int64_t n, const void* a, const 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // the "last block" counter must start at zero in a workspace of unknown
     // contents
+    header_init_kernel<<<1, 64, 0, s>>>(A.hdr);
+    if (d.dtype == ADPAR_F32) return run_reduce<float>(A, d.op, s);
+    return run_reduce<double>(A, d.op, s);
+}
+
+extern "C" int adpar_reduce(adpar_opdesc d, int64_t n, const void* a, void* y_out, int64_t* argidx_out,
+                            adpar_prod_aux* aux_out, void* work, size_t work_bytes, void* stream) {
+    using namespace adpar;
+    if (n < 0 || d.width != 1) return ADPAR_ERR_INVALID;
+    if (d.op != ADPAR_OP_ADD && d.op != ADPAR_OP_MUL && d.op != ADPAR_OP_MIN && d.op != ADPAR_OP_MAX)
+        return ADPAR_ERR_INVALID;
+    if (d.dtype != ADPAR_F32 && d.dtype != ADPAR_F64) return ADPAR_ERR_INVALID;
+    if (!y_out || (n > 0 && !a)) return ADPAR_ERR_INVALID;
+    if (a && !aligned16(a)) return ADPAR_ERR_ALIGN;
+    const size_t need = reduce_workspace_size(d);
+    if (!work || work_bytes < need || (reinterpret_cast<uintptr_t>(work) & 255u)) return ADPAR_ERR_WORKSPACE;
+    ReduceArgs A{};
+    A.op = d.op;
+    A.n = n;
+    A.a = a;
+    A.y_out = y_out;
+    A.argidx_out = argidx_out;
+    A.aux_out = aux_out;
+    A.primal_only = 1;
+    char* w = static_cast<char*>(work);
+    A.hdr = reinterpret_cast<WsHeader*>(w);
+    A.partials = w + sizeof(WsHeader);
+    A.final_state = w + sizeof(WsHeader) + round_up(kRedMaxBlocks * state_bytes(d.op, d.dtype), 256);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
     header_init_kernel<<<1, 64, 0, s>>>(A.hdr);
     if (d.dtype == ADPAR_F32) return run_reduce<float>(A, d.op, s);
     return run_reduce<double>(A, d.op, s);

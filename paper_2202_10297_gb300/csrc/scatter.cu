@@ -120,6 +120,47 @@ __global__ void __launch_bounds__(kBlk) map_acc_kernel(MapAccArgs<T> A) {
     }
 }
 
+// primal of scatter (Sec. 5.3's forward sweep): xs_saved[j] = ys[is_j]
+// (optional), then ys[is_j] = vs[j], in place
+template <class T, class I>
+__global__ void __launch_bounds__(kBlk) scatter_fwd_kernel(int64_t n, int64_t m, const I* is, const T* vs, T* ys,
+                                                          T* xs_saved) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += stride) {
+        const int64_t k = ldi(is, j);
+        if (k < 0 || k >= n) {
+            if (xs_saved) xs_saved[j] = T(0);
+            continue;
+        }
+        if (xs_saved) xs_saved[j] = ys[k];
+        ys[k] = __ldcs(vs + j);
+    }
+}
+
+// primal of map: xs[j] = g(as[is_j, :], ws[j, :]) (0 for an index out of range)
+template <class T, class I>
+__global__ void __launch_bounds__(kBlk) map_fwd_kernel(int g, int64_t nj, int64_t na, int width, const T* as,
+                                                      const I* is, const T* ws, T* xs) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nj; j += stride) {
+        const int64_t i = ldi(is, j);
+        T x = T(0);
+        if (i >= 0 && i < na) {
+            if (g == ADPAR_G_GATHER) {
+                x = __ldg(as + i);
+            } else if (g == ADPAR_G_SCALE) {
+                x = __ldg(as + i) * ws[j];
+            } else {
+                for (int k = 0; k < width; ++k) {
+                    const T d = ws[j * width + k] - __ldg(as + i * width + k);
+                    x += d * d;
+                }
+            }
+        }
+        xs[j] = x;
+    }
+}
+
 template <class T>
 __global__ void zero_kernel(T* p, int64_t n) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -217,5 +258,59 @@ extern "C" int adpar_vjp_map_acc(int gfun, int dtype, int64_t nj, int64_t na, in
         if (itype == ADPAR_I32) ADPAR_MAPACC(double, int32_t); else ADPAR_MAPACC(double, int64_t);
     }
 #undef ADPAR_MAPACC
+    return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
+}
+
+extern "C" int adpar_scatter(int dtype, int64_t n, int64_t m, const void* is, int itype, const void* vs,
+                             void* ys_inout, void* xs_saved_out, void* stream) {
+    using namespace adpar;
+    if (n < 0 || m < 0) return ADPAR_ERR_INVALID;
+    if (dtype != ADPAR_F32 && dtype != ADPAR_F64) return ADPAR_ERR_INVALID;
+    if (itype != ADPAR_I32 && itype != ADPAR_I64) return ADPAR_ERR_INVALID;
+    if (m > 0 && (!is || !vs || !ys_inout)) return ADPAR_ERR_INVALID;
+    const void* ptrs[] = {is, vs, ys_inout, xs_saved_out};
+    for (const void* p : ptrs)
+        if (p && !aligned16(p)) return ADPAR_ERR_ALIGN;
+    if (m == 0) return ADPAR_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((m + kBlk - 1) / kBlk, (int64_t)sm_count() * 8));
+#define ADPAR_SCAT_FWD(T, I)                                                                                   \
+    scatter_fwd_kernel<T, I><<<grid, kBlk, 0, s>>>(n, m, static_cast<const I*>(is), static_cast<const T*>(vs), \
+                                                   static_cast<T*>(ys_inout), static_cast<T*>(xs_saved_out))
+    if (dtype == ADPAR_F32) {
+        if (itype == ADPAR_I32) ADPAR_SCAT_FWD(float, int32_t); else ADPAR_SCAT_FWD(float, int64_t);
+    } else {
+        if (itype == ADPAR_I32) ADPAR_SCAT_FWD(double, int32_t); else ADPAR_SCAT_FWD(double, int64_t);
+    }
+#undef ADPAR_SCAT_FWD
+    return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
+}
+
+extern "C" int adpar_map_acc(int gfun, int dtype, int64_t nj, int64_t na, int width, const void* as,
+                             const void* is, int itype, const void* ws, void* xs_out, void* stream) {
+    using namespace adpar;
+    if (nj < 0 || na < 0 || width < 1) return ADPAR_ERR_INVALID;
+    if (gfun != ADPAR_G_GATHER && gfun != ADPAR_G_SCALE && gfun != ADPAR_G_SQDIST_ROW) return ADPAR_ERR_INVALID;
+    if (gfun != ADPAR_G_SQDIST_ROW && width != 1) return ADPAR_ERR_INVALID;
+    if (dtype != ADPAR_F32 && dtype != ADPAR_F64) return ADPAR_ERR_INVALID;
+    if (itype != ADPAR_I32 && itype != ADPAR_I64) return ADPAR_ERR_INVALID;
+    if (nj > 0 && (!is || !xs_out || !as)) return ADPAR_ERR_INVALID;
+    if (gfun != ADPAR_G_GATHER && nj > 0 && !ws) return ADPAR_ERR_INVALID;
+    const void* ptrs[] = {as, is, ws, xs_out};
+    for (const void* p : ptrs)
+        if (p && !aligned16(p)) return ADPAR_ERR_ALIGN;
+    if (nj == 0) return ADPAR_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((nj + kBlk - 1) / kBlk, (int64_t)sm_count() * 8));
+#define ADPAR_MAP_FWD(T, I)                                                                                    \
+    map_fwd_kernel<T, I><<<grid, kBlk, 0, s>>>(gfun, nj, na, width, static_cast<const T*>(as),                  \
+                                               static_cast<const I*>(is), static_cast<const T*>(ws),            \
+                                               static_cast<T*>(xs_out))
+    if (dtype == ADPAR_F32) {
+        if (itype == ADPAR_I32) ADPAR_MAP_FWD(float, int32_t); else ADPAR_MAP_FWD(float, int64_t);
+    } else {
+        if (itype == ADPAR_I32) ADPAR_MAP_FWD(double, int32_t); else ADPAR_MAP_FWD(double, int64_t);
+    }
+#undef ADPAR_MAP_FWD
     return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
 }

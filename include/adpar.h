@@ -293,6 +293,61 @@ int adpar_kmeans_vjp(int64_t N, int d, int k, const float *X, const float *C, co
                      size_t work_bytes, void *stream);
 
 /* ------------------------------------------------------------------ */
+/* batched VJPs: many instances in one persistent launch               */
+/* ------------------------------------------------------------------ */
+/* Not in the paper (a serving form of its rules).  Each segment is an
+ * independent instance of: the product-reduce VJP of Sec. 5.1.1 over x
+ * (cotangent ybar_prod), and the linear-recurrence scan VJP of Sec. 5.2
+ * over (a, b) with cotangents (ybar_a, ybar_b).  All pointers are device
+ * pointers of the segment's dtype; outputs are overwritten. */
+typedef struct {
+    const void *x;        /* [len] product-reduce input               */
+    void *xbar;           /* [len] its adjoint                        */
+    const void *a;        /* [len] linear-recurrence inputs           */
+    const void *b;
+    const void *ybar_a;   /* [len] cotangents of the scan outputs     */
+    const void *ybar_b;
+    void *abar;           /* [len] adjoints of a and b                */
+    void *bbar;
+    adpar_prod_aux *aux;  /* nullable: the recomputed product sweep   */
+    double ybar_prod;     /* cotangent of the product                 */
+    int64_t len;
+    int32_t dtype;        /* ADPAR_F32 or ADPAR_F64                   */
+    int32_t reserved;
+} adpar_batch_segment;
+
+/* Launch shape chosen by the autotuner: variant = compiled tile shapes
+ * (0: 2048-element scan tiles, 8192-element product tiles; 1: 4096 /
+ * 16384; 2: 1024 / 4096), ctas_per_sm = persistent blocks per SM (1..8),
+ * order = 0 (as given) or 1 (longest segments first). */
+typedef struct {
+    int32_t variant;
+    int32_t ctas_per_sm;
+    int32_t order;
+    int32_t reserved;
+} adpar_batch_config;
+
+/* Bytes of the plan image for nseg segments. */
+size_t adpar_batch_plan_bytes(int nseg);
+
+/* Host-side planning: writes the plan image (segments in scheduling order,
+ * work-item numbering, per-segment state offsets) into plan_host (host
+ * memory, adpar_batch_plan_bytes(nseg) bytes) and the workspace size the
+ * launch needs into *work_bytes_out.  segs is host memory; cfg may be NULL
+ * (variant 0, 2 blocks per SM, longest first).  The caller copies the plan
+ * image to device memory once and keeps it (and every segment buffer)
+ * alive while the batch may run. */
+int adpar_batch_plan(const adpar_batch_segment *segs, int nseg, const adpar_batch_config *cfg,
+                     void *plan_host, size_t plan_bytes, size_t *work_bytes_out);
+
+/* One launch of the batch: a zero-fill of the workspace state and one
+ * persistent kernel.  plan_host and plan_dev are the same image (host copy
+ * for the launch shape, device copy for the kernel).  Only kernel launches
+ * are enqueued, so the call can be captured in a CUDA graph and replayed. */
+int adpar_vjp_batch(const void *plan_host, const void *plan_dev, void *work, size_t work_bytes,
+                    void *stream);
+
+/* ------------------------------------------------------------------ */
 /* primal forward operators                                            */
 /* ------------------------------------------------------------------ */
 /* The forward operators on their own: the forward sweeps of Sec. 5 without

@@ -1,0 +1,385 @@
+// Batched VJPs: many independent instances of uneven length, each a
+// product-reduce VJP (Sec. 5.1.1) followed by a linear-recurrence scan VJP
+// (Sec. 5.2), in ONE persistent launch that a CUDA graph can capture.
+//
+// Work items.  Segment s of length L has R = ceil(L / RT) reduce tiles and
+// S = ceil(L / ST) scan tiles, and contributes, in this order,
+//   R product-reduce tiles, S primal-scan tiles (left to right),
+//   S adjoint-scan tiles (right to left), R product-map tiles.
+// Items are numbered segment after segment and handed out by one global
+// atomic ticket.  An item only ever waits on items with smaller numbers of
+// its own segment (the look-back predecessors, the primal carries, the
+// finished product), which were handed out earlier to blocks that are
+// running, so the schedule cannot deadlock, and every wait is bounded.
+// Small segments are one tile of each kind; no look-back happens there.
+//
+// The scan tiles are the very device functions of the standalone scan
+// kernels (scan_tiles.cuh); the product tiles re-run the forward sweep as
+// a (zero count, lowest zero, scaled product) reduction per tile whose last
+// tile to finish combines the partials and raises the segment's flag.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "prod.cuh"
+#include "scan_tiles.cuh"
+
+namespace adpar {
+namespace {
+
+struct BatchPlanHeader {
+    int64_t nseg;
+    int64_t total_items;
+    int64_t ws_bytes;
+    int64_t seg_off;   // byte offset of the segment array in the plan
+    int64_t meta_off;  // byte offset of the SegMeta array in the plan
+    int32_t variant;
+    int32_t order;
+    int32_t ctas_per_sm;
+    int32_t reserved;
+};
+
+struct SegMeta {
+    int64_t item_base;  // first item number of the segment
+    int64_t state_off;  // byte offset of its state in the workspace
+    int32_t red_tiles;
+    int32_t scan_tiles;
+};
+
+// tile shapes of the compiled variants: scan tile f32 = KF*256*EF,
+// f64 = KD*256*ED; reduce/map tile RT elements
+struct VariantShape {
+    int kf, ef, kd, ed, rt;
+};
+constexpr VariantShape kVariants[] = {
+    {2, 4, 1, 8, 8192},    // 0: 2048-element scan tiles
+    {4, 4, 2, 8, 16384},   // 1: 4096-element scan tiles
+    {1, 4, 1, 4, 4096},    // 2: 1024-element scan tiles (many short segments)
+};
+constexpr int kNumVariants = 3;
+
+// per-segment state layout (bytes from state_off)
+struct StateLayout {
+    int64_t partials, counter, final_state, p_agg, p_incl, r_agg, r_incl, total;
+};
+
+__host__ __device__ inline int64_t al16(int64_t x) { return (x + 15) & ~int64_t(15); }
+
+__host__ __device__ inline StateLayout state_layout(int dtype, int red, int scan) {
+    const int wp = dtype == ADPAR_F64 ? 4 : 2;  // 64-bit words of a primal (A, B) state
+    const int wr = dtype == ADPAR_F64 ? 6 : 3;  // of a lin_o (dA, dB, c) state
+    StateLayout L;
+    int64_t o = 0;
+    L.partials = o; o = al16(o + (int64_t)red * (int64_t)sizeof(ProdState));
+    L.counter = o; o = al16(o + 16);
+    L.final_state = o; o = al16(o + (int64_t)sizeof(ProdState));
+    L.p_agg = o; o = al16(o + (int64_t)scan * wp * 8);
+    L.p_incl = o; o = al16(o + (int64_t)scan * wp * 8);
+    L.r_agg = o; o = al16(o + (int64_t)scan * wr * 8);
+    L.r_incl = o; o = al16(o + (int64_t)scan * wr * 8);
+    L.total = o;
+    return L;
+}
+
+template <class S>
+__device__ __forceinline__ S block_reduce_256(S v, S (*comb)(const S&, const S&), S* s_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = comb(v, shfl_down_s(v, off));
+    if (lane == 0) s_warp[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = s_warp[lane < 8 ? lane : 0];
+#pragma unroll
+        for (int off = 4; off > 0; off >>= 1) {
+            S o = shfl_down_s(v, off);
+            if (lane + off < 8) v = comb(v, o);
+        }
+    }
+    return v;  // valid in thread 0
+}
+
+__device__ ProdState prod_comb(const ProdState& x, const ProdState& y) { return ProdState::comb(x, y); }
+
+// product reduce tile r of a segment
+template <class T>
+__device__ void prod_reduce_tile(const adpar_batch_segment& sg, char* st, const StateLayout& L, int red, int r,
+                                 int RT, WsHeader* hdr) {
+    __shared__ ProdState s_warp[8];
+    __shared__ int s_last;
+    const T* x = static_cast<const T*>(sg.x);
+    const int64_t lo = (int64_t)r * RT, hi = std::min<int64_t>(sg.len, lo + RT);
+    ProdState ps = ProdState::id();
+    constexpr int V = Vec16<T>::N;
+    for (int64_t i = lo + threadIdx.x * V; i < hi; i += 256 * V) {
+        if (i + V <= hi) {
+            Vec16<T> v = ld_vec(x + i);
+#pragma unroll
+            for (int j = 0; j < V; ++j) ps.push((double)v.v[j], i + j);
+        } else {
+            for (int64_t j = i; j < hi; ++j) ps.push((double)x[j], j);
+        }
+    }
+    ProdState bs = block_reduce_256<ProdState>(ps, prod_comb, s_warp);
+    ProdState* partials = reinterpret_cast<ProdState*>(st + L.partials);
+    unsigned int* counter = reinterpret_cast<unsigned int*>(st + L.counter);
+    if (threadIdx.x == 0) {
+        partials[r] = bs;
+        __threadfence();
+        s_last = atomicAdd(counter, 1u) == (unsigned)(red - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    ProdState tot = ProdState::id();
+    for (int q = threadIdx.x; q < red; q += 256) tot = ProdState::comb(tot, ld_cg(partials + q));
+    __syncthreads();
+    tot = block_reduce_256<ProdState>(tot, prod_comb, s_warp);
+    if (threadIdx.x == 0) {
+        *reinterpret_cast<ProdState*>(st + L.final_state) = tot;
+        if (sg.aux) {
+            adpar_prod_aux a;
+            a.nzero = tot.nz;
+            a.first_zero = tot.nz > 0 ? tot.first : -1;
+            a.exp2 = tot.e;
+            a.mant = tot.m;
+            a.log_abs_nz = log(fabs(tot.m)) + (double)tot.e * 0.69314718055994530942;
+            a.sign = tot.m > 0 ? 1 : -1;
+            a.reserved = 0;
+            *sg.aux = a;
+        }
+        __threadfence();
+        st_release_u32(counter + 1, 1u);  // the segment's product is final
+    }
+}
+
+// product map tile r: the three cases of Sec. 5.1.1
+template <class T>
+__device__ void prod_map_tile(const adpar_batch_segment& sg, char* st, const StateLayout& L, int r, int RT,
+                              WsHeader* hdr) {
+    __shared__ ProdState s_fin;
+    unsigned int* counter = reinterpret_cast<unsigned int*>(st + L.counter);
+    if (threadIdx.x == 0) {
+        if (wait_flag(counter + 1, hdr) != 0u) s_fin = ld_cg(reinterpret_cast<const ProdState*>(st + L.final_state));
+        else s_fin = ProdState::id();
+    }
+    __syncthreads();
+    const ProdState f = s_fin;
+    const T* x = static_cast<const T*>(sg.x);
+    T* xb = static_cast<T*>(sg.xbar);
+    const int64_t lo = (int64_t)r * RT, hi = std::min<int64_t>(sg.len, lo + RT);
+    const double yb = sg.ybar_prod;
+    double ym = 0.0;
+    int64_t ye = 0;
+    if (yb != 0.0) split_pow2(yb, ym, ye);
+    for (int64_t i = lo + threadIdx.x; i < hi; i += 256) {
+        double c = 0.0;
+        if (yb != 0.0) {
+            if (f.nz == 0) {
+                double mi;
+                int64_t ei;
+                split_pow2((double)x[i], mi, ei);
+                if constexpr (sizeof(T) == 4) {
+                    const float q = (float)(f.m * ym) / (float)mi;  // FP32 output: FP32 division
+                    c = ldexp_clamped((double)q, f.e + ye - ei);
+                } else {
+                    c = ldexp_clamped(f.m * ym / mi, f.e + ye - ei);
+                }
+            } else if (f.nz == 1 && i == f.first) {
+                c = ldexp_clamped(f.m * ym, f.e + ye);
+            }
+        }
+        xb[i] = (T)c;
+    }
+}
+
+template <class T, int K, int E>
+__device__ void linrec_tile(const adpar_batch_segment& sg, char* st, const StateLayout& L, int scan_tiles,
+                            int64_t t, bool adjoint, WsHeader* hdr) {
+    ScanArgs A{};
+    A.n = sg.len;
+    A.a = sg.a;
+    A.b = sg.b;
+    A.ya = sg.ybar_a;
+    A.yb = sg.ybar_b;
+    A.abar = sg.abar;
+    A.bbar = sg.bbar;
+    A.tiles = scan_tiles;
+    A.hdr = hdr;
+    A.carry = nullptr;  // carries come from the primal look-back slots
+    A.lbP_agg = reinterpret_cast<unsigned long long*>(st + L.p_agg);
+    A.lbP_incl = reinterpret_cast<unsigned long long*>(st + L.p_incl);
+    A.lbR_agg = reinterpret_cast<unsigned long long*>(st + L.r_agg);
+    A.lbR_incl = reinterpret_cast<unsigned long long*>(st + L.r_incl);
+    if (adjoint) scan_adjoint_tile<OpLinrec<T>, T, K, E, false>(A, t);
+    else scan_primal_tile<OpLinrec<T>, T, K, E>(A, t);
+}
+
+__global__ void batch_init_kernel(char* ws, int64_t bytes) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n16 = bytes / 16;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n16; i += stride)
+        reinterpret_cast<uint4*>(ws)[i] = make_uint4(0, 0, 0, 0);
+}
+
+template <int KF, int EF, int KD, int ED, int RT>
+__global__ void __launch_bounds__(256) batch_kernel(const char* plan, char* ws) {
+    const BatchPlanHeader* H = reinterpret_cast<const BatchPlanHeader*>(plan);
+    const adpar_batch_segment* segs = reinterpret_cast<const adpar_batch_segment*>(plan + H->seg_off);
+    const SegMeta* meta = reinterpret_cast<const SegMeta*>(plan + H->meta_off);
+    WsHeader* hdr = reinterpret_cast<WsHeader*>(ws);
+    const int64_t nseg = H->nseg, total = H->total_items;
+    __shared__ uint32_t s_item;
+    __shared__ int s_stop;
+    while (true) {
+        __syncthreads();  // consecutive items reuse the static shared memory
+        if (threadIdx.x == 0) {
+            s_item = atomicAdd(&hdr->ticket[0], 1u);
+            s_stop = ((int64_t)s_item >= total) || gave_up(hdr);
+        }
+        __syncthreads();
+        if (s_stop) break;
+        const int64_t q = s_item;
+        // segment of item q: last s with item_base <= q
+        int64_t lo = 0, hi = nseg - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (meta[mid].item_base <= q) lo = mid;
+            else hi = mid - 1;
+        }
+        const SegMeta m = meta[lo];
+        const adpar_batch_segment sg = segs[lo];
+        const StateLayout L = state_layout(sg.dtype, m.red_tiles, m.scan_tiles);
+        char* st = ws + m.state_off;
+        int64_t j = q - m.item_base;
+        const bool f64 = sg.dtype == ADPAR_F64;
+        if (j < m.red_tiles) {
+            if (f64) prod_reduce_tile<double>(sg, st, L, m.red_tiles, (int)j, RT, hdr);
+            else prod_reduce_tile<float>(sg, st, L, m.red_tiles, (int)j, RT, hdr);
+            continue;
+        }
+        j -= m.red_tiles;
+        if (j < m.scan_tiles) {
+            if (f64) linrec_tile<double, KD, ED>(sg, st, L, m.scan_tiles, j, false, hdr);
+            else linrec_tile<float, KF, EF>(sg, st, L, m.scan_tiles, j, false, hdr);
+            continue;
+        }
+        j -= m.scan_tiles;
+        if (j < m.scan_tiles) {
+            if (f64) linrec_tile<double, KD, ED>(sg, st, L, m.scan_tiles, j, true, hdr);
+            else linrec_tile<float, KF, EF>(sg, st, L, m.scan_tiles, j, true, hdr);
+            continue;
+        }
+        j -= m.scan_tiles;
+        if (f64) prod_map_tile<double>(sg, st, L, (int)j, RT, hdr);
+        else prod_map_tile<float>(sg, st, L, (int)j, RT, hdr);
+    }
+}
+
+typedef void (*BatchKernel)(const char*, char*);
+BatchKernel kernel_of(int v) {
+    switch (v) {
+    case 0: return batch_kernel<2, 4, 1, 8, 8192>;
+    case 1: return batch_kernel<4, 4, 2, 8, 16384>;
+    case 2: return batch_kernel<1, 4, 1, 4, 4096>;
+    }
+    return nullptr;
+}
+
+size_t plan_bytes(int64_t nseg) {
+    return round_up(sizeof(BatchPlanHeader), 64) + round_up((size_t)nseg * sizeof(adpar_batch_segment), 64) +
+           round_up((size_t)nseg * sizeof(SegMeta), 64);
+}
+
+}  // namespace
+}  // namespace adpar
+
+extern "C" size_t adpar_batch_plan_bytes(int nseg) {
+    return nseg < 0 ? (size_t)-1 : adpar::plan_bytes(nseg);
+}
+
+extern "C" int adpar_batch_plan(const adpar_batch_segment* segs, int nseg, const adpar_batch_config* cfg,
+                                void* plan_host, size_t plan_bytes_avail, size_t* work_bytes_out) {
+    using namespace adpar;
+    static_assert(sizeof(adpar_batch_segment) == 96, "segment descriptor is 96 bytes");
+    if (nseg < 0 || (nseg > 0 && !segs) || !plan_host || !work_bytes_out) return ADPAR_ERR_INVALID;
+    adpar_batch_config c{0, 2, 1, 0};
+    if (cfg) c = *cfg;
+    if (c.variant < 0 || c.variant >= kNumVariants || c.ctas_per_sm < 1 || c.ctas_per_sm > 8 || c.order < 0 ||
+        c.order > 1)
+        return ADPAR_ERR_INVALID;
+    const size_t need = plan_bytes(nseg);
+    if (plan_bytes_avail < need) return ADPAR_ERR_WORKSPACE;
+    for (int s = 0; s < nseg; ++s) {
+        const adpar_batch_segment& g = segs[s];
+        if (g.len < 0 || (g.dtype != ADPAR_F32 && g.dtype != ADPAR_F64)) return ADPAR_ERR_INVALID;
+        if (g.len > 0 && (!g.x || !g.xbar || !g.a || !g.b || !g.ybar_a || !g.ybar_b || !g.abar || !g.bbar))
+            return ADPAR_ERR_INVALID;
+        const void* ptrs[] = {g.x, g.xbar, g.a, g.b, g.ybar_a, g.ybar_b, g.abar, g.bbar};
+        for (const void* p : ptrs)
+            if (p && !aligned16(p)) return ADPAR_ERR_ALIGN;
+    }
+    const VariantShape V = kVariants[c.variant];
+    // scheduling order: as given, or the longest (most bytes) first so the
+    // tail of the launch is made of short segments
+    std::vector<int> order(nseg);
+    for (int s = 0; s < nseg; ++s) order[s] = s;
+    if (c.order == 1)
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            const int64_t wx = segs[x].len * (segs[x].dtype == ADPAR_F64 ? 2 : 1);
+            const int64_t wy = segs[y].len * (segs[y].dtype == ADPAR_F64 ? 2 : 1);
+            return wx > wy;
+        });
+    char* P = static_cast<char*>(plan_host);
+    std::memset(P, 0, need);
+    BatchPlanHeader* H = reinterpret_cast<BatchPlanHeader*>(P);
+    H->nseg = nseg;
+    H->seg_off = (int64_t)round_up(sizeof(BatchPlanHeader), 64);
+    H->meta_off = H->seg_off + (int64_t)round_up((size_t)nseg * sizeof(adpar_batch_segment), 64);
+    H->variant = c.variant;
+    H->order = c.order;
+    H->ctas_per_sm = c.ctas_per_sm;
+    adpar_batch_segment* S = reinterpret_cast<adpar_batch_segment*>(P + H->seg_off);
+    SegMeta* M = reinterpret_cast<SegMeta*>(P + H->meta_off);
+    int64_t items = 0, state = (int64_t)sizeof(WsHeader);
+    for (int q = 0; q < nseg; ++q) {
+        const adpar_batch_segment& g = segs[order[q]];
+        const int st = g.dtype == ADPAR_F64 ? V.kd * 256 * V.ed : V.kf * 256 * V.ef;
+        const int64_t red = std::max<int64_t>(1, (g.len + V.rt - 1) / V.rt);
+        const int64_t scan = std::max<int64_t>(1, (g.len + st - 1) / st);
+        if (red > INT32_MAX || scan > INT32_MAX) return ADPAR_ERR_UNSUPPORTED;
+        S[q] = g;
+        M[q].item_base = items;
+        M[q].red_tiles = (int32_t)red;
+        M[q].scan_tiles = (int32_t)scan;
+        M[q].state_off = state;
+        items += 2 * red + 2 * scan;
+        state += state_layout(g.dtype, (int)red, (int)scan).total;
+    }
+    if (items > (int64_t)UINT32_MAX - ((int64_t)1 << 20)) return ADPAR_ERR_UNSUPPORTED;  // 32-bit tickets
+    H->total_items = items;
+    H->ws_bytes = (int64_t)round_up((size_t)state, 256);
+    *work_bytes_out = (size_t)H->ws_bytes;
+    return ADPAR_OK;
+}
+
+extern "C" int adpar_vjp_batch(const void* plan_host, const void* plan_dev, void* work, size_t work_bytes,
+                               void* stream) {
+    using namespace adpar;
+    if (!plan_host || !plan_dev) return ADPAR_ERR_INVALID;
+    const BatchPlanHeader* H = static_cast<const BatchPlanHeader*>(plan_host);
+    if (H->variant < 0 || H->variant >= kNumVariants) return ADPAR_ERR_INVALID;
+    if (!work || work_bytes < (size_t)H->ws_bytes || (reinterpret_cast<uintptr_t>(work) & 255u))
+        return ADPAR_ERR_WORKSPACE;
+    if (H->nseg == 0) return ADPAR_OK;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return ADPAR_ERR_CUDA;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int ib = (int)std::max<int64_t>(1, std::min<int64_t>((H->ws_bytes / 16 + 255) / 256, (int64_t)sms * 4));
+    batch_init_kernel<<<ib, 256, 0, s>>>(static_cast<char*>(work), H->ws_bytes);
+    const int64_t grid = std::min<int64_t>((int64_t)sms * H->ctas_per_sm, H->total_items);
+    kernel_of(H->variant)<<<(unsigned)std::max<int64_t>(1, grid), 256, 0, s>>>(static_cast<const char*>(plan_dev),
+                                                                           static_cast<char*>(work));
+    return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
+}

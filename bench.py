@@ -14,6 +14,21 @@ sampled during the timed region, and an end-to-end figure through host
 buffers.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl adpar|reference]
+
+``--workload NAME`` measures one other row of the hot path instead (one
+JSON line each; these are measurements, not the headline line):
+  prod     product-reduce VJP, n = 65536 FP64 with 0/1/2 zeros (latency), and
+           n = 2^28 FP64 (bandwidth); argmax VJP, n = 2^28 FP32
+  hist     reduce_by_index VJPs, n = 2^27 FP32, m in {256, 2^16, 2^22},
+           uniform / Zipf(1.1) bins, + / * / max
+  scatter  scatter VJP, 2^26 values into 2^28 (random and sorted indices);
+           map-accumulator VJPs at 2^26
+  kmeans   k-means loss and C-gradient, N = 2^20, d = 32, k = 256
+  batch    4096 segments (product-reduce + linear-recurrence VJPs, lengths
+           2^U[8,20], FP32/FP64 mixed): one graph-replayed launch vs 4096
+           plain calls
+  serve    Poisson arrivals of mixed-operator requests sized 2^10..2^24:
+           p50/p99 latency and throughput vs one call at a time
 """
 import argparse
 import json
@@ -368,16 +383,294 @@ def run_adpar(args, ws, rank, local):
     return 0
 
 
+# --------------------------------------------------------------------------
+# Per-row measurements (--workload NAME)
+# --------------------------------------------------------------------------
+def _cuda_ms(fn, reps=10, warm=3):
+    """Average device time of fn() in ms (CUDA events on the current stream)."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(reps):
+        fn()
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / reps
+
+
+def _oracle_rate(fn, elements, budget_s=3.0):
+    """Elements/s of an oracle call on the host (1 core), repeated for about budget_s."""
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        fn()
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt >= budget_s or reps >= 50:
+            return elements * reps / dt
+
+
+def _line(workload, **kw):
+    hbm, kind = measured_peaks()
+    d = {"workload": workload, "data": "synthetic", "peak_hbm_gbs": hbm, "peak_source": kind}
+    d.update(kw)
+    print(json.dumps(d), flush=True)
+    return 0
+
+
+def _dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def row_prod(args):
+    """Product-reduce VJP (Sec. 5.1.1): the 65536-element FP64 latency case with
+    0/1/2 zeros, the 2^28 FP64 bandwidth case; and the argmax VJP at 2^28 FP32."""
+    import torch
+    from oracle import oracle as O
+    from paper_2202_10297_gb300 import adpar as A
+    from paper_2202_10297_gb300 import synth
+    hbm, _ = measured_peaks()
+    cases = {}
+    for z in (0, 1, 2):
+        a, _ = synth.prod_reduce(65536, z)
+        at = _dev(a)
+        yb = torch.ones(1, dtype=torch.float64, device="cuda")
+        ab = torch.empty_like(at)
+        sg = torch.empty(65536, dtype=torch.int8, device="cuda")
+        wk = A.workspace(A.adpar_workspace_size(A.RULE_REDUCE, A.OP_MUL, A.F64, 65536), "cuda")
+        f_log = lambda: A.adpar_vjp_reduce("mul", at, yb, abar=ab, logdomain=True, want_sign=False, work=wk)
+        f_val = lambda: A.adpar_vjp_reduce("mul", at, yb, abar=ab, work=wk)
+        f_pri = lambda: A.adpar_reduce("mul", at, work=wk)
+        t_log, t_val, t_pri = _cuda_ms(f_log, 200, 20), _cuda_ms(f_val, 200, 20), _cuda_ms(f_pri, 200, 20)
+        cases["n65536_z%d" % z] = {"vjp_logdomain_us": 1e3 * t_log, "vjp_value_us": 1e3 * t_val,
+                                   "primal_us": 1e3 * t_pri, "vjp_primal_ratio": t_val / t_pri,
+                                   "launches_per_call": 3,
+                                   "oracle_elements_per_s": _oracle_rate(lambda: O.prod_reduce_vjp(a, 1.0), 65536, 1.0)}
+    n = 1 << 28
+    big = torch.rand(n, dtype=torch.float64, device="cuda") + 0.5
+    abig = torch.empty_like(big)
+    wk = A.workspace(A.adpar_workspace_size(A.RULE_REDUCE, A.OP_MUL, A.F64, n), "cuda")
+    t = _cuda_ms(lambda: A.adpar_vjp_reduce("mul", big, 1.0, abar=abig, work=wk), 5, 2)
+    tp = _cuda_ms(lambda: A.adpar_reduce("mul", big, work=wk), 5, 2)
+    cases["n2^28_f64_value"] = {"ms": t, "algorithmic_bytes": 16 * n, "gbs": 16 * n / t / 1e6,
+                                "hbm_frac_of_measured": 16 * n / t / 1e6 / hbm, "primal_ms": tp,
+                                "vjp_primal_ratio": t / tp}
+    del big, abig
+    x = torch.randn(n, device="cuda")
+    xb = torch.empty_like(x)
+    wk = A.workspace(A.adpar_workspace_size(A.RULE_REDUCE, A.OP_MAX, A.F32, n), "cuda")
+    t = _cuda_ms(lambda: A.adpar_vjp_reduce("max", x, 1.0, abar=xb, work=wk), 5, 2)
+    tp = _cuda_ms(lambda: A.adpar_reduce("max", x, work=wk), 5, 2)
+    cases["argmax_n2^28_f32"] = {"ms": t, "algorithmic_bytes": 8 * n, "gbs": 8 * n / t / 1e6,
+                                 "hbm_frac_of_measured": 8 * n / t / 1e6 / hbm, "primal_ms": tp,
+                                 "vjp_primal_ratio": t / tp}
+    return _line("prod", metric="VJP latency / GB/s", cases=cases, oracle_cores=1)
+
+
+def row_hist(args):
+    """reduce_by_index VJPs (Sec. 5.1.2), n = 2^27 FP32."""
+    import torch
+    from oracle import oracle as O
+    from paper_2202_10297_gb300 import adpar as A
+    from paper_2202_10297_gb300 import synth
+    hbm, _ = measured_peaks()
+    n = 1 << 27
+    # algorithmic bytes per element: inputs read once + adjoint written once
+    alg = {"add": 8, "max": 12, "mul": 12}
+    cases = {}
+    for m in (256, 1 << 16, 1 << 22):
+        for dist in ("uniform", "zipf"):
+            vals, inds, hsbar = synth.hist(n, m, dist, seed=synth.SEED_BASE + 2)
+            v, ix, hb = _dev(vals), _dev(inds), _dev(hsbar)
+            vb = torch.empty_like(v)
+            for op in ("add", "max", "mul"):
+                wk = A.workspace(A.adpar_workspace_size(A.RULE_HIST, A.OPS[op], A.F32, n, m), "cuda")
+                f = lambda: A.adpar_vjp_hist(op, ix, m, hb, vals=v, valsbar=vb, work=wk)
+                fp = lambda: A.adpar_hist(op, v, ix, m, work=wk)
+                t, tp = _cuda_ms(f, 5, 2), _cuda_ms(fp, 5, 2)
+                cases["%s_m%d_%s" % (op, m, dist)] = {
+                    "ms": t, "elements_per_s": n / t * 1e3, "gbs": alg[op] * n / t / 1e6,
+                    "hbm_frac_of_measured": alg[op] * n / t / 1e6 / hbm, "primal_ms": tp, "vjp_primal_ratio": t / tp}
+            del v, ix, hb, vb
+    vals, inds, hsbar = synth.hist(1 << 20, 256, "zipf", seed=1)
+    orate = _oracle_rate(lambda: O.hist_vjp("max", vals, inds, 256, hsbar), 1 << 20, 2.0)
+    return _line("hist", metric="VJP elements/s and % of HBM", n=n, algorithmic_bytes_per_element=alg,
+                 cases=cases, cpu_baseline={"value": orate, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                                            "sample": "hist max, n = 2^20, m = 256, Zipf"})
+
+
+def row_scatter(args):
+    """Scatter VJP (Sec. 5.3) and map-accumulator VJPs (Sec. 5.4)."""
+    import torch
+    from oracle import oracle as O
+    from paper_2202_10297_gb300 import adpar as A
+    from paper_2202_10297_gb300 import synth
+    hbm, _ = measured_peaks()
+    n, m = 1 << 28, 1 << 26
+    cases = {}
+    for sort in (False, True):
+        is_, _, _ = synth.scatter(n, m, sort=sort, seed=synth.SEED_BASE + 2)
+        it = _dev(is_)
+        ysbar = torch.randn(n, device="cuda")
+        vsbar = torch.empty(m, device="cuda")
+        t = _cuda_ms(lambda: A.adpar_vjp_scatter(it, ysbar, vsbar=vsbar), 5, 2)
+        # 16 B per j (is, the gathered ysbar, vsbar, the zeroed ysbar); a random
+        # 4-byte access moves a 32-byte sector: 4 + 32 + 4 + 32 = 72 B per j
+        cases["sorted" if sort else "random"] = {
+            "ms": t, "elements_per_s": m / t * 1e3, "gbs_algorithmic": 16 * m / t / 1e6,
+            "hbm_frac_of_measured": 16 * m / t / 1e6 / hbm, "gbs_sector": 72 * m / t / 1e6,
+            "sector_frac_of_measured": 72 * m / t / 1e6 / hbm}
+        del it, ysbar, vsbar
+    nj = 1 << 26
+    for g, na, width in (("gather", 1 << 20, 1), ("scale", 1 << 20, 1), ("gather", 4096, 1),
+                         ("sqdist_row", 256, 32)):
+        as_, is_, ws, xsbar = synth.map_acc(nj // width if width > 1 else nj, na, width=width, seed=3)
+        at, it, wt, xt = _dev(as_), _dev(is_), _dev(ws), _dev(xsbar)
+        asb = torch.empty_like(at)
+        wsb = torch.empty_like(wt) if g != "gather" else None
+        t = _cuda_ms(lambda: A.adpar_vjp_map_acc(g, at, it, xt, ws=None if g == "gather" else wt, width=width,
+                                                 asbar=asb, wsbar=wsb), 5, 2)
+        cases["map_acc_%s_na%d_w%d" % (g, na, width)] = {"ms": t, "elements_per_s": it.numel() * width / t * 1e3}
+    is_, ys, _ = synth.scatter(1 << 22, 1 << 20, seed=4)
+    orate = _oracle_rate(lambda: O.scatter_vjp(1 << 22, is_, ys), 1 << 20, 2.0)
+    return _line("scatter", metric="VJP elements/s and % of HBM", cases=cases,
+                 cpu_baseline={"value": orate, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                               "sample": "scatter, m = 2^20 into n = 2^22"})
+
+
+def row_kmeans(args):
+    """k-means loss and C-gradient (Sec. 7.3), N = 2^20, d = 32, k = 256."""
+    import torch
+    from oracle import oracle as O
+    from paper_2202_10297_gb300 import adpar as A
+    from paper_2202_10297_gb300 import synth
+    N, d, k = 1 << 20, 32, 256
+    X, Cm = synth.kmeans(N, d, k)
+    Xt, Ct = _dev(X), _dev(Cm)
+    wk = A.workspace(A.adpar_workspace_size(A.RULE_KMEANS, 0, A.F32, N, k), "cuda")
+    cb = torch.empty_like(Ct)
+    yb = torch.ones(1, device="cuda")
+    t_vjp = _cuda_ms(lambda: A.adpar_kmeans_vjp(Xt, Ct, ybar=yb, Cbar=cb, work=wk), 20, 5)
+    t_fwd = _cuda_ms(lambda: A.adpar_kmeans_vjp(Xt, Ct, want_grad=False, work=wk), 20, 5)
+    flops = 2.0 * N * k * d
+    bf16 = 1933.0
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            bf16 = float(json.load(f)["bf16_tflops"])
+    tf32_peak = bf16 * 1.1 / 2.25  # measured bf16 x the nominal tf32/bf16 ratio
+    hbm, _ = measured_peaks()
+    orate = _oracle_rate(lambda: O.kmeans(X[:2048], Cm, 1.0), 2048, 2.0)
+    return _line("kmeans", metric="k-means VJP time", N=N, d=d, k=k, vjp_ms=t_vjp, forward_ms=t_fwd,
+                 vjp_primal_ratio=t_vjp / t_fwd, points_per_s=N / t_vjp * 1e3,
+                 roofline={"bound": "tensor", "achieved": flops / t_vjp / 1e9, "peak": tf32_peak, "unit": "TFLOP/s",
+                           "frac": flops / t_vjp / 1e9 / tf32_peak,
+                           "peak_source": "measured bf16 x 1.1/2.25 (tf32/bf16 nominal)",
+                           "hbm_gbs": N * d * 4 / t_vjp / 1e6, "hbm_frac": N * d * 4 / t_vjp / 1e6 / hbm},
+                 cpu_baseline={"value": orate, "unit": "points/s", "cores": 1, "kind": "oracle",
+                               "sample": "2048 points, k = 256, d = 32"})
+
+
+def _batch_segments(nseg, seed):
+    import torch
+    from paper_2202_10297_gb300 import synth
+    lens, dts, zs = synth.batch_plan(nseg, seed=seed)
+    g = synth.rng(seed + 1)
+    segs = []
+    for i, (L, dt, z) in enumerate(zip(lens, dts, zs)):
+        tdt = torch.float64 if dt else torch.float32
+        x = (torch.rand(int(L), dtype=tdt, device="cuda") + 0.5)
+        if z:
+            x[torch.from_numpy(g.choice(int(L), size=int(z), replace=False)).cuda()] = 0
+        a = torch.rand(int(L), dtype=tdt, device="cuda") * 0.1 + 0.9
+        segs.append(dict(x=x, a=a, b=torch.randn_like(a), ybar_a=torch.randn_like(a), ybar_b=torch.randn_like(a),
+                         ybar_prod=1.0))
+    return segs
+
+
+def row_batch(args):
+    """4096 uneven segments: one graph-replayed persistent launch vs 4096 plain calls."""
+    import torch
+    from paper_2202_10297_gb300 import adpar as A
+    from paper_2202_10297_gb300 import batch as B
+    from paper_2202_10297_gb300 import synth
+    segs = _batch_segments(4096, synth.SEED_BASE + 3)
+    total = sum(s["x"].numel() for s in segs)
+    bytes_alg = sum(s["x"].numel() * (44 if s["x"].dtype == torch.float32 else 88) for s in segs)
+    bt = B.Batch(segs)
+    best, best_ms, results = B.tune(bt, reps=3)
+    g = bt.graph()
+    t_graph = _cuda_ms(g.replay, 10, 2)
+    t_launch = _cuda_ms(bt.run, 10, 2)
+    works = {}
+
+    def plain():
+        for s in segs:
+            dt = A._dtype_code(s["x"])
+            n = s["x"].numel()
+            key = (dt, n)
+            if key not in works:
+                works[key] = (A.workspace(A.adpar_workspace_size(A.RULE_REDUCE, A.OP_MUL, dt, n), "cuda"),
+                              A.workspace(A.adpar_workspace_size(A.RULE_SCAN, A.OP_LINREC, dt, n), "cuda"))
+            w1, w2 = works[key]
+            A.adpar_vjp_reduce("mul", s["x"], s["ybar_prod"], abar=s["xbar"], work=w1)
+            A.adpar_vjp_scan("linrec", s["a"], s["ybar_a"], b=s["b"], ybar_b=s["ybar_b"], abar=s["abar"],
+                             bbar=s["bbar"], work=w2)
+    t_plain = _cuda_ms(plain, 3, 1)
+    hbm, _ = measured_peaks()
+    return _line("batch", metric="batched VJP elements/s", segments=len(segs), elements=total,
+                 tuned_config={"variant": best[0], "ctas_per_sm": best[1], "order": best[2]},
+                 graph_ms=t_graph, launch_ms=t_launch, plain_calls_ms=t_plain,
+                 speedup_vs_plain=t_plain / t_graph, elements_per_s=total / t_graph * 1e3,
+                 hbm_frac_of_measured=bytes_alg / t_graph / 1e6 / hbm,
+                 tuner=[{"config": r[1], "ms": r[0]} for r in results])
+
+
+def row_serve(args):
+    """Poisson arrivals at 50/80/95% of the measured capacity vs one call at a time."""
+    import torch
+    from paper_2202_10297_gb300 import adpar as A
+    from paper_2202_10297_gb300 import serve as S
+    A.lib()
+    srv = S.Server(budget_bytes=32 << 30, slots=8, max_n=1 << 24)
+    warm = S.make_requests(200, rate=None, seed=1)
+    srv.serve(warm)
+    sat = S.make_requests(2000, rate=None, seed=2)
+    cap = srv.serve(sat)
+    plain_slot = S.Slot(1 << 24, torch.device("cuda"))
+    cap_plain = S.serve_plain(S.make_requests(2000, rate=None, seed=2), srv.pool, plain_slot)
+    out = {"capacity": cap, "capacity_plain": cap_plain, "sweep": {}}
+    for frac in (0.5, 0.8, 0.95):
+        rate = frac * cap["throughput_rps"]
+        reqs = S.make_requests(3000, rate=rate, seed=3)
+        res = srv.serve(reqs)
+        res_plain = S.serve_plain(S.make_requests(3000, rate=rate, seed=3), srv.pool, plain_slot)
+        out["sweep"]["%d%%" % int(frac * 100)] = {"rate_rps": rate, "served": res, "plain": res_plain}
+    return _line("serve", metric="served p50/p99 latency and throughput", budget_gib=32, slots=8, **out)
+
+
+ROWS = {"prod": row_prod, "hist": row_hist, "scatter": row_scatter, "kmeans": row_kmeans, "batch": row_batch,
+        "serve": row_serve}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="adpar", choices=["adpar", "reference"])
+    ap.add_argument("--workload", default="scan",
+                    choices=["scan", "prod", "hist", "scatter", "kmeans", "batch", "serve"])
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.workload != "scan":
+        return ROWS[args.workload](args)
     return run_adpar(args, ws, rank, local)
 
 

@@ -179,11 +179,12 @@ __device__ void prod_map_tile(const adpar_batch_segment& sg, char* st, const Sta
                 double mi;
                 int64_t ei;
                 split_pow2((double)x[i], mi, ei);
-                if constexpr (sizeof(T) == 4) {
-                    const float q = (float)(f.m * ym) / (float)mi;  // FP32 output: FP32 division
-                    c = ldexp_clamped((double)q, f.e + ye - ei);
+                if constexpr (sizeof(T) == 4) {  // FP32 output: FP32 arithmetic suffices
+                    const float q = (float)(f.m * ym) * __frcp_rn((float)mi);
+                    xb[i] = scale_pow2f(q, f.e + ye - ei);
+                    continue;
                 } else {
-                    c = ldexp_clamped(f.m * ym / mi, f.e + ye - ei);
+                    c = scale_pow2(f.m * ym * recip_mantissa(mi), f.e + ye - ei);
                 }
             } else if (f.nz == 1 && i == f.first) {
                 c = ldexp_clamped(f.m * ym, f.e + ye);

@@ -31,7 +31,6 @@ namespace {
 
 constexpr int kHistBlock = 512;
 constexpr int kHistSmemKeys = 8192;  // 64 KB of 64-bit bin words per block
-constexpr int kHistSmemProd = 2048;  // bins of the * state per block (40 B each)
 
 __device__ __forceinline__ uint32_t orderkey_f32(float f) {
     uint32_t u = __float_as_uint(f);
@@ -262,78 +261,160 @@ __global__ void hist_arg_finish_kernel(HistArgs A) {
 }
 
 // ------------------------------------------------------------------ *
+// pm *= mi under a CAS loop (global bins).  When the mantissa drops below
+// 2^-823 it is scaled up by 2^900 through its exponent bits and the
+// exponent counter takes -900 (both exact); the check reads the IEEE
+// exponent field, so the loop does one FP64 multiply per attempt.
 __device__ __forceinline__ void mul_into(double* pm, long long* pe, double mi, long long ei) {
-    // pm *= mi under a CAS loop; when the mantissa gets small it is scaled
-    // back up by 2^900 and the exponent counter takes -900 (both exact)
     atomicAdd(reinterpret_cast<unsigned long long*>(pe), (unsigned long long)ei);
     unsigned long long* p = reinterpret_cast<unsigned long long*>(pm);
     unsigned long long old = *reinterpret_cast<volatile unsigned long long*>(p), assumed;
     long long shift;
     do {
         assumed = old;
-        double nv = __longlong_as_double((long long)assumed) * mi;
+        long long nb = __double_as_longlong(__longlong_as_double((long long)assumed) * mi);
         shift = 0;
-        if (fabs(nv) < 1e-250) {
-            nv *= 8.45271249817064e+270;  // 2^900
+        if (((nb >> 52) & 0x7ff) < 200) {  // below 2^-823 (products of mantissas are never 0)
+            nb += 900LL << 52;
             shift = -900;
         }
-        old = atomicCAS(p, assumed, (unsigned long long)__double_as_longlong(nv));
+        old = atomicCAS(p, assumed, (unsigned long long)nb);
     } while (old != assumed);
     if (shift) atomicAdd(reinterpret_cast<unsigned long long*>(pe), (unsigned long long)shift);
 }
 
+// Bin tiers of the * recompute:
+//   [0, H)       warp-private copies: lanes of a warp that hit the same bin
+//                are serialised into rounds (__match_any_sync picks one
+//                leader per bin per round), so every update is a plain
+//                read-modify-write of shared memory, however skewed;
+//   [H, H + H2)  one block-shared copy updated with shared-memory CAS;
+//   the rest     global CAS (L2).
+// Rank-ordered skewed data (Zipf) keeps its hot bins in the first tiers.
+constexpr int kProdWarpBins = 256;
+constexpr int kProdBlockBins = 2048;
+constexpr int kProdBlock = 256;
+
 template <class T, class I>
-__global__ void __launch_bounds__(kHistBlock) hist_prod_kernel(HistArgs A) {
+__global__ void __launch_bounds__(kProdBlock) hist_prod_kernel(HistArgs A) {
     extern __shared__ unsigned char smem_raw[];
-    const int H = (int)std::min<int64_t>(A.m, kHistSmemProd);
-    double* sm = reinterpret_cast<double*>(smem_raw);
-    long long* se = reinterpret_cast<long long*>(sm + H);
-    long long* sf = se + H;
-    unsigned int* sz = reinterpret_cast<unsigned int*>(sf + H);
-    for (int b = threadIdx.x; b < H; b += blockDim.x) {
-        sm[b] = 0.5;
-        se[b] = 1;
-        sf[b] = INT64_MAX;
-        sz[b] = 0u;
+    constexpr int NW = kProdBlock / 32;
+    const int H = (int)std::min<int64_t>(A.m, kProdWarpBins);
+    double* wm = reinterpret_cast<double*>(smem_raw);            // [NW][H] mantissa, [0.5, 1)
+    long long* wf = reinterpret_cast<long long*>(wm + NW * H);   // [NW][H] lowest zero index
+    int* we = reinterpret_cast<int*>(wf + NW * H);               // [NW][H] exponent sum
+    int* wz = we + NW * H;                                        // [NW][H] zero count
+    const int H2 = (int)std::max<int64_t>(0, std::min<int64_t>(A.m - H, kProdBlockBins));
+    double* bm = reinterpret_cast<double*>(wz + NW * H);          // [H2] block-shared tier
+    long long* be = reinterpret_cast<long long*>(bm + H2);
+    long long* bf = be + H2;
+    unsigned int* bz = reinterpret_cast<unsigned int*>(bf + H2);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = threadIdx.x; q < NW * H; q += blockDim.x) {
+        wm[q] = 0.5;
+        we[q] = 1;
+        wz[q] = 0;
+        wf[q] = INT64_MAX;
+    }
+    for (int q = threadIdx.x; q < H2; q += blockDim.x) {
+        bm[q] = 0.5;
+        be[q] = 1;
+        bf[q] = INT64_MAX;
+        bz[q] = 0u;
     }
     __syncthreads();
+    double* mym = wm + warp * H;
+    int* mye = we + warp * H;
+    int* myz = wz + warp * H;
+    long long* myf = wf + warp * H;
     const I* inds = static_cast<const I*>(A.inds);
     const T* vals = static_cast<const T*>(A.vals);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += stride) {
-        const int64_t b = ld_index(inds, i);
-        if (b < 0 || b >= A.m) continue;
-        const double v = (double)__ldcs(vals + i);
-        if (v == 0.0) {
-            if (b < H) {
-                atomicAdd(sz + b, 1u);
-                atomicMin(sf + b, (long long)i);
+    const int64_t nround = (A.n + stride - 1) / stride;  // same trip count in every lane
+    for (int64_t it = 0; it < nround; ++it) {
+        const int64_t i = it * stride + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        int64_t b = -1;
+        double v = 0.0;
+        if (i < A.n) {
+            b = ld_index(inds, i);
+            v = (double)__ldcs(vals + i);
+        }
+        const bool in = b >= 0 && b < A.m;
+        double mi = 0.5;
+        int64_t ei = 1;
+        if (in && v != 0.0) split_pow2(v, mi, ei);
+        if (in && b >= H && b < H + H2) {  // warm bins: block-shared, shared-memory CAS
+            const int q = (int)(b - H);
+            if (v == 0.0) {
+                atomicAdd(bz + q, 1u);
+                atomicMin(bf + q, (long long)i);
             } else {
+                mul_into(bm + q, be + q, mi, ei);
+            }
+        } else if (in && b >= H + H2) {  // cold bins: global atomics
+            if (v == 0.0) {
                 atomicAdd(A.pz + b, 1u);
                 atomicMin(A.pf + b, (long long)i);
+            } else {
+                mul_into(A.pm + b, A.pe + b, mi, ei);
             }
-        } else {
-            double mi;
-            int64_t ei;
-            split_pow2(v, mi, ei);
-            if (b < H) mul_into(sm + b, se + b, mi, ei);
-            else mul_into(A.pm + b, A.pe + b, mi, ei);
+        }
+        bool pending = in && b < H;
+        const unsigned key = pending ? (unsigned)b : (0x80000000u | (unsigned)lane);
+        while (__any_sync(0xffffffffu, pending)) {
+            const unsigned grp = __match_any_sync(0xffffffffu, pending ? key : (0x80000000u | (unsigned)lane));
+            const bool leader = pending && lane == __ffs(grp) - 1;
+            if (leader) {
+                if (v == 0.0) {
+                    myz[b] += 1;
+                    if (i < myf[b]) myf[b] = i;
+                } else {
+                    double mm = mym[b] * mi;
+                    int64_t e2 = 0;
+                    renorm(mm, e2);
+                    mym[b] = mm;
+                    mye[b] += (int)(ei + e2);
+                }
+                pending = false;
+            }
+            __syncwarp();
         }
     }
     __syncthreads();
-    for (int b = threadIdx.x; b < H; b += blockDim.x) {
-        if (sz[b]) {
-            atomicAdd(A.pz + b, sz[b]);
-            atomicMin(A.pf + b, sf[b]);
+    // merge the warps' copies and push each bin once into the global state
+    for (int q = threadIdx.x; q < H; q += blockDim.x) {
+        double mm = 0.5;
+        int64_t ee = 1;
+        int nz = 0;
+        long long first = INT64_MAX;
+        for (int w = 0; w < NW; ++w) {
+            mm *= wm[w * H + q];
+            renorm(mm, ee);
+            ee += we[w * H + q];
+            nz += wz[w * H + q];
+            first = std::min(first, wf[w * H + q]);
         }
-        double mb = sm[b];
-        long long eb = se[b];
-        if (!(mb == 0.5 && eb == 1)) {
-            double mm;
-            int64_t ee;
-            split_pow2(mb, mm, ee);
-            mul_into(A.pm + b, A.pe + b, mm, (long long)(eb + ee));
+        if (nz) {
+            atomicAdd(A.pz + q, (unsigned)nz);
+            atomicMin(A.pf + q, first);
         }
+        double m2;
+        int64_t e2;
+        split_pow2(mm, m2, e2);
+        const long long etot = (long long)(ee + e2);
+        if (!(m2 == 0.5 && etot == 1)) mul_into(A.pm + q, A.pe + q, m2, etot);
+    }
+    for (int q = threadIdx.x; q < H2; q += blockDim.x) {
+        const int64_t b = H + q;
+        if (bz[q]) {
+            atomicAdd(A.pz + b, bz[q]);
+            atomicMin(A.pf + b, bf[q]);
+        }
+        double m2;
+        int64_t e2;
+        split_pow2(bm[q], m2, e2);
+        const long long etot = (long long)(be[q] + e2);
+        if (!(m2 == 0.5 && etot == 1)) mul_into(A.pm + b, A.pe + b, m2, etot);
     }
 }
 
@@ -396,7 +477,7 @@ __global__ void __launch_bounds__(kHistBlock) hist_prod_vjp_kernel(HistArgs A) {
                         double mi;
                         int64_t ei;
                         split_pow2(v, mi, ei);
-                        c = ldexp_clamped(mm * ym / mi, e + ye - ei);
+                        c = scale_pow2(mm * ym * recip_mantissa(mi), e + ye - ei);
                     }
                 } else {
                     if (A.logdomain) {
@@ -487,8 +568,11 @@ int run_hist(HistArgs A, cudaStream_t s) {
         break;
     }
     case ADPAR_OP_MUL: {
-        const size_t sh = (size_t)std::min<int64_t>(A.m, kHistSmemProd) * 28;
-        hist_prod_kernel<T, I><<<gridN, kHistBlock, sh, s>>>(A);
+        const int64_t h1 = std::min<int64_t>(A.m, kProdWarpBins);
+        const int64_t h2 = std::max<int64_t>(0, std::min<int64_t>(A.m - h1, kProdBlockBins));
+        const size_t sh = (size_t)h1 * 24 * (kProdBlock / 32) + (size_t)h2 * 28;
+        const int gridP = (int)std::max<int64_t>(1, std::min<int64_t>((A.n + kProdBlock - 1) / kProdBlock, (int64_t)sms * 8));
+        hist_prod_kernel<T, I><<<gridP, kProdBlock, sh, s>>>(A);
         if (A.hs_out || A.bin_aux) hist_prod_bins_kernel<T><<<gridM, 256, 0, s>>>(A);
         if (!A.primal_only) hist_prod_vjp_kernel<T, I><<<gridN, kHistBlock, 0, s>>>(A);
         break;
@@ -506,7 +590,7 @@ template <class T, class I>
 void configure_smem() {
     // the recompute kernels use up to 64 KB of dynamic shared memory
     cudaFuncSetAttribute(hist_add_primal_kernel<T, I>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    cudaFuncSetAttribute(hist_prod_kernel<T, I>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(hist_prod_kernel<T, I>, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
     if constexpr (sizeof(T) == 4) {
         cudaFuncSetAttribute(hist_arg_f32_kernel<I, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
         cudaFuncSetAttribute(hist_arg_f32_kernel<I, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);

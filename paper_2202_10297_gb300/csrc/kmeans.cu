@@ -7,15 +7,16 @@
 // which Sec. 6.1 turns into a reduction; here that reduction is a per-block
 // histogram of rows (counts and row sums per centroid) in shared memory.
 //
-// One persistent kernel, one CTA per SM, 8 warps:
+// One persistent kernel, one CTA per SM, 12 warps:
 //   warp 0     TMA producer: X tiles of 128 rows x 32 FP32 (128-byte rows,
 //              128-byte swizzle) into a 4-stage ring; C (k x 32) once.
 //   warp 1     MMA issuer: S = X_tile C^T with tcgen05.mma kind::tf32
 //              (M = 128, N = k, K = 32 in four steps of 8) into one of two
 //              TMEM accumulators (2 x 256 columns).
 //   warp 2     TMEM allocation and release.
-//   warps 4-7  epilogue, one thread per row: tcgen05.ld of the k
-//              distances  v_k = |c_k|^2 - 2 x.c_k, the minimum, and a
+//   warps 4-11 epilogue, two threads per row (each half of the columns):
+//              tcgen05.ld of the distances  v_k = |c_k|^2 - 2 x.c_k, the
+//              minimum (next chunk's load in flight meanwhile), and a
 //              certified argmin: every centroid within the TF32 error
 //              bound of the minimum is recomputed exactly in FP32; if two
 //              remain within the FP32 bound, FP64 (the oracle's own
@@ -35,7 +36,7 @@
 namespace adpar {
 namespace {
 
-constexpr int KM_THREADS = 256;
+constexpr int KM_THREADS = 384;  // warps 0-3 roles, 4-11 epilogue
 constexpr int KM_STAGES = 4;
 constexpr int KM_D = 32;
 constexpr int KM_KMAX = 256;
@@ -51,7 +52,9 @@ constexpr uint32_t OFF_CNT = OFF_SUM + KM_KMAX * KM_D * 4;              // 1 KB
 constexpr uint32_t OFF_CN2 = OFF_CNT + KM_KMAX * 4;                     // 1 KB
 constexpr uint32_t OFF_CAND = OFF_CN2 + KM_KMAX * 4;                    // 4 KB
 constexpr uint32_t OFF_ARG = OFF_CAND + KM_TILE * KM_MAXCAND * 4;       // 512 B
-constexpr uint32_t OFF_BAR = OFF_ARG + KM_TILE * 4;                     // barriers
+constexpr uint32_t OFF_MIN = OFF_ARG + KM_TILE * 4;                     // 1 KB: [2][128] minima
+constexpr uint32_t OFF_NC = OFF_MIN + 2 * KM_TILE * 4;                  // 512 B: candidate counts
+constexpr uint32_t OFF_BAR = OFF_NC + KM_TILE * 4;                      // barriers
 constexpr uint32_t NBAR = 2 * KM_STAGES + 5;
 constexpr uint32_t OFF_MISC = OFF_BAR + NBAR * 8;
 constexpr uint32_t KM_SMEM = OFF_MISC + 64 + 1024;  // + alignment slack
@@ -120,6 +123,51 @@ __global__ void km_empty_kernel(float* loss_out, float* Cbar, int kd, int accumu
         for (int q = t; q < kd; q += gridDim.x * blockDim.x) Cbar[q] = 0.f;
 }
 
+// The 8 epilogue warps (256 threads, warps 4-11) synchronise on named
+// barrier 1.  epi_any is a barrier that also ORs a predicate over them, so
+// a decision to stop is taken by all of them together.
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ bool epi_any(bool p) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred q, o;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred o, 1, 256, q;\n\t"
+        "selp.u32 %0, 1, 0, o;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)p)
+        : "memory");
+    return r != 0;
+}
+
+// min over one 32-column chunk of v_k = |c_k|^2 - 2 S_k, two chains for ILP
+__device__ __forceinline__ void chunk_min(const uint32_t (&v)[32], const float* cn2, float& ma, float& mb) {
+#pragma unroll
+    for (int c4 = 0; c4 < 8; ++c4) {
+        const float4 c = *reinterpret_cast<const float4*>(cn2 + 4 * c4);
+        ma = fminf(ma, fmaf(-2.f, __uint_as_float(v[4 * c4 + 0]), c.x));
+        mb = fminf(mb, fmaf(-2.f, __uint_as_float(v[4 * c4 + 1]), c.y));
+        ma = fminf(ma, fmaf(-2.f, __uint_as_float(v[4 * c4 + 2]), c.z));
+        mb = fminf(mb, fmaf(-2.f, __uint_as_float(v[4 * c4 + 3]), c.w));
+    }
+}
+// candidates of one chunk: columns with v_k <= thr, appended to the row's list
+__device__ __forceinline__ void chunk_cand(const uint32_t (&v)[32], const float* cn2, int k0, float thr,
+                                           int* ncand, int* list) {
+#pragma unroll
+    for (int c4 = 0; c4 < 8; ++c4) {
+        const float4 c = *reinterpret_cast<const float4*>(cn2 + 4 * c4);
+        const float cc[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (fmaf(-2.f, __uint_as_float(v[4 * c4 + j]), cc[j]) <= thr) {
+                const int slot = atomicAdd(ncand, 1);
+                if (slot < KM_MAXCAND) list[slot] = k0 + 4 * c4 + j;
+            }
+        }
+    }
+}
+
 __global__ void km_init_kernel(KmArgs A) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < 64) reinterpret_cast<uint32_t*>(A.hdr)[t] = 0u;
@@ -139,6 +187,8 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
     float* s_cn2 = reinterpret_cast<float*>(base + OFF_CN2);
     int* s_cand = reinterpret_cast<int*>(base + OFF_CAND);
     int* s_arg = reinterpret_cast<int*>(base + OFF_ARG);
+    float* s_min = reinterpret_cast<float*>(base + OFF_MIN);
+    int* s_ncand = reinterpret_cast<int*>(base + OFF_NC);
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + OFF_BAR);
     uint64_t* x_full = bars;
     uint64_t* x_empty = bars + KM_STAGES;
@@ -157,11 +207,11 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < KM_STAGES; ++s) {
             tc::mbar_init(&x_full[s], 1);
-            tc::mbar_init(&x_empty[s], 128);
+            tc::mbar_init(&x_empty[s], 256);
         }
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(&t_full[b], 1);
-            tc::mbar_init(&t_empty[b], 128);
+            tc::mbar_init(&t_empty[b], 256);
         }
         tc::mbar_init(c_bar, 1);
         *s_abort = 0;
@@ -233,120 +283,151 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
             }
         }
     } else if (warp >= 4) {
-        const int r = (warp - 4) * 32 + lane;  // row of the tile == TMEM lane
-        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+        // 8 epilogue warps: warp (quarter, half) reads TMEM lanes of its
+        // quarter and the 32-column chunks q with q % 2 == half
+        const int ew = warp - 4;
+        const int quarter = warp & 3, half = ew >> 2;
+        const int r = quarter * 32 + lane;  // row of the tile == TMEM lane
+        const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+        const int nq = k / 32;
         double loss_local = 0.0;
         if (!tc::mbar_wait(c_bar, 0, s_abort)) *s_abort = 1;
         int i = 0;
-        for (int64_t t = blockIdx.x; t < A.ntiles && !*s_abort; t += gridDim.x, ++i) {
+        for (int64_t t = blockIdx.x; t < A.ntiles; t += gridDim.x, ++i) {
             const int s = i % KM_STAGES, b = i & 1;
-            if (!tc::mbar_wait(&t_full[b], (i >> 1) & 1, s_abort)) { *s_abort = 1; break; }
-            if (!tc::mbar_wait(&x_full[s], (i / KM_STAGES) & 1, s_abort)) { *s_abort = 1; break; }
+            const bool ok = tc::mbar_wait(&t_full[b], (i >> 1) & 1, s_abort) &&
+                            tc::mbar_wait(&x_full[s], (i / KM_STAGES) & 1, s_abort);
+            if (epi_any(!ok)) {  // every epilogue thread leaves together
+                *s_abort = 1;
+                break;
+            }
             tc::fence_after_sync();
             const float* xt = sX + s * (KM_X_BYTES / 4);
             const int64_t row = t * KM_TILE + r;
             const bool valid = row < A.N;
-            float x[32];
-            sw_row(xt, r, x);
             float xn2 = 0.f;
+            {
+                float x[32];
+                sw_row(xt, r, x);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) xn2 = fmaf(x[j], x[j], xn2);
+                for (int j = 0; j < 32; ++j) xn2 = fmaf(x[j], x[j], xn2);
+            }
             const float xn = sqrtf(xn2);
             // |v~_k - v_k| <= 2 |S~ - S| + rounding <= 2^-8 |x| |c_k| (TF32 keeps 10
             // mantissa bits of each operand) plus FP32 terms; 2x margin
             const float tol = 8.0e-3f * xn * cmax + 1.0e-5f * (cmax * cmax + xn * cmax) + 1e-20f;
             const uint32_t tb = tmem + lane_base + (uint32_t)(b * 256);
-            float m1 = CUDART_INF_F;
-            for (int q = 0; q < k / 32; ++q) {
-                uint32_t v[32];
-                __syncwarp();
-                tc::tmem_ld32(tb + (uint32_t)(q * 32), v);
-                tc::tmem_ld_wait();
-#pragma unroll
-                for (int c = 0; c < 32; ++c) m1 = fminf(m1, fmaf(-2.f, __uint_as_float(v[c]), s_cn2[q * 32 + c]));
+
+            // pass 1: the minimum of v_k over this thread's chunks; the load
+            // of the next chunk is in flight while the current one is scanned
+            float m1a = CUDART_INF_F, m1b = CUDART_INF_F;
+            {
+                uint32_t va[32], vb[32];
+                int q = half;
+                if (q < nq) { __syncwarp(); tc::tmem_ld32(tb + (uint32_t)(q * 32), va); }
+                for (; q < nq; q += 4) {
+                    tc::tmem_ld_wait();
+                    if (q + 2 < nq) { __syncwarp(); tc::tmem_ld32(tb + (uint32_t)((q + 2) * 32), vb); }
+                    chunk_min(va, s_cn2 + q * 32, m1a, m1b);
+                    if (q + 2 >= nq) break;
+                    tc::tmem_ld_wait();
+                    if (q + 4 < nq) { __syncwarp(); tc::tmem_ld32(tb + (uint32_t)((q + 4) * 32), va); }
+                    chunk_min(vb, s_cn2 + (q + 2) * 32, m1a, m1b);
+                }
             }
-            const float thr = m1 + 2.f * tol;
-            int nc = 0;
-            for (int q = 0; q < k / 32; ++q) {
-                uint32_t v[32];
-                __syncwarp();
-                tc::tmem_ld32(tb + (uint32_t)(q * 32), v);
-                tc::tmem_ld_wait();
-#pragma unroll
-                for (int c = 0; c < 32; ++c) {
-                    if (fmaf(-2.f, __uint_as_float(v[c]), s_cn2[q * 32 + c]) <= thr) {
-                        if (nc < KM_MAXCAND) s_cand[r * KM_MAXCAND + nc] = q * 32 + c;
-                        ++nc;
-                    }
+            s_min[half * KM_TILE + r] = fminf(m1a, m1b);
+            if (half == 0) s_ncand[r] = 0;
+            epi_sync();
+            const float thr = fminf(s_min[r], s_min[KM_TILE + r]) + 2.f * tol;
+            // pass 2: every k with v_k <= min + 2 tol is a candidate argmin
+            {
+                uint32_t va[32], vb[32];
+                int q = half;
+                if (q < nq) { __syncwarp(); tc::tmem_ld32(tb + (uint32_t)(q * 32), va); }
+                for (; q < nq; q += 4) {
+                    tc::tmem_ld_wait();
+                    if (q + 2 < nq) { __syncwarp(); tc::tmem_ld32(tb + (uint32_t)((q + 2) * 32), vb); }
+                    chunk_cand(va, s_cn2 + q * 32, q * 32, thr, s_ncand + r, s_cand + r * KM_MAXCAND);
+                    if (q + 2 >= nq) break;
+                    tc::tmem_ld_wait();
+                    if (q + 4 < nq) { __syncwarp(); tc::tmem_ld32(tb + (uint32_t)((q + 4) * 32), va); }
+                    chunk_cand(vb, s_cn2 + (q + 2) * 32, (q + 2) * 32, thr, s_ncand + r, s_cand + r * KM_MAXCAND);
                 }
             }
             tc::fence_before_sync();
             tc::mbar_arrive(&t_empty[b]);  // the accumulator may be overwritten now
+            epi_sync();
 
-            // certify the argmin among the candidates (ascending k)
-            int best = 0;
-            double dist = 0.0;
-            if (nc == 1) {
-                best = s_cand[r * KM_MAXCAND];
-                dist = (double)exact_f32(xt, r, sC, best);
-            } else {
-                const int ncc = nc <= KM_MAXCAND ? nc : 0;  // 0: fall back to all k
-                float u32 = CUDART_INF_F;
-                for (int c = 0; c < ncc; ++c) {
-                    const float e = exact_f32(xt, r, sC, s_cand[r * KM_MAXCAND + c]);
-                    u32 = fminf(u32, e + 4.0e-6f * e + 1e-30f);
-                }
-                int n2 = 0, only = -1;
-                float only_e = 0.f;
-                for (int c = 0; c < ncc; ++c) {
-                    const int kc = s_cand[r * KM_MAXCAND + c];
-                    const float e = exact_f32(xt, r, sC, kc);
-                    if (e - 4.0e-6f * e <= u32) {
-                        ++n2;
-                        if (only < 0) { only = kc; only_e = e; }
-                    }
-                }
-                if (ncc > 0 && n2 == 1) {
-                    best = only;
-                    dist = (double)only_e;
+            // certify the argmin among the candidates (half 0 of each row)
+            if (half == 0) {
+                const int nc = s_ncand[r];
+                int best = 0;
+                double dist = 0.0;
+                if (nc == 1) {
+                    best = s_cand[r * KM_MAXCAND];
+                    dist = (double)exact_f32(xt, r, sC, best);
                 } else {
-                    double bd = CUDART_INF;
-                    const int lim = ncc > 0 ? ncc : k;
-                    for (int c = 0; c < lim; ++c) {
-                        const int kc = ncc > 0 ? s_cand[r * KM_MAXCAND + c] : c;
-                        if (ncc > 0) {
-                            const float e = exact_f32(xt, r, sC, kc);
-                            if (!(e - 4.0e-6f * e <= u32)) continue;
-                        }
-                        const double d = exact_f64(xt, r, sC, kc);
-                        if (d < bd) { bd = d; best = kc; }
+                    const int ncc = nc <= KM_MAXCAND ? nc : 0;  // 0: fall back to all k
+                    float u32 = CUDART_INF_F;
+                    for (int c = 0; c < ncc; ++c) {
+                        const float e = exact_f32(xt, r, sC, s_cand[r * KM_MAXCAND + c]);
+                        u32 = fminf(u32, e + 4.0e-6f * e + 1e-30f);
                     }
-                    dist = bd;
+                    int n2 = 0, only = -1;
+                    float only_e = 0.f;
+                    for (int c = 0; c < ncc; ++c) {
+                        const int kc = s_cand[r * KM_MAXCAND + c];
+                        const float e = exact_f32(xt, r, sC, kc);
+                        if (e - 4.0e-6f * e <= u32) {
+                            ++n2;
+                            only = kc;
+                            only_e = e;
+                        }
+                    }
+                    if (ncc > 0 && n2 == 1) {
+                        best = only;
+                        dist = (double)only_e;
+                    } else {
+                        // FP64 over what FP32 cannot separate; ties to the lowest k
+                        double bd = CUDART_INF;
+                        best = k;
+                        const int lim = ncc > 0 ? ncc : k;
+                        for (int c = 0; c < lim; ++c) {
+                            const int kc = ncc > 0 ? s_cand[r * KM_MAXCAND + c] : c;
+                            if (ncc > 0) {
+                                const float e = exact_f32(xt, r, sC, kc);
+                                if (!(e - 4.0e-6f * e <= u32)) continue;
+                            }
+                            const double d = exact_f64(xt, r, sC, kc);
+                            if (d < bd || (d == bd && kc < best)) { bd = d; best = kc; }
+                        }
+                        dist = bd;
+                    }
                 }
-            }
-            if (valid) {
-                loss_local += dist;
-                if (A.argmin_out) A.argmin_out[row] = best;
+                if (valid) {
+                    loss_local += dist;
+                    if (A.argmin_out) A.argmin_out[row] = best;
+                }
+                s_arg[r] = valid ? best : -1;
             }
             if (want_grad) {
-                s_arg[r] = valid ? best : -1;
-                __syncwarp();
-                const int r0 = (warp - 4) * 32;
-                for (int rr = 0; rr < 32; ++rr) {
-                    const int kc = s_arg[r0 + rr];
+                epi_sync();
+                // row sums: warp ew takes rows [16 ew, 16 ew + 16), one row per step,
+                // lanes = coordinates (32 consecutive floats: no bank conflicts)
+                for (int rr = ew * 16; rr < ew * 16 + 16; ++rr) {
+                    const int kc = s_arg[rr];
                     if (kc >= 0) {
-                        atomicAdd(&s_sum[kc * KM_D + lane], sw_elem(xt, r0 + rr, lane));
+                        atomicAdd(&s_sum[kc * KM_D + lane], sw_elem(xt, rr, lane));
                         if (lane == 0) atomicAdd(&s_cnt[kc], 1.f);
                     }
                 }
-                __syncwarp();
             }
             tc::mbar_arrive(&x_empty[s]);  // the X stage may be refilled now
         }
         // loss: warp reduce, then one double atomic per warp
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) loss_local += __shfl_xor_sync(0xffffffffu, loss_local, off);
-        if (lane == 0) atomicAdd(A.loss_acc, loss_local);
+        if (lane == 0 && loss_local != 0.0) atomicAdd(A.loss_acc, loss_local);
     }
 
     // drain: no TMA copy or MMA may be in flight when the CTA leaves

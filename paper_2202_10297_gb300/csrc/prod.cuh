@@ -78,4 +78,50 @@ __device__ __forceinline__ double ldexp_clamped(double x, int64_t e) {
     return ldexp(x, (int)e);
 }
 
+// x * 2^e for a normal x with |x| in [2^-4, 2^4): the exponent field is
+// adjusted directly when the result is normal (exact); a result in the
+// subnormal range is formed by one multiply by 2^-1000 (one rounding,
+// correct); below that it is a signed zero, above it an infinity.
+__device__ __forceinline__ double scale_pow2(double x, int64_t e) {
+    const long long b = __double_as_longlong(x);
+    const int64_t ex = ((b >> 52) & 0x7ff) + e;
+    const long long sign = b & (long long)0x8000000000000000ULL;
+    if (ex >= 1 && ex <= 2046) return __longlong_as_double((b & ~(0x7ffLL << 52)) | ((long long)ex << 52));
+    if (ex > 2046) return __longlong_as_double(sign | (0x7ffLL << 52));
+    if (ex < -60) return __longlong_as_double(sign);
+    return __longlong_as_double((b & ~(0x7ffLL << 52)) | ((long long)(ex + 1000) << 52)) * 9.332636185032189e-302;
+}
+// the same for FP32 results (x a float in [2^-4, 2^4))
+__device__ __forceinline__ float scale_pow2f(float x, int64_t e) {
+    const int b = __float_as_int(x);
+    const int64_t ex = ((b >> 23) & 0xff) + e;
+    const int sign = b & (int)0x80000000u;
+    if (ex >= 1 && ex <= 254) return __int_as_float((b & ~(0xff << 23)) | ((int)ex << 23));
+    if (ex > 254) return __int_as_float(sign | (0xff << 23));
+    if (ex < -30) return __int_as_float(sign);
+    return __int_as_float((b & ~(0xff << 23)) | ((int)(ex + 100) << 23)) * 7.888609052210118e-31f;  // 2^-100
+}
+
+// 1 / m for a mantissa with 0.5 <= |m| < 1, by Newton-Raphson on
+// f(r) = 1/r - |m|: the seed is the FP32 reciprocal of |m| truncated to 24
+// bits (relative error below 2^-22), and each step  r <- r + r (1 - |m| r)
+// squares the relative error, so two steps reach FP64 rounding (1-2 ulp).
+// The sign of m is put back at the end.
+__device__ __forceinline__ double recip_mantissa(double m) {
+    const long long bm = __double_as_longlong(m);
+    const long long sign = bm & (long long)0x8000000000000000ULL;
+    const double am = __longlong_as_double(bm ^ sign);
+    const float mf = __int_as_float(0x3F000000 | (int)((bm >> 29) & 0x7FFFFF));  // |m| truncated, in [0.5, 1)
+    const float rf = __frcp_rn(mf);                                             // in (1, 2]
+    const int br = __float_as_int(rf);
+    // widen the float (exponent 127 or 128) to a double without a conversion instruction
+    double r = __longlong_as_double(((long long)(((br >> 23) & 0xff) - 127 + 1023) << 52) |
+                                    ((long long)(br & 0x7FFFFF) << 29));
+    double e = fma(-am, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-am, r, 1.0);
+    r = fma(r, e, r);
+    return __longlong_as_double(__double_as_longlong(r) | sign);
+}
+
 }  // namespace adpar

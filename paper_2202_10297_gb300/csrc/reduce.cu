@@ -297,7 +297,12 @@ __global__ void __launch_bounds__(kRedBlock) prod_adjoint_kernel(ReduceArgs A) {
                 double mi;
                 int64_t ei;
                 split_pow2((double)a[i], mi, ei);
-                c = ldexp_clamped(st.m * ym / mi, st.e + ye - ei);
+                if constexpr (sizeof(T) == 4) {  // FP32 result: FP32 arithmetic suffices
+                    const float q = (float)(st.m * ym) * __frcp_rn((float)mi);
+                    abar[i] = A.accumulate ? abar[i] + scale_pow2f(q, st.e + ye - ei) : scale_pow2f(q, st.e + ye - ei);
+                    continue;
+                }
+                c = scale_pow2(st.m * ym * recip_mantissa(mi), st.e + ye - ei);
             } else if (st.nz == 1 && i == st.first) {
                 c = ldexp_clamped(st.m * ym, st.e + ye);
             }

@@ -26,23 +26,40 @@ __device__ __forceinline__ int64_t ldi(const I* p, int64_t j) {
     return (int64_t)__ldcs(p + j);
 }
 
+// Four indices per thread per step: the four random reads (and then the
+// four random zeroing writes) are independent, so each thread keeps four
+// scattered accesses in flight instead of one dependent chain.
 template <class T, class I>
 __global__ void __launch_bounds__(kBlk) scatter_vjp_kernel(int64_t n, int64_t m, const I* is, T* ysbar,
                                                           T* vsbar, T* ys, const T* xs_saved, int accumulate) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += stride) {
-        const int64_t k = ldi(is, j);
-        T g = T(0);
-        const bool in = k >= 0 && k < n;
-        if (in) {
-            g = ysbar[k];
-            ysbar[k] = T(0);
-            if (ys) ys[k] = __ldcs(xs_saved + j);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * 4;
+    for (int64_t j0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * 4; j0 < m; j0 += stride) {
+        const int cnt = (int)(m - j0 < 4 ? m - j0 : 4);
+        int64_t k[4];
+        bool in[4];
+        T g[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            k[u] = u < cnt ? ldi(is, j0 + u) : -1;
+            in[u] = k[u] >= 0 && k[u] < n;
         }
-        if (accumulate) {
-            if (in) vsbar[j] += g;
-        } else {
-            __stcs(vsbar + j, g);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) g[u] = in[u] ? ysbar[k[u]] : T(0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (in[u]) {
+                ysbar[k[u]] = T(0);
+                if (ys) ys[k[u]] = __ldcs(xs_saved + j0 + u);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (u >= cnt) break;
+            if (accumulate) {
+                if (in[u]) vsbar[j0 + u] += g[u];
+            } else {
+                __stcs(vsbar + j0 + u, g[u]);
+            }
         }
     }
 }
@@ -195,7 +212,7 @@ extern "C" int adpar_vjp_scatter(int dtype, int64_t n, int64_t m, const void* is
         if (p && !aligned16(p)) return ADPAR_ERR_ALIGN;
     if (m == 0) return ADPAR_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((m + kBlk - 1) / kBlk, (int64_t)sm_count() * 8));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((m / 4 + kBlk) / kBlk, (int64_t)sm_count() * 8));
     const int acc = (flags & ADPAR_ACCUMULATE) ? 1 : 0;
     void* ys = restore ? ys_restore : nullptr;
 #define ADPAR_SCATTER(T, I)                                                                               \

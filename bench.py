@@ -29,6 +29,9 @@ JSON line each; these are measurements, not the headline line):
            plain calls
   serve    Poisson arrivals of mixed-operator requests sized 2^10..2^24:
            p50/p99 latency and throughput vs one call at a time
+  call     one entry point on a small case, --reps times (the profiling
+           driver: --call NAME, --log2n L), e.g.
+           python bench.py --workload call --call scan-linrec-f64 --log2n 24
 """
 import argparse
 import json
@@ -134,6 +137,21 @@ def dist_setup():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(value, dist=None, device=None):
+    """The maximum of a per-rank number over all ranks (the timing rule)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device or "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, max_ms, steps):
+    """Units processed by all ranks per second, timed by the slowest rank."""
+    return units_per_rank * world * steps / (max_ms / 1000.0)
 
 
 def make_inputs(scale_log2=0):
@@ -281,13 +299,9 @@ def run_adpar(args, ws, rank, local):
     t1.record(stream)
     barrier()
     clocks = clk.stop()
-    ms = t0.elapsed_time(t1)
-    if ws > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(t0.elapsed_time(t1), dist if ws > 1 else None, dev)
     el_step = sum(1 << c[3] for c in CALLS)
-    value = el_step * ws * args.steps / (ms / 1000.0)
+    value = whole_job_rate(el_step, ws, ms, args.steps)
 
     # per-call averages and the roofline of the dominant call
     hbm, peak_kind = measured_peaks()
@@ -351,12 +365,8 @@ def run_adpar(args, ws, rank, local):
         e2e_step()
     e.record(stream)
     barrier()
-    ems = s.elapsed_time(e)
-    if ws > 1:
-        tt = torch.tensor([ems], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ems = float(tt.item())
-    e2e = {"value": el_step * ws * e2e_steps / (ems / 1000.0), "unit": "elements/s",
+    ems = max_over_ranks(s.elapsed_time(e), dist if ws > 1 else None, dev)
+    e2e = {"value": whole_job_rate(el_step, ws, ems, e2e_steps), "unit": "elements/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps}
 
     # device status words: every bounded wait finished
@@ -653,8 +663,56 @@ def row_serve(args):
     return _line("serve", metric="served p50/p99 latency and throughput", budget_gib=32, slots=8, **out)
 
 
+def _one_call(name, log2n):
+    """A closure running one entry point on seeded synthetic inputs of 2^log2n elements."""
+    import torch
+    from paper_2202_10297_gb300 import adpar as A
+    from paper_2202_10297_gb300 import synth
+    n = 1 << log2n
+    if name.startswith("scan-"):
+        _, op, dt = name.split("-")
+        npdt = np.float64 if dt == "f64" else np.float32
+        if op == "linrec":
+            a, b, ya, yb = (_dev(v) for v in synth.linrec(n, npdt, seed=synth.SEED_BASE + 1))
+            return lambda: A.adpar_vjp_scan("linrec", a, ya, b=b, ybar_b=yb)
+        x = _dev(synth.normal(n, npdt, seed=synth.SEED_BASE + 1))
+        y = _dev(synth.normal(n, npdt, seed=synth.SEED_BASE + 11))
+        return lambda: A.adpar_vjp_scan(op, x, y)
+    if name == "kmeans":
+        X, Cm = synth.kmeans(n, 32, 256)
+        Xt, Ct = _dev(X), _dev(Cm)
+        return lambda: A.adpar_kmeans_vjp(Xt, Ct, ybar=1.0)
+    if name.startswith("hist-"):
+        op = name.split("-")[1]
+        vals, inds, hsbar = synth.hist(n, 256, "zipf", seed=synth.SEED_BASE + 2)
+        v, ix, hb = _dev(vals), _dev(inds), _dev(hsbar)
+        return lambda: A.adpar_vjp_hist(op, ix, 256, hb, vals=v)
+    if name == "prod-f64":
+        a = _dev(synth.prod_reduce(n, 0)[0])
+        return lambda: A.adpar_vjp_reduce("mul", a, 1.0)
+    if name == "scatter":
+        is_, ysbar, _ = synth.scatter(4 * n, n, seed=synth.SEED_BASE + 2)
+        it, yt = _dev(is_), _dev(ysbar)
+        return lambda: A.adpar_vjp_scatter(it, yt)
+    raise ValueError(name)
+
+
+CALLS_ONE = ("scan-linrec-f64", "scan-linrec-f32", "scan-add-f32", "scan-max-f32", "kmeans", "hist-mul",
+             "hist-max", "hist-add", "prod-f64", "scatter")
+
+
+def row_call(args):
+    """Runs one entry point --reps times on a small case (the ncu driver)."""
+    import torch
+    f = _one_call(args.call, args.log2n)
+    for _ in range(args.reps):
+        f()
+    torch.cuda.synchronize()
+    return _line("call", call=args.call, log2n=args.log2n, reps=args.reps)
+
+
 ROWS = {"prod": row_prod, "hist": row_hist, "scatter": row_scatter, "kmeans": row_kmeans, "batch": row_batch,
-        "serve": row_serve}
+        "serve": row_serve, "call": row_call}
 
 
 def main():
@@ -664,7 +722,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="adpar", choices=["adpar", "reference"])
     ap.add_argument("--workload", default="scan",
-                    choices=["scan", "prod", "hist", "scatter", "kmeans", "batch", "serve"])
+                    choices=["scan", "prod", "hist", "scatter", "kmeans", "batch", "serve", "call"])
+    ap.add_argument("--call", default="scan-linrec-f64", choices=sorted(CALLS_ONE))
+    ap.add_argument("--log2n", type=int, default=24)
+    ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":

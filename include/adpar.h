@@ -134,6 +134,13 @@ size_t adpar_workspace_size(int rule, adpar_opdesc desc, int64_t n, int64_t m);
  * (host pointer).  Returns ADPAR_ERR_CUDA if the read itself fails. */
 int adpar_workspace_status(const void *work, void *stream, int *device_status);
 
+/* Diagnostic of the failure detection (no counterpart in the paper):
+ * enqueues one kernel whose bounded wait on a flag that nothing sets runs
+ * out (after about a second), so adpar_workspace_status(work) then reports
+ * ADPAR_ERR_TIMEOUT while the CUDA context stays usable.  work: at least
+ * 512 bytes, 256-byte aligned. */
+int adpar_selftest_timeout(void *work, size_t work_bytes, void *stream);
+
 /* ------------------------------------------------------------------ */
 /* reduce (Sec. 5.1 and 5.1.1)                                         */
 /* ------------------------------------------------------------------ */

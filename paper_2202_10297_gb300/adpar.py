@@ -91,6 +91,7 @@ def _bind_optional(L):
         "adpar_kmeans_vjp": [C.c_int64, C.c_int, C.c_int, _VP, _VP, _VP, _VP, _VP, _VP, C.c_uint32, _VP,
                              C.c_size_t, _VP],
         "adpar_reduce": [OpDesc, C.c_int64, _VP, _VP, _VP, _VP, _VP, C.c_size_t, _VP],
+        "adpar_selftest_timeout": [_VP, C.c_size_t, _VP],
         "adpar_hist": [OpDesc, C.c_int64, C.c_int64, _VP, _VP, C.c_int, _VP, _VP, _VP, _VP, C.c_size_t, _VP],
         "adpar_scatter": [C.c_int, C.c_int64, C.c_int64, _VP, C.c_int, _VP, _VP, _VP, _VP],
         "adpar_map_acc": [C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int, _VP, _VP, C.c_int, _VP, _VP, _VP],
@@ -451,3 +452,11 @@ def adpar_map_acc(g, as_, is_, ws=None, width=1, stream=None):
                                                 _ptr(is_), _itype_code(is_), _ptr(ws), _ptr(xs),
                                                 _stream(stream)))
     return xs
+
+
+def adpar_selftest_timeout(work=None, stream=None):
+    """Run the bounded-wait timeout diagnostic; returns the workspace used."""
+    if work is None:
+        work = workspace(512)
+    _check("adpar_selftest_timeout", lib().adpar_selftest_timeout(_ptr(work), work.numel(), _stream(stream)))
+    return work

@@ -45,3 +45,21 @@ extern "C" int adpar_workspace_status(const void* work, void* stream, int* devic
     *device_status = (int)v;
     return ADPAR_OK;
 }
+
+namespace {
+__global__ void selftest_init_kernel(uint32_t* words) { words[threadIdx.x] = 0u; }
+// one bounded wait on a flag that nothing sets: it gives up after the
+// wait limit and records ADPAR_ERR_TIMEOUT in the workspace header
+__global__ void selftest_wait_kernel(adpar::WsHeader* hdr, const uint32_t* flag) {
+    if (threadIdx.x == 0) (void)adpar::wait_flag(flag, hdr);
+}
+}  // namespace
+
+extern "C" int adpar_selftest_timeout(void* work, size_t work_bytes, void* stream) {
+    if (!work || work_bytes < 512 || (reinterpret_cast<uintptr_t>(work) & 255u)) return ADPAR_ERR_WORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint32_t* w = static_cast<uint32_t*>(work);
+    selftest_init_kernel<<<1, 128, 0, s>>>(w);  // header and the flag word at byte 256
+    selftest_wait_kernel<<<1, 32, 0, s>>>(reinterpret_cast<adpar::WsHeader*>(w), w + 64);
+    return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
+}

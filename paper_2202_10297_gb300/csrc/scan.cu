@@ -20,6 +20,7 @@
 #include <algorithm>
 
 #include "scan_tiles.cuh"
+#include "tc.cuh"
 
 namespace adpar {
 namespace {
@@ -62,6 +63,94 @@ __global__ void __launch_bounds__(kScanBlock) scan_adjoint_kernel(ScanArgs A) {
     scan_adjoint_tile<Op, T, Cfg::K, Cfg::E, WYS>(A, (int64_t)s_tile);
 }
 
+
+// ------------------------------------------------ persistent adjoint pass
+// The adjoint pass as a persistent kernel: each block keeps kStages tiles in
+// a shared-memory ring, filled by bulk asynchronous copies (1D TMA) that
+// complete on one mbarrier per stage, so the next tiles' inputs stream in
+// while warp 0 waits in the look-back.  Tiles still come from the atomic
+// ticket in reverse order; a block processes its tickets in increasing
+// order, so the smallest unfinished tile is always being processed and the
+// look-back cannot deadlock.  The one partial tile (the first in reverse
+// order) is read straight from global memory.
+constexpr int kStages = 3;
+
+template <class Op, class T>
+struct Persist {
+    using Cfg = ScanCfg<Op, T>;
+    static constexpr int W = Op::kWidth;
+    static constexpr bool kNeedA = Op::kNeedPrimal || Op::kCoefNeedsPrimal || !Op::kCoefOne;
+    static constexpr int NA = W + (kNeedA ? W : 0);  // staged arrays: ya, [yb], [a], [b]
+    static constexpr uint32_t kArrBytes = (uint32_t)(Cfg::TILE * sizeof(T));
+    static constexpr uint32_t kStageBytes = NA * kArrBytes;
+    static constexpr uint32_t kSmem = kStages * kStageBytes;
+    static constexpr int kBlocksPerSm = (int)((200u * 1024u) / kSmem) > 0 ? (int)((200u * 1024u) / kSmem) : 1;
+};
+
+template <class Op, class T>
+__global__ void __launch_bounds__(kScanBlock) scan_adjoint_persistent_kernel(ScanArgs A) {
+    using Cfg = ScanCfg<Op, T>;
+    using PS = Persist<Op, T>;
+    constexpr int TILE = Cfg::TILE, W = Op::kWidth;
+    extern __shared__ __align__(128) unsigned char stage_raw[];
+    __shared__ __align__(8) uint64_t full[kStages];
+    __shared__ int64_t s_tick[kStages];
+    __shared__ int s_dummy;
+    const T* src[4];
+    int na = 0;
+    src[na++] = static_cast<const T*>(A.ya);
+    if constexpr (W == 2) src[na++] = static_cast<const T*>(A.yb);
+    if constexpr (PS::kNeedA) {
+        src[na++] = static_cast<const T*>(A.a);
+        if constexpr (W == 2) src[na++] = static_cast<const T*>(A.b);
+    }
+    auto issue = [&](int s) {  // thread 0: next ticket into stage s
+        const int64_t t = (int64_t)atomicAdd(&A.hdr->ticket[1], 1u);
+        s_tick[s] = t;
+        if (t >= A.tiles) return;
+        const int64_t tile = A.tiles - 1 - t;
+        if ((tile + 1) * TILE <= A.n) {
+            tc::mbar_arrive_expect_tx(&full[s], PS::kStageBytes);
+            for (int j = 0; j < PS::NA; ++j)
+                tc::bulk_load(stage_raw + (size_t)s * PS::kStageBytes + (size_t)j * PS::kArrBytes,
+                              src[j] + tile * TILE, PS::kArrBytes, &full[s]);
+        } else {
+            tc::mbar_arrive(&full[s]);  // partial tile: read from global memory
+        }
+    };
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) tc::mbar_init(&full[s], 1);
+        tc::fence_mbar_init();
+        for (int s = 0; s < kStages; ++s) issue(s);
+    }
+    s_dummy = 0;
+    __syncthreads();
+    volatile int* never = &s_dummy;
+    for (int i = 0;; ++i) {
+        const int s = i % kStages;
+        const int64_t t_log = s_tick[s];
+        if (t_log >= A.tiles) break;
+        const int64_t tile = A.tiles - 1 - t_log;
+        if (!tc::mbar_wait(&full[s], (uint32_t)((i / kStages) & 1), never)) record_status(A.hdr, ADPAR_ERR_TIMEOUT);
+        if ((tile + 1) * TILE <= A.n) {
+            const T* base = reinterpret_cast<const T*>(stage_raw + (size_t)s * PS::kStageBytes);
+            StagedTile<T> st{};
+            st.ya = base;
+            if constexpr (W == 2) st.yb = base + TILE;
+            if constexpr (PS::kNeedA) {
+                st.a = base + W * TILE;
+                if constexpr (W == 2) st.b = base + 3 * TILE;
+            }
+            scan_adjoint_tile<Op, T, Cfg::K, Cfg::E, false, true>(A, t_log, st);
+        } else {
+            scan_adjoint_tile<Op, T, Cfg::K, Cfg::E, false, false>(A, t_log);
+        }
+        __syncthreads();  // stage s and the tile's shared memory are free again
+        if (threadIdx.x == 0) issue(s);
+        __syncthreads();
+    }
+}
+
 // The forward operator itself (ys = scan (.) as), used as the primal
 // baseline of the VJP/primal time ratio.  One single pass with look-back.
 template <class Op, class T>
@@ -100,6 +189,20 @@ ScanLayout scan_layout(int64_t n) {
     return s;
 }
 
+// Opts the persistent kernel into its dynamic shared memory (once per
+// device); false if the device refuses, in which case the plain kernel runs.
+template <class Op, class T>
+bool persistent_ready() {
+    static int state[64] = {};  // 0 unknown, 1 ready, 2 refused
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    if (state[dev] == 0)
+        state[dev] = cudaFuncSetAttribute(scan_adjoint_persistent_kernel<Op, T>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)Persist<Op, T>::kSmem) == cudaSuccess ? 1 : 2;
+    return state[dev] == 1;
+}
+
 inline void set_slots(ScanArgs& A, char* w, const ScanLayout& L) {
     A.carry = w + L.off_carry;
     A.lbP_agg = reinterpret_cast<unsigned long long*>(w + L.off_pA);
@@ -136,8 +239,18 @@ int run_scan(int64_t n, const void* a, const void* b, const void* ya, const void
     const bool need_primal = Op::kNeedPrimal || Op::kCoefNeedsPrimal || ys_a != nullptr;
     launch_init(A, w, L, stream);
     if (need_primal) scan_primal_kernel<Op, T><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
-    if (ys_a) scan_adjoint_kernel<Op, T, true><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
-    else scan_adjoint_kernel<Op, T, false><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
+    if (ys_a) {
+        scan_adjoint_kernel<Op, T, true><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
+    } else if (sizeof(T) == 4 && A.tiles > 1 && persistent_ready<Op, T>()) {
+        using PS = Persist<Op, T>;
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t grid = std::min<int64_t>(A.tiles, (int64_t)sms * PS::kBlocksPerSm);
+        scan_adjoint_persistent_kernel<Op, T><<<(unsigned)grid, kScanBlock, PS::kSmem, stream>>>(A);
+    } else {
+        scan_adjoint_kernel<Op, T, false><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
+    }
     return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
 }
 

@@ -121,8 +121,36 @@ __device__ __forceinline__ void scan_primal_tile(const ScanArgs& A, int64_t tile
 }
 
 // ---------------------------------------------------------------- pass R
-template <class Op, class T, int K, int V, bool WYS>
-__device__ __forceinline__ void scan_adjoint_tile(const ScanArgs& A, int64_t t_log) {
+// A full tile's input arrays staged in shared memory (the persistent
+// kernel copies them there with bulk asynchronous copies): each array holds
+// the tile's TILE elements contiguously, in data order.
+template <class T>
+struct StagedTile {
+    const T* ya;
+    const T* yb;
+    const T* a;
+    const T* b;
+};
+
+template <int E, class T>
+__device__ __forceinline__ void load_smem_chunk(const T* p, int off, T (&out)[E]) {
+    constexpr int VV = Vec16<T>::N;
+#pragma unroll
+    for (int q = 0; q < E / VV; ++q) {
+        if constexpr (sizeof(T) == 4) {
+            const float4 x = *reinterpret_cast<const float4*>(p + off + q * VV);
+            out[q * VV + 0] = x.x; out[q * VV + 1] = x.y; out[q * VV + 2] = x.z; out[q * VV + 3] = x.w;
+        } else {
+            const double2 x = *reinterpret_cast<const double2*>(p + off + q * VV);
+            out[q * VV + 0] = x.x; out[q * VV + 1] = x.y;
+        }
+    }
+}
+
+// SMEM: the inputs of this (full) tile are read from the staged copy.
+template <class Op, class T, int K, int V, bool WYS, bool SMEM = false>
+__device__ __forceinline__ void scan_adjoint_tile(const ScanArgs& A, int64_t t_log,
+                                                  StagedTile<T> st = StagedTile<T>{}) {
     using P = typename Op::P;
     constexpr int NW = kScanBlock / 32, W = Op::kWidth, TILE = K * kScanBlock * V;
     using L = Lin<T, W, !Op::kCoefOne>;
@@ -146,12 +174,22 @@ __device__ __forceinline__ void scan_adjoint_tile(const ScanArgs& A, int64_t t_l
     T av[K][V], bv[K][V], yav[K][V], ybv[K][V];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const int64_t e = base + (int64_t)k * kScanBlock * V + threadIdx.x * V;
-        load_chunk(ya, e, A.n, T(0), yav[k]);
-        if constexpr (W == 2) load_chunk(yb, e, A.n, T(0), ybv[k]);
-        if constexpr (need_primal || !Op::kCoefOne) {
-            load_chunk(a, e, A.n, Op::pad_a(), av[k]);
-            if constexpr (W == 2) load_chunk(b, e, A.n, T(0), bv[k]);
+        if constexpr (SMEM) {
+            const int off = k * kScanBlock * V + threadIdx.x * V;
+            load_smem_chunk<V>(st.ya, off, yav[k]);
+            if constexpr (W == 2) load_smem_chunk<V>(st.yb, off, ybv[k]);
+            if constexpr (need_primal || !Op::kCoefOne) {
+                load_smem_chunk<V>(st.a, off, av[k]);
+                if constexpr (W == 2) load_smem_chunk<V>(st.b, off, bv[k]);
+            }
+        } else {
+            const int64_t e = base + (int64_t)k * kScanBlock * V + threadIdx.x * V;
+            load_chunk(ya, e, A.n, T(0), yav[k]);
+            if constexpr (W == 2) load_chunk(yb, e, A.n, T(0), ybv[k]);
+            if constexpr (need_primal || !Op::kCoefOne) {
+                load_chunk(a, e, A.n, Op::pad_a(), av[k]);
+                if constexpr (W == 2) load_chunk(b, e, A.n, T(0), bv[k]);
+            }
         }
     }
 

@@ -22,7 +22,10 @@
  *            flags has ADPAR_ACCUMULATE, in which case the contribution is
  *            added (x_bar += contribution), as in Eq. rewrite-adj (Sec. 2).
  * Recompute. Every rule re-executes the primal from its inputs (Sec. 4's
- *            redundant execution); no tape or saved intermediate is read.
+ *            redundant execution); nothing saved by an earlier call (no
+ *            tape) is read.  Within one call a pass may leave the
+ *            re-executed forward result in the workspace for the next
+ *            pass (the FP64 scan, see adpar_vjp_scan).
  * Errors.    Argument errors are detected on the host and returned before
  *            anything is enqueued.  Device-side give-ups (a bounded wait
  *            that ran out) are recorded in the workspace and read back with
@@ -72,6 +75,11 @@ typedef enum {
     ADPAR_RULE_MAP_ACC = 4,
     ADPAR_RULE_KMEANS = 5
 } adpar_rule;
+
+/* or'ed into the rule of adpar_workspace_size: the smallest workspace the
+ * call accepts instead of the size that runs it at full speed (the two
+ * differ only for the FP64 MUL and LINREC scans) */
+#define ADPAR_WS_MINIMAL 0x100
 
 typedef enum {
     ADPAR_OK = 0,
@@ -125,7 +133,8 @@ const char *adpar_version(void);
  * elements (m = number of bins for HIST, of destination elements for
  * SCATTER, of accumulator rows for MAP_ACC; for KMEANS n = points, m =
  * centroids).  Returns 0 when the rule needs none, and (size_t)-1 for an
- * invalid request. */
+ * invalid request.  With ADPAR_WS_MINIMAL or'ed into rule: the smallest
+ * size the call accepts. */
 size_t adpar_workspace_size(int rule, adpar_opdesc desc, int64_t n, int64_t m);
 
 /* Waits for `stream`, then reads the device-side status word that the
@@ -193,7 +202,14 @@ int adpar_vjp_reduce(adpar_opdesc desc, int64_t n, const void *a, const void *yb
  *   abar, bbar   [n] output adjoints (bbar only for LINREC).
  *   ys_a, ys_b   nullable [n]: the recomputed primal outputs.
  * Flags: ADPAR_ACCUMULATE.
- * Workspace: adpar_workspace_size(ADPAR_RULE_SCAN, desc, n, 0). */
+ * Workspace: adpar_workspace_size(ADPAR_RULE_SCAN, desc, n, 0).  For the
+ * F64 MUL and LINREC scans that size includes room for the re-executed
+ * forward result in factored form (each thread's local prefixes and its
+ * carry, about 8 * width bytes per element), which saves the return sweep
+ * a third of its FP64 arithmetic; any workspace of at least the
+ * ADPAR_WS_MINIMAL size is accepted, and with less than the full size the
+ * return sweep re-forms the primal prefixes itself (same results up to
+ * rounding). */
 int adpar_vjp_scan(adpar_opdesc desc, int64_t n, const void *a, const void *b,
                    const void *ybar_a, const void *ybar_b, void *abar, void *bbar,
                    void *ys_a, void *ys_b, uint32_t flags, void *work,

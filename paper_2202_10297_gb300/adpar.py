@@ -23,6 +23,7 @@ OPS = {"add": OP_ADD, "mul": OP_MUL, "min": OP_MIN, "max": OP_MAX, "linrec": OP_
 G_GATHER, G_SCALE, G_SQDIST_ROW = 0, 1, 2
 GFUNS = {"gather": G_GATHER, "scale": G_SCALE, "sqdist_row": G_SQDIST_ROW}
 RULE_REDUCE, RULE_SCAN, RULE_HIST, RULE_SCATTER, RULE_MAP_ACC, RULE_KMEANS = range(6)
+WS_MINIMAL = 0x100  # or'ed into a rule: the smallest accepted workspace
 ACCUMULATE, PROD_LOGDOMAIN, SCATTER_RESTORE = 0x1, 0x4, 0x8
 OK, ERR_TIMEOUT, ERR_TOO_LARGE = 0, 6, 7
 
@@ -186,9 +187,10 @@ def adpar_vjp_scan(op, a, ybar_a, b=None, ybar_b=None, abar=None, bbar=None, ys_
         abar = torch.empty_like(ref) if not accumulate else torch.zeros_like(ref)
     if w == 2 and bbar is None:
         bbar = torch.empty_like(ref) if not accumulate else torch.zeros_like(ref)
-    need = adpar_workspace_size(RULE_SCAN, opc, dt, n)
-    if work is None or work.numel() < need:
-        work = workspace(need, ref.device)
+    # a given workspace is used if it has at least the minimal size (the
+    # FP64 MUL/LINREC return sweep then re-forms the primal prefixes)
+    if work is None or work.numel() < adpar_workspace_size(RULE_SCAN | WS_MINIMAL, opc, dt, n):
+        work = workspace(adpar_workspace_size(RULE_SCAN, opc, dt, n), ref.device)
     for t in (a, b, ybar_b, abar, bbar, ys_a, ys_b):
         if t is not None and (t.dtype != ref.dtype or t.numel() != n):
             raise ValueError("all scan arrays must share dtype and length")
@@ -210,7 +212,7 @@ def adpar_scan(op, a, b=None, ys_a=None, ys_b=None, work=None, stream=None):
         ys_a = torch.empty_like(a)
     if w == 2 and ys_b is None:
         ys_b = torch.empty_like(a)
-    need = adpar_workspace_size(RULE_SCAN, opc, dt, n)
+    need = adpar_workspace_size(RULE_SCAN | WS_MINIMAL, opc, dt, n)  # the forward scan needs no more
     if work is None or work.numel() < need:
         work = workspace(need, a.device)
     st = lib().adpar_scan(OpDesc(opc, dt, w), n, _ptr(a), _ptr(b), _ptr(ys_a), _ptr(ys_b),

@@ -3,7 +3,7 @@
 #include "common.cuh"
 
 namespace adpar {
-size_t scan_workspace_size(adpar_opdesc d, int64_t n);
+size_t scan_workspace_size(adpar_opdesc d, int64_t n, bool minimal);
 size_t reduce_workspace_size(adpar_opdesc d);
 size_t hist_workspace_size(adpar_opdesc d, int64_t m);
 size_t kmeans_workspace_size(int64_t k);
@@ -26,9 +26,10 @@ extern "C" const char* adpar_status_string(int status) {
 extern "C" const char* adpar_version(void) { return "adpar 0.1 (sm_103a)"; }
 
 extern "C" size_t adpar_workspace_size(int rule, adpar_opdesc d, int64_t n, int64_t m) {
-    (void)m;
+    const bool minimal = (rule & ADPAR_WS_MINIMAL) != 0;
+    rule &= ~ADPAR_WS_MINIMAL;
     switch (rule) {
-    case ADPAR_RULE_SCAN: return adpar::scan_workspace_size(d, n);
+    case ADPAR_RULE_SCAN: return adpar::scan_workspace_size(d, n, minimal);
     case ADPAR_RULE_REDUCE: return n < 0 ? (size_t)-1 : adpar::reduce_workspace_size(d);
     case ADPAR_RULE_HIST: return n < 0 ? (size_t)-1 : adpar::hist_workspace_size(d, m);
     case ADPAR_RULE_KMEANS: return n < 0 ? (size_t)-1 : adpar::kmeans_workspace_size(m);

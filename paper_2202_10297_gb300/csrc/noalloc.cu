@@ -17,7 +17,7 @@
 #include "common.cuh"
 
 namespace adpar {
-size_t scan_workspace_size(adpar_opdesc d, int64_t n);
+size_t scan_workspace_size(adpar_opdesc d, int64_t n, bool minimal);
 }
 
 namespace {
@@ -56,7 +56,7 @@ extern "C" int adpar_vjp_scan_noalloc(adpar_opdesc d, int64_t n, const void* a, 
                                       void* ys_a, void* ys_b, uint32_t flags, void* stream) {
     // size first: a request beyond the static array is refused before any
     // pointer is looked at or anything is enqueued
-    const size_t need = adpar::scan_workspace_size(d, n);
+    const size_t need = adpar::scan_workspace_size(d, n, true);
     if (need == (size_t)-1) return ADPAR_ERR_INVALID;
     if (need > kNoAllocScratchBytes) return ADPAR_ERR_TOO_LARGE;
     void* scratch = nullptr;

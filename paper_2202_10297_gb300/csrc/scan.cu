@@ -20,7 +20,6 @@
 #include <algorithm>
 
 #include "scan_tiles.cuh"
-#include "tc.cuh"
 
 namespace adpar {
 namespace {
@@ -54,6 +53,24 @@ __global__ void __launch_bounds__(kScanBlock) scan_primal_kernel(ScanArgs A) {
     scan_primal_tile<Op, T, Cfg::K, Cfg::E>(A, (int64_t)s_tile);
 }
 
+template <class Op, class T>
+__global__ void __launch_bounds__(kScanBlock) scan_primal_fac_kernel(ScanArgs A) {
+    using Cfg = ScanCfg<Op, T>;
+    __shared__ uint32_t s_tile;
+    if (threadIdx.x == 0) s_tile = atomicAdd(&A.hdr->ticket[0], 1u);
+    __syncthreads();
+    scan_primal_fac_tile<Op, T, Cfg::K, Cfg::E>(A, (int64_t)s_tile);
+}
+
+template <class Op, class T, bool WYS>
+__global__ void __launch_bounds__(kScanBlock, 2) scan_adjoint_fac_kernel(ScanArgs A) {
+    using Cfg = ScanCfg<Op, T>;
+    __shared__ uint32_t s_tile;
+    if (threadIdx.x == 0) s_tile = atomicAdd(&A.hdr->ticket[1], 1u);
+    __syncthreads();
+    scan_adjoint_fac_tile<Op, T, Cfg::K, Cfg::E, WYS>(A, (int64_t)s_tile);
+}
+
 template <class Op, class T, bool WYS>
 __global__ void __launch_bounds__(kScanBlock) scan_adjoint_kernel(ScanArgs A) {
     using Cfg = ScanCfg<Op, T>;
@@ -63,93 +80,6 @@ __global__ void __launch_bounds__(kScanBlock) scan_adjoint_kernel(ScanArgs A) {
     scan_adjoint_tile<Op, T, Cfg::K, Cfg::E, WYS>(A, (int64_t)s_tile);
 }
 
-
-// ------------------------------------------------ persistent adjoint pass
-// The adjoint pass as a persistent kernel: each block keeps kStages tiles in
-// a shared-memory ring, filled by bulk asynchronous copies (1D TMA) that
-// complete on one mbarrier per stage, so the next tiles' inputs stream in
-// while warp 0 waits in the look-back.  Tiles still come from the atomic
-// ticket in reverse order; a block processes its tickets in increasing
-// order, so the smallest unfinished tile is always being processed and the
-// look-back cannot deadlock.  The one partial tile (the first in reverse
-// order) is read straight from global memory.
-constexpr int kStages = 3;
-
-template <class Op, class T>
-struct Persist {
-    using Cfg = ScanCfg<Op, T>;
-    static constexpr int W = Op::kWidth;
-    static constexpr bool kNeedA = Op::kNeedPrimal || Op::kCoefNeedsPrimal || !Op::kCoefOne;
-    static constexpr int NA = W + (kNeedA ? W : 0);  // staged arrays: ya, [yb], [a], [b]
-    static constexpr uint32_t kArrBytes = (uint32_t)(Cfg::TILE * sizeof(T));
-    static constexpr uint32_t kStageBytes = NA * kArrBytes;
-    static constexpr uint32_t kSmem = kStages * kStageBytes;
-    static constexpr int kBlocksPerSm = (int)((200u * 1024u) / kSmem) > 0 ? (int)((200u * 1024u) / kSmem) : 1;
-};
-
-template <class Op, class T>
-__global__ void __launch_bounds__(kScanBlock) scan_adjoint_persistent_kernel(ScanArgs A) {
-    using Cfg = ScanCfg<Op, T>;
-    using PS = Persist<Op, T>;
-    constexpr int TILE = Cfg::TILE, W = Op::kWidth;
-    extern __shared__ __align__(128) unsigned char stage_raw[];
-    __shared__ __align__(8) uint64_t full[kStages];
-    __shared__ int64_t s_tick[kStages];
-    __shared__ int s_dummy;
-    const T* src[4];
-    int na = 0;
-    src[na++] = static_cast<const T*>(A.ya);
-    if constexpr (W == 2) src[na++] = static_cast<const T*>(A.yb);
-    if constexpr (PS::kNeedA) {
-        src[na++] = static_cast<const T*>(A.a);
-        if constexpr (W == 2) src[na++] = static_cast<const T*>(A.b);
-    }
-    auto issue = [&](int s) {  // thread 0: next ticket into stage s
-        const int64_t t = (int64_t)atomicAdd(&A.hdr->ticket[1], 1u);
-        s_tick[s] = t;
-        if (t >= A.tiles) return;
-        const int64_t tile = A.tiles - 1 - t;
-        if ((tile + 1) * TILE <= A.n) {
-            tc::mbar_arrive_expect_tx(&full[s], PS::kStageBytes);
-            for (int j = 0; j < PS::NA; ++j)
-                tc::bulk_load(stage_raw + (size_t)s * PS::kStageBytes + (size_t)j * PS::kArrBytes,
-                              src[j] + tile * TILE, PS::kArrBytes, &full[s]);
-        } else {
-            tc::mbar_arrive(&full[s]);  // partial tile: read from global memory
-        }
-    };
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) tc::mbar_init(&full[s], 1);
-        tc::fence_mbar_init();
-        for (int s = 0; s < kStages; ++s) issue(s);
-    }
-    s_dummy = 0;
-    __syncthreads();
-    volatile int* never = &s_dummy;
-    for (int i = 0;; ++i) {
-        const int s = i % kStages;
-        const int64_t t_log = s_tick[s];
-        if (t_log >= A.tiles) break;
-        const int64_t tile = A.tiles - 1 - t_log;
-        if (!tc::mbar_wait(&full[s], (uint32_t)((i / kStages) & 1), never)) record_status(A.hdr, ADPAR_ERR_TIMEOUT);
-        if ((tile + 1) * TILE <= A.n) {
-            const T* base = reinterpret_cast<const T*>(stage_raw + (size_t)s * PS::kStageBytes);
-            StagedTile<T> st{};
-            st.ya = base;
-            if constexpr (W == 2) st.yb = base + TILE;
-            if constexpr (PS::kNeedA) {
-                st.a = base + W * TILE;
-                if constexpr (W == 2) st.b = base + 3 * TILE;
-            }
-            scan_adjoint_tile<Op, T, Cfg::K, Cfg::E, false, true>(A, t_log, st);
-        } else {
-            scan_adjoint_tile<Op, T, Cfg::K, Cfg::E, false, false>(A, t_log);
-        }
-        __syncthreads();  // stage s and the tile's shared memory are free again
-        if (threadIdx.x == 0) issue(s);
-        __syncthreads();
-    }
-}
 
 // The forward operator itself (ys = scan (.) as), used as the primal
 // baseline of the VJP/primal time ratio.  One single pass with look-back.
@@ -164,11 +94,18 @@ __global__ void __launch_bounds__(kScanBlock) scan_forward_kernel(ScanArgs A) {
 
 // ------------------------------------------------------------ host side
 struct ScanLayout {
-    size_t off_carry, off_slots, off_pA, off_pI, off_rA, off_rI, slot_words, total;
+    size_t off_carry, off_slots, off_pA, off_pI, off_rA, off_rI, slot_words, total_min;
+    size_t off_loc_a, off_loc_b, off_thc, total;
 };
 
+// The FP64 operators with J_left = a_i take the factored forward result
+// (scan_primal_fac_tile) when the workspace holds it.
+template <class Op, class T>
+constexpr bool kFactored = Op::kCoefIsA && sizeof(T) == 8;
+
 // header | carry[tiles] | look-back slots (primal agg, primal incl,
-// adjoint agg, adjoint incl), the slots contiguous so one kernel zeroes them
+// adjoint agg, adjoint incl), the slots contiguous so one kernel zeroes
+// them  [total_min]  | loc_a | loc_b | thread carries  [total]
 template <class Op, class T>
 ScanLayout scan_layout(int64_t n) {
     using Cfg = ScanCfg<Op, T>;
@@ -185,22 +122,17 @@ ScanLayout scan_layout(int64_t n) {
     s.off_rA = o; o += wr * 8;
     s.off_rI = o; o += wr * 8;
     s.slot_words = (o - s.off_slots) / 8;
-    s.total = round_up(o, 256);
+    s.total_min = round_up(o, 256);
+    o = s.total_min;
+    s.off_loc_a = s.off_loc_b = s.off_thc = 0;
+    if (kFactored<Op, T>) {
+        const size_t elems = tiles * (size_t)Cfg::TILE;
+        s.off_loc_a = o; o = round_up(o + elems * sizeof(T), 256);
+        if (Op::kWidth == 2) { s.off_loc_b = o; o = round_up(o + elems * sizeof(T), 256); }
+        s.off_thc = o; o = round_up(o + tiles * (size_t)Cfg::K * kScanBlock * sizeof(P), 256);
+    }
+    s.total = o;
     return s;
-}
-
-// Opts the persistent kernel into its dynamic shared memory (once per
-// device); false if the device refuses, in which case the plain kernel runs.
-template <class Op, class T>
-bool persistent_ready() {
-    static int state[64] = {};  // 0 unknown, 1 ready, 2 refused
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
-    if (state[dev] == 0)
-        state[dev] = cudaFuncSetAttribute(scan_adjoint_persistent_kernel<Op, T>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)Persist<Op, T>::kSmem) == cudaSuccess ? 1 : 2;
-    return state[dev] == 1;
 }
 
 inline void set_slots(ScanArgs& A, char* w, const ScanLayout& L) {
@@ -224,11 +156,11 @@ int run_scan(int64_t n, const void* a, const void* b, const void* ya, const void
              cudaStream_t stream) {
     using Cfg = ScanCfg<Op, T>;
     const ScanLayout L = scan_layout<Op, T>(n);
-    if (work == nullptr || work_bytes < L.total || (reinterpret_cast<uintptr_t>(work) & 255u))
+    if (work == nullptr || work_bytes < L.total_min || (reinterpret_cast<uintptr_t>(work) & 255u))
         return ADPAR_ERR_WORKSPACE;
     if (n == 0) return ADPAR_OK;
     char* w = static_cast<char*>(work);
-    ScanArgs A;
+    ScanArgs A{};
     A.n = n;
     A.a = a; A.b = b; A.ya = ya; A.yb = yb;
     A.abar = abar; A.bbar = bbar; A.ys_a = ys_a; A.ys_b = ys_b;
@@ -238,32 +170,35 @@ int run_scan(int64_t n, const void* a, const void* b, const void* ya, const void
     set_slots(A, w, L);
     const bool need_primal = Op::kNeedPrimal || Op::kCoefNeedsPrimal || ys_a != nullptr;
     launch_init(A, w, L, stream);
-    if (need_primal) scan_primal_kernel<Op, T><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
-    if (ys_a) {
-        scan_adjoint_kernel<Op, T, true><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
-    } else if (sizeof(T) == 4 && A.tiles > 1 && persistent_ready<Op, T>()) {
-        using PS = Persist<Op, T>;
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const int64_t grid = std::min<int64_t>(A.tiles, (int64_t)sms * PS::kBlocksPerSm);
-        scan_adjoint_persistent_kernel<Op, T><<<(unsigned)grid, kScanBlock, PS::kSmem, stream>>>(A);
-    } else {
-        scan_adjoint_kernel<Op, T, false><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
+    if constexpr (kFactored<Op, T>) {
+        if (work_bytes >= L.total) {
+            A.loc_a = w + L.off_loc_a;
+            A.loc_b = Op::kWidth == 2 ? w + L.off_loc_b : nullptr;
+            A.thr_carry = w + L.off_thc;
+            scan_primal_fac_kernel<Op, T><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
+            if (ys_a) scan_adjoint_fac_kernel<Op, T, true><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
+            else scan_adjoint_fac_kernel<Op, T, false><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
+            return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
+        }
     }
+    if (need_primal) scan_primal_kernel<Op, T><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
+    if (ys_a) scan_adjoint_kernel<Op, T, true><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
+    else scan_adjoint_kernel<Op, T, false><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
     return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
 }
 
 template <class T>
-size_t scan_ws_bytes(int op, int64_t n) {
+ScanLayout scan_layout_of(int op, int64_t n, bool& ok) {
+    ok = true;
     switch (op) {
-    case ADPAR_OP_ADD: return scan_layout<OpAdd<T>, T>(n).total;
-    case ADPAR_OP_MUL: return scan_layout<OpMul<T>, T>(n).total;
-    case ADPAR_OP_MIN: return scan_layout<OpMin<T>, T>(n).total;
-    case ADPAR_OP_MAX: return scan_layout<OpMax<T>, T>(n).total;
-    case ADPAR_OP_LINREC: return scan_layout<OpLinrec<T>, T>(n).total;
+    case ADPAR_OP_ADD: return scan_layout<OpAdd<T>, T>(n);
+    case ADPAR_OP_MUL: return scan_layout<OpMul<T>, T>(n);
+    case ADPAR_OP_MIN: return scan_layout<OpMin<T>, T>(n);
+    case ADPAR_OP_MAX: return scan_layout<OpMax<T>, T>(n);
+    case ADPAR_OP_LINREC: return scan_layout<OpLinrec<T>, T>(n);
     }
-    return (size_t)-1;
+    ok = false;
+    return ScanLayout{};
 }
 
 template <class T>
@@ -290,7 +225,7 @@ int run_scan_forward(int64_t n, const void* a, const void* b, void* ys_a, void* 
                      size_t work_bytes, cudaStream_t stream) {
     using Cfg = ScanCfg<Op, T>;
     const ScanLayout L = scan_layout<Op, T>(n);
-    if (work == nullptr || work_bytes < L.total || (reinterpret_cast<uintptr_t>(work) & 255u))
+    if (work == nullptr || work_bytes < L.total_min || (reinterpret_cast<uintptr_t>(work) & 255u))
         return ADPAR_ERR_WORKSPACE;
     if (n == 0) return ADPAR_OK;
     char* w = static_cast<char*>(work);
@@ -320,11 +255,16 @@ int dispatch_scan_forward(int op, int64_t n, const void* a, const void* b, void*
 
 }  // namespace
 
-size_t scan_workspace_size(adpar_opdesc d, int64_t n) {
+// minimal = false: the size that runs every pass at full speed (the
+// factored forward result included); minimal = true: the smallest accepted
+size_t scan_workspace_size(adpar_opdesc d, int64_t n, bool minimal) {
     if (n < 0) return (size_t)-1;
-    if (d.dtype == ADPAR_F32) return scan_ws_bytes<float>(d.op, n);
-    if (d.dtype == ADPAR_F64) return scan_ws_bytes<double>(d.op, n);
-    return (size_t)-1;
+    bool ok = false;
+    ScanLayout L{};
+    if (d.dtype == ADPAR_F32) L = scan_layout_of<float>(d.op, n, ok);
+    else if (d.dtype == ADPAR_F64) L = scan_layout_of<double>(d.op, n, ok);
+    if (!ok) return (size_t)-1;
+    return minimal ? L.total_min : L.total;
 }
 
 }  // namespace adpar

@@ -12,7 +12,11 @@
 //                    the width-2 LINREC element (its J_left is a_i * I).
 //   vjp_right(...)   J_right(i)^T rs_bar_i = the adjoint of as_i.
 // kNeedPrimal says whether vjp_right reads prev; kCoefNeedsPrimal whether
-// coef does (MIN/MAX: the tie rule compares against prev).
+// coef does (MIN/MAX: the tie rule compares against prev).  kCoefIsA says
+// that J_left(i) is the element's own a_i (MUL, LINREC): then the product
+// of the J_left factors over a run of elements is out_a of the run's
+// primal prefix, which the return sweep reuses instead of re-multiplying;
+// for these operators P is exactly (out_a, out_b) and pelem rebuilds it.
 // To add an operator, write one more struct of this shape.
 #pragma once
 
@@ -39,6 +43,7 @@ struct OpAdd {
     static constexpr bool kNeedPrimal = false;
     static constexpr bool kCoefNeedsPrimal = false;
     static constexpr bool kCoefOne = true;
+    static constexpr bool kCoefIsA = false;
     using P = ScalarP<T>;
     __device__ static P pid() { return {T(0)}; }
     __device__ static P pcomb(P l, P r) { return {l.v + r.v}; }
@@ -56,6 +61,7 @@ struct OpMul {
     static constexpr bool kNeedPrimal = true;
     static constexpr bool kCoefNeedsPrimal = false;
     static constexpr bool kCoefOne = false;
+    static constexpr bool kCoefIsA = true;
     using P = ScalarP<T>;
     __device__ static P pid() { return {T(1)}; }
     __device__ static P pcomb(P l, P r) { return {l.v * r.v}; }
@@ -74,6 +80,7 @@ struct OpMax {
     static constexpr bool kNeedPrimal = true;
     static constexpr bool kCoefNeedsPrimal = true;
     static constexpr bool kCoefOne = false;
+    static constexpr bool kCoefIsA = false;
     using P = ScalarP<T>;
     __device__ static P pid() { return {-pos_inf<T>()}; }
     __device__ static P pcomb(P l, P r) { return {r.v > l.v ? r.v : l.v}; }
@@ -93,6 +100,7 @@ struct OpMin {
     static constexpr bool kNeedPrimal = true;
     static constexpr bool kCoefNeedsPrimal = true;
     static constexpr bool kCoefOne = false;
+    static constexpr bool kCoefIsA = false;
     using P = ScalarP<T>;
     __device__ static P pid() { return {pos_inf<T>()}; }
     __device__ static P pcomb(P l, P r) { return {r.v < l.v ? r.v : l.v}; }
@@ -116,6 +124,7 @@ struct OpLinrec {
     static constexpr bool kNeedPrimal = true;
     static constexpr bool kCoefNeedsPrimal = false;
     static constexpr bool kCoefOne = false;
+    static constexpr bool kCoefIsA = true;
     using P = PairP<T>;
     __device__ static P pid() { return {T(1), T(0)}; }
     __device__ static P pcomb(P l, P r) { return {r.A * l.A, fma(r.A, l.B, r.B)}; }

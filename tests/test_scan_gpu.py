@@ -124,6 +124,43 @@ def test_primal_scan(A, oracle, op, dt):
         assert rel_l2(ya.cpu().numpy(), rya) < tol(dt, n)
 
 
+@pytest.mark.parametrize("op", ["mul", "linrec"])
+@pytest.mark.parametrize("n", [1, 2047, 2049, 3 * 2048 + 5, 4 * 4096 + 3, 100001])
+def test_fp64_factored_and_minimal_workspace_paths(A, oracle, op, n):
+    """FP64 MUL and LINREC read the factored forward result when the
+    workspace has room for it and re-form the primal prefixes in the return
+    sweep when it has only the minimal size: both match the oracle, with the
+    recomputed ys and with accumulation into existing adjoints."""
+    dt = np.float64
+    code = A.OPS[op]
+    if op == "linrec":
+        a, b, ya, yb = synth.linrec(n, dt, seed=n + 11)
+    else:
+        a, ya = inputs("mul", n, dt, seed=n + 11)
+        b = yb = None
+    base = synth.normal(n, dt, seed=12)
+    base_b = base[::-1].copy() if op == "linrec" else None
+    rab, rbb, rya, ryb = oracle.scan_vjp(op, a, ya, b, yb, abar=base, bbar=base_b)
+    full = A.adpar_workspace_size(A.RULE_SCAN, code, A.F64, n)
+    minimal = A.adpar_workspace_size(A.RULE_SCAN | A.WS_MINIMAL, code, A.F64, n)
+    assert full >= minimal + 8 * n
+    for nbytes in (full, minimal):
+        work = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        ab0 = dev(base)
+        bb0 = dev(base_b) if op == "linrec" else None
+        ysa = torch.empty(n, dtype=torch.float64, device="cuda")
+        ysb = torch.empty_like(ysa) if op == "linrec" else None
+        A.adpar_vjp_scan(op, dev(a), dev(ya), b=None if b is None else dev(b), ybar_b=None if yb is None else dev(yb),
+                         abar=ab0, bbar=bb0, ys_a=ysa, ys_b=ysb, accumulate=True, work=work)
+        torch.cuda.synchronize()
+        assert A.adpar_workspace_status(work) == A.OK
+        assert rel_l2(ab0.cpu().numpy(), rab) < 1e-12, (nbytes, rel_l2(ab0.cpu().numpy(), rab))
+        assert rel_l2(ysa.cpu().numpy(), rya) < 1e-12
+        if op == "linrec":
+            assert rel_l2(bb0.cpu().numpy(), rbb) < 1e-12
+            assert rel_l2(ysb.cpu().numpy(), ryb) < 1e-12
+
+
 def test_scan_zero_length_and_errors(A):
     e = torch.empty(0, device="cuda")
     ab, _, _ = A.adpar_vjp_scan("add", e, e)

@@ -80,4 +80,4 @@ def test_noalloc_refuses_sizes_beyond_static_scratch(A):
     # the largest benchmark-size scans fit
     for op, dt, n in ((A.OP_ADD, A.F32, 1 << 28), (A.OP_MAX, A.F32, 1 << 28),
                       (A.OP_LINREC, A.F64, 1 << 26), (A.OP_LINREC, A.F32, 1 << 26)):
-        assert A.adpar_workspace_size(A.RULE_SCAN, op, dt, n) <= A.adpar_noalloc_scratch_bytes()
+        assert A.adpar_workspace_size(A.RULE_SCAN | A.WS_MINIMAL, op, dt, n) <= A.adpar_noalloc_scratch_bytes()

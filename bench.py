@@ -64,6 +64,20 @@ CALLS = [
 # kernel launches of one call: init + (primal pass) + adjoint pass
 LAUNCHES = {"linrec": 3, "max": 3, "add": 2, "mul": 3, "min": 3}
 
+# FP64 arithmetic of the linear-recurrence VJP per pair, counted on the
+# sequential definition (an FMA is 2 flops): forward A_i = a_i A_{i-1} (1)
+# and B_i = a_i B_{i-1} + b_i (2); backward rs_bar = ybar + a_{i+1} rs_bar_{i+1}
+# for both components (4); abar_i = A_{i-1} rA_i + B_{i-1} rB_i (3).
+LINREC_FLOP_PER_PAIR = 10
+# FP64 peak of a GB300: 152 SMs x 2 FP64 FMA lanes per clock (one warp
+# instruction per 16 cycles per SM) x 2 flops x the maximum SM clock
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# DRAM bytes per call of the FP64 linear-recurrence VJP (init + primal pass +
+# adjoint pass), from the ncu capture at n = 2^24 scaled by 4 to 2^26
+# (traffic grows in proportion to n); the capture is summarised in
+# profiles/scan_linrec_f64_n2p24.md
+LINREC_F64_TRAFFIC_PER_CALL = None
+
 WORKLOAD = ("scan VJPs: linear-recurrence n=2^26 pairs FP32 and FP64 (a~U[0.9,1], b,ybar~N(0,1)); "
             "+ scan and max scan n=2^28 FP32 N(0,1)")
 
@@ -311,12 +325,22 @@ def run_adpar(args, ws, rank, local):
         n = 1 << lg
         per_call[name] = {"ms": float(t), "elements_per_s": n / (t / 1000.0),
                           "hbm_frac_of_measured": (vb * n / (t / 1000.0)) / (hbm * 1e9)}
+    f64 = per_call["linrec_f64"]
+    f64["fp64_tflops"] = LINREC_FLOP_PER_PAIR * (1 << LOG2_LINREC) / (f64["ms"] / 1000.0) / 1e12
+    f64["fp64_frac_of_derived_peak"] = f64["fp64_tflops"] / FP64_PEAK_TFLOPS
     dom = max(per_call, key=lambda k: per_call[k]["ms"])
     dcall = [c for c in CALLS if c[0] == dom][0]
-    ach = dcall[4] * (1 << dcall[3]) / (per_call[dom]["ms"] / 1000.0) / 1e9
-    roofline = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": None, "kernel": "adpar_vjp_scan(%s): init + primal pass + adjoint pass" % dom,
-                "peak_source": peak_kind}
+    kernel = "adpar_vjp_scan(%s): init + primal pass + adjoint pass" % dom
+    if dom == "linrec_f64":
+        # FP64 arithmetic, not HBM, bounds this call on GB300
+        roofline = {"bound": "alu", "achieved": f64["fp64_tflops"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": f64["fp64_frac_of_derived_peak"], "traffic": LINREC_F64_TRAFFIC_PER_CALL,
+                    "kernel": kernel, "peak_source": "derived (FP64 lanes x SMs x max SM clock)",
+                    "hbm_frac_of_measured": f64["hbm_frac_of_measured"]}
+    else:
+        ach = dcall[4] * (1 << dcall[3]) / (per_call[dom]["ms"] / 1000.0) / 1e9
+        roofline = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                    "traffic": None, "kernel": kernel, "peak_source": peak_kind}
 
     # primal (forward operator) times for the AD overhead ratio
     for name, op, dt, lg, vb, pb in CALLS:

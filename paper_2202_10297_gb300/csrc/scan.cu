@@ -53,22 +53,30 @@ __global__ void __launch_bounds__(kScanBlock) scan_primal_kernel(ScanArgs A) {
     scan_primal_tile<Op, T, Cfg::K, Cfg::E>(A, (int64_t)s_tile);
 }
 
-template <class Op, class T>
+// The factored path (FP64 operators with J_left = a_i): the return sweep's
+// tiles are kScanBlock runs of kFacV elements; the primal pass takes
+// kFacKP of them per tile (its carries keep the return sweep's indexing),
+// so it runs a quarter of the look-backs.  A.tiles is each kernel's own
+// tile count.
+constexpr int kFacKP = 4;
+constexpr int64_t kFacTile = (int64_t)kScanBlock * kFacV;
+
+template <class Op>
 __global__ void __launch_bounds__(kScanBlock) scan_primal_fac_kernel(ScanArgs A) {
-    using Cfg = ScanCfg<Op, T>;
     __shared__ uint32_t s_tile;
     if (threadIdx.x == 0) s_tile = atomicAdd(&A.hdr->ticket[0], 1u);
     __syncthreads();
-    scan_primal_fac_tile<Op, T, Cfg::K, Cfg::E>(A, (int64_t)s_tile);
+    scan_primal_fac_tile<Op, kFacKP>(A, (int64_t)s_tile);
 }
 
-template <class Op, class T, bool WYS>
-__global__ void __launch_bounds__(kScanBlock, 2) scan_adjoint_fac_kernel(ScanArgs A) {
-    using Cfg = ScanCfg<Op, T>;
+// 3 resident blocks per SM for the pair operator, 4 for width 1 (the
+// register caps where neither spills much)
+template <class Op, bool WYS>
+__global__ void __launch_bounds__(kScanBlock, Op::kWidth == 2 ? 3 : 4) scan_adjoint_fac_kernel(ScanArgs A) {
     __shared__ uint32_t s_tile;
     if (threadIdx.x == 0) s_tile = atomicAdd(&A.hdr->ticket[1], 1u);
     __syncthreads();
-    scan_adjoint_fac_tile<Op, T, Cfg::K, Cfg::E, WYS>(A, (int64_t)s_tile);
+    scan_adjoint_fac_tile<Op, WYS>(A, (int64_t)s_tile);
 }
 
 template <class Op, class T, bool WYS>
@@ -125,11 +133,16 @@ ScanLayout scan_layout(int64_t n) {
     s.total_min = round_up(o, 256);
     o = s.total_min;
     s.off_loc_a = s.off_loc_b = s.off_thc = 0;
-    if (kFactored<Op, T>) {
-        const size_t elems = tiles * (size_t)Cfg::TILE;
+    if constexpr (kFactored<Op, T>) {
+        // padded to whole tiles of the factored primal pass; its look-back
+        // slots fit in those above (fewer, no larger tiles)
+        static_assert(kFacTile >= Cfg::TILE, "factored tiles are no smaller");
+        const size_t ftiles = (size_t)((n + kFacTile - 1) / kFacTile);
+        const size_t ptiles = round_up(ftiles, (size_t)kFacKP);
+        const size_t elems = ptiles * (size_t)kFacTile;
         s.off_loc_a = o; o = round_up(o + elems * sizeof(T), 256);
         if (Op::kWidth == 2) { s.off_loc_b = o; o = round_up(o + elems * sizeof(T), 256); }
-        s.off_thc = o; o = round_up(o + tiles * (size_t)Cfg::K * kScanBlock * sizeof(P), 256);
+        s.off_thc = o; o = round_up(o + ptiles * (size_t)kScanBlock * sizeof(P), 256);
     }
     s.total = o;
     return s;
@@ -175,9 +188,12 @@ int run_scan(int64_t n, const void* a, const void* b, const void* ya, const void
             A.loc_a = w + L.off_loc_a;
             A.loc_b = Op::kWidth == 2 ? w + L.off_loc_b : nullptr;
             A.thr_carry = w + L.off_thc;
-            scan_primal_fac_kernel<Op, T><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
-            if (ys_a) scan_adjoint_fac_kernel<Op, T, true><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
-            else scan_adjoint_fac_kernel<Op, T, false><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
+            A.tiles = (n + kFacTile - 1) / kFacTile;
+            ScanArgs AP = A;
+            AP.tiles = (A.tiles + kFacKP - 1) / kFacKP;
+            scan_primal_fac_kernel<Op><<<(unsigned)AP.tiles, kScanBlock, 0, stream>>>(AP);
+            if (ys_a) scan_adjoint_fac_kernel<Op, true><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
+            else scan_adjoint_fac_kernel<Op, false><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
             return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
         }
     }

@@ -319,20 +319,68 @@ __device__ __forceinline__ void scan_adjoint_tile(const ScanArgs& A, int64_t t_l
 // ------------------------------------------ factored forward result (FP64)
 // For operators whose J_left is the element's own a_i (kCoefIsA) the primal
 // pass can hand the return sweep the forward scan result ys that the VJP of
-// Sec. 5.2 reads, in factored form: for each thread and chunk, its local
-// inclusive prefixes l_j = as_0 (.) ... (.) as_j of its V elements (started
-// from the neutral element; out_a and out_b stored per element) and its
+// Sec. 5.2 reads, in factored form: for each thread's run of kFacV elements,
+// its local inclusive prefixes l_j = as_0 (.) ... (.) as_j (started from the
+// neutral element; out_a and out_b stored per element) and the run's
 // exclusive carry c, so that ys_j = c (.) l_j.  The return sweep then runs
 // neither the primal fold nor the primal block scan, and out_a(l_j) is the
 // product c_0 ... c_j of J_left factors its reverse aggregate needs.  This
 // trades 2 W sizeof(T) bytes per element of traffic for about a third of the
 // FP64 operations, which pays where FP64 arithmetic, not HBM, is the bound.
-template <class Op, class T, int K, int V>
+//
+// Tiles of the return sweep are kScanBlock runs of kFacV = 16 elements; a
+// run is handled in groups of kFacG = 4 so that few registers stay live.
+constexpr int kFacV = 16;
+constexpr int kFacG = 4;
+
+// L2 policies for data that a tile reads twice: kept on the first read,
+// dropped on the second
+__device__ __forceinline__ uint64_t l2_policy_keep() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_drop() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+// E consecutive doubles at p + e (16-byte aligned) under an L2 policy; past
+// n the values are `pad`
+template <int E>
+__device__ __forceinline__ void load_run_pol(const double* p, int64_t e, int64_t n, double pad, double (&out)[E],
+                                             uint64_t pol) {
+    static_assert(E % 2 == 0, "whole 16-byte vectors");
+    if (e + E <= n) {
+#pragma unroll
+        for (int q = 0; q < E / 2; ++q)
+            asm volatile("ld.global.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;"
+                         : "=d"(out[2 * q]), "=d"(out[2 * q + 1])
+                         : "l"(p + e + 2 * q), "l"(pol));
+    } else {
+#pragma unroll
+        for (int j = 0; j < E; ++j) out[j] = (e + j < n) ? p[e + j] : pad;
+    }
+}
+// pulls the 128-byte lines holding p[e, e + E) into L2 (no registers used)
+template <int E>
+__device__ __forceinline__ void prefetch_run_l2(const double* p, int64_t e, int64_t n) {
+    if (e >= n) return;
+    const int64_t last = (e + E <= n ? e + E : n) - 1;
+    asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(p + e));
+    asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(p + last));
+}
+
+// Primal pass: KC runs per thread (KC kFacV-runs of consecutive threads
+// make one tile of KC * kScanBlock * kFacV elements); stores the local
+// prefixes and each run's carry, indexed by the return sweep's tiles.
+template <class Op, int KC>
 __device__ __forceinline__ void scan_primal_fac_tile(const ScanArgs& A, int64_t tile) {
+    using T = double;
     using P = typename Op::P;
-    constexpr int NW = kScanBlock / 32, W = Op::kWidth, TILE = K * kScanBlock * V;
+    constexpr int NW = kScanBlock / 32, W = Op::kWidth, V = kFacV, G = kFacG, TILE = KC * kScanBlock * V;
     static_assert(Op::kCoefIsA, "factored form is for J_left = a_i operators");
-    __shared__ P s_tot[K * NW];
+    __shared__ P s_tot[KC * NW];
     __shared__ P s_pre;
     const int64_t base = tile * TILE;
     const int64_t padded = A.tiles * TILE;
@@ -341,33 +389,34 @@ __device__ __forceinline__ void scan_primal_fac_tile(const ScanArgs& A, int64_t 
     T* la = static_cast<T*>(A.loc_a);
     T* lb = static_cast<T*>(A.loc_b);
 
-    P agg[K];
+    P agg[KC];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
+    for (int k = 0; k < KC; ++k) {
         const int64_t e = base + (int64_t)k * kScanBlock * V + threadIdx.x * V;
-        T av[V], bv[V], oa[V], ob[V];
-        load_chunk_keep(a, e, A.n, Op::pad_a(), av);
-        if constexpr (W == 2) load_chunk_keep(b, e, A.n, T(0), bv);
-        else {
+        P acc = Op::pid();
 #pragma unroll
-            for (int j = 0; j < V; ++j) bv[j] = T(0);
-        }
-        P acc = Op::pelem(av[0], bv[0]);
-        oa[0] = Op::out_a(acc);
-        ob[0] = Op::out_b(acc);
+        for (int g = 0; g < V / G; ++g) {
+            T av[G], bv[G], oa[G], ob[G];
+            load_chunk_keep(a, e + g * G, A.n, Op::pad_a(), av);
+            if constexpr (W == 2) load_chunk_keep(b, e + g * G, A.n, T(0), bv);
+            else {
 #pragma unroll
-        for (int j = 1; j < V; ++j) {
-            acc = Op::pcomb(acc, Op::pelem(av[j], bv[j]));
-            oa[j] = Op::out_a(acc);
-            ob[j] = Op::out_b(acc);
+                for (int j = 0; j < G; ++j) bv[j] = T(0);
+            }
+#pragma unroll
+            for (int j = 0; j < G; ++j) {
+                acc = (g == 0 && j == 0) ? Op::pelem(av[j], bv[j]) : Op::pcomb(acc, Op::pelem(av[j], bv[j]));
+                oa[j] = Op::out_a(acc);
+                ob[j] = Op::out_b(acc);
+            }
+            store_chunk(la, e + g * G, padded, oa);
+            if constexpr (W == 2) store_chunk(lb, e + g * G, padded, ob);
         }
-        store_chunk(la, e, padded, oa);
-        if constexpr (W == 2) store_chunk(lb, e, padded, ob);
         agg[k] = acc;
     }
     auto comb = [](const P& l, const P& r) { return Op::pcomb(l, r); };
-    P wex[K];
-    P total = block_scan_part1<P, false, K, NW>(agg, wex, s_tot, Op::pid(), comb);
+    P wex[KC];
+    P total = block_scan_part1<P, false, KC, NW>(agg, wex, s_tot, Op::pid(), comb);
     if ((threadIdx.x >> 5) == 0) {
         LookbackState<P> st{A.lbP_agg, A.lbP_incl};
         P prefix = lookback(tile, st, total, Op::pid(), comb, A.hdr);
@@ -376,112 +425,142 @@ __device__ __forceinline__ void scan_primal_fac_tile(const ScanArgs& A, int64_t 
     __syncthreads();
     P* thc = static_cast<P*>(A.thr_carry);
 #pragma unroll
-    for (int k = 0; k < K; ++k)
-        thc[(tile * K + k) * kScanBlock + threadIdx.x] = block_scan_excl<P, false, K, NW>(k, wex, s_tot, s_pre, comb);
+    for (int k = 0; k < KC; ++k)
+        thc[(tile * KC + k) * kScanBlock + threadIdx.x] = block_scan_excl<P, false, KC, NW>(k, wex, s_tot, s_pre, comb);
 }
 
-// The return sweep on the factored forward result.  Per element it reads
-// a_i (its J_left factor), ybar_i and the local prefix l_i; the reverse
-// aggregate of a thread's run is x -> sum_j out_a(l_j) ybar_j + out_a(l_last) x,
-// and rs_{i-1} = c (.) l_{i-1} (c itself for the run's first element) is
-// what J_right(i)^T needs.  Same outputs as scan_adjoint_tile.
-template <class Op, class T, int K, int V, bool WYS>
+// The return sweep on the factored forward result, one kFacV-run per
+// thread.  Phase 1 streams the run's local prefixes and cotangents to form
+// its reverse aggregate  x -> sum_j out_a(l_j) ybar_j + out_a(l_last) x
+// (loads kept in L2; a and l_b are prefetched into L2).  After the block
+// scan and look-back, phase 2 re-reads the run from L2 in groups of kFacG,
+// right to left: rs_bar_j = ybar_j + a_{j+1} rs_bar_{j+1}, and with
+// rs_{j-1} = c (.) l_{j-1} (c itself for the run's first element) the
+// adjoint J_right(j)^T rs_bar_j.  Same outputs as scan_adjoint_tile.
+template <class Op, bool WYS>
 __device__ __forceinline__ void scan_adjoint_fac_tile(const ScanArgs& A, int64_t t_log) {
+    using T = double;
     using P = typename Op::P;
-    constexpr int NW = kScanBlock / 32, W = Op::kWidth, TILE = K * kScanBlock * V;
+    constexpr int NW = kScanBlock / 32, W = Op::kWidth, V = kFacV, G = kFacG, TILE = kScanBlock * V;
     using L = Lin<T, W, true>;
     static_assert(Op::kCoefIsA, "factored form is for J_left = a_i operators");
-    __shared__ L s_totR[K * NW];
+    __shared__ L s_totR[NW];
     __shared__ L s_prefR;
 
     const int64_t tile = A.tiles - 1 - t_log;  // data tile (t_log counts from the right)
-    const int64_t base = tile * TILE;
+    const int64_t e0 = tile * TILE + threadIdx.x * V;
     const int64_t padded = A.tiles * TILE;
     const T* a = static_cast<const T*>(A.a);
     const T* ya = static_cast<const T*>(A.ya);
     const T* yb = static_cast<const T*>(A.yb);
     const T* la = static_cast<const T*>(A.loc_a);
     const T* lb = static_cast<const T*>(A.loc_b);
-    const P* thc = static_cast<const P*>(A.thr_carry);
+    const uint64_t keep = l2_policy_keep();
 
-    T av[K][V], yav[K][V], ybv[K][V], lav[K][V], lbv[K][V];
-    P carry[K];
-    L aggR[K];
+    // ---- phase 1: the run's reverse aggregate
+    prefetch_run_l2<V>(a, e0, A.n);
+    if constexpr (W == 2) prefetch_run_l2<V>(lb, e0, padded);
+    L agg[1];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int64_t e = base + (int64_t)k * kScanBlock * V + threadIdx.x * V;
-        load_chunk(ya, e, A.n, T(0), yav[k]);
-        if constexpr (W == 2) load_chunk(yb, e, A.n, T(0), ybv[k]);
-        load_chunk(a, e, A.n, Op::pad_a(), av[k]);
-        load_chunk(la, e, padded, T(0), lav[k]);
-        if constexpr (W == 2) load_chunk(lb, e, padded, T(0), lbv[k]);
-        carry[k] = thc[(tile * K + k) * kScanBlock + threadIdx.x];
-    }
+    for (int i = 0; i < W; ++i) agg[0].d[i] = T(0);
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        aggR[k].d[0] = lav[k][0] * yav[k][0];
-        if constexpr (W == 2) aggR[k].d[1] = lav[k][0] * ybv[k][0];
+    for (int g = 0; g < V / G; ++g) {
+        T lv[G], y1[G], y2[G];
+        load_run_pol(la, e0 + g * G, padded, T(0), lv, keep);
+        load_run_pol(ya, e0 + g * G, A.n, T(0), y1, keep);
+        if constexpr (W == 2) load_run_pol(yb, e0 + g * G, A.n, T(0), y2, keep);
 #pragma unroll
-        for (int j = 1; j < V; ++j) {
-            aggR[k].d[0] = fma(lav[k][j], yav[k][j], aggR[k].d[0]);
-            if constexpr (W == 2) aggR[k].d[1] = fma(lav[k][j], ybv[k][j], aggR[k].d[1]);
+        for (int j = 0; j < G; ++j) {
+            agg[0].d[0] = fma(lv[j], y1[j], agg[0].d[0]);
+            if constexpr (W == 2) agg[0].d[1] = fma(lv[j], y2[j], agg[0].d[1]);
         }
-        aggR[k].c = lav[k][V - 1];
+        if (g == V / G - 1) agg[0].c = lv[G - 1];
     }
     auto lc = [](const L& e, const L& l) { return L::comb(e, l); };
-    L wexR[K];
-    L totR = block_scan_part1<L, true, K, NW>(aggR, wexR, s_totR, L::id(), lc);
+    L wexR[1];
+    L totR = block_scan_part1<L, true, 1, NW>(agg, wexR, s_totR, L::id(), lc);
     if ((threadIdx.x >> 5) == 0) {
         LookbackState<L> st{A.lbR_agg, A.lbR_incl};
         L pre = lookback(t_log, st, totR, L::id(), lc, A.hdr);
         if ((threadIdx.x & 31) == 0) s_prefR = pre;
     }
     __syncthreads();
+    if (e0 >= A.n) return;  // no barrier follows
 
+    // ---- phase 2: outputs, groups right to left
+    const uint64_t drop = l2_policy_drop();
+    const L ex = block_scan_excl<L, true, 1, NW>(0, wexR, s_totR, s_prefR, lc);
+    const P carry = static_cast<const P*>(A.thr_carry)[tile * kScanBlock + threadIdx.x];
     T* abar = static_cast<T*>(A.abar);
     T* bbar = static_cast<T*>(A.bbar);
+    T a_up = T(1), r_upA = ex.d[0], r_upB = ex.d[W - 1];  // rs_bar of the run's right neighbour is ex.d
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int64_t e = base + (int64_t)k * kScanBlock * V + threadIdx.x * V;
-        if (e >= A.n) continue;
-        const L ex = block_scan_excl<L, true, K, NW>(k, wexR, s_totR, s_prefR, lc);
-        yav[k][V - 1] += ex.d[0];
-        if constexpr (W == 2) ybv[k][V - 1] += ex.d[W - 1];
+    for (int g = V / G - 1; g >= 0; --g) {
+        const int64_t e = e0 + g * G;
+        T av[G], y1[G], y2[G], lv[G], lw[G];
+        load_run_pol(a, e, A.n, Op::pad_a(), av, drop);
+        load_run_pol(ya, e, A.n, T(0), y1, drop);
+        load_run_pol(la, e, padded, T(0), lv, drop);
+        if constexpr (W == 2) {
+            load_run_pol(yb, e, A.n, T(0), y2, drop);
+            load_run_pol(lb, e, padded, T(0), lw, drop);
+        } else {
 #pragma unroll
-        for (int j = V - 1; j > 0; --j) {
-            yav[k][j - 1] = fma(av[k][j], yav[k][j], yav[k][j - 1]);
-            if constexpr (W == 2) ybv[k][j - 1] = fma(av[k][j], ybv[k][j], ybv[k][j - 1]);
+            for (int j = 0; j < G; ++j) y2[j] = lw[j] = T(0);
         }
-        T y1[V], y2[V];
+        // l_{j-1} of the group's first element: the previous group's last
+        T lpA = T(1), lpB = T(0);
+        if (g > 0) {
+            lpA = la[e - 1];
+            if constexpr (W == 2) lpB = lb[e - 1];
+        }
+        // rs_bar, right to left (the run's last element adds the carry ex.d)
 #pragma unroll
-        for (int j = 0; j < V; ++j) {
-            const P prev = j == 0 ? carry[k]
-                                  : Op::pcomb(carry[k], Op::pelem(lav[k][j - 1], W == 2 ? lbv[k][j - 1] : T(0)));
-            T o1 = T(0), o2 = T(0);
-            Op::vjp_right(prev, av[k][j], T(0), yav[k][j], W == 2 ? ybv[k][j] : T(0), o1, o2);
-            if constexpr (WYS) {
-                const P inc = Op::pcomb(carry[k], Op::pelem(lav[k][j], W == 2 ? lbv[k][j] : T(0)));
-                y1[j] = Op::out_a(inc);
-                y2[j] = Op::out_b(inc);
+        for (int j = G - 1; j >= 0; --j) {
+            if (g == V / G - 1 && j == G - 1) {
+                y1[j] += r_upA;
+                if constexpr (W == 2) y2[j] += r_upB;
+            } else {
+                const T c = j == G - 1 ? a_up : av[j + 1];
+                y1[j] = fma(c, j == G - 1 ? r_upA : y1[j + 1], y1[j]);
+                if constexpr (W == 2) y2[j] = fma(c, j == G - 1 ? r_upB : y2[j + 1], y2[j]);
             }
-            av[k][j] = o1;
+        }
+        a_up = av[0];
+        r_upA = y1[0];
+        r_upB = y2[0];
+        T o1v[G], ysa[G], ysb[G];
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            P prev;
+            if (g == 0 && j == 0) prev = carry;
+            else if (j == 0) prev = Op::pcomb(carry, Op::pelem(lpA, lpB));
+            else prev = Op::pcomb(carry, Op::pelem(lv[j - 1], lw[j - 1]));
+            T o1 = T(0), o2 = T(0);
+            Op::vjp_right(prev, av[j], T(0), y1[j], y2[j], o1, o2);
+            o1v[j] = o1;
+            if constexpr (WYS) {
+                const P inc = Op::pcomb(carry, Op::pelem(lv[j], lw[j]));
+                ysa[j] = Op::out_a(inc);
+                ysb[j] = Op::out_b(inc);
+            }
         }
         if (A.accumulate) {
-            T old[V];
+            T old[G];
             load_chunk_keep(static_cast<const T*>(A.abar), e, A.n, T(0), old);
 #pragma unroll
-            for (int j = 0; j < V; ++j) av[k][j] += old[j];
+            for (int j = 0; j < G; ++j) o1v[j] += old[j];
             if constexpr (W == 2) {
                 load_chunk_keep(static_cast<const T*>(A.bbar), e, A.n, T(0), old);
 #pragma unroll
-                for (int j = 0; j < V; ++j) ybv[k][j] += old[j];
+                for (int j = 0; j < G; ++j) y2[j] += old[j];
             }
         }
-        store_chunk(abar, e, A.n, av[k]);
-        if constexpr (W == 2) store_chunk(bbar, e, A.n, ybv[k]);
+        store_chunk(abar, e, A.n, o1v);
+        if constexpr (W == 2) store_chunk(bbar, e, A.n, y2);
         if constexpr (WYS) {
-            store_chunk(static_cast<T*>(A.ys_a), e, A.n, y1);
-            if constexpr (W == 2) store_chunk(static_cast<T*>(A.ys_b), e, A.n, y2);
+            store_chunk(static_cast<T*>(A.ys_a), e, A.n, ysa);
+            if constexpr (W == 2) store_chunk(static_cast<T*>(A.ys_b), e, A.n, ysb);
         }
     }
 }

@@ -362,15 +362,6 @@ __device__ __forceinline__ void load_run_pol(const double* p, int64_t e, int64_t
         for (int j = 0; j < E; ++j) out[j] = (e + j < n) ? p[e + j] : pad;
     }
 }
-// pulls the 128-byte lines holding p[e, e + E) into L2 (no registers used)
-template <int E>
-__device__ __forceinline__ void prefetch_run_l2(const double* p, int64_t e, int64_t n) {
-    if (e >= n) return;
-    const int64_t last = (e + E <= n ? e + E : n) - 1;
-    asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(p + e));
-    asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(p + last));
-}
-
 // Primal pass: KC runs per thread (KC kFacV-runs of consecutive threads
 // make one tile of KC * kScanBlock * kFacV elements); stores the local
 // prefixes and each run's carry, indexed by the return sweep's tiles.
@@ -392,26 +383,25 @@ __device__ __forceinline__ void scan_primal_fac_tile(const ScanArgs& A, int64_t 
     P agg[KC];
 #pragma unroll
     for (int k = 0; k < KC; ++k) {
+        // the whole run is loaded before any of it is stored, so its loads
+        // are all in flight at once
         const int64_t e = base + (int64_t)k * kScanBlock * V + threadIdx.x * V;
-        P acc = Op::pid();
+        T av[V], bv[V];
+        load_chunk_keep(a, e, A.n, Op::pad_a(), av);
+        if constexpr (W == 2) load_chunk_keep(b, e, A.n, T(0), bv);
+        else {
 #pragma unroll
-        for (int g = 0; g < V / G; ++g) {
-            T av[G], bv[G], oa[G], ob[G];
-            load_chunk_keep(a, e + g * G, A.n, Op::pad_a(), av);
-            if constexpr (W == 2) load_chunk_keep(b, e + g * G, A.n, T(0), bv);
-            else {
-#pragma unroll
-                for (int j = 0; j < G; ++j) bv[j] = T(0);
-            }
-#pragma unroll
-            for (int j = 0; j < G; ++j) {
-                acc = (g == 0 && j == 0) ? Op::pelem(av[j], bv[j]) : Op::pcomb(acc, Op::pelem(av[j], bv[j]));
-                oa[j] = Op::out_a(acc);
-                ob[j] = Op::out_b(acc);
-            }
-            store_chunk(la, e + g * G, padded, oa);
-            if constexpr (W == 2) store_chunk(lb, e + g * G, padded, ob);
+            for (int j = 0; j < V; ++j) bv[j] = T(0);
         }
+        P acc = Op::pelem(av[0], bv[0]);
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            if (j > 0) acc = Op::pcomb(acc, Op::pelem(av[j], bv[j]));
+            av[j] = Op::out_a(acc);  // the local prefix replaces the input
+            bv[j] = Op::out_b(acc);
+        }
+        store_chunk(la, e, padded, av);
+        if constexpr (W == 2) store_chunk(lb, e, padded, bv);
         agg[k] = acc;
     }
     auto comb = [](const P& l, const P& r) { return Op::pcomb(l, r); };
@@ -432,7 +422,7 @@ __device__ __forceinline__ void scan_primal_fac_tile(const ScanArgs& A, int64_t 
 // The return sweep on the factored forward result, one kFacV-run per
 // thread.  Phase 1 streams the run's local prefixes and cotangents to form
 // its reverse aggregate  x -> sum_j out_a(l_j) ybar_j + out_a(l_last) x
-// (loads kept in L2; a and l_b are prefetched into L2).  After the block
+// (loaded with a keep-in-L2 policy).  After the block
 // scan and look-back, phase 2 re-reads the run from L2 in groups of kFacG,
 // right to left: rs_bar_j = ybar_j + a_{j+1} rs_bar_{j+1}, and with
 // rs_{j-1} = c (.) l_{j-1} (c itself for the run's first element) the
@@ -458,8 +448,6 @@ __device__ __forceinline__ void scan_adjoint_fac_tile(const ScanArgs& A, int64_t
     const uint64_t keep = l2_policy_keep();
 
     // ---- phase 1: the run's reverse aggregate
-    prefetch_run_l2<V>(a, e0, A.n);
-    if constexpr (W == 2) prefetch_run_l2<V>(lb, e0, padded);
     L agg[1];
 #pragma unroll
     for (int i = 0; i < W; ++i) agg[0].d[i] = T(0);

@@ -76,7 +76,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # adjoint pass), from the ncu capture at n = 2^24 scaled by 4 to 2^26
 # (traffic grows in proportion to n); the capture is summarised in
 # profiles/scan_linrec_f64_n2p24.md
-LINREC_F64_TRAFFIC_PER_CALL = None
+LINREC_F64_TRAFFIC_PER_CALL = 4 * 1798297088
 
 WORKLOAD = ("scan VJPs: linear-recurrence n=2^26 pairs FP32 and FP64 (a~U[0.9,1], b,ybar~N(0,1)); "
             "+ scan and max scan n=2^28 FP32 N(0,1)")

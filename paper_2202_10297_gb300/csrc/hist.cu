@@ -77,6 +77,26 @@ struct HistArgs {
     long long* pe;            // [m] * : its exponent
     unsigned int* pz;         // [m] * : zero count
     long long* pf;            // [m] * : lowest zero index
+    struct BinQ* binq;        // [m] * with FP32 values: per-bin factor of the adjoint
+    int q62;                  // * with FP32 values: pm holds the fixed-point mantissa
+    // * : per-block partial states of the shared-memory bins [0, hw), merged
+    // by hist_prod_merge_kernel ([blocks][hw] each)
+    int64_t hw;
+    unsigned long long* part_m;
+    long long* part_e;
+    long long* part_f;
+    unsigned* part_z;
+};
+
+// Per-bin factor of the * adjoint for FP32 values (value domain): (qm, qe)
+// with P_nz * hsbar_b = qm * 2^qe, qm an FP32 mantissa (0.5 <= |qm| < 1),
+// and `sel`: -1 = the bin has no zero (every element gets P_nz/v_i * hsbar),
+// an index = the bin's only zero (that element gets P_nz * hsbar), -2 =
+// nothing (two or more zeros, or hsbar_b = 0).
+struct alignas(16) BinQ {
+    float qm;
+    int qe;
+    long long sel;
 };
 
 __global__ void hist_init_kernel(HistArgs A, unsigned long long key_empty) {
@@ -86,9 +106,10 @@ __global__ void hist_init_kernel(HistArgs A, unsigned long long key_empty) {
     for (int64_t b = t0; b < A.m; b += stride) {
         if (A.key) A.key[b] = key_empty;
         if (A.idx) A.idx[b] = 0xffffffffffffffffull;
-        if (A.pm) {
-            A.pm[b] = 0.5;
-            A.pe[b] = 1;
+        if (A.pm) {  // the neutral product: fixed point 2^62 * 2^-62, or 0.5 * 2^1
+            if (A.q62) reinterpret_cast<unsigned long long*>(A.pm)[b] = 1ull << 62;
+            else A.pm[b] = 0.5;
+            A.pe[b] = A.q62 ? 0 : 1;
             A.pz[b] = 0u;
             A.pf[b] = INT64_MAX;
         }
@@ -261,9 +282,9 @@ __global__ void hist_arg_finish_kernel(HistArgs A) {
 }
 
 // ------------------------------------------------------------------ *
-// pm *= mi under a CAS loop (global bins).  When the mantissa drops below
-// 2^-823 it is scaled up by 2^900 through its exponent bits and the
-// exponent counter takes -900 (both exact); the check reads the IEEE
+// pm *= mi under a CAS loop (global bins, FP64 values).  When the mantissa
+// drops below 2^-823 it is scaled up by 2^900 through its exponent bits and
+// the exponent counter takes -900 (both exact); the check reads the IEEE
 // exponent field, so the loop does one FP64 multiply per attempt.
 __device__ __forceinline__ void mul_into(double* pm, long long* pe, double mi, long long ei) {
     atomicAdd(reinterpret_cast<unsigned long long*>(pe), (unsigned long long)ei);
@@ -283,6 +304,86 @@ __device__ __forceinline__ void mul_into(double* pm, long long* pe, double mi, l
     if (shift) atomicAdd(reinterpret_cast<unsigned long long*>(pe), (unsigned long long)shift);
 }
 
+// FP32 values: the product of a bin's nonzeros is kept in integer fixed
+// point so that no FP64 instruction runs per element (GB300 issues FP64 at
+// 1/64 of the FP32 rate).  A mantissa M in [2^62, 2^63) stands for
+// M * 2^(E - 62); the sign is a parity bit (bit 31 of the zero counter).
+// Each product is truncated to 63 significant bits, a relative error below
+// 2^-61 per factor, so a bin of 2^27 factors stays within 1e-10.
+constexpr unsigned long long kQ62One = 1ull << 62;
+
+// M * mv for a 24-bit mantissa mv in [2^23, 2^24); returns the new M and
+// the exponent increment (23 or 24)
+__device__ __forceinline__ unsigned long long q62_mul24(unsigned long long M, unsigned mv, int& de) {
+    const unsigned long long hi = (unsigned long long)(unsigned)(M >> 32) * mv;  // < 2^55
+    const unsigned long long lo = (unsigned long long)(unsigned)M * mv;          // < 2^56
+    const unsigned long long t24 = (hi << 8) + (lo >> 24);
+    if (t24 >= kQ62One) {
+        de = 24;
+        return t24;
+    }
+    de = 23;
+    return (hi << 9) + (lo >> 23);
+}
+// M1 * M2; returns the new M and the exponent increment (62 or 63)
+__device__ __forceinline__ unsigned long long q62_mul(unsigned long long M1, unsigned long long M2, int& de) {
+    const unsigned long long hi = __umul64hi(M1, M2), lo = M1 * M2;  // product in [2^124, 2^126)
+    if (hi >= (1ull << 61)) {
+        de = 63;
+        return (hi << 1) | (lo >> 63);
+    }
+    de = 62;
+    return (hi << 2) | (lo >> 62);
+}
+// an FP32 value v != 0 as (sign, 24-bit mantissa, exponent): |v| = mv * 2^ev
+__device__ __forceinline__ void split_f32_int(float v, unsigned& sg, unsigned& mv, int& ev) {
+    int bits = __float_as_int(v);
+    sg = (unsigned)bits >> 31;
+    int ex = (bits >> 23) & 0xff;
+    int adj = 0;
+    if (ex == 0) {  // subnormal
+        bits = __float_as_int(v * 16777216.0f);
+        ex = (bits >> 23) & 0xff;
+        adj = -24;
+    }
+    mv = (unsigned)(bits & 0x7fffff) | 0x800000u;
+    ev = ex - 150 + adj;
+}
+// fixed-point state -> (FP64 mantissa in [0.5, 1) with the sign, exponent)
+__device__ __forceinline__ void q62_to_pow2(unsigned long long M, long long E, unsigned sign, double& mm,
+                                            int64_t& e) {
+    // M has its top bit at 62: as a double, 1 <= M * 2^-62 < 2 (rounded to 53 bits)
+    const double x = __longlong_as_double((long long)((1023ull << 52) | ((M << 2) >> 12)));
+    split_pow2(sign ? -x : x, mm, e);
+    e += E;
+}
+// global CAS: *pM = *pM * mv (fixed point); the exponent gets ev + the increment
+__device__ __forceinline__ void q62_mul24_into(unsigned long long* pM, long long* pE, unsigned mv, int ev) {
+    unsigned long long old = *reinterpret_cast<volatile unsigned long long*>(pM), assumed, nb;
+    int de;
+    do {
+        assumed = old;
+        nb = q62_mul24(assumed, mv, de);
+        old = atomicCAS(pM, assumed, nb);
+    } while (old != assumed);
+    atomicAdd(reinterpret_cast<unsigned long long*>(pE), (unsigned long long)(long long)(ev + de));
+}
+
+// A bin's recomputed state, for either representation.
+template <class T>
+__device__ __forceinline__ void read_bin(const HistArgs& A, int64_t b, double& mm, int64_t& e, unsigned& nz) {
+    const unsigned z = A.pz[b];
+    if constexpr (sizeof(T) == 4) {
+        nz = z & 0x7fffffffu;
+        q62_to_pow2(reinterpret_cast<const unsigned long long*>(A.pm)[b], A.pe[b], z >> 31, mm, e);
+    } else {
+        nz = z;
+        int64_t ee;
+        split_pow2(A.pm[b], mm, ee);
+        e = A.pe[b] + ee;
+    }
+}
+
 // Bin tiers of the * recompute:
 //   [0, H)       warp-private copies: lanes of a warp that hit the same bin
 //                are serialised into rounds (__match_any_sync picks one
@@ -291,42 +392,65 @@ __device__ __forceinline__ void mul_into(double* pm, long long* pe, double mi, l
 //   [H, H + H2)  one block-shared copy updated with shared-memory CAS;
 //   the rest     global CAS (L2).
 // Rank-ordered skewed data (Zipf) keeps its hot bins in the first tiers.
+// FP32 values use the fixed-point state above in every tier; FP64 values
+// an FP64 mantissa in [0.5, 1) and an integer exponent.
 constexpr int kProdWarpBins = 256;
 constexpr int kProdBlockBins = 2048;
 constexpr int kProdBlock = 256;
+constexpr int kProdMaxGrid = 1024;  // rows of the partial-state arrays
+
+// One warp-private bin: mantissa (fixed point, or FP64 bits), exponent and
+// zero count (with the sign parity in bit 31 for fixed point), read and
+// written as one 16-byte word.
+struct alignas(16) WBin {
+    unsigned long long M;
+    int E;
+    unsigned Z;
+};
 
 template <class T, class I>
-__global__ void __launch_bounds__(kProdBlock) hist_prod_kernel(HistArgs A) {
+__global__ void __launch_bounds__(kProdBlock, 4) hist_prod_kernel(HistArgs A) {
     extern __shared__ unsigned char smem_raw[];
+    constexpr bool kQ = sizeof(T) == 4;
     constexpr int NW = kProdBlock / 32;
     const int H = (int)std::min<int64_t>(A.m, kProdWarpBins);
-    double* wm = reinterpret_cast<double*>(smem_raw);            // [NW][H] mantissa, [0.5, 1)
-    long long* wf = reinterpret_cast<long long*>(wm + NW * H);   // [NW][H] lowest zero index
-    int* we = reinterpret_cast<int*>(wf + NW * H);               // [NW][H] exponent sum
-    int* wz = we + NW * H;                                        // [NW][H] zero count
+    WBin* wb = reinterpret_cast<WBin*>(smem_raw);              // [NW][H]
+    long long* wf = reinterpret_cast<long long*>(wb + NW * H);  // [NW][H] lowest zero index
     const int H2 = (int)std::max<int64_t>(0, std::min<int64_t>(A.m - H, kProdBlockBins));
-    double* bm = reinterpret_cast<double*>(wz + NW * H);          // [H2] block-shared tier
+    unsigned long long* bm = reinterpret_cast<unsigned long long*>(wf + NW * H);  // [H2] block-shared tier
     long long* be = reinterpret_cast<long long*>(bm + H2);
     long long* bf = be + H2;
     unsigned int* bz = reinterpret_cast<unsigned int*>(bf + H2);
+    const unsigned long long one = kQ ? kQ62One : (unsigned long long)__double_as_longlong(0.5);
+    const int e_one = kQ ? 0 : 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int q = threadIdx.x; q < NW * H; q += blockDim.x) {
-        wm[q] = 0.5;
-        we[q] = 1;
-        wz[q] = 0;
+        wb[q] = WBin{one, e_one, 0u};
         wf[q] = INT64_MAX;
     }
     for (int q = threadIdx.x; q < H2; q += blockDim.x) {
-        bm[q] = 0.5;
-        be[q] = 1;
+        bm[q] = one;
+        be[q] = e_one;
         bf[q] = INT64_MAX;
         bz[q] = 0u;
     }
     __syncthreads();
-    double* mym = wm + warp * H;
-    int* mye = we + warp * H;
-    int* myz = wz + warp * H;
+    WBin* myb = wb + warp * H;
     long long* myf = wf + warp * H;
+    unsigned long long* gM = reinterpret_cast<unsigned long long*>(A.pm);
+    // FP32 values: each lane keeps the nonzero factors of bins [0, kHot) in
+    // registers (the hottest bins of rank-ordered skewed data), so they take
+    // no part in the warp's serialised rounds; merged once at the end
+    constexpr int kHot = kQ ? 8 : 0;
+    const int hot = (int)std::min<int64_t>(A.m, kHot);
+    unsigned long long cM[kHot > 0 ? kHot : 1];
+    int cE[kHot > 0 ? kHot : 1];
+    unsigned cS = 0;  // sign parities, bit k for bin k
+#pragma unroll
+    for (int k = 0; k < kHot; ++k) {
+        cM[k] = kQ62One;
+        cE[k] = 0;
+    }
     const I* inds = static_cast<const I*>(A.inds);
     const T* vals = static_cast<const T*>(A.vals);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -334,87 +458,207 @@ __global__ void __launch_bounds__(kProdBlock) hist_prod_kernel(HistArgs A) {
     for (int64_t it = 0; it < nround; ++it) {
         const int64_t i = it * stride + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
         int64_t b = -1;
-        double v = 0.0;
+        T v = T(0);
         if (i < A.n) {
             b = ld_index(inds, i);
-            v = (double)__ldcs(vals + i);
+            v = __ldcs(vals + i);
         }
-        const bool in = b >= 0 && b < A.m;
+        const bool zero = v == T(0);
+        // the element's factor: fixed point (sg, mv, ev) or FP64 (mi, ei)
+        unsigned sg = 0, mv = 0;
+        int ev = 0;
         double mi = 0.5;
         int64_t ei = 1;
-        if (in && v != 0.0) split_pow2(v, mi, ei);
+        const bool in = b >= 0 && b < A.m;
+        if (in && !zero) {
+            if constexpr (kQ) split_f32_int(v, sg, mv, ev);
+            else split_pow2(v, mi, ei);
+        }
         if (in && b >= H && b < H + H2) {  // warm bins: block-shared, shared-memory CAS
             const int q = (int)(b - H);
-            if (v == 0.0) {
+            if (zero) {
                 atomicAdd(bz + q, 1u);
                 atomicMin(bf + q, (long long)i);
+            } else if constexpr (kQ) {
+                q62_mul24_into(bm + q, be + q, mv, ev);
+                if (sg) atomicXor(bz + q, 0x80000000u);
             } else {
-                mul_into(bm + q, be + q, mi, ei);
+                mul_into(reinterpret_cast<double*>(bm + q), be + q, mi, ei);
             }
         } else if (in && b >= H + H2) {  // cold bins: global atomics
-            if (v == 0.0) {
+            if (zero) {
                 atomicAdd(A.pz + b, 1u);
                 atomicMin(A.pf + b, (long long)i);
+            } else if constexpr (kQ) {
+                q62_mul24_into(gM + b, A.pe + b, mv, ev);
+                if (sg) atomicXor(A.pz + b, 0x80000000u);
             } else {
                 mul_into(A.pm + b, A.pe + b, mi, ei);
             }
         }
         bool pending = in && b < H;
+        if constexpr (kHot > 0) {
+            if (pending && !zero && b < hot) {
+#pragma unroll
+                for (int k = 0; k < kHot; ++k) {
+                    if (b == k) {
+                        int de;
+                        cM[k] = q62_mul24(cM[k], mv, de);
+                        cE[k] += ev + de;
+                        cS ^= sg << k;
+                    }
+                }
+                pending = false;
+            }
+        }
         const unsigned key = pending ? (unsigned)b : (0x80000000u | (unsigned)lane);
         while (__any_sync(0xffffffffu, pending)) {
             const unsigned grp = __match_any_sync(0xffffffffu, pending ? key : (0x80000000u | (unsigned)lane));
             const bool leader = pending && lane == __ffs(grp) - 1;
             if (leader) {
-                if (v == 0.0) {
-                    myz[b] += 1;
+                WBin x = myb[b];
+                if (zero) {
+                    x.Z += 1;
                     if (i < myf[b]) myf[b] = i;
+                } else if constexpr (kQ) {
+                    int de;
+                    x.M = q62_mul24(x.M, mv, de);
+                    x.E += ev + de;
+                    x.Z ^= sg << 31;
                 } else {
-                    double mm = mym[b] * mi;
+                    double mm = __longlong_as_double((long long)x.M) * mi;
                     int64_t e2 = 0;
                     renorm(mm, e2);
-                    mym[b] = mm;
-                    mye[b] += (int)(ei + e2);
+                    x.M = (unsigned long long)__double_as_longlong(mm);
+                    x.E += (int)(ei + e2);
                 }
+                myb[b] = x;
                 pending = false;
             }
             __syncwarp();
         }
     }
+    // the lanes' register bins: a shuffle tree per bin, then lane 0 folds
+    // the warp's product into its shared-memory copy
+    if constexpr (kHot > 0) {
+#pragma unroll
+        for (int k = 0; k < kHot; ++k) {
+            unsigned long long M = cM[k];
+            long long E = cE[k];
+            unsigned sgn = (cS >> k) & 1u;
+#pragma unroll
+            for (int off = 16; off; off >>= 1) {
+                const unsigned long long M2 = __shfl_xor_sync(0xffffffffu, M, off);
+                const long long E2 = __shfl_xor_sync(0xffffffffu, E, off);
+                int de;
+                M = q62_mul(M, M2, de);
+                E += E2 + de - 62;
+                sgn ^= __shfl_xor_sync(0xffffffffu, sgn, off);
+            }
+            if (lane == 0 && k < hot) {
+                WBin x = myb[k];
+                int de;
+                x.M = q62_mul(x.M, M, de);
+                x.E += (int)(E + de - 62);
+                x.Z ^= sgn << 31;
+                myb[k] = x;
+            }
+        }
+    }
     __syncthreads();
-    // merge the warps' copies and push each bin once into the global state
+    // this block's state of the shared-memory bins goes to its partial row
+    // (no global atomics); hist_prod_merge_kernel combines the rows
+    const int64_t row = (int64_t)blockIdx.x * A.hw;
     for (int q = threadIdx.x; q < H; q += blockDim.x) {
-        double mm = 0.5;
-        int64_t ee = 1;
-        int nz = 0;
+        unsigned nz = 0, sign = 0;
         long long first = INT64_MAX;
+        unsigned long long M;
+        long long E;
+        if constexpr (kQ) {
+            M = kQ62One;
+            E = 0;
+        } else {
+            M = (unsigned long long)__double_as_longlong(0.5);
+            E = 1;
+        }
         for (int w = 0; w < NW; ++w) {
-            mm *= wm[w * H + q];
-            renorm(mm, ee);
-            ee += we[w * H + q];
-            nz += wz[w * H + q];
+            const WBin x = wb[w * H + q];
+            nz += x.Z & 0x7fffffffu;
+            sign ^= x.Z >> 31;
             first = std::min(first, wf[w * H + q]);
+            if constexpr (kQ) {
+                int de;
+                M = q62_mul(M, x.M, de);
+                E += x.E + de - 62;
+            } else {
+                double mm = __longlong_as_double((long long)M) * __longlong_as_double((long long)x.M);
+                int64_t e2 = 0;
+                renorm(mm, e2);
+                M = (unsigned long long)__double_as_longlong(mm);
+                E += x.E + e2;
+            }
         }
-        if (nz) {
-            atomicAdd(A.pz + q, (unsigned)nz);
-            atomicMin(A.pf + q, first);
-        }
-        double m2;
-        int64_t e2;
-        split_pow2(mm, m2, e2);
-        const long long etot = (long long)(ee + e2);
-        if (!(m2 == 0.5 && etot == 1)) mul_into(A.pm + q, A.pe + q, m2, etot);
+        A.part_m[row + q] = M;
+        A.part_e[row + q] = E;
+        A.part_z[row + q] = nz | (sign << 31);
+        A.part_f[row + q] = first;
     }
     for (int q = threadIdx.x; q < H2; q += blockDim.x) {
-        const int64_t b = H + q;
-        if (bz[q]) {
-            atomicAdd(A.pz + b, bz[q]);
-            atomicMin(A.pf + b, bf[q]);
+        A.part_m[row + H + q] = bm[q];
+        A.part_e[row + H + q] = be[q];
+        A.part_z[row + H + q] = bz[q];
+        A.part_f[row + H + q] = bf[q];
+    }
+}
+
+// Combines the per-block partial states of the shared-memory bins: one
+// warp per bin, lanes take every 32nd block row, then a shuffle tree.  It is
+// the only writer of these bins' global state.
+template <class T>
+__global__ void hist_prod_merge_kernel(HistArgs A, int rows) {
+    constexpr bool kQ = sizeof(T) == 4;
+    const int lane = threadIdx.x & 31;
+    const int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (b >= A.hw) return;
+    unsigned long long M = kQ ? kQ62One : (unsigned long long)__double_as_longlong(0.5);
+    long long E = kQ ? 0 : 1;
+    unsigned nz = 0, sign = 0;
+    long long first = INT64_MAX;
+    auto comb = [](unsigned long long& M1, long long& E1, unsigned long long M2, long long E2) {
+        if constexpr (kQ) {
+            int de;
+            M1 = q62_mul(M1, M2, de);
+            E1 += E2 + de - 62;
+        } else {
+            double mm = __longlong_as_double((long long)M1) * __longlong_as_double((long long)M2);
+            int64_t e2 = 0;
+            renorm(mm, e2);
+            M1 = (unsigned long long)__double_as_longlong(mm);
+            E1 += E2 + e2;
         }
-        double m2;
-        int64_t e2;
-        split_pow2(bm[q], m2, e2);
-        const long long etot = (long long)(be[q] + e2);
-        if (!(m2 == 0.5 && etot == 1)) mul_into(A.pm + b, A.pe + b, m2, etot);
+    };
+    for (int r = lane; r < rows; r += 32) {
+        const int64_t k = (int64_t)r * A.hw + b;
+        comb(M, E, A.part_m[k], A.part_e[k]);
+        const unsigned z = A.part_z[k];
+        nz += z & 0x7fffffffu;
+        sign ^= z >> 31;
+        first = std::min(first, A.part_f[k]);
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        const unsigned long long M2 = __shfl_xor_sync(0xffffffffu, M, off);
+        const long long E2 = __shfl_xor_sync(0xffffffffu, E, off);
+        comb(M, E, M2, E2);
+        nz += __shfl_xor_sync(0xffffffffu, nz, off);
+        sign ^= __shfl_xor_sync(0xffffffffu, sign, off);
+        first = std::min(first, (long long)__shfl_xor_sync(0xffffffffu, first, off));
+    }
+    if (lane == 0) {
+        A.pm[b] = __longlong_as_double((long long)M);  // the bits, in either representation
+        A.pe[b] = E;
+        A.pz[b] = kQ ? (nz | (sign << 31)) : nz;
+        A.pf[b] = first;
     }
 }
 
@@ -424,10 +668,9 @@ __global__ void hist_prod_bins_kernel(HistArgs A) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < A.m; b += stride) {
         double mm;
-        int64_t ee;
-        split_pow2(A.pm[b], mm, ee);
-        const int64_t e = A.pe[b] + ee;
-        const int64_t nz = A.pz[b];
+        int64_t e;
+        unsigned nz;
+        read_bin<T>(A, b, mm, e, nz);
         if (A.hs_out) static_cast<T*>(A.hs_out)[b] = nz ? T(0) : (T)ldexp_clamped(mm, e);
         if (A.bin_aux) {
             adpar_prod_aux x;
@@ -458,12 +701,11 @@ __global__ void __launch_bounds__(kHistBlock) hist_prod_vjp_kernel(HistArgs A) {
         int sg = 0;
         if (in) {
             const double yb = (double)hsbar[b];
-            const unsigned int nz = A.pz[b];
+            double mm;
+            int64_t e;
+            unsigned nz;
+            read_bin<T>(A, b, mm, e, nz);
             if (yb != 0.0 && (nz == 0 || (nz == 1 && A.pf[b] == i))) {
-                double mm;
-                int64_t ee;
-                split_pow2(A.pm[b], mm, ee);
-                const int64_t e = A.pe[b] + ee;
                 double ym;
                 int64_t ye;
                 split_pow2(yb, ym, ye);
@@ -500,9 +742,76 @@ __global__ void __launch_bounds__(kHistBlock) hist_prod_vjp_kernel(HistArgs A) {
     }
 }
 
+// per-bin factors of the FP32 value-domain adjoint (see BinQ)
+template <class T>
+__global__ void hist_prod_binq_kernel(HistArgs A) {
+    const T* hsbar = static_cast<const T*>(A.hsbar);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < A.m; b += stride) {
+        BinQ q;
+        q.qm = 0.0f;
+        q.qe = 0;
+        q.sel = -2;
+        const double yb = (double)hsbar[b];
+        double mm;
+        int64_t ee;
+        unsigned nz;
+        read_bin<T>(A, b, mm, ee, nz);
+        if (yb != 0.0 && nz <= 1) {
+            double ym, m2;
+            int64_t ye, e2;
+            split_pow2(yb, ym, ye);
+            split_pow2(mm * ym, m2, e2);  // in [0.25, 1): one more split
+            float qf = (float)m2;        // rounding may reach 1.0
+            int64_t e = ee + ye + e2;
+            if (fabsf(qf) >= 1.0f) {
+                qf *= 0.5f;
+                e += 1;
+            }
+            q.qm = qf;
+            q.qe = (int)(e > (1 << 30) ? (1 << 30) : (e < -(1 << 30) ? -(1 << 30) : e));
+            q.sel = nz == 0 ? -1 : A.pf[b];
+        }
+        A.binq[b] = q;
+    }
+}
+
+// per element, FP32 values in the value domain: the three cases of
+// Sec. 5.1.1 from the bin's factor, in FP32 arithmetic with the exponent
+// kept apart (qm / m_v, then 2^(qe - e_v) applied to the exponent field)
+template <class I>
+__global__ void __launch_bounds__(kHistBlock) hist_prod_vjp_f32_kernel(HistArgs A) {
+    const I* inds = static_cast<const I*>(A.inds);
+    const float* vals = static_cast<const float*>(A.vals);
+    float* vb = static_cast<float*>(A.valsbar);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += stride) {
+        const int64_t b = ld_index(inds, i);
+        const bool in = b >= 0 && b < A.m;
+        float c = 0.0f;
+        if (in) {
+            const BinQ q = A.binq[b];
+            if (q.sel == -1) {
+                float mv;
+                int ev;
+                split_pow2_f32m(__ldcs(vals + i), mv, ev);
+                c = scale_pow2f(q.qm * __frcp_rn(mv), (int64_t)q.qe - ev);
+            } else if (q.sel == i) {
+                c = scale_pow2f(q.qm, (int64_t)q.qe);
+            }
+        }
+        if (A.accumulate) {
+            if (in) vb[i] += c;
+        } else {
+            vb[i] = c;
+        }
+    }
+}
+
 // ------------------------------------------------------------ host side
 struct HistLayout {
-    size_t off_key, off_idx, off_pm, off_pe, off_pz, off_pf, total;
+    size_t off_key, off_idx, off_pm, off_pe, off_pz, off_pf, off_binq, off_part_m, off_part_e, off_part_f,
+        off_part_z, total;
 };
 
 HistLayout hist_layout(int op, int dtype, int64_t m) {
@@ -517,6 +826,13 @@ HistLayout hist_layout(int op, int dtype, int64_t m) {
         L.off_pe = o; o = round_up(o + mm * 8, 256);
         L.off_pf = o; o = round_up(o + mm * 8, 256);
         L.off_pz = o; o = round_up(o + mm * 4, 256);
+        if (dtype == ADPAR_F32) { L.off_binq = o; o = round_up(o + mm * sizeof(BinQ), 256); }
+        const size_t hw = (size_t)std::min<int64_t>(m, kProdWarpBins + kProdBlockBins);
+        const size_t np = hw * (size_t)kProdMaxGrid;
+        L.off_part_m = o; o = round_up(o + np * 8, 256);
+        L.off_part_e = o; o = round_up(o + np * 8, 256);
+        L.off_part_f = o; o = round_up(o + np * 8, 256);
+        L.off_part_z = o; o = round_up(o + np * 4, 256);
     }
     L.total = o;
     return L;
@@ -571,10 +887,19 @@ int run_hist(HistArgs A, cudaStream_t s) {
         const int64_t h1 = std::min<int64_t>(A.m, kProdWarpBins);
         const int64_t h2 = std::max<int64_t>(0, std::min<int64_t>(A.m - h1, kProdBlockBins));
         const size_t sh = (size_t)h1 * 24 * (kProdBlock / 32) + (size_t)h2 * 28;
-        const int gridP = (int)std::max<int64_t>(1, std::min<int64_t>((A.n + kProdBlock - 1) / kProdBlock, (int64_t)sms * 8));
+        const int gridP = (int)std::max<int64_t>(
+            1, std::min<int64_t>((A.n + kProdBlock - 1) / kProdBlock, std::min<int64_t>(sms * 4, kProdMaxGrid)));
+        A.hw = h1 + h2;
         hist_prod_kernel<T, I><<<gridP, kProdBlock, sh, s>>>(A);
+        if (A.hw > 0) hist_prod_merge_kernel<T><<<(unsigned)((A.hw * 32 + 255) / 256), 256, 0, s>>>(A, gridP);
         if (A.hs_out || A.bin_aux) hist_prod_bins_kernel<T><<<gridM, 256, 0, s>>>(A);
-        if (!A.primal_only) hist_prod_vjp_kernel<T, I><<<gridN, kHistBlock, 0, s>>>(A);
+        if (A.primal_only) break;
+        if (sizeof(T) == 4 && !A.logdomain) {
+            hist_prod_binq_kernel<T><<<gridM, 256, 0, s>>>(A);
+            hist_prod_vjp_f32_kernel<I><<<gridN, kHistBlock, 0, s>>>(A);
+        } else {
+            hist_prod_vjp_kernel<T, I><<<gridN, kHistBlock, 0, s>>>(A);
+        }
         break;
     }
     default:
@@ -654,6 +979,14 @@ int hist_impl(adpar_opdesc d, int64_t n, int64_t m, const void* vals, const void
     A.hdr = reinterpret_cast<WsHeader*>(w);
     if (L.off_key) A.key = reinterpret_cast<unsigned long long*>(w + L.off_key);
     if (L.off_idx) A.idx = reinterpret_cast<unsigned long long*>(w + L.off_idx);
+    if (L.off_binq) A.binq = reinterpret_cast<BinQ*>(w + L.off_binq);
+    if (L.off_part_m) {
+        A.part_m = reinterpret_cast<unsigned long long*>(w + L.off_part_m);
+        A.part_e = reinterpret_cast<long long*>(w + L.off_part_e);
+        A.part_f = reinterpret_cast<long long*>(w + L.off_part_f);
+        A.part_z = reinterpret_cast<unsigned*>(w + L.off_part_z);
+    }
+    A.q62 = (d.op == ADPAR_OP_MUL && d.dtype == ADPAR_F32) ? 1 : 0;
     if (L.off_pm) {
         A.pm = reinterpret_cast<double*>(w + L.off_pm);
         A.pe = reinterpret_cast<long long*>(w + L.off_pe);

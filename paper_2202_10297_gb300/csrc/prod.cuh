@@ -30,6 +30,31 @@ __device__ __forceinline__ void split_pow2(double x, double& m, int64_t& e) {
     e = (int64_t)(ex - 1022 + adj);
 }
 
+// FP32 x != 0 finite:  x = m * 2^e, 0.5 <= |m| < 1, with m as an FP32 and
+// as an FP64 (formed from the bits: no conversion instruction)
+__device__ __forceinline__ void split_pow2_f32m(float x, float& m, int& e) {
+    int bits = __float_as_int(x);
+    int ex = (bits >> 23) & 0xff;
+    int adj = 0;
+    if (ex == 0) {  // subnormal
+        x *= 16777216.0f;  // 2^24
+        bits = __float_as_int(x);
+        ex = (bits >> 23) & 0xff;
+        adj = -24;
+    }
+    m = __int_as_float((bits & ~(0xff << 23)) | (126 << 23));
+    e = ex - 126 + adj;
+}
+__device__ __forceinline__ void split_pow2_f32(float x, double& m, int64_t& e) {
+    float mf;
+    int ef;
+    split_pow2_f32m(x, mf, ef);
+    const int b = __float_as_int(mf);
+    const unsigned long long sign = (unsigned long long)((unsigned)b & 0x80000000u) << 32;
+    m = __longlong_as_double((long long)(sign | (1022ULL << 52) | ((unsigned long long)(b & 0x7fffff) << 29)));
+    e = ef;
+}
+
 // Renormalise m (nonzero, normal) into [0.5, 1), moving its exponent into e.
 __device__ __forceinline__ void renorm(double& m, int64_t& e) {
     long long bits = __double_as_longlong(m);

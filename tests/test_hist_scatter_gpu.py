@@ -120,6 +120,31 @@ def test_hist_prod_representable_values(A, oracle):
     assert rel_l2(out["valsbar"].cpu().numpy(), ref["valsbar"]) < 1e-5
 
 
+def test_hist_prod_f32_accumulate_subnormal_and_hsbar_zero(A, oracle):
+    """FP32 values, few elements per bin (products in range): accumulation into
+    existing adjoints, subnormal FP32 inputs, bins with one zero, bins whose
+    hsbar is 0, and int64 indices -- values within the FP32 tolerance."""
+    n, m = 30000, 4000
+    vals, inds, hsbar = synth.hist(n, m, "uniform", seed=91)
+    g = synth.rng(92)
+    vals = (g.uniform(0.5, 1.5, n) * np.sign(vals)).astype(np.float32)
+    vals[10:20] = (np.float32(3e-39) * np.sign(vals[10:20])).astype(np.float32)  # subnormal
+    vals[30:33] = 0
+    hsbar = hsbar.copy()
+    hsbar[::7] = 0
+    base = synth.normal(n, np.float32, seed=93)
+    ref = oracle.hist_prod_vjp(vals, inds, m, hsbar, valsbar=base)
+    vbt = dev(base)
+    A.adpar_vjp_hist("mul", dev(inds.astype(np.int64)), m, dev(hsbar), vals=dev(vals), valsbar=vbt,
+                     accumulate=True)
+    got = vbt.cpu().numpy()
+    assert rel_l2(got, ref["valsbar"]) < 1e-5
+    # elements of bins with hsbar 0 (or out of range) keep their old adjoint exactly
+    inr = (inds >= 0) & (inds < m)
+    keep = ~inr | (hsbar[np.clip(inds, 0, m - 1)] == 0)
+    np.testing.assert_array_equal(got[keep], base[keep])
+
+
 def test_hist_all_out_of_range_and_one_bin(A, oracle):
     n = 5000
     vals = synth.normal(n, np.float32, seed=1)

@@ -316,6 +316,54 @@ int oracle_scan_vjp(int op, int64_t n,
 }
 
 /* ---------------------------------------------------------------------
+ * Reduce with an arbitrary associative operator (Sec. 5.1.1, the general
+ * rule), any width: y = e (.) a_0 (.) ... (.) a_{n-1}.  Plain tape sweep:
+ * the forward loop records t_i = e (.) a_0 (.) ... (.) a_{i-1}; the reverse
+ * loop keeps g = adjoint of t_{i+1} (starting at ybar) and does
+ *   asbar_i += J_right(t_i, a_i)^T g;   g = J_left(t_i, a_i)^T g
+ * with the same per-operator Jacobians as the scan sweep above.  The rule
+ * the library implements (l_i and r_i from two exclusive scans, then
+ * d(l_i (.) a_i (.) r_i)/d a_i) is not used here.
+ * ------------------------------------------------------------------- */
+int oracle_reduce_general_vjp(int op, int64_t n,
+                              const double *as0, const double *as1,
+                              double ybar0, double ybar1,
+                              double *asbar0, double *asbar1,
+                              double *y_out)
+{
+    if (op < O_ADD || op > O_LINREC) return 1;
+    int w = (op == O_LINREC) ? 2 : 1;
+    double *t = (double *)malloc(sizeof(double) * (size_t)(n + 1) * (size_t)w);
+    if (!t) return 2;
+    const double *as[2] = { as0, as1 };
+    double *asb[2] = { asbar0, asbar1 };
+    /* the neutral element */
+    if (op == O_LINREC) { t[0] = 1.0; t[1] = 0.0; }
+    else t[0] = neutral_of(op);
+    for (int64_t i = 0; i < n; ++i) {
+        double x[2];
+        for (int c = 0; c < w; ++c) x[c] = as[c][i];
+        scan_combine(op, &t[i * w], x, &t[(i + 1) * w]);
+    }
+    if (y_out) for (int c = 0; c < w; ++c) y_out[c] = t[n * w + c];
+    double g[2] = { ybar0, ybar1 };
+    for (int64_t i = n - 1; i >= 0; --i) {
+        double x[2], dl[2], dr[2];
+        mat2 Jl, Jr;
+        for (int c = 0; c < w; ++c) x[c] = as[c][i];
+        scan_jacobians(op, &t[i * w], x, &Jl, &Jr);
+        mat_t_vec(&Jr, g, dr, w);
+        mat_t_vec(&Jl, g, dl, w);
+        for (int c = 0; c < w; ++c) {
+            asb[c][i] += dr[c];
+            g[c] = dl[c];
+        }
+    }
+    free(t);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------
  * reduce_by_index with +, min, max (Sec. 5.1.2).  The primal is the
  * semantic loop
  *   hs = replicate m e;  for i: hs[inds[i]] = hs[inds[i]] (.) vals[i]

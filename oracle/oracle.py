@@ -44,9 +44,10 @@ def lib():
                                          _D, _D, _D]
         L.oracle_kmeans.argtypes = [i64, C.c_int, C.c_int, _D, _D, dbl, _D, _I64,
                                     _D, _D]
+        L.oracle_reduce_general_vjp.argtypes = [C.c_int, i64, _D, _D, dbl, dbl, _D, _D, _D]
         for f in ("oracle_reduce_vjp", "oracle_prod_reduce_vjp", "oracle_scan_vjp",
                   "oracle_hist_vjp", "oracle_hist_prod_vjp", "oracle_scatter_vjp",
-                  "oracle_map_acc_vjp", "oracle_kmeans"):
+                  "oracle_map_acc_vjp", "oracle_kmeans", "oracle_reduce_general_vjp"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -79,6 +80,24 @@ def reduce_vjp(op, a, ybar=1.0, abar=None):
     _check(lib().oracle_reduce_vjp(OPS[op], n, _p(a), float(ybar), C.byref(y),
                                    _p(out), C.byref(arg)), "reduce_vjp")
     return y.value, out, arg.value
+
+
+def reduce_general_vjp(op, a, ybar, b=None, ybar_b=0.0, abar=None, bbar=None):
+    """Reduce with any supported operator by the plain tape sweep (Sec. 5.1.1,
+    general rule).  Returns (y tuple, abar, bbar); ``bbar`` only for linrec."""
+    a = _f64(a)
+    n = a.size
+    w2 = op == "linrec"
+    ab = np.zeros(n) if abar is None else _f64(abar).copy()
+    bb = None
+    if w2:
+        b = _f64(b)
+        bb = np.zeros(n) if bbar is None else _f64(bbar).copy()
+    y = np.zeros(2)
+    _check(lib().oracle_reduce_general_vjp(OPS[op], n, _p(a), _p(b) if w2 else None, float(ybar),
+                                           float(ybar_b), _p(ab), _p(bb) if w2 else None, _p(y)),
+           "reduce_general_vjp")
+    return (tuple(y) if w2 else (y[0],)), ab, bb
 
 
 def prod_reduce_vjp(a, ybar=1.0, abar=None):

@@ -35,6 +35,11 @@ MUTANTS = {
                     "ybar * (2.0) * (X[i * d + j] - C[arg * d + j]);"),
     "prod_zero_count_off": ("if (first < 0) first = i;\n            ++nz;",
                             "if (first < 0) first = i + 1;\n            ++nz;"),
+    "reduce_general_jacobians_swapped": ("mat_t_vec(&Jr, g, dr, w);\n        mat_t_vec(&Jl, g, dl, w);",
+                                         "mat_t_vec(&Jl, g, dr, w);\n        mat_t_vec(&Jr, g, dl, w);"),
+    "reduce_general_linrec_neutral": ("if (op == O_LINREC) { t[0] = 1.0; t[1] = 0.0; }",
+                                      "if (op == O_LINREC) { t[0] = 1.0; t[1] = 1.0; }"),
+    "reduce_general_chain_not_carried": ("            g[c] = dl[c];\n", "            g[c] = g[c] + 0.0 * dl[c];\n"),
 }
 
 

@@ -301,6 +301,89 @@ def test_linrec_closed_form(oracle):
     np.testing.assert_allclose(bb, ref, rtol=1e-12)
 
 
+# ------------------------------------------------ general reduce rule (Sec. 5.1.1)
+def test_reduce_general_linrec_finite_differences(oracle):
+    """y = (A_n, B_n) of the linear recurrence is multilinear in (a, b):
+    central differences of the plain forward loop are exact up to rounding."""
+    g = synth.rng(21)
+    n = 40
+    a = g.uniform(0.9, 1.1, n)
+    b = g.normal(size=n)
+    ya, yb = 0.7, -1.3
+
+    def L(a_, b_):
+        A, B = _linrec_forward(a_, b_)
+        return ya * A[-1] + yb * B[-1]
+
+    (yA, yB), ab, bb = oracle.reduce_general_vjp("linrec", a, ya, b=b, ybar_b=yb)
+    A, B = _linrec_forward(a, b)
+    assert abs(yA - A[-1]) <= 1e-13 * abs(A[-1]) and abs(yB - B[-1]) <= 1e-12 * (1 + abs(B[-1]))
+    h = 0.125
+    for k in range(n):
+        e = np.zeros(n)
+        e[k] = h
+        fa = (L(a + e, b) - L(a - e, b)) / (2 * h)
+        fb = (L(a, b + e) - L(a, b - e)) / (2 * h)
+        assert abs(fa - ab[k]) <= 1e-10 * (1 + abs(fa))
+        assert abs(fb - bb[k]) <= 1e-10 * (1 + abs(fb))
+
+
+@pytest.mark.parametrize("op", ["add", "mul", "min", "max", "linrec"])
+def test_reduce_general_is_scan_with_last_cotangent(oracle, op):
+    """A reduce is the last output of the inclusive scan, so its VJP equals the
+    scan VJP with ybar zero everywhere but the last position."""
+    g = synth.rng(22)
+    n = 57
+    if op in ("min", "max"):
+        a = np.round(g.normal(size=n) * 4) / 4  # ties
+    elif op == "mul":
+        a = g.uniform(0.5, 1.5, n)
+        a[[5, 40]] = 0.0
+    else:
+        a = g.uniform(0.9, 1.1, n)
+    b = g.normal(size=n)
+    ya = np.zeros(n)
+    yb = np.zeros(n)
+    ya[-1], yb[-1] = 0.8, 1.7
+    if op == "linrec":
+        sab, sbb, _, _ = oracle.scan_vjp("linrec", a, ya, b, yb)
+        _, ab, bb = oracle.reduce_general_vjp("linrec", a, 0.8, b=b, ybar_b=1.7)
+        np.testing.assert_allclose(bb, sbb, rtol=1e-13, atol=1e-15)
+    else:
+        sab, _, _, _ = oracle.scan_vjp(op, a, ya)
+        _, ab, _ = oracle.reduce_general_vjp(op, a, 0.8)
+    np.testing.assert_allclose(ab, sab, rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("op", ["add", "min", "max", "mul"])
+def test_reduce_general_matches_plain_reduce_definitions(oracle, op):
+    """+ broadcasts ybar; min/max put it at the lowest index of the extremum;
+    * gives prod_{j != i} a_j * ybar (brute force, no division)."""
+    g = synth.rng(23)
+    n = 33
+    a = np.round(g.normal(size=n) * 3) / 3 if op in ("min", "max") else g.uniform(0.5, 1.5, n)
+    (y,), ab, _ = oracle.reduce_general_vjp(op, a, 2.5)
+    if op == "add":
+        assert abs(y - a.sum()) <= 1e-12 * (1 + abs(a.sum()))
+        np.testing.assert_array_equal(ab, np.full(n, 2.5))
+    elif op == "mul":
+        ref = np.array([np.prod(np.delete(a, i)) * 2.5 for i in range(n)])
+        np.testing.assert_allclose(ab, ref, rtol=1e-12)
+    else:
+        i0 = int(np.argmax(a) if op == "max" else np.argmin(a))  # numpy: first index on ties
+        ref = np.zeros(n)
+        ref[i0] = 2.5
+        np.testing.assert_array_equal(ab, ref)
+        assert y == a[i0]
+
+
+def test_reduce_general_empty_and_accumulate(oracle):
+    (yA, yB), ab, bb = oracle.reduce_general_vjp("linrec", np.zeros(0), 1.0, b=np.zeros(0), ybar_b=1.0)
+    assert (yA, yB) == (1.0, 0.0) and ab.size == 0 and bb.size == 0
+    _, ab, _ = oracle.reduce_general_vjp("add", [1.0, 2.0], 3.0, abar=[10.0, -1.0])
+    np.testing.assert_array_equal(ab, [13.0, 2.0])
+
+
 def test_scan_accumulates(oracle):
     """Adjoints are added into the given arrays (Eq. rewrite-adj, +=)."""
     yb = np.array([1.0, 2.0, 3.0])

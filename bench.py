@@ -27,6 +27,9 @@ JSON line each; these are measurements, not the headline line):
   batch    4096 segments (product-reduce + linear-recurrence VJPs, lengths
            2^U[8,20], FP32/FP64 mixed): one graph-replayed launch vs 4096
            plain calls
+  reduce_general  reduce VJP by the general rule (two exclusive scans): the
+           linear recurrence at 2^26 pairs FP32/FP64; general vs special
+           rules for +, max and * at 2^28 FP32
   serve    Poisson arrivals of mixed-operator requests sized 2^10..2^24:
            p50/p99 latency and throughput vs one call at a time
   call     one entry point on a small case, --reps times (the profiling
@@ -505,6 +508,52 @@ def row_prod(args):
     return _line("prod", metric="VJP latency / GB/s", cases=cases, oracle_cores=1)
 
 
+def row_reduce_general(args):
+    """Reduce VJP by the general rule (Sec. 5.1.1: two exclusive scans, then a
+    map): the linear recurrence (no special rule) at 2^26 pairs FP32/FP64, and
+    the general vs the special rules for +, max and * at 2^28 FP32."""
+    import torch
+    from oracle import oracle as O
+    from paper_2202_10297_gb300 import adpar as A
+    from paper_2202_10297_gb300 import synth
+    hbm, _ = measured_peaks()
+    cases = {}
+    n = 1 << LOG2_LINREC
+    for dt, code, name in ((np.float32, A.F32, "linrec_f32"), (np.float64, A.F64, "linrec_f64")):
+        a, b, _, _ = synth.linrec(n, dt, seed=synth.SEED_BASE + 1)
+        at, bt = _dev(a), _dev(b)
+        ab, bb = torch.empty_like(at), torch.empty_like(at)
+        wk = A.workspace(A.adpar_workspace_size(A.RULE_REDUCE_GENERAL, A.OP_LINREC, code, n), "cuda")
+        t = _cuda_ms(lambda: A.adpar_vjp_reduce_general("linrec", at, 1.0, b=bt, ybar_b=1.0, abar=ab, bbar=bb,
+                                                         work=wk), 10, 3)
+        w = np.dtype(dt).itemsize
+        alg = 4 * w * n          # a, b read once; abar, bbar written once
+        moved = 6 * w * n        # a, b read by both passes; abar, bbar written
+        cases[name] = {"ms": t, "elements_per_s": n / t * 1e3, "algorithmic_bytes": alg,
+                       "hbm_frac_of_measured": alg / t / 1e6 / hbm, "bytes_moved_by_design": moved,
+                       "design_frac_of_measured": moved / t / 1e6 / hbm}
+        del at, bt, ab, bb, wk
+    # general vs special rules, FP32 2^28
+    n = 1 << LOG2_SCAN
+    x = torch.randn(n, device="cuda")
+    xm = torch.rand(n, device="cuda") * 0.2 + 0.9
+    xb = torch.empty_like(x)
+    for op, inp in (("add", x), ("max", x), ("mul", xm)):
+        wg = A.workspace(A.adpar_workspace_size(A.RULE_REDUCE_GENERAL, A.OPS[op], A.F32, n), "cuda")
+        ws = A.workspace(A.adpar_workspace_size(A.RULE_REDUCE, A.OPS[op], A.F32, n), "cuda")
+        tg = _cuda_ms(lambda: A.adpar_vjp_reduce_general(op, inp, 1.0, abar=xb, work=wg), 10, 3)
+        tsp = _cuda_ms(lambda: A.adpar_vjp_reduce(op, inp, 1.0, abar=xb, work=ws), 10, 3)
+        tp = _cuda_ms(lambda: A.adpar_reduce(op, inp, work=ws), 10, 3)
+        cases["%s_f32_2^28" % op] = {"general_ms": tg, "special_ms": tsp, "primal_ms": tp,
+                                     "general_over_special": tg / tsp, "general_over_primal": tg / tp,
+                                     "special_over_primal": tsp / tp}
+    small = synth.linrec(1 << 20, np.float64, seed=synth.SEED_BASE + 1)
+    rate = _oracle_rate(lambda: O.reduce_general_vjp("linrec", small[0], 1.0, b=small[1], ybar_b=1.0), 1 << 20, 2.0)
+    return _line("reduce_general", metric="general-rule reduce VJP elements/s and % of HBM", cases=cases,
+                 cpu_baseline={"value": rate, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                               "sample": "linear recurrence, n = 2^20 FP64"})
+
+
 def row_hist(args):
     """reduce_by_index VJPs (Sec. 5.1.2), n = 2^27 FP32."""
     import torch
@@ -736,7 +785,7 @@ def row_call(args):
 
 
 ROWS = {"prod": row_prod, "hist": row_hist, "scatter": row_scatter, "kmeans": row_kmeans, "batch": row_batch,
-        "serve": row_serve, "call": row_call}
+        "serve": row_serve, "call": row_call, "reduce_general": row_reduce_general}
 
 
 def main():
@@ -746,7 +795,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="adpar", choices=["adpar", "reference"])
     ap.add_argument("--workload", default="scan",
-                    choices=["scan", "prod", "hist", "scatter", "kmeans", "batch", "serve", "call"])
+                    choices=["scan", "prod", "hist", "scatter", "kmeans", "batch", "serve", "call",
+                             "reduce_general"])
     ap.add_argument("--call", default="scan-linrec-f64", choices=sorted(CALLS_ONE))
     ap.add_argument("--log2n", type=int, default=24)
     ap.add_argument("--reps", type=int, default=3)

@@ -73,7 +73,8 @@ typedef enum {
     ADPAR_RULE_HIST = 2,
     ADPAR_RULE_SCATTER = 3,
     ADPAR_RULE_MAP_ACC = 4,
-    ADPAR_RULE_KMEANS = 5
+    ADPAR_RULE_KMEANS = 5,
+    ADPAR_RULE_REDUCE_GENERAL = 6
 } adpar_rule;
 
 /* or'ed into the rule of adpar_workspace_size: the smallest workspace the
@@ -214,6 +215,30 @@ int adpar_vjp_scan(adpar_opdesc desc, int64_t n, const void *a, const void *b,
                    const void *ybar_a, const void *ybar_b, void *abar, void *bbar,
                    void *ys_a, void *ys_b, uint32_t flags, void *work,
                    size_t work_bytes, void *stream);
+
+/* Reduce by the GENERAL rule of Sec. 5.1.1, for any operator of this
+ * library (ADD, MUL, MIN, MAX, and LINREC, which has no special rule):
+ *   y = a_0 (.) a_1 (.) ... (.) a_{n-1},
+ *   a_bar_i (+)= d(l_i (.) a_i (.) r_i)/d a_i ^T y_bar,
+ * with l_i = a_0 (.) ... (.) a_{i-1} and r_i = a_{i+1} (.) ... (.) a_{n-1}
+ * from a forward and a reverse exclusive scan (the neutral element at the
+ * ends).  For LINREC that is (abar, bbar)_i = (rA (lA ybar_A + lB ybar_B),
+ * rA ybar_B); for MUL the product of all other elements (no division, so
+ * zeros are safe; values may underflow where adpar_vjp_reduce's scaled
+ * rule would not); for MIN/MAX the lowest index of the extremum.  Two
+ * single-pass kernels: the forward carries, then the reverse pass.
+ * Arguments (as for adpar_vjp_scan; b, ybar_b, bbar, y_out_b for LINREC):
+ *   n            number of elements (0 allowed: y = neutral element).
+ *   a, b         [n] inputs.
+ *   ybar_a/_b    device scalars (dtype): the cotangent of y.
+ *   abar, bbar   [n] output adjoints.
+ *   y_out_a/_b   nullable device scalars: the recomputed y.
+ * Flags: ADPAR_ACCUMULATE.
+ * Workspace: adpar_workspace_size(ADPAR_RULE_REDUCE_GENERAL, desc, n, 0). */
+int adpar_vjp_reduce_general(adpar_opdesc desc, int64_t n, const void *a, const void *b,
+                             const void *ybar_a, const void *ybar_b, void *abar, void *bbar,
+                             void *y_out_a, void *y_out_b, uint32_t flags, void *work,
+                             size_t work_bytes, void *stream);
 
 /* The primal forward scan ys = scan (.) as (Sec. 5.2's forward sweep), on
  * its own.  It is the baseline of the AD overhead ratio (VJP time / primal

@@ -22,7 +22,7 @@ OP_ADD, OP_MUL, OP_MIN, OP_MAX, OP_LINREC = 0, 1, 2, 3, 4
 OPS = {"add": OP_ADD, "mul": OP_MUL, "min": OP_MIN, "max": OP_MAX, "linrec": OP_LINREC}
 G_GATHER, G_SCALE, G_SQDIST_ROW = 0, 1, 2
 GFUNS = {"gather": G_GATHER, "scale": G_SCALE, "sqdist_row": G_SQDIST_ROW}
-RULE_REDUCE, RULE_SCAN, RULE_HIST, RULE_SCATTER, RULE_MAP_ACC, RULE_KMEANS = range(6)
+RULE_REDUCE, RULE_SCAN, RULE_HIST, RULE_SCATTER, RULE_MAP_ACC, RULE_KMEANS, RULE_REDUCE_GENERAL = range(7)
 WS_MINIMAL = 0x100  # or'ed into a rule: the smallest accepted workspace
 ACCUMULATE, PROD_LOGDOMAIN, SCATTER_RESTORE = 0x1, 0x4, 0x8
 OK, ERR_TIMEOUT, ERR_TOO_LARGE = 0, 6, 7
@@ -73,6 +73,8 @@ def lib():
         L.adpar_noalloc_scratch_bytes.argtypes = []
         L.adpar_scan.restype = C.c_int
         L.adpar_scan.argtypes = [OpDesc, C.c_int64] + [_VP] * 4 + [_VP, C.c_size_t, _VP]
+        L.adpar_vjp_reduce_general.restype = C.c_int
+        L.adpar_vjp_reduce_general.argtypes = [OpDesc, C.c_int64] + [_VP] * 8 + [C.c_uint32, _VP, C.c_size_t, _VP]
         _bind_optional(L)
         _lib = L
     return _lib
@@ -200,6 +202,43 @@ def adpar_vjp_scan(op, a, ybar_a, b=None, ybar_b=None, abar=None, bbar=None, ys_
                               _stream(stream))
     _check("adpar_vjp_scan", st)
     return abar, bbar, work
+
+
+def adpar_vjp_reduce_general(op, a, ybar_a, b=None, ybar_b=None, abar=None, bbar=None, accumulate=False,
+                             work=None, stream=None):
+    """Reduce VJP by the general rule (C: adpar_vjp_reduce_general).
+
+    ``ybar_a``/``ybar_b`` are scalars or one-element device tensors.
+    Returns (abar, bbar, y) with y a device tensor of the operator's width.
+    """
+    opc = OPS[op] if isinstance(op, str) else int(op)
+    n = a.numel()
+    dt = _dtype_code(a)
+    w = 2 if opc == OP_LINREC else 1
+
+    def scalar(v):
+        if isinstance(v, torch.Tensor):
+            return v.to(device=a.device, dtype=a.dtype).reshape(1).contiguous()
+        return torch.full((1,), float(v), dtype=a.dtype, device=a.device)
+    ya = scalar(ybar_a)
+    yb = scalar(ybar_b if ybar_b is not None else 0.0) if w == 2 else None
+    if abar is None:
+        abar = torch.zeros_like(a) if accumulate else torch.empty_like(a)
+    if w == 2 and bbar is None:
+        bbar = torch.zeros_like(a) if accumulate else torch.empty_like(a)
+    for t in (b, abar, bbar):
+        if t is not None and (t.dtype != a.dtype or t.numel() != n):
+            raise ValueError("all reduce arrays must share dtype and length")
+    y = torch.empty(2 if w == 2 else 1, dtype=a.dtype, device=a.device)
+    need = adpar_workspace_size(RULE_REDUCE_GENERAL, opc, dt, n)
+    if work is None or work.numel() < need:
+        work = workspace(need, a.device)
+    st = lib().adpar_vjp_reduce_general(OpDesc(opc, dt, w), n, _ptr(a), _ptr(b), _ptr(ya), _ptr(yb), _ptr(abar),
+                                        _ptr(bbar), _ptr(y[0:1]), _ptr(y[1:2]) if w == 2 else None,
+                                        ACCUMULATE if accumulate else 0, _ptr(work), work.numel(),
+                                        _stream(stream))
+    _check("adpar_vjp_reduce_general", st)
+    return abar, bbar, y
 
 
 def adpar_scan(op, a, b=None, ys_a=None, ys_b=None, work=None, stream=None):

@@ -30,6 +30,7 @@ extern "C" size_t adpar_workspace_size(int rule, adpar_opdesc d, int64_t n, int6
     rule &= ~ADPAR_WS_MINIMAL;
     switch (rule) {
     case ADPAR_RULE_SCAN: return adpar::scan_workspace_size(d, n, minimal);
+    case ADPAR_RULE_REDUCE_GENERAL: return adpar::scan_workspace_size(d, n, true);  // the scan's slots
     case ADPAR_RULE_REDUCE: return n < 0 ? (size_t)-1 : adpar::reduce_workspace_size(d);
     case ADPAR_RULE_HIST: return n < 0 ? (size_t)-1 : adpar::hist_workspace_size(d, m);
     case ADPAR_RULE_KMEANS: return n < 0 ? (size_t)-1 : adpar::kmeans_workspace_size(m);

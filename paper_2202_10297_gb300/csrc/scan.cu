@@ -269,6 +269,173 @@ int dispatch_scan_forward(int op, int64_t n, const void* a, const void* b, void*
     return ADPAR_ERR_INVALID;
 }
 
+// ------------------------------------------- reduce, general rule (Sec. 5.1.1)
+// y = a_0 (.) ... (.) a_{n-1} for any operator above, and
+//   a_bar_i (+)= d(l_i (.) a_i (.) r_i)/d a_i ^T y_bar
+// with l_i = a_0 (.) ... (.) a_{i-1} (forward exclusive scan) and
+// r_i = a_{i+1} (.) ... (.) a_{n-1} (reverse exclusive scan).  Pass P above
+// gives every tile's l at its first element; this pass takes tiles right to
+// left, re-forms l inside the tile from that carry, forms r with a reverse
+// block scan of the operator's own state and a look-back over the tiles to
+// the right, and applies mid_vjp per element.
+template <class Op, class T, int K, int V>
+__device__ __forceinline__ void reduce_general_tile(const ScanArgs& A, int64_t t_log, const T* ybar_a,
+                                                    const T* ybar_b, T* y_a, T* y_b) {
+    using P = typename Op::P;
+    constexpr int NW = kScanBlock / 32, W = Op::kWidth, TILE = K * kScanBlock * V;
+    __shared__ P s_totF[K * NW];
+    __shared__ P s_totR[K * NW];
+    __shared__ P s_carry;
+    __shared__ P s_suf;
+    const int64_t tile = A.tiles - 1 - t_log;  // data tile (t_log counts from the right)
+    const int64_t base = tile * TILE;
+    const T* a = static_cast<const T*>(A.a);
+    const T* b = static_cast<const T*>(A.b);
+
+    T av[K][V], bv[K][V];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int64_t e = base + (int64_t)k * kScanBlock * V + threadIdx.x * V;
+        load_chunk(a, e, A.n, Op::pad_a(), av[k]);  // padding is the neutral element
+        if constexpr (W == 2) load_chunk(b, e, A.n, T(0), bv[k]);
+        else {
+#pragma unroll
+            for (int j = 0; j < V; ++j) bv[k][j] = T(0);
+        }
+    }
+    if (threadIdx.x == 0) s_carry = static_cast<const P*>(A.carry)[tile];
+    P agg[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        P acc = Op::pelem(av[k][0], bv[k][0]);
+#pragma unroll
+        for (int j = 1; j < V; ++j) acc = Op::pcomb(acc, Op::pelem(av[k][j], bv[k][j]));
+        agg[k] = acc;
+    }
+    auto fc = [](const P& l, const P& r) { return Op::pcomb(l, r); };
+    // reverse scan order: e holds elements later in the array, l earlier ones
+    auto rc = [](const P& e, const P& l) { return Op::pcomb(l, e); };
+    P wexF[K], wexR[K];
+    const P totF = block_scan_part1<P, false, K, NW>(agg, wexF, s_totF, Op::pid(), fc);
+    const P totR = block_scan_part1<P, true, K, NW>(agg, wexR, s_totR, Op::pid(), rc);
+    if ((threadIdx.x >> 5) == 0) {
+        LookbackState<P> st{A.lbR_agg, A.lbR_incl};
+        const P suf = lookback(t_log, st, totR, Op::pid(), rc, A.hdr);
+        if ((threadIdx.x & 31) == 0) {
+            s_suf = suf;
+            if (tile == A.tiles - 1 && y_a) {  // y = (everything before this tile) (.) this tile
+                const P y = Op::pcomb(s_carry, totF);
+                *y_a = Op::out_a(y);
+                if constexpr (W == 2) *y_b = Op::out_b(y);
+            }
+        }
+    }
+    __syncthreads();
+
+    const T ya = *ybar_a;
+    const T yb = W == 2 ? *ybar_b : T(0);
+    T* abar = static_cast<T*>(A.abar);
+    T* bbar = static_cast<T*>(A.bbar);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int64_t e = base + (int64_t)k * kScanBlock * V + threadIdx.x * V;
+        if (e >= A.n) continue;
+        P lj[V];
+        lj[0] = block_scan_excl<P, false, K, NW>(k, wexF, s_totF, s_carry, fc);
+#pragma unroll
+        for (int j = 1; j < V; ++j) lj[j] = Op::pcomb(lj[j - 1], Op::pelem(av[k][j - 1], bv[k][j - 1]));
+        P r = block_scan_excl<P, true, K, NW>(k, wexR, s_totR, s_suf, rc);
+        T oa[V], ob[V];
+#pragma unroll
+        for (int j = V - 1; j >= 0; --j) {
+            T o1 = T(0), o2 = T(0);
+            Op::mid_vjp(lj[j], av[k][j], bv[k][j], r, ya, yb, o1, o2);
+            oa[j] = o1;
+            ob[j] = o2;
+            if (j > 0) r = Op::pcomb(Op::pelem(av[k][j], bv[k][j]), r);
+        }
+        if (A.accumulate) {
+            T old[V];
+            load_chunk_keep(static_cast<const T*>(A.abar), e, A.n, T(0), old);
+#pragma unroll
+            for (int j = 0; j < V; ++j) oa[j] += old[j];
+            if constexpr (W == 2) {
+                load_chunk_keep(static_cast<const T*>(A.bbar), e, A.n, T(0), old);
+#pragma unroll
+                for (int j = 0; j < V; ++j) ob[j] += old[j];
+            }
+        }
+        store_chunk(abar, e, A.n, oa);
+        if constexpr (W == 2) store_chunk(bbar, e, A.n, ob);
+    }
+}
+
+template <class Op, class T>
+__global__ void __launch_bounds__(kScanBlock) reduce_general_kernel(ScanArgs A, const T* ybar_a, const T* ybar_b,
+                                                                     T* y_a, T* y_b) {
+    using Cfg = ScanCfg<Op, T>;
+    __shared__ uint32_t s_tile;
+    if (threadIdx.x == 0) s_tile = atomicAdd(&A.hdr->ticket[1], 1u);
+    __syncthreads();
+    reduce_general_tile<Op, T, Cfg::K, Cfg::E>(A, (int64_t)s_tile, ybar_a, ybar_b, y_a, y_b);
+}
+
+// n = 0: y is the neutral element
+template <class Op, class T>
+__global__ void reduce_neutral_kernel(T* y_a, T* y_b) {
+    if (y_a) *y_a = Op::out_a(Op::pid());
+    if (y_b) *y_b = Op::out_b(Op::pid());
+}
+
+template <class Op, class T>
+int run_reduce_general(int64_t n, const void* a, const void* b, const void* ybar_a, const void* ybar_b,
+                       void* abar, void* bbar, void* y_a, void* y_b, uint32_t flags, void* work,
+                       size_t work_bytes, cudaStream_t stream) {
+    using Cfg = ScanCfg<Op, T>;
+    const ScanLayout L = scan_layout<Op, T>(n);
+    if (work == nullptr || work_bytes < L.total_min || (reinterpret_cast<uintptr_t>(work) & 255u))
+        return ADPAR_ERR_WORKSPACE;
+    if (n == 0) {
+        if (y_a) reduce_neutral_kernel<Op, T><<<1, 1, 0, stream>>>(static_cast<T*>(y_a), static_cast<T*>(y_b));
+        return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
+    }
+    char* w = static_cast<char*>(work);
+    ScanArgs A{};
+    A.n = n;
+    A.a = a; A.b = b;
+    A.abar = abar; A.bbar = bbar;
+    A.accumulate = (flags & ADPAR_ACCUMULATE) ? 1 : 0;
+    A.tiles = (n + Cfg::TILE - 1) / Cfg::TILE;
+    A.hdr = reinterpret_cast<WsHeader*>(w);
+    set_slots(A, w, L);  // the reverse pass's slots hold operator states (no wider than lin_o's)
+    static_assert(lb_words<typename Op::P>() <= lb_words<Lin<T, Op::kWidth, !Op::kCoefOne>>(), "slot width");
+    launch_init(A, w, L, stream);
+    scan_primal_kernel<Op, T><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
+    reduce_general_kernel<Op, T><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(
+        A, static_cast<const T*>(ybar_a), static_cast<const T*>(ybar_b), static_cast<T*>(y_a), static_cast<T*>(y_b));
+    return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
+}
+
+template <class T>
+int dispatch_reduce_general(int op, int64_t n, const void* a, const void* b, const void* ya, const void* yb,
+                            void* abar, void* bbar, void* y_a, void* y_b, uint32_t flags, void* work,
+                            size_t work_bytes, cudaStream_t s) {
+    switch (op) {
+    case ADPAR_OP_ADD:
+        return run_reduce_general<OpAdd<T>, T>(n, a, b, ya, yb, abar, bbar, y_a, y_b, flags, work, work_bytes, s);
+    case ADPAR_OP_MUL:
+        return run_reduce_general<OpMul<T>, T>(n, a, b, ya, yb, abar, bbar, y_a, y_b, flags, work, work_bytes, s);
+    case ADPAR_OP_MIN:
+        return run_reduce_general<OpMin<T>, T>(n, a, b, ya, yb, abar, bbar, y_a, y_b, flags, work, work_bytes, s);
+    case ADPAR_OP_MAX:
+        return run_reduce_general<OpMax<T>, T>(n, a, b, ya, yb, abar, bbar, y_a, y_b, flags, work, work_bytes, s);
+    case ADPAR_OP_LINREC:
+        return run_reduce_general<OpLinrec<T>, T>(n, a, b, ya, yb, abar, bbar, y_a, y_b, flags, work, work_bytes,
+                                                  s);
+    }
+    return ADPAR_ERR_INVALID;
+}
+
 }  // namespace
 
 // minimal = false: the size that runs every pass at full speed (the
@@ -332,4 +499,31 @@ extern "C" int adpar_scan(adpar_opdesc d, int64_t n, const void* a, const void* 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (d.dtype == ADPAR_F32) return dispatch_scan_forward<float>(d.op, n, a, b, ys_a, ys_b, work, work_bytes, s);
     return dispatch_scan_forward<double>(d.op, n, a, b, ys_a, ys_b, work, work_bytes, s);
+}
+
+extern "C" int adpar_vjp_reduce_general(adpar_opdesc d, int64_t n, const void* a, const void* b,
+                                        const void* ybar_a, const void* ybar_b, void* abar, void* bbar,
+                                        void* y_out_a, void* y_out_b, uint32_t flags, void* work,
+                                        size_t work_bytes, void* stream) {
+    using namespace adpar;
+    if (n < 0) return ADPAR_ERR_INVALID;
+    if (d.op < ADPAR_OP_ADD || d.op > ADPAR_OP_LINREC) return ADPAR_ERR_INVALID;
+    if (d.dtype != ADPAR_F32 && d.dtype != ADPAR_F64) return ADPAR_ERR_INVALID;
+    const int want_w = d.op == ADPAR_OP_LINREC ? 2 : 1;
+    if (d.width != want_w) return ADPAR_ERR_INVALID;
+    if (flags & ~(uint32_t)ADPAR_ACCUMULATE) return ADPAR_ERR_UNSUPPORTED;
+    if (want_w == 2 && y_out_a && !y_out_b) return ADPAR_ERR_INVALID;
+    if (n > 0) {
+        if (!a || !ybar_a || !abar) return ADPAR_ERR_INVALID;
+        if (want_w == 2 && (!b || !ybar_b || !bbar)) return ADPAR_ERR_INVALID;
+        const void* ptrs[] = {a, b, abar, bbar};
+        for (const void* p : ptrs)
+            if (p && !aligned16(p)) return ADPAR_ERR_ALIGN;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (d.dtype == ADPAR_F32)
+        return dispatch_reduce_general<float>(d.op, n, a, b, ybar_a, ybar_b, abar, bbar, y_out_a, y_out_b, flags,
+                                              work, work_bytes, s);
+    return dispatch_reduce_general<double>(d.op, n, a, b, ybar_a, ybar_b, abar, bbar, y_out_a, y_out_b, flags,
+                                           work, work_bytes, s);
 }

@@ -11,6 +11,10 @@
 //                    here has J_left = c * I, so c is one scalar even for
 //                    the width-2 LINREC element (its J_left is a_i * I).
 //   vjp_right(...)   J_right(i)^T rs_bar_i = the adjoint of as_i.
+// and, for the general reduce rule of Sec. 5.1.1 (l = the elements before,
+// r = the elements after, as states):
+//   mid_vjp(l, a, b, r, yA, yB)  the adjoint of the element (a, b) in
+//                    y = l (.) (a, b) (.) r, i.e. d(l (.) x (.) r)/dx^T ybar.
 // kNeedPrimal says whether vjp_right reads prev; kCoefNeedsPrimal whether
 // coef does (MIN/MAX: the tie rule compares against prev).  kCoefIsA says
 // that J_left(i) is the element's own a_i (MUL, LINREC): then the product
@@ -51,6 +55,7 @@ struct OpAdd {
     __device__ static T pad_a() { return T(0); }
     __device__ static T coef(P, T) { return T(1); }
     __device__ static void vjp_right(P, T, T, T ra, T, T& oa, T&) { oa = ra; }
+    __device__ static void mid_vjp(P, T, T, P, T ya, T, T& oa, T&) { oa = ya; }
     __device__ static T out_a(P p) { return p.v; }
     __device__ static T out_b(P) { return T(0); }
 };
@@ -69,6 +74,8 @@ struct OpMul {
     __device__ static T pad_a() { return T(1); }
     __device__ static T coef(P, T a) { return a; }
     __device__ static void vjp_right(P prev, T, T, T ra, T, T& oa, T&) { oa = prev.v * ra; }
+    // l a r: the product of all the others (no division, zeros are safe)
+    __device__ static void mid_vjp(P l, T, T, P r, T ya, T, T& oa, T&) { oa = (l.v * r.v) * ya; }
     __device__ static T out_a(P p) { return p.v; }
     __device__ static T out_b(P) { return T(0); }
 };
@@ -90,6 +97,11 @@ struct OpMax {
     __device__ static void vjp_right(P prev, T a, T, T ra, T, T& oa, T&) {
         oa = a > prev.v ? ra : T(0);
     }
+    // the extremum's lowest index: strictly above everything before it, at
+    // least everything after it
+    __device__ static void mid_vjp(P l, T a, T, P r, T ya, T, T& oa, T&) {
+        oa = (a > l.v && a >= r.v) ? ya : T(0);
+    }
     __device__ static T out_a(P p) { return p.v; }
     __device__ static T out_b(P) { return T(0); }
 };
@@ -109,6 +121,9 @@ struct OpMin {
     __device__ static T coef(P prev, T a) { return prev.v <= a ? T(1) : T(0); }
     __device__ static void vjp_right(P prev, T a, T, T ra, T, T& oa, T&) {
         oa = a < prev.v ? ra : T(0);
+    }
+    __device__ static void mid_vjp(P l, T a, T, P r, T ya, T, T& oa, T&) {
+        oa = (a < l.v && a <= r.v) ? ya : T(0);
     }
     __device__ static T out_a(P p) { return p.v; }
     __device__ static T out_b(P) { return T(0); }
@@ -134,6 +149,12 @@ struct OpLinrec {
     __device__ static void vjp_right(P prev, T, T, T ra, T rb, T& oa, T& ob) {
         oa = fma(prev.A, ra, prev.B * rb);
         ob = rb;
+    }
+    // y = l (.) (a, b) (.) r = (rA a lA, rA (a lB + b) + rB):
+    //   dy/da = (rA lA, rA lB),  dy/db = (0, rA)
+    __device__ static void mid_vjp(P l, T, T, P r, T ya, T yb, T& oa, T& ob) {
+        oa = r.A * fma(l.A, ya, l.B * yb);
+        ob = r.A * yb;
     }
     __device__ static T out_a(P p) { return p.A; }
     __device__ static T out_b(P p) { return p.B; }

@@ -25,7 +25,10 @@ MUTANTS = {
     "linrec_jleft_dropped_term": ("Jl->v[1][1] = x[0];", "Jl->v[1][1] = 1.0;"),
     "scan_first_element_dropped": ("for (int c = 0; c < w; ++c) asb[c][0] += rsbar[c];",
                                    "for (int c = 0; c < w; ++c) asb[c][0] += 0.0 * rsbar[c];"),
-    "scan_overwrites_adjoint": ("asb[c][i] += dr[c];", "asb[c][i] = dr[c];"),
+    "scan_overwrites_adjoint": ("rsbar[(i - 1) * w + c] += dl[c];\n            asb[c][i] += dr[c];",
+                                "rsbar[(i - 1) * w + c] += dl[c];\n            asb[c][i] = dr[c];"),
+    "reduce_general_overwrites_adjoint": ("asb[c][i] += dr[c];\n            g[c] = dl[c];",
+                                          "asb[c][i] = dr[c];\n            g[c] = dl[c];"),
     "xd_exponent_dropped": ("r.e = a.e + b.e + e;", "r.e = a.e + b.e;"),
     "hist_chain_wrong_factor": ("g[b] = ft * g[b];", "g[b] = fa * g[b];"),
     "scatter_wrong_index": ("vsbar[j] += ysbar_inout[k];", "vsbar[j] += ysbar_inout[j];"),

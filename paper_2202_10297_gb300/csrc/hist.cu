@@ -304,59 +304,6 @@ __device__ __forceinline__ void mul_into(double* pm, long long* pe, double mi, l
     if (shift) atomicAdd(reinterpret_cast<unsigned long long*>(pe), (unsigned long long)shift);
 }
 
-// FP32 values: the product of a bin's nonzeros is kept in integer fixed
-// point so that no FP64 instruction runs per element (GB300 issues FP64 at
-// 1/64 of the FP32 rate).  A mantissa M in [2^62, 2^63) stands for
-// M * 2^(E - 62); the sign is a parity bit (bit 31 of the zero counter).
-// Each product is truncated to 63 significant bits, a relative error below
-// 2^-61 per factor, so a bin of 2^27 factors stays within 1e-10.
-constexpr unsigned long long kQ62One = 1ull << 62;
-
-// M * mv for a 24-bit mantissa mv in [2^23, 2^24); returns the new M and
-// the exponent increment (23 or 24)
-__device__ __forceinline__ unsigned long long q62_mul24(unsigned long long M, unsigned mv, int& de) {
-    const unsigned long long hi = (unsigned long long)(unsigned)(M >> 32) * mv;  // < 2^55
-    const unsigned long long lo = (unsigned long long)(unsigned)M * mv;          // < 2^56
-    const unsigned long long t24 = (hi << 8) + (lo >> 24);
-    if (t24 >= kQ62One) {
-        de = 24;
-        return t24;
-    }
-    de = 23;
-    return (hi << 9) + (lo >> 23);
-}
-// M1 * M2; returns the new M and the exponent increment (62 or 63)
-__device__ __forceinline__ unsigned long long q62_mul(unsigned long long M1, unsigned long long M2, int& de) {
-    const unsigned long long hi = __umul64hi(M1, M2), lo = M1 * M2;  // product in [2^124, 2^126)
-    if (hi >= (1ull << 61)) {
-        de = 63;
-        return (hi << 1) | (lo >> 63);
-    }
-    de = 62;
-    return (hi << 2) | (lo >> 62);
-}
-// an FP32 value v != 0 as (sign, 24-bit mantissa, exponent): |v| = mv * 2^ev
-__device__ __forceinline__ void split_f32_int(float v, unsigned& sg, unsigned& mv, int& ev) {
-    int bits = __float_as_int(v);
-    sg = (unsigned)bits >> 31;
-    int ex = (bits >> 23) & 0xff;
-    int adj = 0;
-    if (ex == 0) {  // subnormal
-        bits = __float_as_int(v * 16777216.0f);
-        ex = (bits >> 23) & 0xff;
-        adj = -24;
-    }
-    mv = (unsigned)(bits & 0x7fffff) | 0x800000u;
-    ev = ex - 150 + adj;
-}
-// fixed-point state -> (FP64 mantissa in [0.5, 1) with the sign, exponent)
-__device__ __forceinline__ void q62_to_pow2(unsigned long long M, long long E, unsigned sign, double& mm,
-                                            int64_t& e) {
-    // M has its top bit at 62: as a double, 1 <= M * 2^-62 < 2 (rounded to 53 bits)
-    const double x = __longlong_as_double((long long)((1023ull << 52) | ((M << 2) >> 12)));
-    split_pow2(sign ? -x : x, mm, e);
-    e += E;
-}
 // global CAS: *pM = *pM * mv (fixed point); the exponent gets ev + the increment
 __device__ __forceinline__ void q62_mul24_into(unsigned long long* pM, long long* pE, unsigned mv, int ev) {
     unsigned long long old = *reinterpret_cast<volatile unsigned long long*>(pM), assumed, nb;

@@ -95,6 +95,126 @@ struct ProdState {
     }
 };
 
+// FP32 values: a product of nonzeros is kept in integer fixed point so
+// that no FP64 instruction runs per element (GB300 issues FP64 at 1/64 of
+// the FP32 rate).  A mantissa M in [2^62, 2^63) stands for
+// M * 2^(E - 62); the sign is a parity bit (bit 31 of the zero counter).
+// Each product is truncated to 63 significant bits, a relative error below
+// 2^-61 per factor, so a product of 2^27 factors stays within 1e-10.
+constexpr unsigned long long kQ62One = 1ull << 62;
+
+// M * mv for a 24-bit mantissa mv in [2^23, 2^24); returns the new M and
+// the exponent increment (23 or 24)
+__device__ __forceinline__ unsigned long long q62_mul24(unsigned long long M, unsigned mv, int& de) {
+    const unsigned long long hi = (unsigned long long)(unsigned)(M >> 32) * mv;  // < 2^55
+    const unsigned long long lo = (unsigned long long)(unsigned)M * mv;          // < 2^56
+    const unsigned long long t24 = (hi << 8) + (lo >> 24);
+    if (t24 >= kQ62One) {
+        de = 24;
+        return t24;
+    }
+    de = 23;
+    return (hi << 9) + (lo >> 23);
+}
+// M1 * M2; returns the new M and the exponent increment (62 or 63)
+__device__ __forceinline__ unsigned long long q62_mul(unsigned long long M1, unsigned long long M2, int& de) {
+    const unsigned long long hi = __umul64hi(M1, M2), lo = M1 * M2;  // product in [2^124, 2^126)
+    if (hi >= (1ull << 61)) {
+        de = 63;
+        return (hi << 1) | (lo >> 63);
+    }
+    de = 62;
+    return (hi << 2) | (lo >> 62);
+}
+// an FP32 value v != 0 as (sign, 24-bit mantissa, exponent): |v| = mv * 2^ev
+__device__ __forceinline__ void split_f32_int(float v, unsigned& sg, unsigned& mv, int& ev) {
+    int bits = __float_as_int(v);
+    sg = (unsigned)bits >> 31;
+    int ex = (bits >> 23) & 0xff;
+    int adj = 0;
+    if (ex == 0) {  // subnormal
+        bits = __float_as_int(v * 16777216.0f);
+        ex = (bits >> 23) & 0xff;
+        adj = -24;
+    }
+    mv = (unsigned)(bits & 0x7fffff) | 0x800000u;
+    ev = ex - 150 + adj;
+}
+// fixed-point state -> (FP64 mantissa in [0.5, 1) with the sign, exponent)
+__device__ __forceinline__ void q62_to_pow2(unsigned long long M, long long E, unsigned sign, double& mm,
+                                            int64_t& e) {
+    // M has its top bit at 62: as a double, 1 <= M * 2^-62 < 2 (rounded to 53 bits)
+    const double x = __longlong_as_double((long long)((1023ull << 52) | ((M << 2) >> 12)));
+    split_pow2(sign ? -x : x, mm, e);
+    e += E;
+}
+
+// (zero count, lowest zero index, product of the nonzeros) in the
+// fixed-point form above, for FP32 values (24-bit mantissas) and FP64 values
+// (53-bit mantissas, one 64x64-bit product per factor); to_state() gives the
+// FP64 form.
+struct ProdStateQ {
+    unsigned long long M;  // [2^62, 2^63): the product is M * 2^(E - 62)
+    long long E;
+    long long nz;
+    long long first;
+    unsigned sign;  // parity of the negative factors
+
+    __device__ static ProdStateQ id() { return {kQ62One, 0, 0, INT64_MAX, 0u}; }
+    __device__ static ProdStateQ comb(const ProdStateQ& x, const ProdStateQ& y) {
+        ProdStateQ r;
+        int de;
+        r.M = q62_mul(x.M, y.M, de);
+        r.E = x.E + y.E + de - 62;
+        r.nz = x.nz + y.nz;
+        r.first = x.first < y.first ? x.first : y.first;
+        r.sign = x.sign ^ y.sign;
+        return r;
+    }
+    __device__ void push(float a, int64_t i) {
+        if (a == 0.0f) {
+            ++nz;
+            if (i < first) first = i;
+        } else {
+            unsigned sg, mv;
+            int ev, de;
+            split_f32_int(a, sg, mv, ev);
+            M = q62_mul24(M, mv, de);
+            E += ev + de;
+            sign ^= sg;
+        }
+    }
+    __device__ void push(double a, int64_t i) {
+        if (a == 0.0) {
+            ++nz;
+            if (i < first) first = i;
+            return;
+        }
+        long long bits = __double_as_longlong(a);
+        int ex = (int)((bits >> 52) & 0x7ff);
+        int adj = 0;
+        if (ex == 0) {  // subnormal
+            bits = __double_as_longlong(a * 18014398509481984.0);  // 2^54
+            ex = (int)((bits >> 52) & 0x7ff);
+            adj = -54;
+        }
+        // |a| = m53 * 2^(ex - 1075), m53 in [2^52, 2^53): as fixed point
+        // m53 * 2^10 stands for |a| with exponent ex - 1075 + 52
+        const unsigned long long m = ((unsigned long long)(bits & 0xfffffffffffffLL) | (1ull << 52)) << 10;
+        int de;
+        M = q62_mul(M, m, de);
+        E += (ex - 1075 + adj + 52) + de - 62;
+        sign ^= (unsigned)((unsigned long long)bits >> 63);
+    }
+    __device__ ProdState to_state() const {
+        ProdState s;
+        q62_to_pow2(M, E, sign, s.m, s.e);
+        s.nz = nz;
+        s.first = first;
+        return s;
+    }
+};
+
 // ldexp with the exponent clamped to a range where the result is already
 // 0 or infinite, so that a 64-bit exponent never overflows the int argument.
 __device__ __forceinline__ double ldexp_clamped(double x, int64_t e) {
@@ -125,6 +245,22 @@ __device__ __forceinline__ float scale_pow2f(float x, int64_t e) {
     if (ex > 254) return __int_as_float(sign | (0xff << 23));
     if (ex < -30) return __int_as_float(sign);
     return __int_as_float((b & ~(0xff << 23)) | ((int)(ex + 100) << 23)) * 7.888609052210118e-31f;  // 2^-100
+}
+
+// k / m for mantissas with 0.25 <= |k| <= 1 and 0.5 <= |m| < 1: the FP32
+// reciprocal of |m| (relative error below 2^-22) gives q0 = k r0, and one
+// Newton correction of the quotient, q = q0 + (k - m q0) r0, squares that
+// error (below 2^-43 relative): one multiply and two FMAs in FP64.
+__device__ __forceinline__ double quot_mantissa(double k, double m) {
+    const long long bm = __double_as_longlong(m);
+    const long long sign = bm & (long long)0x8000000000000000ULL;
+    const float mf = __int_as_float(0x3F000000 | (int)((bm >> 29) & 0x7FFFFF));  // |m| truncated
+    const int br = __float_as_int(__frcp_rn(mf));
+    double r0 = __longlong_as_double(((long long)(((br >> 23) & 0xff) - 127 + 1023) << 52) |
+                                     ((long long)(br & 0x7FFFFF) << 29));
+    r0 = __longlong_as_double(__double_as_longlong(r0) | sign);  // 1/m carries m's sign
+    const double q0 = k * r0;
+    return fma(fma(-m, q0, k), r0, q0);
 }
 
 // 1 / m for a mantissa with 0.5 <= |m| < 1, by Newton-Raphson on

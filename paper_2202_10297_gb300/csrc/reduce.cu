@@ -14,6 +14,7 @@
 // ticket) combines the per-block partials, so the reduction needs no second
 // launch; the * rule adds one map launch.
 #include <algorithm>
+#include <type_traits>
 #include <math_constants.h>
 
 #include "common.cuh"
@@ -199,33 +200,48 @@ __global__ void __launch_bounds__(kRedBlock) reduce_arg_kernel(ReduceArgs A) {
 }
 
 // ------------------------------------------------------------------ MUL
+// The recompute multiplies mantissas in fixed point on the integer pipes
+// (no FP64 instruction per element for either dtype).
 template <class T>
 __global__ void __launch_bounds__(kRedBlock) reduce_prod_kernel(ReduceArgs A) {
-    __shared__ ProdState s_warp[kRedBlock / 32];
+    using S = ProdStateQ;
+    __shared__ S s_warp[kRedBlock / 32];
     const T* a = static_cast<const T*>(A.a);
     constexpr int V = Vec16<T>::N;
     const int64_t nvec = A.n / V;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    ProdState st = ProdState::id();
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nvec; v += stride) {
+    S st = S::id();
+    constexpr int U = 4;  // vectors in flight per thread
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (; v + (U - 1) * stride < nvec; v += U * stride) {
+        Vec16<T> x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) x[u] = ld_vec(a + (v + u * stride) * V);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int j = 0; j < V; ++j) st.push(x[u].v[j], (v + u * stride) * V + j);
+    }
+    for (; v < nvec; v += stride) {
         Vec16<T> x = ld_vec(a + v * V);
 #pragma unroll
-        for (int j = 0; j < V; ++j) st.push((double)x.v[j], v * V + j);
+        for (int j = 0; j < V; ++j) st.push(x.v[j], v * V + j);
     }
     if (blockIdx.x == 0 && threadIdx.x < A.n - nvec * V) {
         const int64_t i = nvec * V + threadIdx.x;
-        st.push((double)a[i], i);
+        st.push(a[i], i);
     }
-    auto comb = [](const ProdState& x, const ProdState& y) { return ProdState::comb(x, y); };
-    ProdState bs = block_reduce(st, comb, s_warp);
-    if (threadIdx.x == 0) static_cast<ProdState*>(A.partials)[blockIdx.x] = bs;
+    auto comb = [](const S& x, const S& y) { return S::comb(x, y); };
+    S bs = block_reduce(st, comb, s_warp);
+    if (threadIdx.x == 0) static_cast<S*>(A.partials)[blockIdx.x] = bs;
     if (!last_block(A.hdr)) return;
-    ProdState tot = ProdState::id();
+    S totq = S::id();
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-        tot = ProdState::comb(tot, ld_cg(static_cast<ProdState*>(A.partials) + b));
+        totq = S::comb(totq, ld_cg(static_cast<S*>(A.partials) + b));
     __syncthreads();
-    tot = block_reduce(tot, comb, s_warp);
+    totq = block_reduce(totq, comb, s_warp);
     if (threadIdx.x == 0) {
+        const ProdState tot = totq.to_state();
         *static_cast<ProdState*>(A.final_state) = tot;
         if (A.y_out)
             *static_cast<T*>(A.y_out) = tot.nz > 0 ? T(0) : (T)ldexp_clamped(tot.m, tot.e);
@@ -248,23 +264,25 @@ __global__ void __launch_bounds__(kRedBlock) reduce_prod_kernel(ReduceArgs A) {
 // the nonzeros (scaled):  z = 0: abar_i = p / a_i * ybar;  z = 1: only the
 // zero at i0 gets p * ybar;  z >= 2: nothing.  In log mode abar_i holds
 // ln|contribution| (-inf for none) and abar_sign its sign.
+// The map over elements t0, t0 + stride, ... (t0 = 0 writes the single-
+// element cases); st is the recomputed forward state.
 template <class T>
-__global__ void __launch_bounds__(kRedBlock) prod_adjoint_kernel(ReduceArgs A) {
-    const ProdState st = *static_cast<const ProdState*>(A.final_state);
+__device__ __forceinline__ void prod_adjoint_body(const ReduceArgs& A, const ProdState& st, int64_t t0,
+                                                  int64_t stride) {
     const double yb = (double)*static_cast<const T*>(A.ybar);
     T* abar = static_cast<T*>(A.abar);
     const T* a = static_cast<const T*>(A.a);
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     // ybar as (mantissa, exponent) so every factor has a bounded mantissa
     double ym = 0.0;
     int64_t ye = 0;
     if (yb != 0.0) split_pow2(yb, ym, ye);
+    const float qf = (float)(st.m * ym);  // the FP32 path's factor, in [0.25, 1]
     const double lg_p = log(fabs(st.m)) + (double)st.e * 0.69314718055994530942;
     const double lg_y = yb != 0.0 ? log(fabs(yb)) : -CUDART_INF;
     const int sgn_py = (st.m > 0 ? 1 : -1) * (yb > 0 ? 1 : (yb < 0 ? -1 : 0));
 
     if (A.logdomain) {
-        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += stride) {
+        for (int64_t i = t0; i < A.n; i += stride) {
             double lg = -CUDART_INF;
             int sg = 0;
             if (yb != 0.0) {
@@ -284,31 +302,87 @@ __global__ void __launch_bounds__(kRedBlock) prod_adjoint_kernel(ReduceArgs A) {
     }
     if (A.accumulate && st.nz >= 2) return;  // nothing changes
     if (A.accumulate && st.nz == 1) {
-        if (blockIdx.x == 0 && threadIdx.x == 0 && yb != 0.0) {
+        if (t0 == 0 && yb != 0.0) {
             const double c = ldexp_clamped(st.m * ym, st.e + ye);
             abar[st.first] = (T)((double)abar[st.first] + c);
         }
         return;
     }
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += stride) {
+    if constexpr (sizeof(T) == 4) {
+        // FP32, no zero: abar_i = p / a_i * ybar in FP32 arithmetic with the
+        // exponent kept apart (qf = the mantissa of p * ybar), 4 per thread
+        if (st.nz == 0 && yb != 0.0) {
+            const int64_t nv = A.n / 4;
+            const int64_t eb = st.e + ye;
+            auto one = [&](float x) {
+                float mf;
+                int ef;
+                split_pow2_f32m(x, mf, ef);
+                return scale_pow2f(qf * __frcp_rn(mf), eb - ef);
+            };
+            for (int64_t v = t0; v < nv; v += stride) {
+                const float4 x = __ldcs(reinterpret_cast<const float4*>(a) + v);
+                float4 o = make_float4(one(x.x), one(x.y), one(x.z), one(x.w));
+                if (A.accumulate) {
+                    const float4 p = reinterpret_cast<const float4*>(abar)[v];
+                    o.x += p.x; o.y += p.y; o.z += p.z; o.w += p.w;
+                }
+                __stcs(reinterpret_cast<float4*>(abar) + v, o);
+            }
+            const int64_t i = nv * 4 + t0;
+            if (i < A.n) abar[i] = A.accumulate ? abar[i] + one(a[i]) : one(a[i]);
+            return;
+        }
+    }
+    const double kq = st.m * ym;  // the FP64 path's numerator mantissa, in [0.25, 1)
+    if constexpr (sizeof(T) == 8) {
+        // FP64, no zero: abar_i = p / a_i * ybar, two elements per 16-byte vector
+        if (st.nz == 0 && yb != 0.0) {
+            const int64_t nv = A.n / 2;
+            const int64_t eb = st.e + ye;
+            auto one = [&](double x) {
+                double mi;
+                int64_t ei;
+                split_pow2(x, mi, ei);
+                return scale_pow2(quot_mantissa(kq, mi), eb - ei);
+            };
+            for (int64_t v = t0; v < nv; v += stride) {
+                const double2 x = __ldcs(reinterpret_cast<const double2*>(a) + v);
+                double2 o = make_double2(one(x.x), one(x.y));
+                if (A.accumulate) {
+                    const double2 p = reinterpret_cast<const double2*>(abar)[v];
+                    o.x += p.x;
+                    o.y += p.y;
+                }
+                __stcs(reinterpret_cast<double2*>(abar) + v, o);
+            }
+            if (t0 == 0 && (A.n & 1)) {
+                const int64_t i = A.n - 1;
+                abar[i] = A.accumulate ? abar[i] + one(a[i]) : one(a[i]);
+            }
+            return;
+        }
+    }
+    for (int64_t i = t0; i < A.n; i += stride) {
         double c = 0.0;
         if (yb != 0.0) {
             if (st.nz == 0) {
                 double mi;
                 int64_t ei;
                 split_pow2((double)a[i], mi, ei);
-                if constexpr (sizeof(T) == 4) {  // FP32 result: FP32 arithmetic suffices
-                    const float q = (float)(st.m * ym) * __frcp_rn((float)mi);
-                    abar[i] = A.accumulate ? abar[i] + scale_pow2f(q, st.e + ye - ei) : scale_pow2f(q, st.e + ye - ei);
-                    continue;
-                }
-                c = scale_pow2(st.m * ym * recip_mantissa(mi), st.e + ye - ei);
+                c = scale_pow2(quot_mantissa(kq, mi), st.e + ye - ei);
             } else if (st.nz == 1 && i == st.first) {
                 c = ldexp_clamped(st.m * ym, st.e + ye);
             }
         }
         abar[i] = A.accumulate ? (T)((double)abar[i] + c) : (T)c;
     }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kRedBlock) prod_adjoint_kernel(ReduceArgs A) {
+    const ProdState st = *static_cast<const ProdState*>(A.final_state);
+    prod_adjoint_body<T>(A, st, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
 }
 
 // ------------------------------------------------------------ host side
@@ -318,7 +392,7 @@ size_t state_bytes(int op, int dtype) {
     case ADPAR_OP_ADD: return t;
     case ADPAR_OP_MIN:
     case ADPAR_OP_MAX: return 16;
-    case ADPAR_OP_MUL: return sizeof(ProdState);
+    case ADPAR_OP_MUL: return std::max(sizeof(ProdState), sizeof(ProdStateQ));
     }
     return 0;
 }

@@ -63,8 +63,9 @@ def test_prod_reduce_config_logdomain(A, oracle, nz):
 
 @pytest.mark.parametrize("dt", [np.float32, np.float64])
 @pytest.mark.parametrize("nz", [0, 1, 2, 3])
-@pytest.mark.parametrize("n", [1, 2, 3, 7, 1000, 4097, 100003])
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 1000, 4097, 100003, (1 << 18) + 1, 1000003])
 def test_prod_reduce_sizes(A, oracle, dt, nz, n):
+    """Sizes from 1 to past 2^20: one and many blocks in the reduce and the map."""
     g = synth.rng(n * 10 + nz)
     a = g.uniform(0.5, 1.5, n) * np.where(g.random(n) < 0.3, -1.0, 1.0)
     if n < 200:  # representable products: check values too
@@ -89,6 +90,18 @@ def test_prod_reduce_sizes(A, oracle, dt, nz, n):
         np.testing.assert_array_equal(np.isfinite(got), fin)
         assert np.all(np.abs(got[fin] - ref["log"][fin]) <= 1e-5 * np.maximum(1, np.abs(ref["log"][fin])))
         np.testing.assert_array_equal(lg["sign"].cpu().numpy(), ref["sign"])
+
+
+@pytest.mark.parametrize("n", [65536, 1 << 20])
+def test_prod_reduce_clears_status_of_a_dirty_workspace(A, n):
+    """The workspace needs no initialisation: a call leaves its status word ok
+    even in a workspace full of stale bytes."""
+    a, _ = synth.prod_reduce(n, 1)
+    work = torch.full((A.adpar_workspace_size(A.RULE_REDUCE, A.OP_MUL, A.F64, n),), 0xFF, dtype=torch.uint8,
+                      device="cuda")
+    A.adpar_vjp_reduce("mul", dev(a), 1.0, work=work)
+    torch.cuda.synchronize()
+    assert A.adpar_workspace_status(work) == A.OK
 
 
 def test_prod_reduce_accumulate(A, oracle):

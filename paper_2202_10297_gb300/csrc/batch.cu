@@ -70,7 +70,7 @@ __host__ __device__ inline StateLayout state_layout(int dtype, int red, int scan
     const int wr = dtype == ADPAR_F64 ? 6 : 3;  // of a lin_o (dA, dB, c) state
     StateLayout L;
     int64_t o = 0;
-    L.partials = o; o = al16(o + (int64_t)red * (int64_t)sizeof(ProdState));
+    L.partials = o; o = al16(o + (int64_t)red * (int64_t)sizeof(ProdStateQ));
     L.counter = o; o = al16(o + 16);
     L.final_state = o; o = al16(o + (int64_t)sizeof(ProdState));
     L.p_agg = o; o = al16(o + (int64_t)scan * wp * 8);
@@ -99,29 +99,29 @@ __device__ __forceinline__ S block_reduce_256(S v, S (*comb)(const S&, const S&)
     return v;  // valid in thread 0
 }
 
-__device__ ProdState prod_comb(const ProdState& x, const ProdState& y) { return ProdState::comb(x, y); }
+__device__ ProdStateQ prod_comb(const ProdStateQ& x, const ProdStateQ& y) { return ProdStateQ::comb(x, y); }
 
 // product reduce tile r of a segment
 template <class T>
 __device__ void prod_reduce_tile(const adpar_batch_segment& sg, char* st, const StateLayout& L, int red, int r,
                                  int RT, WsHeader* hdr) {
-    __shared__ ProdState s_warp[8];
+    __shared__ ProdStateQ s_warp[8];
     __shared__ int s_last;
     const T* x = static_cast<const T*>(sg.x);
     const int64_t lo = (int64_t)r * RT, hi = std::min<int64_t>(sg.len, lo + RT);
-    ProdState ps = ProdState::id();
+    ProdStateQ ps = ProdStateQ::id();  // fixed-point products: no FP64 per element
     constexpr int V = Vec16<T>::N;
     for (int64_t i = lo + threadIdx.x * V; i < hi; i += 256 * V) {
         if (i + V <= hi) {
             Vec16<T> v = ld_vec(x + i);
 #pragma unroll
-            for (int j = 0; j < V; ++j) ps.push((double)v.v[j], i + j);
+            for (int j = 0; j < V; ++j) ps.push(v.v[j], i + j);
         } else {
-            for (int64_t j = i; j < hi; ++j) ps.push((double)x[j], j);
+            for (int64_t j = i; j < hi; ++j) ps.push(x[j], j);
         }
     }
-    ProdState bs = block_reduce_256<ProdState>(ps, prod_comb, s_warp);
-    ProdState* partials = reinterpret_cast<ProdState*>(st + L.partials);
+    ProdStateQ bs = block_reduce_256<ProdStateQ>(ps, prod_comb, s_warp);
+    ProdStateQ* partials = reinterpret_cast<ProdStateQ*>(st + L.partials);
     unsigned int* counter = reinterpret_cast<unsigned int*>(st + L.counter);
     if (threadIdx.x == 0) {
         partials[r] = bs;
@@ -131,11 +131,12 @@ __device__ void prod_reduce_tile(const adpar_batch_segment& sg, char* st, const 
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    ProdState tot = ProdState::id();
-    for (int q = threadIdx.x; q < red; q += 256) tot = ProdState::comb(tot, ld_cg(partials + q));
+    ProdStateQ totq = ProdStateQ::id();
+    for (int q = threadIdx.x; q < red; q += 256) totq = ProdStateQ::comb(totq, ld_cg(partials + q));
     __syncthreads();
-    tot = block_reduce_256<ProdState>(tot, prod_comb, s_warp);
+    totq = block_reduce_256<ProdStateQ>(totq, prod_comb, s_warp);
     if (threadIdx.x == 0) {
+        const ProdState tot = totq.to_state();
         *reinterpret_cast<ProdState*>(st + L.final_state) = tot;
         if (sg.aux) {
             adpar_prod_aux a;
@@ -172,19 +173,23 @@ __device__ void prod_map_tile(const adpar_batch_segment& sg, char* st, const Sta
     double ym = 0.0;
     int64_t ye = 0;
     if (yb != 0.0) split_pow2(yb, ym, ye);
+    const double kq = f.m * ym;     // mantissa of p * ybar
+    const float qf = (float)kq;
     for (int64_t i = lo + threadIdx.x; i < hi; i += 256) {
         double c = 0.0;
         if (yb != 0.0) {
             if (f.nz == 0) {
-                double mi;
-                int64_t ei;
-                split_pow2((double)x[i], mi, ei);
                 if constexpr (sizeof(T) == 4) {  // FP32 output: FP32 arithmetic suffices
-                    const float q = (float)(f.m * ym) * __frcp_rn((float)mi);
-                    xb[i] = scale_pow2f(q, f.e + ye - ei);
+                    float mf;
+                    int ef;
+                    split_pow2_f32m(static_cast<const float*>(sg.x)[i], mf, ef);
+                    xb[i] = scale_pow2f(qf * __frcp_rn(mf), f.e + ye - ef);
                     continue;
                 } else {
-                    c = scale_pow2(f.m * ym * recip_mantissa(mi), f.e + ye - ei);
+                    double mi;
+                    int64_t ei;
+                    split_pow2((double)x[i], mi, ei);
+                    c = scale_pow2(quot_mantissa(kq, mi), f.e + ye - ei);
                 }
             } else if (f.nz == 1 && i == f.first) {
                 c = ldexp_clamped(f.m * ym, f.e + ye);

@@ -316,6 +316,55 @@ int oracle_scan_vjp(int op, int64_t n,
 }
 
 /* ---------------------------------------------------------------------
+ * Forward mode (JVP) of the inclusive scan: the primal loop carried with
+ * dual numbers, rs_i = rs_{i-1} (.) as_i and
+ *   rsdot_i = J_left(i) rsdot_{i-1} + J_right(i) asdot_i,
+ * with the same per-operator Jacobians as the reverse sweep above (applied
+ * forward, not transposed) and rs_0 = as_0, rsdot_0 = asdot_0.
+ * ------------------------------------------------------------------- */
+static void mat_vec(const mat2 *M, const double *x, double *y, int w)
+{
+    for (int i = 0; i < w; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < w; ++j) s += M->v[i][j] * x[j];
+        y[i] = s;
+    }
+}
+
+int oracle_scan_jvp(int op, int64_t n,
+                    const double *as0, const double *as1,
+                    const double *ad0, const double *ad1,
+                    double *ys0, double *ys1, double *yd0, double *yd1)
+{
+    if (op < O_ADD || op > O_LINREC) return 1;
+    int w = (op == O_LINREC) ? 2 : 1;
+    if (n == 0) return 0;
+    const double *as[2] = { as0, as1 };
+    const double *ad[2] = { ad0, ad1 };
+    double *ys[2] = { ys0, ys1 };
+    double *yd[2] = { yd0, yd1 };
+    double rs[2], rd[2];
+    for (int c = 0; c < w; ++c) { rs[c] = as[c][0]; rd[c] = ad[c][0]; }
+    for (int c = 0; c < w; ++c) { ys[c][0] = rs[c]; yd[c][0] = rd[c]; }
+    for (int64_t i = 1; i < n; ++i) {
+        double x[2], xd[2], out[2], t1[2], t2[2];
+        mat2 Jl, Jr;
+        for (int c = 0; c < w; ++c) { x[c] = as[c][i]; xd[c] = ad[c][i]; }
+        scan_jacobians(op, rs, x, &Jl, &Jr);
+        mat_vec(&Jl, rd, t1, w);
+        mat_vec(&Jr, xd, t2, w);
+        scan_combine(op, rs, x, out);
+        for (int c = 0; c < w; ++c) {
+            rs[c] = out[c];
+            rd[c] = t1[c] + t2[c];
+            ys[c][i] = rs[c];
+            yd[c][i] = rd[c];
+        }
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------------------
  * Reduce with an arbitrary associative operator (Sec. 5.1.1, the general
  * rule), any width: y = e (.) a_0 (.) ... (.) a_{n-1}.  Plain tape sweep:
  * the forward loop records t_i = e (.) a_0 (.) ... (.) a_{i-1}; the reverse

@@ -45,9 +45,10 @@ def lib():
         L.oracle_kmeans.argtypes = [i64, C.c_int, C.c_int, _D, _D, dbl, _D, _I64,
                                     _D, _D]
         L.oracle_reduce_general_vjp.argtypes = [C.c_int, i64, _D, _D, dbl, dbl, _D, _D, _D]
+        L.oracle_scan_jvp.argtypes = [C.c_int, i64, _D, _D, _D, _D, _D, _D, _D, _D]
         for f in ("oracle_reduce_vjp", "oracle_prod_reduce_vjp", "oracle_scan_vjp",
                   "oracle_hist_vjp", "oracle_hist_prod_vjp", "oracle_scatter_vjp",
-                  "oracle_map_acc_vjp", "oracle_kmeans", "oracle_reduce_general_vjp"):
+                  "oracle_map_acc_vjp", "oracle_kmeans", "oracle_reduce_general_vjp", "oracle_scan_jvp"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -80,6 +81,23 @@ def reduce_vjp(op, a, ybar=1.0, abar=None):
     _check(lib().oracle_reduce_vjp(OPS[op], n, _p(a), float(ybar), C.byref(y),
                                    _p(out), C.byref(arg)), "reduce_vjp")
     return y.value, out, arg.value
+
+
+def scan_jvp(op, a, adot, b=None, bdot=None):
+    """Forward mode of the inclusive scan (dual numbers).  Returns
+    (ys_a, ys_b, ysdot_a, ysdot_b); the b parts only for linrec."""
+    a = _f64(a)
+    ad = _f64(adot)
+    n = a.size
+    w2 = op == "linrec"
+    ya, yd = np.empty(n), np.empty(n)
+    yb = ydb = None
+    if w2:
+        b, bd = _f64(b), _f64(bdot)
+        yb, ydb = np.empty(n), np.empty(n)
+    _check(lib().oracle_scan_jvp(OPS[op], n, _p(a), _p(b) if w2 else None, _p(ad), _p(bd) if w2 else None,
+                                 _p(ya), _p(yb), _p(yd), _p(ydb)), "scan_jvp")
+    return ya, yb, yd, ydb
 
 
 def reduce_general_vjp(op, a, ybar, b=None, ybar_b=0.0, abar=None, bbar=None):

@@ -38,6 +38,8 @@ MUTANTS = {
                     "ybar * (2.0) * (X[i * d + j] - C[arg * d + j]);"),
     "prod_zero_count_off": ("if (first < 0) first = i;\n            ++nz;",
                             "if (first < 0) first = i + 1;\n            ++nz;"),
+    "jvp_right_jacobian_transposed": ("mat_vec(&Jr, xd, t2, w);", "mat_t_vec(&Jr, xd, t2, w);"),
+    "jvp_left_term_dropped": ("rd[c] = t1[c] + t2[c];", "rd[c] = t2[c];"),
     "reduce_general_jacobians_swapped": ("mat_t_vec(&Jr, g, dr, w);\n        mat_t_vec(&Jl, g, dl, w);",
                                          "mat_t_vec(&Jl, g, dr, w);\n        mat_t_vec(&Jr, g, dl, w);"),
     "reduce_general_linrec_neutral": ("if (op == O_LINREC) { t[0] = 1.0; t[1] = 0.0; }",

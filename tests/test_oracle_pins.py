@@ -384,6 +384,64 @@ def test_reduce_general_empty_and_accumulate(oracle):
     np.testing.assert_array_equal(ab, [13.0, 2.0])
 
 
+# ------------------------------------------------------- forward mode (JVP)
+@pytest.mark.parametrize("op", ["add", "mul", "min", "max", "linrec"])
+def test_scan_jvp_vjp_duality(oracle, op):
+    """<ybar, J xdot> = <J^T ybar, xdot> against the (separately pinned) VJP."""
+    g = synth.rng(31)
+    n = 45
+    if op in ("min", "max"):
+        a = g.normal(size=n)  # no ties: the derivative is defined
+    elif op == "mul":
+        a = g.uniform(0.5, 1.5, n)
+    else:
+        a = g.uniform(0.9, 1.1, n)
+    b = g.normal(size=n)
+    ad, bd = g.normal(size=n), g.normal(size=n)
+    ya, yb = g.normal(size=n), g.normal(size=n)
+    if op == "linrec":
+        _, _, yda, ydb = oracle.scan_jvp(op, a, ad, b, bd)
+        vab, vbb, _, _ = oracle.scan_vjp(op, a, ya, b, yb)
+        lhs = ya @ yda + yb @ ydb
+        rhs = vab @ ad + vbb @ bd
+    else:
+        _, _, yda, _ = oracle.scan_jvp(op, a, ad)
+        vab, _, _, _ = oracle.scan_vjp(op, a, ya)
+        lhs, rhs = ya @ yda, vab @ ad
+    assert abs(lhs - rhs) <= 1e-12 * (1 + abs(lhs))
+
+
+def test_scan_jvp_linrec_finite_differences(oracle):
+    """A, B are multilinear: the central difference along (adot, bdot) is exact up to rounding."""
+    g = synth.rng(32)
+    n = 30
+    a = g.uniform(0.9, 1.1, n)
+    b = g.normal(size=n)
+    ad, bd = g.normal(size=n), g.normal(size=n)
+    ya, yb, yda, ydb = oracle.scan_jvp("linrec", a, ad, b, bd)
+    A, B = _linrec_forward(a, b)
+    np.testing.assert_allclose(ya, A, rtol=1e-13)
+    np.testing.assert_allclose(yb, B, rtol=1e-12, atol=1e-14)
+    # the tangent is a polynomial of degree <= n in h: use exact-ish small h on both sides
+    h = 1e-4
+    Ap, Bp = _linrec_forward(a + h * ad, b + h * bd)
+    Am, Bm = _linrec_forward(a - h * ad, b - h * bd)
+    np.testing.assert_allclose(yda, (Ap - Am) / (2 * h), rtol=1e-6, atol=1e-8)
+    np.testing.assert_allclose(ydb, (Bp - Bm) / (2 * h), rtol=1e-6, atol=1e-8)
+
+
+def test_scan_jvp_add_and_max_definitions(oracle):
+    g = synth.rng(33)
+    n = 50
+    a = np.round(g.normal(size=n) * 4) / 4  # ties: the earlier element keeps the record
+    ad = g.normal(size=n)
+    _, _, yd, _ = oracle.scan_jvp("add", a, ad)
+    np.testing.assert_allclose(yd, np.cumsum(ad), rtol=1e-13, atol=1e-14)
+    _, _, yd, _ = oracle.scan_jvp("max", a, ad)
+    arg = np.array([int(np.argmax(a[: i + 1])) for i in range(n)])  # first index of the running max
+    np.testing.assert_array_equal(yd, ad[arg])
+
+
 def test_scan_accumulates(oracle):
     """Adjoints are added into the given arrays (Eq. rewrite-adj, +=)."""
     yb = np.array([1.0, 2.0, 3.0])

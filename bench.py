@@ -30,6 +30,8 @@ JSON line each; these are measurements, not the headline line):
   reduce_general  reduce VJP by the general rule (two exclusive scans): the
            linear recurrence at 2^26 pairs FP32/FP64; general vs special
            rules for +, max and * at 2^28 FP32
+  jvp      forward-mode scan rule: linear recurrence 2^26 FP32/FP64, max scan
+           2^28 FP32, against the primal forward scan
   serve    Poisson arrivals of mixed-operator requests sized 2^10..2^24:
            p50/p99 latency and throughput vs one call at a time
   call     one entry point on a small case, --reps times (the profiling
@@ -565,6 +567,47 @@ def row_reduce_general(args):
                                "sample": "linear recurrence, n = 2^20 FP64"})
 
 
+def row_jvp(args):
+    """Forward-mode (JVP) scan rule: the linear recurrence at 2^26 pairs FP32/FP64
+    and the max scan at 2^28 FP32, against the primal forward scan."""
+    import torch
+    from oracle import oracle as O
+    from paper_2202_10297_gb300 import adpar as A
+    from paper_2202_10297_gb300 import synth
+    hbm, _ = measured_peaks()
+    cases = {}
+    n = 1 << LOG2_LINREC
+    for dt, name in ((np.float32, "linrec_f32"), (np.float64, "linrec_f64")):
+        a, b, _, _ = synth.linrec(n, dt, seed=synth.SEED_BASE + 1)
+        at, bt = _dev(a), _dev(b)
+        ad, bd = torch.randn_like(at), torch.randn_like(at)
+        oa, ob = torch.empty_like(at), torch.empty_like(at)
+        code = A.F64 if dt == np.float64 else A.F32
+        wk = A.workspace(A.adpar_workspace_size(A.RULE_SCAN | A.WS_MINIMAL, A.OP_LINREC, code, n), "cuda")
+        t = _cuda_ms(lambda: A.adpar_jvp_scan("linrec", at, ad, b=bt, bdot=bd, ysdot_a=oa, ysdot_b=ob, work=wk), 10, 3)
+        tp = _cuda_ms(lambda: A.adpar_scan("linrec", at, b=bt, ys_a=oa, ys_b=ob, work=wk), 10, 3)
+        w = np.dtype(dt).itemsize
+        alg = 6 * w * n  # a, b, adot, bdot in; ysdot_a, ysdot_b out
+        cases[name] = {"ms": t, "elements_per_s": n / t * 1e3, "algorithmic_bytes": alg,
+                       "hbm_frac_of_measured": alg / t / 1e6 / hbm, "primal_ms": tp, "jvp_primal_ratio": t / tp}
+        del at, bt, ad, bd, oa, ob, wk
+    n = 1 << LOG2_SCAN
+    x = torch.randn(n, device="cuda")
+    xd = torch.randn_like(x)
+    o = torch.empty_like(x)
+    wk = A.workspace(A.adpar_workspace_size(A.RULE_SCAN | A.WS_MINIMAL, A.OP_MAX, A.F32, n), "cuda")
+    t = _cuda_ms(lambda: A.adpar_jvp_scan("max", x, xd, ysdot_a=o, work=wk), 10, 3)
+    tp = _cuda_ms(lambda: A.adpar_scan("max", x, ys_a=o, work=wk), 10, 3)
+    cases["max_f32_2^28"] = {"ms": t, "elements_per_s": n / t * 1e3, "algorithmic_bytes": 12 * n,
+                             "hbm_frac_of_measured": 12 * n / t / 1e6 / hbm, "primal_ms": tp, "jvp_primal_ratio": t / tp}
+    small = synth.linrec(1 << 20, np.float64, seed=synth.SEED_BASE + 1)
+    sd = np.ones(1 << 20)
+    rate = _oracle_rate(lambda: O.scan_jvp("linrec", small[0], sd, small[1], sd), 1 << 20, 2.0)
+    return _line("jvp", metric="forward-mode scan elements/s and % of HBM", cases=cases,
+                 cpu_baseline={"value": rate, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                               "sample": "linear recurrence, n = 2^20 FP64"})
+
+
 def row_hist(args):
     """reduce_by_index VJPs (Sec. 5.1.2), n = 2^27 FP32."""
     import torch
@@ -796,7 +839,7 @@ def row_call(args):
 
 
 ROWS = {"prod": row_prod, "hist": row_hist, "scatter": row_scatter, "kmeans": row_kmeans, "batch": row_batch,
-        "serve": row_serve, "call": row_call, "reduce_general": row_reduce_general}
+        "serve": row_serve, "call": row_call, "reduce_general": row_reduce_general, "jvp": row_jvp}
 
 
 def main():
@@ -807,7 +850,7 @@ def main():
     ap.add_argument("--impl", default="adpar", choices=["adpar", "reference"])
     ap.add_argument("--workload", default="scan",
                     choices=["scan", "prod", "hist", "scatter", "kmeans", "batch", "serve", "call",
-                             "reduce_general"])
+                             "reduce_general", "jvp"])
     ap.add_argument("--call", default="scan-linrec-f64", choices=sorted(CALLS_ONE))
     ap.add_argument("--log2n", type=int, default=24)
     ap.add_argument("--reps", type=int, default=3)

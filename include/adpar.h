@@ -240,6 +240,23 @@ int adpar_vjp_reduce_general(adpar_opdesc desc, int64_t n, const void *a, const 
                              void *y_out_a, void *y_out_b, uint32_t flags, void *work,
                              size_t work_bytes, void *stream);
 
+/* Forward mode (JVP) of the inclusive scan: the tangent ysdot = d ys(as)
+ * [asdot] of ys = scan (.) as, i.e. the forward-mode rule of the scan in the
+ * sense of Sec. 3 (dual numbers carried through the operator):
+ *   ys_i = ys_{i-1} (.) as_i,
+ *   ysdot_i = J_left(i) ysdot_{i-1} + J_right(i) asdot_i,
+ * computed as one single-pass scan of (value, tangent) pairs.  MIN/MAX give
+ * the tangent of the running record (the earlier element on ties).
+ * Arguments (b, bdot, ys_b, ysdot_b for LINREC only):
+ *   n              number of elements (0 allowed).
+ *   a, b           [n] inputs;  adot, bdot [n] their tangents.
+ *   ys_a, ys_b     nullable [n]: the primal outputs.
+ *   ysdot_a/_b     [n] the output tangents.
+ * Workspace: as for adpar_scan (ADPAR_RULE_SCAN | ADPAR_WS_MINIMAL). */
+int adpar_jvp_scan(adpar_opdesc desc, int64_t n, const void *a, const void *b, const void *adot,
+                   const void *bdot, void *ys_a, void *ys_b, void *ysdot_a, void *ysdot_b, void *work,
+                   size_t work_bytes, void *stream);
+
 /* The primal forward scan ys = scan (.) as (Sec. 5.2's forward sweep), on
  * its own.  It is the baseline of the AD overhead ratio (VJP time / primal
  * time, Sec. 7).  Arguments as for adpar_vjp_scan; ys_a (and ys_b for

@@ -73,6 +73,8 @@ def lib():
         L.adpar_noalloc_scratch_bytes.argtypes = []
         L.adpar_scan.restype = C.c_int
         L.adpar_scan.argtypes = [OpDesc, C.c_int64] + [_VP] * 4 + [_VP, C.c_size_t, _VP]
+        L.adpar_jvp_scan.restype = C.c_int
+        L.adpar_jvp_scan.argtypes = [OpDesc, C.c_int64] + [_VP] * 8 + [_VP, C.c_size_t, _VP]
         L.adpar_vjp_reduce_general.restype = C.c_int
         L.adpar_vjp_reduce_general.argtypes = [OpDesc, C.c_int64] + [_VP] * 8 + [C.c_uint32, _VP, C.c_size_t, _VP]
         _bind_optional(L)
@@ -239,6 +241,34 @@ def adpar_vjp_reduce_general(op, a, ybar_a, b=None, ybar_b=None, abar=None, bbar
                                         _stream(stream))
     _check("adpar_vjp_reduce_general", st)
     return abar, bbar, y
+
+
+def adpar_jvp_scan(op, a, adot, b=None, bdot=None, want_ys=False, ysdot_a=None, ysdot_b=None, work=None,
+                   stream=None):
+    """Forward-mode tangent of an inclusive scan (C: adpar_jvp_scan).
+
+    Returns (ysdot_a, ysdot_b, ys_a, ys_b); the b parts for linrec only, the
+    ys parts when ``want_ys``."""
+    opc = OPS[op] if isinstance(op, str) else int(op)
+    n = a.numel()
+    dt = _dtype_code(a)
+    w = 2 if opc == OP_LINREC else 1
+    for t in (adot, b, bdot, ysdot_a, ysdot_b):
+        if t is not None and (t.dtype != a.dtype or t.numel() != n):
+            raise ValueError("all scan arrays must share dtype and length")
+    if ysdot_a is None:
+        ysdot_a = torch.empty_like(a)
+    if w == 2 and ysdot_b is None:
+        ysdot_b = torch.empty_like(a)
+    ys_a = torch.empty_like(a) if want_ys else None
+    ys_b = torch.empty_like(a) if (want_ys and w == 2) else None
+    need = adpar_workspace_size(RULE_SCAN | WS_MINIMAL, opc, dt, n)
+    if work is None or work.numel() < need:
+        work = workspace(need, a.device)
+    st = lib().adpar_jvp_scan(OpDesc(opc, dt, w), n, _ptr(a), _ptr(b), _ptr(adot), _ptr(bdot), _ptr(ys_a),
+                              _ptr(ys_b), _ptr(ysdot_a), _ptr(ysdot_b), _ptr(work), work.numel(), _stream(stream))
+    _check("adpar_jvp_scan", st)
+    return ysdot_a, ysdot_b, ys_a, ys_b
 
 
 def adpar_scan(op, a, b=None, ys_a=None, ys_b=None, work=None, stream=None):

@@ -269,6 +269,56 @@ int dispatch_scan_forward(int op, int64_t n, const void* a, const void* b, void*
     return ADPAR_ERR_INVALID;
 }
 
+// ----------------------------------------------------- forward mode (JVP)
+template <class Op, class T>
+__global__ void __launch_bounds__(kScanBlock) scan_jvp_kernel(ScanArgs A, const T* ad, const T* bd, T* yd_a,
+                                                               T* yd_b) {
+    using Cfg = ScanCfg<Op, T>;
+    __shared__ uint32_t s_tile;
+    if (threadIdx.x == 0) s_tile = atomicAdd(&A.hdr->ticket[0], 1u);
+    __syncthreads();
+    scan_jvp_tile<Op, T, Cfg::K, Cfg::E>(A, (int64_t)s_tile, ad, bd, yd_a, yd_b);
+}
+
+template <class Op, class T>
+int run_scan_jvp(int64_t n, const void* a, const void* b, const void* ad, const void* bd, void* ys_a, void* ys_b,
+                 void* yd_a, void* yd_b, void* work, size_t work_bytes, cudaStream_t stream) {
+    using Cfg = ScanCfg<Op, T>;
+    using P = typename Op::P;
+    const ScanLayout L = scan_layout<Op, T>(n);
+    if (work == nullptr || work_bytes < L.total_min || (reinterpret_cast<uintptr_t>(work) & 255u))
+        return ADPAR_ERR_WORKSPACE;
+    if (n == 0) return ADPAR_OK;
+    // the dual state's slots: 2 words(P) per tile in each of the two regions
+    static_assert(lb_words<DualState<Op>>() == 2 * lb_words<P>(), "dual slots");
+    static_assert(lb_words<P>() <= lb_words<Lin<T, Op::kWidth, !Op::kCoefOne>>(), "slot width");
+    char* w = static_cast<char*>(work);
+    ScanArgs A{};
+    A.n = n;
+    A.a = a; A.b = b; A.ys_a = ys_a; A.ys_b = ys_b;
+    A.tiles = (n + Cfg::TILE - 1) / Cfg::TILE;
+    A.hdr = reinterpret_cast<WsHeader*>(w);
+    set_slots(A, w, L);
+    launch_init(A, w, L, stream);
+    scan_jvp_kernel<Op, T><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(
+        A, static_cast<const T*>(ad), static_cast<const T*>(bd), static_cast<T*>(yd_a), static_cast<T*>(yd_b));
+    return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
+}
+
+template <class T>
+int dispatch_scan_jvp(int op, int64_t n, const void* a, const void* b, const void* ad, const void* bd, void* ys_a,
+                      void* ys_b, void* yd_a, void* yd_b, void* work, size_t work_bytes, cudaStream_t s) {
+    switch (op) {
+    case ADPAR_OP_ADD: return run_scan_jvp<OpAdd<T>, T>(n, a, b, ad, bd, ys_a, ys_b, yd_a, yd_b, work, work_bytes, s);
+    case ADPAR_OP_MUL: return run_scan_jvp<OpMul<T>, T>(n, a, b, ad, bd, ys_a, ys_b, yd_a, yd_b, work, work_bytes, s);
+    case ADPAR_OP_MIN: return run_scan_jvp<OpMin<T>, T>(n, a, b, ad, bd, ys_a, ys_b, yd_a, yd_b, work, work_bytes, s);
+    case ADPAR_OP_MAX: return run_scan_jvp<OpMax<T>, T>(n, a, b, ad, bd, ys_a, ys_b, yd_a, yd_b, work, work_bytes, s);
+    case ADPAR_OP_LINREC:
+        return run_scan_jvp<OpLinrec<T>, T>(n, a, b, ad, bd, ys_a, ys_b, yd_a, yd_b, work, work_bytes, s);
+    }
+    return ADPAR_ERR_INVALID;
+}
+
 // ------------------------------------------- reduce, general rule (Sec. 5.1.1)
 // y = a_0 (.) ... (.) a_{n-1} for any operator above, and
 //   a_bar_i (+)= d(l_i (.) a_i (.) r_i)/d a_i ^T y_bar
@@ -526,4 +576,27 @@ extern "C" int adpar_vjp_reduce_general(adpar_opdesc d, int64_t n, const void* a
                                               work, work_bytes, s);
     return dispatch_reduce_general<double>(d.op, n, a, b, ybar_a, ybar_b, abar, bbar, y_out_a, y_out_b, flags,
                                            work, work_bytes, s);
+}
+
+extern "C" int adpar_jvp_scan(adpar_opdesc d, int64_t n, const void* a, const void* b, const void* adot,
+                              const void* bdot, void* ys_a, void* ys_b, void* ysdot_a, void* ysdot_b, void* work,
+                              size_t work_bytes, void* stream) {
+    using namespace adpar;
+    if (n < 0) return ADPAR_ERR_INVALID;
+    if (d.op < ADPAR_OP_ADD || d.op > ADPAR_OP_LINREC) return ADPAR_ERR_INVALID;
+    if (d.dtype != ADPAR_F32 && d.dtype != ADPAR_F64) return ADPAR_ERR_INVALID;
+    const int want_w = d.op == ADPAR_OP_LINREC ? 2 : 1;
+    if (d.width != want_w) return ADPAR_ERR_INVALID;
+    if (n > 0) {
+        if (!a || !adot || !ysdot_a) return ADPAR_ERR_INVALID;
+        if (want_w == 2 && (!b || !bdot || !ysdot_b)) return ADPAR_ERR_INVALID;
+        if (want_w == 2 && ys_a && !ys_b) return ADPAR_ERR_INVALID;
+        const void* ptrs[] = {a, b, adot, bdot, ys_a, ys_b, ysdot_a, ysdot_b};
+        for (const void* p : ptrs)
+            if (p && !aligned16(p)) return ADPAR_ERR_ALIGN;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (d.dtype == ADPAR_F32)
+        return dispatch_scan_jvp<float>(d.op, n, a, b, adot, bdot, ys_a, ys_b, ysdot_a, ysdot_b, work, work_bytes, s);
+    return dispatch_scan_jvp<double>(d.op, n, a, b, adot, bdot, ys_a, ys_b, ysdot_a, ysdot_b, work, work_bytes, s);
 }

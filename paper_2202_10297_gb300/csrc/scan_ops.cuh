@@ -15,6 +15,9 @@
 // r = the elements after, as states):
 //   mid_vjp(l, a, b, r, yA, yB)  the adjoint of the element (a, b) in
 //                    y = l (.) (a, b) (.) r, i.e. d(l (.) x (.) r)/dx^T ybar.
+// and, for forward mode (JVP):
+//   tcomb(l, tl, r, tr)  the tangent of l (.) r given the tangents tl, tr of
+//                    l and r (a state of the same shape).
 // kNeedPrimal says whether vjp_right reads prev; kCoefNeedsPrimal whether
 // coef does (MIN/MAX: the tie rule compares against prev).  kCoefIsA says
 // that J_left(i) is the element's own a_i (MUL, LINREC): then the product
@@ -56,6 +59,7 @@ struct OpAdd {
     __device__ static T coef(P, T) { return T(1); }
     __device__ static void vjp_right(P, T, T, T ra, T, T& oa, T&) { oa = ra; }
     __device__ static void mid_vjp(P, T, T, P, T ya, T, T& oa, T&) { oa = ya; }
+    __device__ static P tcomb(P, P tl, P, P tr) { return {tl.v + tr.v}; }
     __device__ static T out_a(P p) { return p.v; }
     __device__ static T out_b(P) { return T(0); }
 };
@@ -76,6 +80,7 @@ struct OpMul {
     __device__ static void vjp_right(P prev, T, T, T ra, T, T& oa, T&) { oa = prev.v * ra; }
     // l a r: the product of all the others (no division, zeros are safe)
     __device__ static void mid_vjp(P l, T, T, P r, T ya, T, T& oa, T&) { oa = (l.v * r.v) * ya; }
+    __device__ static P tcomb(P l, P tl, P r, P tr) { return {fma(tl.v, r.v, l.v * tr.v)}; }
     __device__ static T out_a(P p) { return p.v; }
     __device__ static T out_b(P) { return T(0); }
 };
@@ -102,6 +107,7 @@ struct OpMax {
     __device__ static void mid_vjp(P l, T a, T, P r, T ya, T, T& oa, T&) {
         oa = (a > l.v && a >= r.v) ? ya : T(0);
     }
+    __device__ static P tcomb(P l, P tl, P r, P tr) { return r.v > l.v ? tr : tl; }  // ties: the earlier
     __device__ static T out_a(P p) { return p.v; }
     __device__ static T out_b(P) { return T(0); }
 };
@@ -125,6 +131,7 @@ struct OpMin {
     __device__ static void mid_vjp(P l, T a, T, P r, T ya, T, T& oa, T&) {
         oa = (a < l.v && a <= r.v) ? ya : T(0);
     }
+    __device__ static P tcomb(P l, P tl, P r, P tr) { return r.v < l.v ? tr : tl; }
     __device__ static T out_a(P p) { return p.v; }
     __device__ static T out_b(P) { return T(0); }
 };
@@ -155,6 +162,10 @@ struct OpLinrec {
     __device__ static void mid_vjp(P l, T, T, P r, T ya, T yb, T& oa, T& ob) {
         oa = r.A * fma(l.A, ya, l.B * yb);
         ob = r.A * yb;
+    }
+    // d(rA lA, rA lB + rB) = (trA lA + rA tlA, trA lB + rA tlB + trB)
+    __device__ static P tcomb(P l, P tl, P r, P tr) {
+        return {fma(tr.A, l.A, r.A * tl.A), fma(tr.A, l.B, fma(r.A, tl.B, tr.B))};
     }
     __device__ static T out_a(P p) { return p.A; }
     __device__ static T out_b(P p) { return p.B; }

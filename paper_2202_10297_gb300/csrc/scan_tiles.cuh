@@ -553,6 +553,80 @@ __device__ __forceinline__ void scan_adjoint_fac_tile(const ScanArgs& A, int64_t
     }
 }
 
+// ----------------------------------------------------- forward mode (JVP)
+// The tangent of ys = scan (.) as along asdot: one forward single-pass scan
+// of dual elements (value, tangent) whose combine is (l (.) r, tcomb).  The
+// tangent of the padding (and of the neutral element) is zero.
+template <class Op>
+struct DualState {
+    typename Op::P v, t;
+};
+
+template <class Op, class T, int K, int V>
+__device__ __forceinline__ void scan_jvp_tile(const ScanArgs& A, int64_t tile, const T* ad, const T* bd, T* yd_a,
+                                              T* yd_b) {
+    using D = DualState<Op>;
+    constexpr int NW = kScanBlock / 32, W = Op::kWidth, TILE = K * kScanBlock * V;
+    __shared__ D s_tot[K * NW];
+    __shared__ D s_pref;
+    const int64_t base = tile * TILE;
+    const T* a = static_cast<const T*>(A.a);
+    const T* b = static_cast<const T*>(A.b);
+
+    T av[K][V], bv[K][V], tav[K][V], tbv[K][V];
+    D agg[K];
+    auto delem = [&](int k, int j) {
+        return D{Op::pelem(av[k][j], W == 2 ? bv[k][j] : T(0)), Op::pelem(tav[k][j], W == 2 ? tbv[k][j] : T(0))};
+    };
+    auto comb = [](const D& l, const D& r) { return D{Op::pcomb(l.v, r.v), Op::tcomb(l.v, l.t, r.v, r.t)}; };
+    const D ident{Op::pid(), Op::pelem(T(0), T(0))};
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int64_t e = base + (int64_t)k * kScanBlock * V + threadIdx.x * V;
+        load_chunk(a, e, A.n, Op::pad_a(), av[k]);
+        load_chunk(ad, e, A.n, T(0), tav[k]);
+        if constexpr (W == 2) {
+            load_chunk(b, e, A.n, T(0), bv[k]);
+            load_chunk(bd, e, A.n, T(0), tbv[k]);
+        }
+        D acc = delem(k, 0);
+#pragma unroll
+        for (int j = 1; j < V; ++j) acc = comb(acc, delem(k, j));
+        agg[k] = acc;
+    }
+    D wex[K];
+    const D total = block_scan_part1<D, false, K, NW>(agg, wex, s_tot, ident, comb);
+    if ((threadIdx.x >> 5) == 0) {
+        // a dual state is two primal states: its aggregate and inclusive
+        // slots take the primal and the adjoint slot regions
+        LookbackState<D> st{A.lbP_agg, A.lbR_agg};
+        const D pre = lookback(tile, st, total, ident, comb, A.hdr);
+        if ((threadIdx.x & 31) == 0) s_pref = pre;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int64_t e = base + (int64_t)k * kScanBlock * V + threadIdx.x * V;
+        if (e >= A.n) continue;
+        D cur = block_scan_excl<D, false, K, NW>(k, wex, s_tot, s_pref, comb);
+        T y1[V], y2[V], t1[V], t2[V];
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            cur = comb(cur, delem(k, j));
+            y1[j] = Op::out_a(cur.v);
+            y2[j] = Op::out_b(cur.v);
+            t1[j] = Op::out_a(cur.t);
+            t2[j] = Op::out_b(cur.t);
+        }
+        if (A.ys_a) {
+            store_chunk(static_cast<T*>(A.ys_a), e, A.n, y1);
+            if constexpr (W == 2) store_chunk(static_cast<T*>(A.ys_b), e, A.n, y2);
+        }
+        store_chunk(yd_a, e, A.n, t1);
+        if constexpr (W == 2) store_chunk(yd_b, e, A.n, t2);
+    }
+}
+
 // ------------------------------------------------------- primal forward scan
 // The forward operator itself (ys = scan (.) as), used as the primal
 // baseline of the VJP/primal time ratio.  One single pass with look-back.

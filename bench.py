@@ -30,6 +30,8 @@ JSON line each; these are measurements, not the headline line):
   reduce_general  reduce VJP by the general rule (two exclusive scans): the
            linear recurrence at 2^26 pairs FP32/FP64; general vs special
            rules for +, max and * at 2^28 FP32
+  scan_vec vectorised scan VJP (d column scans of row-major [n][d]): linear
+           recurrence and max over [2^14, 2^12]
   jvp      forward-mode scan rule: linear recurrence 2^26 FP32/FP64, max scan
            2^28 FP32, against the primal forward scan
   serve    Poisson arrivals of mixed-operator requests sized 2^10..2^24:
@@ -567,6 +569,38 @@ def row_reduce_general(args):
                                "sample": "linear recurrence, n = 2^20 FP64"})
 
 
+def row_scan_vec(args):
+    """Vectorised scan VJP (Sec. 5.2: a scan over d-vectors = d column scans):
+    the linear recurrence over [2^14 rows, 2^12 channels] FP32/FP64 and the
+    max scan over the same shape FP32 (2^26 elements each)."""
+    import torch
+    from paper_2202_10297_gb300 import adpar as A
+    hbm, _ = measured_peaks()
+    n, d = 1 << 14, 1 << 12
+    cases = {}
+    g = torch.Generator(device="cuda").manual_seed(20220221 + 6)
+    for dt, name in ((torch.float32, "linrec_f32"), (torch.float64, "linrec_f64")):
+        a = torch.rand((n, d), device="cuda", dtype=dt, generator=g) * 0.1 + 0.9
+        b, ya, yb = (torch.randn((n, d), device="cuda", dtype=dt, generator=g) for _ in range(3))
+        ab, bb = torch.empty_like(a), torch.empty_like(a)
+        code = A.F64 if dt == torch.float64 else A.F32
+        wk = A.workspace(A.adpar_workspace_size(A.RULE_SCAN_VEC, A.OP_LINREC, code, n, d), "cuda")
+        t = _cuda_ms(lambda: A.adpar_vjp_scan_vec("linrec", a, ya, b=b, ybar_b=yb, abar=ab, bbar=bb, work=wk), 10, 3)
+        w = a.element_size()
+        alg = 6 * w * n * d
+        cases[name] = {"rows": n, "channels": d, "ms": t, "elements_per_s": n * d / t * 1e3,
+                       "algorithmic_bytes": alg, "hbm_frac_of_measured": alg / t / 1e6 / hbm}
+        del a, b, ya, yb, ab, bb, wk
+    x = torch.randn((n, d), device="cuda", generator=g)
+    y = torch.randn((n, d), device="cuda", generator=g)
+    xb = torch.empty_like(x)
+    wk = A.workspace(A.adpar_workspace_size(A.RULE_SCAN_VEC, A.OP_MAX, A.F32, n, d), "cuda")
+    t = _cuda_ms(lambda: A.adpar_vjp_scan_vec("max", x, y, abar=xb, work=wk), 10, 3)
+    cases["max_f32"] = {"rows": n, "channels": d, "ms": t, "elements_per_s": n * d / t * 1e3,
+                        "algorithmic_bytes": 12 * n * d, "hbm_frac_of_measured": 12 * n * d / t / 1e6 / hbm}
+    return _line("scan_vec", metric="vectorised scan VJP elements/s and % of HBM", cases=cases)
+
+
 def row_jvp(args):
     """Forward-mode (JVP) scan rule: the linear recurrence at 2^26 pairs FP32/FP64
     and the max scan at 2^28 FP32, against the primal forward scan."""
@@ -839,7 +873,8 @@ def row_call(args):
 
 
 ROWS = {"prod": row_prod, "hist": row_hist, "scatter": row_scatter, "kmeans": row_kmeans, "batch": row_batch,
-        "serve": row_serve, "call": row_call, "reduce_general": row_reduce_general, "jvp": row_jvp}
+        "serve": row_serve, "call": row_call, "reduce_general": row_reduce_general, "jvp": row_jvp,
+        "scan_vec": row_scan_vec}
 
 
 def main():
@@ -850,7 +885,7 @@ def main():
     ap.add_argument("--impl", default="adpar", choices=["adpar", "reference"])
     ap.add_argument("--workload", default="scan",
                     choices=["scan", "prod", "hist", "scatter", "kmeans", "batch", "serve", "call",
-                             "reduce_general", "jvp"])
+                             "reduce_general", "jvp", "scan_vec"])
     ap.add_argument("--call", default="scan-linrec-f64", choices=sorted(CALLS_ONE))
     ap.add_argument("--log2n", type=int, default=24)
     ap.add_argument("--reps", type=int, default=3)

@@ -74,7 +74,8 @@ typedef enum {
     ADPAR_RULE_SCATTER = 3,
     ADPAR_RULE_MAP_ACC = 4,
     ADPAR_RULE_KMEANS = 5,
-    ADPAR_RULE_REDUCE_GENERAL = 6
+    ADPAR_RULE_REDUCE_GENERAL = 6,
+    ADPAR_RULE_SCAN_VEC = 7   /* m = the vector length d */
 } adpar_rule;
 
 /* or'ed into the rule of adpar_workspace_size: the smallest workspace the
@@ -239,6 +240,20 @@ int adpar_vjp_reduce_general(adpar_opdesc desc, int64_t n, const void *a, const 
                              const void *ybar_a, const void *ybar_b, void *abar, void *bbar,
                              void *y_out_a, void *y_out_b, uint32_t flags, void *work,
                              size_t work_bytes, void *stream);
+
+/* VJP of a scan over d-vectors with an elementwise operator (Sec. 5.2, the
+ * vectorised case): the arrays are row-major [n][d] and
+ *   scan (map (.)) e xs = transpose xs |> map (scan (.) e) |> transpose,
+ * i.e. d independent scans down the columns (for LINREC: d channels of the
+ * recurrence h_t = a_t h_{t-1} + b_t).  Outputs as adpar_vjp_scan, column
+ * by column; no transpose is materialised.
+ * Arguments: n rows, d columns; a, b, ybar_a, ybar_b, abar, bbar [n][d]
+ * (b, ybar_b, bbar for LINREC only; a may be NULL for ADD).
+ * Flags: ADPAR_ACCUMULATE.
+ * Workspace: adpar_workspace_size(ADPAR_RULE_SCAN_VEC, desc, n, d). */
+int adpar_vjp_scan_vec(adpar_opdesc desc, int64_t n, int64_t d, const void *a, const void *b,
+                       const void *ybar_a, const void *ybar_b, void *abar, void *bbar, uint32_t flags,
+                       void *work, size_t work_bytes, void *stream);
 
 /* Forward mode (JVP) of the inclusive scan: the tangent ysdot = d ys(as)
  * [asdot] of ys = scan (.) as, i.e. the forward-mode rule of the scan in the

@@ -22,7 +22,7 @@ OP_ADD, OP_MUL, OP_MIN, OP_MAX, OP_LINREC = 0, 1, 2, 3, 4
 OPS = {"add": OP_ADD, "mul": OP_MUL, "min": OP_MIN, "max": OP_MAX, "linrec": OP_LINREC}
 G_GATHER, G_SCALE, G_SQDIST_ROW = 0, 1, 2
 GFUNS = {"gather": G_GATHER, "scale": G_SCALE, "sqdist_row": G_SQDIST_ROW}
-RULE_REDUCE, RULE_SCAN, RULE_HIST, RULE_SCATTER, RULE_MAP_ACC, RULE_KMEANS, RULE_REDUCE_GENERAL = range(7)
+RULE_REDUCE, RULE_SCAN, RULE_HIST, RULE_SCATTER, RULE_MAP_ACC, RULE_KMEANS, RULE_REDUCE_GENERAL, RULE_SCAN_VEC = range(8)
 WS_MINIMAL = 0x100  # or'ed into a rule: the smallest accepted workspace
 ACCUMULATE, PROD_LOGDOMAIN, SCATTER_RESTORE = 0x1, 0x4, 0x8
 OK, ERR_TIMEOUT, ERR_TOO_LARGE = 0, 6, 7
@@ -73,6 +73,8 @@ def lib():
         L.adpar_noalloc_scratch_bytes.argtypes = []
         L.adpar_scan.restype = C.c_int
         L.adpar_scan.argtypes = [OpDesc, C.c_int64] + [_VP] * 4 + [_VP, C.c_size_t, _VP]
+        L.adpar_vjp_scan_vec.restype = C.c_int
+        L.adpar_vjp_scan_vec.argtypes = [OpDesc, C.c_int64, C.c_int64] + [_VP] * 6 + [C.c_uint32, _VP, C.c_size_t, _VP]
         L.adpar_jvp_scan.restype = C.c_int
         L.adpar_jvp_scan.argtypes = [OpDesc, C.c_int64] + [_VP] * 8 + [_VP, C.c_size_t, _VP]
         L.adpar_vjp_reduce_general.restype = C.c_int
@@ -241,6 +243,33 @@ def adpar_vjp_reduce_general(op, a, ybar_a, b=None, ybar_b=None, abar=None, bbar
                                         _stream(stream))
     _check("adpar_vjp_reduce_general", st)
     return abar, bbar, y
+
+
+def adpar_vjp_scan_vec(op, a, ybar_a, b=None, ybar_b=None, abar=None, bbar=None, accumulate=False, work=None,
+                       stream=None):
+    """VJP of a scan over the rows of [n, d] arrays, column by column (C: adpar_vjp_scan_vec).
+    Returns (abar, bbar, work)."""
+    opc = OPS[op] if isinstance(op, str) else int(op)
+    if ybar_a.dim() != 2:
+        raise ValueError("arrays must be [n, d]")
+    n, d = ybar_a.shape
+    dt = _dtype_code(ybar_a)
+    w = 2 if opc == OP_LINREC else 1
+    for t in (a, b, ybar_b, abar, bbar):
+        if t is not None and (t.dtype != ybar_a.dtype or tuple(t.shape) != (n, d) or not t.is_contiguous()):
+            raise ValueError("all arrays must be contiguous [n, d] of one dtype")
+    if abar is None:
+        abar = torch.zeros_like(ybar_a) if accumulate else torch.empty_like(ybar_a)
+    if w == 2 and bbar is None:
+        bbar = torch.zeros_like(ybar_a) if accumulate else torch.empty_like(ybar_a)
+    need = adpar_workspace_size(RULE_SCAN_VEC, opc, dt, n, d)
+    if work is None or work.numel() < need:
+        work = workspace(need, ybar_a.device)
+    st = lib().adpar_vjp_scan_vec(OpDesc(opc, dt, w), n, d, _ptr(a), _ptr(b), _ptr(ybar_a), _ptr(ybar_b),
+                                  _ptr(abar), _ptr(bbar), ACCUMULATE if accumulate else 0, _ptr(work),
+                                  work.numel(), _stream(stream))
+    _check("adpar_vjp_scan_vec", st)
+    return abar, bbar, work
 
 
 def adpar_jvp_scan(op, a, adot, b=None, bdot=None, want_ys=False, ysdot_a=None, ysdot_b=None, work=None,

@@ -5,7 +5,8 @@ only its INPUTS; every backward re-executes the primal inside the VJP
 kernels (the redundant-execution policy of Sec. 4: no tape, no stored
 intermediate) and returns the adjoints the paper's rule gives.
 
-    scan(op, a, b=None)           inclusive scan; LINREC returns (A, B)
+    scan(op, a, b=None)           inclusive scan; LINREC returns (A, B); reverse
+                                  and forward mode (torch.autograd.forward_ad)
     reduce(op, a)                 0-dim result
     reduce_by_index(op, vals, inds, m)
     scatter(xs, is_, vs)          out of place: xs is not modified
@@ -27,7 +28,20 @@ class _Scan(torch.autograd.Function):
         ya, yb, _ = A.adpar_scan(op, a, b=b)
         ctx.op = op
         ctx.save_for_backward(a, b)
+        ctx.save_for_forward(a, b)
         return (ya, yb) if op == "linrec" else ya
+
+    @staticmethod
+    def jvp(ctx, _, ta, tb):
+        # forward mode: the dual-number scan (adpar_jvp_scan)
+        a, b = ctx.saved_tensors
+        ta = torch.zeros_like(a) if ta is None else ta.contiguous()
+        if ctx.op == "linrec":
+            tb = torch.zeros_like(a) if tb is None else tb.contiguous()
+            yd_a, yd_b, _, _ = A.adpar_jvp_scan("linrec", a, ta, b=b, bdot=tb)
+            return yd_a, yd_b
+        yd_a, _, _, _ = A.adpar_jvp_scan(ctx.op, a, ta)
+        return yd_a
 
     @staticmethod
     def backward(ctx, ga, gb=None):

@@ -43,6 +43,35 @@ def test_gradcheck_linrec(AG):
     assert gradcheck(lambda x, y: AG.scan("linrec", x, y), (a, b), eps=1e-6, atol=1e-8)
 
 
+@pytest.mark.parametrize("op", ["add", "mul", "max", "min"])
+def test_forward_ad_scan_gradcheck(AG, op):
+    """Forward mode through the Function's jvp (the library's dual-number scan),
+    checked by torch against numerical directional derivatives."""
+    g = synth.rng(3)
+    a = g.uniform(0.6, 1.4, 37) if op == "mul" else g.permutation(37).astype(np.float64) + g.uniform(0, 0.5, 37)
+    assert gradcheck(lambda x: AG.scan(op, x), (t64(a),), eps=1e-6, atol=1e-8, nondet_tol=1e-12,
+                     check_forward_ad=True, check_backward_ad=False, check_undefined_grad=False,
+                     check_batched_grad=False)
+
+
+def test_forward_ad_linrec_vs_oracle(AG, oracle):
+    """torch.autograd.forward_ad dual tensors through scan("linrec") give the
+    oracle's dual-number tangents (FP64, several tiles)."""
+    import torch.autograd.forward_ad as fwAD
+    g = synth.rng(4)
+    n = 20011
+    a = g.uniform(0.9, 1.0, n)
+    b, ad, bd = g.standard_normal(n), g.standard_normal(n), g.standard_normal(n)
+    with fwAD.dual_level():
+        da = fwAD.make_dual(t64(a, False), t64(ad, False))
+        db = fwAD.make_dual(t64(b, False), t64(bd, False))
+        ya, yb = AG.scan("linrec", da, db)
+        ta, tb = fwAD.unpack_dual(ya).tangent, fwAD.unpack_dual(yb).tangent
+    _, _, rda, rdb = oracle.scan_jvp("linrec", a, ad, b, bd)
+    assert rel_l2(ta.cpu().numpy(), rda) < 1e-12
+    assert rel_l2(tb.cpu().numpy(), rdb) < 1e-12
+
+
 @pytest.mark.parametrize("op,zeros", [("add", 0), ("mul", 0), ("mul", 1), ("mul", 2), ("max", 0), ("min", 0)])
 def test_gradcheck_reduce(AG, op, zeros):
     g = synth.rng(3)

@@ -627,3 +627,74 @@ int oracle_kmeans(int64_t N, int d, int k, const double *X, const double *C,
     if (loss_out) *loss_out = loss;
     return 0;
 }
+
+/* ---------------------------------------------------------------------
+ * reduce_by_index with any operator of this file, any width (Sec. 5.1.2,
+ * the general rule; LINREC included): the semantic loop
+ *   hs = replicate m e;  for i: hs[inds[i]] = hs[inds[i]] (.) vals[i]
+ * taken in increasing i, so an operator that does not commute combines
+ * each bin's elements in index order.  Tape: tp_i = the bin's running
+ * value before element i.  Reverse sweep with one adjoint per bin,
+ * starting at hsbar[bin]:
+ *   for i = n-1..0 (bin k = inds[i] in range):
+ *     valsbar_i += J_right(tp_i, v_i)^T gk;   gk = J_left(tp_i, v_i)^T gk
+ * with the per-operator Jacobians of the scan sweep.  Indices outside
+ * [0, m) are skipped.  vals0/vals1, hsbar0/hsbar1, vbar0/vbar1 and
+ * hs_out0/hs_out1 are the width components (the *1 ones for LINREC only);
+ * vbar is accumulated, hs_out (nullable) receives the primal.
+ * ------------------------------------------------------------------- */
+int oracle_hist_general_vjp(int op, int64_t n, int64_t m,
+                            const double *vals0, const double *vals1,
+                            const int64_t *inds,
+                            const double *hsbar0, const double *hsbar1,
+                            double *vbar0, double *vbar1,
+                            double *hs_out0, double *hs_out1)
+{
+    if (op < O_ADD || op > O_LINREC) return 1;
+    int w = (op == O_LINREC) ? 2 : 1;
+    size_t mm = (size_t)(m > 0 ? m : 1), nn = (size_t)(n > 0 ? n : 1);
+    double *bins = (double *)malloc(sizeof(double) * mm * (size_t)w);
+    double *tp = (double *)malloc(sizeof(double) * nn * (size_t)w);
+    double *gb = (double *)malloc(sizeof(double) * mm * (size_t)w);
+    if (!bins || !tp || !gb) { free(bins); free(tp); free(gb); return 2; }
+    const double *vs[2] = { vals0, vals1 };
+    const double *hb[2] = { hsbar0, hsbar1 };
+    double *vb[2] = { vbar0, vbar1 };
+    double *ho[2] = { hs_out0, hs_out1 };
+    for (int64_t k = 0; k < m; ++k) {
+        if (op == O_LINREC) { bins[k * 2] = 1.0; bins[k * 2 + 1] = 0.0; }
+        else bins[k] = neutral_of(op);
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t k = inds[i];
+        if (k < 0 || k >= m) continue;
+        double x[2], out[2];
+        for (int c = 0; c < w; ++c) {
+            x[c] = vs[c][i];
+            tp[i * w + c] = bins[k * w + c];
+        }
+        scan_combine(op, &tp[i * w], x, out);
+        for (int c = 0; c < w; ++c) bins[k * w + c] = out[c];
+    }
+    for (int64_t k = 0; k < m; ++k)
+        for (int c = 0; c < w; ++c) {
+            if (ho[c]) ho[c][k] = bins[k * w + c];
+            gb[k * w + c] = hb[c] ? hb[c][k] : 0.0;
+        }
+    for (int64_t i = n - 1; i >= 0; --i) {
+        int64_t k = inds[i];
+        if (k < 0 || k >= m) continue;
+        double x[2], to_v[2], to_t[2];
+        mat2 Jl, Jr;
+        for (int c = 0; c < w; ++c) x[c] = vs[c][i];
+        scan_jacobians(op, &tp[i * w], x, &Jl, &Jr);
+        mat_t_vec(&Jr, &gb[k * w], to_v, w);
+        mat_t_vec(&Jl, &gb[k * w], to_t, w);
+        for (int c = 0; c < w; ++c) {
+            vb[c][i] += to_v[c];
+            gb[k * w + c] = to_t[c];
+        }
+    }
+    free(bins); free(tp); free(gb);
+    return 0;
+}

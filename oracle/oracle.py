@@ -46,9 +46,12 @@ def lib():
                                     _D, _D]
         L.oracle_reduce_general_vjp.argtypes = [C.c_int, i64, _D, _D, dbl, dbl, _D, _D, _D]
         L.oracle_scan_jvp.argtypes = [C.c_int, i64, _D, _D, _D, _D, _D, _D, _D, _D]
+        L.oracle_hist_general_vjp.argtypes = [C.c_int, i64, i64, _D, _D, _I64, _D, _D, _D, _D,
+                                              _D, _D]
         for f in ("oracle_reduce_vjp", "oracle_prod_reduce_vjp", "oracle_scan_vjp",
                   "oracle_hist_vjp", "oracle_hist_prod_vjp", "oracle_scatter_vjp",
-                  "oracle_map_acc_vjp", "oracle_kmeans", "oracle_reduce_general_vjp", "oracle_scan_jvp"):
+                  "oracle_map_acc_vjp", "oracle_kmeans", "oracle_reduce_general_vjp", "oracle_scan_jvp",
+                  "oracle_hist_general_vjp"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -197,6 +200,27 @@ def hist_prod_vjp(vals, inds, m, hsbar, valsbar=None):
                                       _p(lnz), _p(snz)), "hist_prod_vjp")
     return dict(valsbar=vb, log=lg, sign=sg, nzero=nz[:m], first_zero=fz[:m],
                 lognz=lnz[:m], signnz=snz[:m].astype(np.int64))
+
+
+def hist_general_vjp(op, vals, inds, m, hsbar, b=None, hsbar_b=None, valsbar=None, bbar=None):
+    """reduce_by_index with any operator by the plain tape sweep (Sec. 5.1.2,
+    general rule), bins combined in index order.  Returns
+    (valsbar, bbar, hs_a, hs_b); the b parts only for linrec."""
+    v = _f64(vals)
+    ix = _i64(inds)
+    n = v.size
+    w2 = op == "linrec"
+    hb = _f64(hsbar)
+    vb = np.zeros(n) if valsbar is None else _f64(valsbar).copy()
+    hs_a = np.empty(max(m, 1))
+    bv = hbb = bb = hs_b = None
+    if w2:
+        bv, hbb = _f64(b), _f64(hsbar_b)
+        bb = np.zeros(n) if bbar is None else _f64(bbar).copy()
+        hs_b = np.empty(max(m, 1))
+    _check(lib().oracle_hist_general_vjp(OPS[op], n, m, _p(v), _p(bv), _p(ix, _I64), _p(hb), _p(hbb),
+                                         _p(vb), _p(bb), _p(hs_a), _p(hs_b)), "hist_general_vjp")
+    return vb, bb, hs_a[:m], (hs_b[:m] if w2 else None)
 
 
 def scatter_vjp(n, is_, ysbar, vsbar=None, ys=None, xs_saved=None):

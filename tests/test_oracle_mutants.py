@@ -45,6 +45,12 @@ MUTANTS = {
     "reduce_general_linrec_neutral": ("if (op == O_LINREC) { t[0] = 1.0; t[1] = 0.0; }",
                                       "if (op == O_LINREC) { t[0] = 1.0; t[1] = 1.0; }"),
     "reduce_general_chain_not_carried": ("            g[c] = dl[c];\n", "            g[c] = g[c] + 0.0 * dl[c];\n"),
+    "hist_general_jacobians_swapped": ("mat_t_vec(&Jr, &gb[k * w], to_v, w);\n        mat_t_vec(&Jl, &gb[k * w], to_t, w);",
+                                       "mat_t_vec(&Jl, &gb[k * w], to_v, w);\n        mat_t_vec(&Jr, &gb[k * w], to_t, w);"),
+    "hist_general_chain_not_carried": ("gb[k * w + c] = to_t[c];", "gb[k * w + c] += 0.0 * to_t[c];"),
+    "hist_general_operands_transposed": ("scan_combine(op, &tp[i * w], x, out);",
+                                         "scan_combine(op, x, &tp[i * w], out);"),
+    "hist_general_linrec_neutral": ("bins[k * 2 + 1] = 0.0;", "bins[k * 2 + 1] = 1.0;"),
 }
 
 

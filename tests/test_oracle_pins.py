@@ -512,6 +512,140 @@ def test_hist_minmax_equal_reduce_with_one_bin(oracle):
 
 
 # ------------------------------------------------------------------- scatter
+def _bins_of(inds, m):
+    return [np.flatnonzero(inds == k) for k in range(m)]
+
+
+@pytest.mark.parametrize("op", ["add", "mul", "min", "max"])
+def test_hist_general_definitions(oracle, op):
+    """General-rule reduce_by_index against each operator's definition, bin
+    by bin: + gathers hsbar; * is the product of the bin's other elements
+    (brute force, zeros included); min/max put hsbar at the lowest index of
+    the bin's extremum (numpy's first-index argmax); out-of-range elements
+    get nothing; hs is the bin's reduction and empty bins hold e."""
+    g = synth.rng(41)
+    n, m = 300, 13
+    inds = g.integers(-2, m + 2, n)
+    if op in ("min", "max"):
+        v = np.round(g.normal(size=n) * 3) / 3  # many ties
+    elif op == "mul":
+        v = g.uniform(0.5, 1.5, n)
+        first = [np.flatnonzero(inds == k) for k in (2, 5)]
+        v[first[0][:1]] = 0.0   # one zero in bin 2
+        v[first[1][:2]] = 0.0   # two zeros in bin 5
+    else:
+        v = g.normal(size=n)
+    inds[inds == 7] = -1        # bin 7 empty
+    hsbar = g.normal(size=m)
+    vb, _, hs, _ = oracle.hist_general_vjp(op, v, inds, m, hsbar)
+    ref = np.zeros(n)
+    neutral = {"add": 0.0, "mul": 1.0, "min": np.inf, "max": -np.inf}[op]
+    for k, idx in enumerate(_bins_of(inds, m)):
+        if idx.size == 0:
+            assert hs[k] == neutral
+            continue
+        x = v[idx]
+        if op == "add":
+            ref[idx] = hsbar[k]
+            assert abs(hs[k] - x.sum()) <= 1e-12 * (1 + np.abs(x).sum())
+        elif op == "mul":
+            ref[idx] = [np.prod(np.delete(x, j)) * hsbar[k] for j in range(x.size)]
+            assert abs(hs[k] - np.prod(x)) <= 1e-12 * abs(np.prod(x)) + 1e-300
+        else:
+            j = int(np.argmax(x) if op == "max" else np.argmin(x))
+            ref[idx[j]] = hsbar[k]
+            assert hs[k] == x[j]
+    if op == "mul":
+        np.testing.assert_allclose(vb, ref, rtol=1e-12, atol=0)
+    else:
+        np.testing.assert_allclose(vb, ref, rtol=1e-13, atol=0)
+    assert np.all(vb[(inds < 0) | (inds >= m)] == 0)
+
+
+@pytest.mark.parametrize("op", ["add", "min", "max"])
+def test_hist_general_agrees_with_special_rule_oracle(oracle, op):
+    """The general rule and the special rules of Sec. 5.1.2 (a separate tape
+    sweep with scalar derivatives) give the same adjoint and bins."""
+    g = synth.rng(42)
+    n, m = 500, 9
+    inds = g.integers(-1, m + 1, n)
+    v = np.round(g.normal(size=n) * 2) / 2
+    hsbar = g.normal(size=m)
+    vb, _, hs, _ = oracle.hist_general_vjp(op, v, inds, m, hsbar)
+    vb2, hs2, _ = oracle.hist_vjp(op, v, inds, m, hsbar)
+    np.testing.assert_allclose(vb, vb2, rtol=1e-14, atol=0)
+    np.testing.assert_allclose(hs, hs2, rtol=1e-14, atol=0)
+
+
+def test_hist_general_linrec_finite_differences(oracle):
+    """LINREC bins are (A, B) of each bin's subsequence in index order; the
+    loss sum_k hsbar_A[k] A_k + hsbar_B[k] B_k is multilinear in (a, b), so
+    central differences of the plain per-bin forward loop are exact up to
+    rounding."""
+    g = synth.rng(43)
+    n, m = 60, 5
+    a = g.uniform(0.8, 1.2, n)
+    b = g.normal(size=n)
+    inds = g.integers(-1, m + 1, n)
+    ha, hb = g.normal(size=m), g.normal(size=m)
+
+    def L(a_, b_):
+        tot = 0.0
+        for k, idx in enumerate(_bins_of(inds, m)):
+            if idx.size == 0:
+                tot += ha[k] * 1.0
+                continue
+            A, B = _linrec_forward(a_[idx], b_[idx])
+            tot += ha[k] * A[-1] + hb[k] * B[-1]
+        return tot
+
+    ab, bb, hsA, hsB = oracle.hist_general_vjp("linrec", a, inds, m, ha, b=b, hsbar_b=hb)
+    for k, idx in enumerate(_bins_of(inds, m)):
+        if idx.size:
+            A, B = _linrec_forward(a[idx], b[idx])
+            assert abs(hsA[k] - A[-1]) <= 1e-13 and abs(hsB[k] - B[-1]) <= 1e-12 * (1 + abs(B[-1]))
+        else:
+            assert (hsA[k], hsB[k]) == (1.0, 0.0)
+    h = 0.125
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = h
+        fa = (L(a + e, b) - L(a - e, b)) / (2 * h)
+        fb = (L(a, b + e) - L(a, b - e)) / (2 * h)
+        assert abs(fa - ab[i]) <= 1e-10 * (1 + abs(fa))
+        assert abs(fb - bb[i]) <= 1e-10 * (1 + abs(fb))
+
+
+def test_hist_general_linrec_keeps_index_order(oracle):
+    """LINREC does not commute: reversing the order of one bin's elements
+    changes that bin (and only that bin), so the sweep must combine each
+    bin in index order."""
+    a = np.array([2.0, 3.0, 0.5, 4.0])
+    b = np.array([1.0, -1.0, 2.0, 0.25])
+    inds = np.array([0, 1, 0, 1])
+    _, _, hsA, hsB = oracle.hist_general_vjp("linrec", a, inds, 2, np.ones(2), b=b, hsbar_b=np.ones(2))
+    # bin 0: (2,1) then (0.5,2) -> (1, 0.5*1 + 2); bin 1: (3,-1) then (4,0.25) -> (12, -4 + 0.25)
+    np.testing.assert_array_equal(hsA, [1.0, 12.0])
+    np.testing.assert_array_equal(hsB, [2.5, -3.75])
+
+
+def test_hist_general_one_bin_is_reduce_and_accumulates(oracle):
+    """With every index in bin 0 the rule is the general reduce; ADPAR-style
+    accumulation adds onto the given adjoint and leaves skipped elements."""
+    g = synth.rng(44)
+    n = 31
+    a, b = g.uniform(0.9, 1.1, n), g.normal(size=n)
+    ab, bb, hsA, hsB = oracle.hist_general_vjp("linrec", a, np.zeros(n, np.int64), 1, [0.6], b=b,
+                                               hsbar_b=[-1.1])
+    (yA, yB), rab, rbb = oracle.reduce_general_vjp("linrec", a, 0.6, b=b, ybar_b=-1.1)
+    np.testing.assert_allclose(ab, rab, rtol=1e-14, atol=0)
+    np.testing.assert_allclose(bb, rbb, rtol=1e-14, atol=0)
+    assert abs(hsA[0] - yA) <= 1e-15 and abs(hsB[0] - yB) <= 1e-14
+    vb, _, _, _ = oracle.hist_general_vjp("add", [1.0, 2.0, 3.0], [0, 5, 1], 2, [10.0, 20.0],
+                                          valsbar=[1.0, 1.0, 1.0])
+    np.testing.assert_array_equal(vb, [11.0, 1.0, 21.0])
+
+
 def test_scatter_closed_form(oracle):
     n, m = 4096, 1000
     is_, ysbar, xs_saved = synth.scatter(n, m, seed=3)

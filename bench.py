@@ -21,6 +21,9 @@ JSON line each; these are measurements, not the headline line):
            n = 2^28 FP64 (bandwidth); argmax VJP, n = 2^28 FP32
   hist     reduce_by_index VJPs, n = 2^27 FP32, m in {256, 2^16, 2^22},
            uniform / Zipf(1.1) bins, + / * / max
+  hist_general  reduce_by_index VJP by the general rule (radix sort by bin,
+           segmented scans): linear recurrence at n = 2^27 FP32 with m in
+           {256, 2^16, 2^22}; + and max beside the special rules
   scatter  scatter VJP, 2^26 values into 2^28 (random and sorted indices);
            map-accumulator VJPs at 2^26
   kmeans   k-means loss and C-gradient, N = 2^20, d = 32, k = 256
@@ -674,6 +677,50 @@ def row_hist(args):
                                             "sample": "hist max, n = 2^20, m = 256, Zipf"})
 
 
+def row_hist_general(args):
+    """reduce_by_index VJP by the general rule (Sec. 5.1.2: radix sort by bin,
+    forward and reverse segmented scans, map), n = 2^27 FP32; LINREC has no
+    special rule, + and max are timed beside the special-rule kernels."""
+    import torch
+    from oracle import oracle as O
+    from paper_2202_10297_gb300 import adpar as A
+    from paper_2202_10297_gb300 import synth
+    hbm, _ = measured_peaks()
+    n = 1 << 27
+    # algorithmic bytes per element: (a, b), inds in; (abar, bbar) out
+    alg = {"linrec": 20, "add": 12, "max": 12}
+    cases = {}
+    for op, m, dist in (("linrec", 1 << 16, "zipf"), ("linrec", 256, "uniform"), ("linrec", 1 << 22, "uniform"),
+                        ("add", 1 << 16, "zipf"), ("max", 1 << 16, "zipf")):
+        vals, inds, hsbar = synth.hist(n, m, dist, seed=synth.SEED_BASE + 2)
+        v, ix, hb = _dev(vals), _dev(inds), _dev(hsbar)
+        w2 = op == "linrec"
+        b = torch.randn(n, device="cuda") if w2 else None
+        hbb = torch.randn(m, device="cuda") if w2 else None
+        ab = torch.empty_like(v)
+        bb = torch.empty_like(v) if w2 else None
+        wk = A.workspace(A.adpar_workspace_size(A.RULE_HIST_GENERAL, A.OPS[op], A.F32, n, m), "cuda")
+        f = lambda: A.adpar_vjp_hist_general(op, v, ix, m, hb, b=b, hsbar_b=hbb, abar=ab, bbar=bb, work=wk)
+        t = _cuda_ms(f, 5, 2)
+        c = {"ms": t, "elements_per_s": n / t * 1e3, "gbs": alg[op] * n / t / 1e6,
+             "hbm_frac_of_measured": alg[op] * n / t / 1e6 / hbm}
+        if not w2:
+            wk2 = A.workspace(A.adpar_workspace_size(A.RULE_HIST, A.OPS[op], A.F32, n, m), "cuda")
+            c["special_rule_ms"] = _cuda_ms(lambda: A.adpar_vjp_hist(op, ix, m, hb, vals=v, valsbar=ab, work=wk2),
+                                            5, 2)
+            del wk2
+        cases["%s_m%d_%s" % (op, m, dist)] = c
+        del v, ix, hb, b, hbb, ab, bb, wk
+    vals, inds, hsbar = synth.hist(1 << 20, 1 << 16, "zipf", seed=1)
+    g = synth.rng(2)
+    bv, hbv = g.standard_normal(1 << 20), g.standard_normal(1 << 16)
+    orate = _oracle_rate(lambda: O.hist_general_vjp("linrec", vals, inds, 1 << 16, hsbar, b=bv, hsbar_b=hbv),
+                         1 << 20, 2.0)
+    return _line("hist_general", metric="VJP elements/s and % of HBM", n=n, algorithmic_bytes_per_element=alg,
+                 cases=cases, cpu_baseline={"value": orate, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                                            "sample": "hist LINREC, n = 2^20, m = 2^16, Zipf"})
+
+
 def row_scatter(args):
     """Scatter VJP (Sec. 5.3) and map-accumulator VJPs (Sec. 5.4)."""
     import torch
@@ -848,6 +895,11 @@ def _one_call(name, log2n):
         vals, inds, hsbar = synth.hist(n, 256, "zipf", seed=synth.SEED_BASE + 2)
         v, ix, hb = _dev(vals), _dev(inds), _dev(hsbar)
         return lambda: A.adpar_vjp_hist(op, ix, 256, hb, vals=v)
+    if name == "hist_general-linrec":
+        vals, inds, hsbar = synth.hist(n, 1 << 16, "zipf", seed=synth.SEED_BASE + 2)
+        v, ix, hb = _dev(vals), _dev(inds), _dev(hsbar)
+        b, hbb = torch.randn_like(v), torch.randn_like(hb)
+        return lambda: A.adpar_vjp_hist_general("linrec", v, ix, 1 << 16, hb, b=b, hsbar_b=hbb)
     if name == "prod-f64":
         a = _dev(synth.prod_reduce(n, 0)[0])
         return lambda: A.adpar_vjp_reduce("mul", a, 1.0)
@@ -859,7 +911,7 @@ def _one_call(name, log2n):
 
 
 CALLS_ONE = ("scan-linrec-f64", "scan-linrec-f32", "scan-add-f32", "scan-max-f32", "kmeans", "hist-mul",
-             "hist-max", "hist-add", "prod-f64", "scatter")
+             "hist-max", "hist-add", "prod-f64", "scatter", "hist_general-linrec")
 
 
 def row_call(args):
@@ -872,8 +924,8 @@ def row_call(args):
     return _line("call", call=args.call, log2n=args.log2n, reps=args.reps)
 
 
-ROWS = {"prod": row_prod, "hist": row_hist, "scatter": row_scatter, "kmeans": row_kmeans, "batch": row_batch,
-        "serve": row_serve, "call": row_call, "reduce_general": row_reduce_general, "jvp": row_jvp,
+ROWS = {"prod": row_prod, "hist": row_hist, "hist_general": row_hist_general, "scatter": row_scatter,
+        "kmeans": row_kmeans, "batch": row_batch, "serve": row_serve, "call": row_call, "reduce_general": row_reduce_general, "jvp": row_jvp,
         "scan_vec": row_scan_vec}
 
 
@@ -884,7 +936,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="adpar", choices=["adpar", "reference"])
     ap.add_argument("--workload", default="scan",
-                    choices=["scan", "prod", "hist", "scatter", "kmeans", "batch", "serve", "call",
+                    choices=["scan", "prod", "hist", "hist_general", "scatter", "kmeans", "batch", "serve", "call",
                              "reduce_general", "jvp", "scan_vec"])
     ap.add_argument("--call", default="scan-linrec-f64", choices=sorted(CALLS_ONE))
     ap.add_argument("--log2n", type=int, default=24)

@@ -75,7 +75,8 @@ typedef enum {
     ADPAR_RULE_MAP_ACC = 4,
     ADPAR_RULE_KMEANS = 5,
     ADPAR_RULE_REDUCE_GENERAL = 6,
-    ADPAR_RULE_SCAN_VEC = 7   /* m = the vector length d */
+    ADPAR_RULE_SCAN_VEC = 7,  /* m = the vector length d */
+    ADPAR_RULE_HIST_GENERAL = 8
 } adpar_rule;
 
 /* or'ed into the rule of adpar_workspace_size: the smallest workspace the
@@ -312,6 +313,44 @@ int adpar_vjp_hist(adpar_opdesc desc, int64_t n, int64_t m, const void *vals, co
                    int itype, const void *hsbar, void *valsbar, void *hs_out, int64_t *argidx_out,
                    adpar_prod_aux *bin_aux_out, int8_t *valsbar_sign, uint32_t flags, void *work,
                    size_t work_bytes, void *stream);
+
+/* reduce_by_index by the GENERAL rule of Sec. 5.1.2, for any operator of
+ * this library (ADD, MUL, MIN, MAX, and LINREC, which has no special rule):
+ *   hs[k] = e (.) (a, b)_{i_1} (.) (a, b)_{i_2} (.) ...  over the elements
+ *           with inds = k in increasing index order (so a bin of the
+ *           non-commutative LINREC is the recurrence over its elements in
+ *           index order; the paper states the rule for commutative
+ *           operators, where the order does not matter),
+ *   (abar, bbar)_i (+)= d(l_i (.) (a, b)_i (.) r_i)/d(a, b)_i ^T hsbar[inds_i]
+ * with l_i and r_i the combination of the bin's elements before and after
+ * i (the neutral element at the bin's ends).  Computed as Sec. 5.1.2
+ * proposes: a stable radix sort of the elements by bin (the values travel
+ * with the keys), a forward and a reverse segmented single-pass scan over
+ * the sorted sequence, and the per-element map.  Indices outside [0, m)
+ * are ignored: those elements get 0 (overwrite) or keep their adjoint
+ * (ADPAR_ACCUMULATE).  MUL is the product of the bin's other elements
+ * (no division, zeros safe, no extended exponent: it may underflow where
+ * adpar_vjp_hist's scaled rule would not); MIN/MAX give hsbar to the
+ * lowest index of the bin's extremum.
+ * Arguments:
+ *   desc         op, dtype and width (2 for LINREC, else 1).
+ *   n, m         elements and bins; n < 2^32 - 2048 and m <= 2^31
+ *                (ADPAR_ERR_UNSUPPORTED beyond).
+ *   a, b         [n] element arrays, dtype (b: LINREC only).
+ *   inds         [n] bin indices, itype.
+ *   hsbar_a/_b   [m] cotangents of hs (the _b one for LINREC).
+ *   abar, bbar   [n] output adjoints.
+ *   hs_a, hs_b   nullable [m]: the recomputed bins (neutral element for an
+ *                empty bin); both or neither for LINREC.
+ * No alignment is required of the caller's arrays.
+ * Flags: ADPAR_ACCUMULATE.
+ * Workspace: adpar_workspace_size(ADPAR_RULE_HIST_GENERAL, desc, n, m):
+ * about 2 * (8 + width * sizeof(dtype)) bytes per element (the sort's two
+ * buffers) plus the scans' slots. */
+int adpar_vjp_hist_general(adpar_opdesc desc, int64_t n, int64_t m, const void *a, const void *b,
+                           const void *inds, int itype, const void *hsbar_a, const void *hsbar_b,
+                           void *abar, void *bbar, void *hs_a, void *hs_b, uint32_t flags, void *work,
+                           size_t work_bytes, void *stream);
 
 /* ------------------------------------------------------------------ */
 /* scatter (Sec. 5.3)                                                  */

@@ -22,7 +22,8 @@ OP_ADD, OP_MUL, OP_MIN, OP_MAX, OP_LINREC = 0, 1, 2, 3, 4
 OPS = {"add": OP_ADD, "mul": OP_MUL, "min": OP_MIN, "max": OP_MAX, "linrec": OP_LINREC}
 G_GATHER, G_SCALE, G_SQDIST_ROW = 0, 1, 2
 GFUNS = {"gather": G_GATHER, "scale": G_SCALE, "sqdist_row": G_SQDIST_ROW}
-RULE_REDUCE, RULE_SCAN, RULE_HIST, RULE_SCATTER, RULE_MAP_ACC, RULE_KMEANS, RULE_REDUCE_GENERAL, RULE_SCAN_VEC = range(8)
+RULE_REDUCE, RULE_SCAN, RULE_HIST, RULE_SCATTER, RULE_MAP_ACC, RULE_KMEANS, RULE_REDUCE_GENERAL, RULE_SCAN_VEC, \
+    RULE_HIST_GENERAL = range(9)
 WS_MINIMAL = 0x100  # or'ed into a rule: the smallest accepted workspace
 ACCUMULATE, PROD_LOGDOMAIN, SCATTER_RESTORE = 0x1, 0x4, 0x8
 OK, ERR_TIMEOUT, ERR_TOO_LARGE = 0, 6, 7
@@ -77,6 +78,9 @@ def lib():
         L.adpar_vjp_scan_vec.argtypes = [OpDesc, C.c_int64, C.c_int64] + [_VP] * 6 + [C.c_uint32, _VP, C.c_size_t, _VP]
         L.adpar_jvp_scan.restype = C.c_int
         L.adpar_jvp_scan.argtypes = [OpDesc, C.c_int64] + [_VP] * 8 + [_VP, C.c_size_t, _VP]
+        L.adpar_vjp_hist_general.restype = C.c_int
+        L.adpar_vjp_hist_general.argtypes = [OpDesc, C.c_int64, C.c_int64, _VP, _VP, _VP, C.c_int] + [_VP] * 6 + \
+            [C.c_uint32, _VP, C.c_size_t, _VP]
         L.adpar_vjp_reduce_general.restype = C.c_int
         L.adpar_vjp_reduce_general.argtypes = [OpDesc, C.c_int64] + [_VP] * 8 + [C.c_uint32, _VP, C.c_size_t, _VP]
         _bind_optional(L)
@@ -243,6 +247,39 @@ def adpar_vjp_reduce_general(op, a, ybar_a, b=None, ybar_b=None, abar=None, bbar
                                         _stream(stream))
     _check("adpar_vjp_reduce_general", st)
     return abar, bbar, y
+
+
+def adpar_vjp_hist_general(op, a, inds, m, hsbar_a, b=None, hsbar_b=None, abar=None, bbar=None, want_hs=False,
+                           accumulate=False, work=None, stream=None):
+    """reduce_by_index VJP by the general rule (C: adpar_vjp_hist_general).
+
+    Returns (abar, bbar, hs_a, hs_b); bbar and hs_b only for linrec, the hs
+    arrays only with ``want_hs``.
+    """
+    opc = OPS[op] if isinstance(op, str) else int(op)
+    n = a.numel()
+    dt = _dtype_code(a)
+    it = _itype_code(inds)
+    w = 2 if opc == OP_LINREC else 1
+    if abar is None:
+        abar = torch.zeros_like(a) if accumulate else torch.empty_like(a)
+    if w == 2 and bbar is None:
+        bbar = torch.zeros_like(a) if accumulate else torch.empty_like(a)
+    for t in (b, abar, bbar):
+        if t is not None and (t.dtype != a.dtype or t.numel() != n):
+            raise ValueError("all element arrays must share dtype and length")
+    if inds.numel() != n:
+        raise ValueError("inds must have one index per element")
+    hs_a = torch.empty(m, dtype=a.dtype, device=a.device) if want_hs else None
+    hs_b = torch.empty(m, dtype=a.dtype, device=a.device) if want_hs and w == 2 else None
+    need = adpar_workspace_size(RULE_HIST_GENERAL, opc, dt, n, m)
+    if work is None or work.numel() < need:
+        work = workspace(need, a.device)
+    st = lib().adpar_vjp_hist_general(OpDesc(opc, dt, w), n, m, _ptr(a), _ptr(b), _ptr(inds), it, _ptr(hsbar_a),
+                                      _ptr(hsbar_b), _ptr(abar), _ptr(bbar), _ptr(hs_a), _ptr(hs_b),
+                                      ACCUMULATE if accumulate else 0, _ptr(work), work.numel(), _stream(stream))
+    _check("adpar_vjp_hist_general", st)
+    return abar, bbar, hs_a, hs_b
 
 
 def adpar_vjp_scan_vec(op, a, ybar_a, b=None, ybar_b=None, abar=None, bbar=None, accumulate=False, work=None,

@@ -698,3 +698,110 @@ int oracle_hist_general_vjp(int op, int64_t n, int64_t m,
     free(bins); free(tp); free(gb);
     return 0;
 }
+
+/* ---------------------------------------------------------------------
+ * Scan VJP with an element of d scalars and full d x d Jacobians (Sec. 5.2,
+ * the generalisation to any element type linearised to a vector: J_left
+ * and J_right become d x d matrices, lin_o multiplies matrices).  The
+ * element i is the row a[i*d .. i*d+d).  Operators:
+ *   O_LINREC  (d = 2)  (a1, b1) (.) (a2, b2) = (a2 a1, a2 b1 + b2)
+ *   O_MATREC2 (d = 6)  a 2x2 matrix M (row-major, 4 entries) and a 2-vector
+ *                      v: (M1, v1) (.) (M2, v2) = (M2 M1, M2 v1 + v2), the
+ *                      affine maps x -> M x + v composed in scan order.
+ * The tape sweep is the unrolled loop of Sec. 5.2: rs_0 = a_0,
+ * rs_i = rs_{i-1} (.) a_i; then rsbar = ybar and, for i = n-1..1,
+ *   rsbar_{i-1} += J_left(i)^T rsbar_i;  abar_i += J_right(i)^T rsbar_i,
+ * and abar_0 += rsbar_0.  abar is accumulated; ys (nullable) gets rs.
+ * ------------------------------------------------------------------- */
+enum { O_MATREC2 = 5 };
+#define WIDE_MAX 6
+
+typedef struct { double v[WIDE_MAX][WIDE_MAX]; } matw;
+
+static int wide_width(int op)
+{
+    return op == O_LINREC ? 2 : (op == O_MATREC2 ? 6 : 0);
+}
+
+static void wide_combine(int op, const double *l, const double *r, double *out)
+{
+    if (op == O_LINREC) {
+        out[0] = r[0] * l[0];
+        out[1] = r[0] * l[1] + r[1];
+        return;
+    }
+    /* r's matrix times l's matrix, r's matrix times l's vector plus r's vector */
+    for (int j = 0; j < 2; ++j) {
+        for (int k = 0; k < 2; ++k)
+            out[2 * j + k] = r[2 * j + 0] * l[0 + k] + r[2 * j + 1] * l[2 + k];
+        out[4 + j] = r[2 * j + 0] * l[4] + r[2 * j + 1] * l[5] + r[4 + j];
+    }
+}
+
+/* J_left = d(prev (.) x)/d prev and J_right = d(prev (.) x)/d x, rows are
+ * the output components, columns the input ones */
+static void wide_jacobians(int op, const double *prev, const double *x, matw *Jl, matw *Jr)
+{
+    memset(Jl, 0, sizeof(*Jl));
+    memset(Jr, 0, sizeof(*Jr));
+    if (op == O_LINREC) {
+        /* (A, B) -> (x0 A, x0 B + x1) */
+        const double jr[2][2] = { { prev[0], 0.0 }, { prev[1], 1.0 } };
+        for (int r = 0; r < 2; ++r) {
+            Jl->v[r][r] = x[0];
+            for (int c = 0; c < 2; ++c) Jr->v[r][c] = jr[r][c];
+        }
+        return;
+    }
+    /* out P[j][k] = sum_m X[j][m] P[m][k];  out h[j] = sum_m X[j][m] h[m] + xv[j] */
+    for (int j = 0; j < 2; ++j) {
+        for (int k = 0; k < 2; ++k)
+            for (int m = 0; m < 2; ++m) {
+                Jl->v[2 * j + k][2 * m + k] = x[2 * j + m];   /* d out P[j][k] / d P[m][k] */
+                Jr->v[2 * j + k][2 * j + m] = prev[2 * m + k]; /* d out P[j][k] / d X[j][m] */
+            }
+        for (int m = 0; m < 2; ++m) {
+            Jl->v[4 + j][4 + m] = x[2 * j + m];     /* d out h[j] / d h[m] */
+            Jr->v[4 + j][2 * j + m] = prev[4 + m];  /* d out h[j] / d X[j][m] */
+        }
+        Jr->v[4 + j][4 + j] = 1.0;                 /* d out h[j] / d xv[j] */
+    }
+}
+
+/* y = M^T x for d x d M */
+static void matw_t_vec(const matw *M, const double *x, double *y, int d)
+{
+    for (int c = 0; c < d; ++c) {
+        double s = 0.0;
+        for (int r = 0; r < d; ++r) s += M->v[r][c] * x[r];
+        y[c] = s;
+    }
+}
+
+int oracle_scan_wide_vjp(int op, int64_t n, int d, const double *a, const double *ybar,
+                         double *abar, double *ys)
+{
+    if (wide_width(op) == 0 || d != wide_width(op)) return 1;
+    if (n == 0) return 0;
+    double *rs = (double *)malloc(sizeof(double) * (size_t)n * (size_t)d);
+    double *rsb = (double *)malloc(sizeof(double) * (size_t)n * (size_t)d);
+    if (!rs || !rsb) { free(rs); free(rsb); return 2; }
+    for (int c = 0; c < d; ++c) rs[c] = a[c];
+    for (int64_t i = 1; i < n; ++i) wide_combine(op, &rs[(i - 1) * d], &a[i * d], &rs[i * d]);
+    if (ys) memcpy(ys, rs, sizeof(double) * (size_t)n * (size_t)d);
+    memcpy(rsb, ybar, sizeof(double) * (size_t)n * (size_t)d);
+    for (int64_t i = n - 1; i >= 1; --i) {
+        matw Jl, Jr;
+        double back[WIDE_MAX], into[WIDE_MAX];
+        wide_jacobians(op, &rs[(i - 1) * d], &a[i * d], &Jl, &Jr);
+        matw_t_vec(&Jl, &rsb[i * d], back, d);
+        matw_t_vec(&Jr, &rsb[i * d], into, d);
+        for (int c = 0; c < d; ++c) {
+            rsb[(i - 1) * d + c] += back[c];
+            abar[i * d + c] += into[c];
+        }
+    }
+    for (int c = 0; c < d; ++c) abar[c] += rsb[c];
+    free(rs); free(rsb);
+    return 0;
+}

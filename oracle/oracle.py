@@ -16,7 +16,8 @@ from . import build as _build
 _lib = None
 
 ADD, MUL, MIN, MAX, LINREC = 0, 1, 2, 3, 4
-OPS = {"add": ADD, "mul": MUL, "min": MIN, "max": MAX, "linrec": LINREC}
+OPS = {"add": ADD, "mul": MUL, "min": MIN, "max": MAX, "linrec": LINREC, "matrec2": 5}
+WIDE = {"linrec": 2, "matrec2": 6}  # element width of the wide-element scan
 GATHER, SCALE, SQDIST_ROW = 0, 1, 2
 GFUNS = {"gather": GATHER, "scale": SCALE, "sqdist_row": SQDIST_ROW}
 
@@ -48,10 +49,11 @@ def lib():
         L.oracle_scan_jvp.argtypes = [C.c_int, i64, _D, _D, _D, _D, _D, _D, _D, _D]
         L.oracle_hist_general_vjp.argtypes = [C.c_int, i64, i64, _D, _D, _I64, _D, _D, _D, _D,
                                               _D, _D]
+        L.oracle_scan_wide_vjp.argtypes = [C.c_int, i64, C.c_int, _D, _D, _D, _D]
         for f in ("oracle_reduce_vjp", "oracle_prod_reduce_vjp", "oracle_scan_vjp",
                   "oracle_hist_vjp", "oracle_hist_prod_vjp", "oracle_scatter_vjp",
                   "oracle_map_acc_vjp", "oracle_kmeans", "oracle_reduce_general_vjp", "oracle_scan_jvp",
-                  "oracle_hist_general_vjp"):
+                  "oracle_hist_general_vjp", "oracle_scan_wide_vjp"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -200,6 +202,19 @@ def hist_prod_vjp(vals, inds, m, hsbar, valsbar=None):
                                       _p(lnz), _p(snz)), "hist_prod_vjp")
     return dict(valsbar=vb, log=lg, sign=sg, nzero=nz[:m], first_zero=fz[:m],
                 lognz=lnz[:m], signnz=snz[:m].astype(np.int64))
+
+
+def scan_wide_vjp(op, a, ybar, abar=None):
+    """Scan over elements of d scalars (rows of [n, d]) with full d x d
+    Jacobians (Sec. 5.2, generalised lin_o).  Returns (abar [n, d], ys [n, d])."""
+    d = WIDE[op]
+    a = _f64(a).reshape(-1, d)
+    yb = _f64(ybar).reshape(-1, d)
+    n = a.shape[0]
+    ab = np.zeros((n, d)) if abar is None else _f64(abar).reshape(n, d).copy()
+    ys = np.empty((n, d))
+    _check(lib().oracle_scan_wide_vjp(OPS[op], n, d, _p(a), _p(yb), _p(ab), _p(ys)), "scan_wide_vjp")
+    return ab, ys
 
 
 def hist_general_vjp(op, vals, inds, m, hsbar, b=None, hsbar_b=None, valsbar=None, bbar=None):

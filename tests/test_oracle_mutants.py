@@ -51,6 +51,14 @@ MUTANTS = {
     "hist_general_operands_transposed": ("scan_combine(op, &tp[i * w], x, out);",
                                          "scan_combine(op, x, &tp[i * w], out);"),
     "hist_general_linrec_neutral": ("bins[k * 2 + 1] = 0.0;", "bins[k * 2 + 1] = 1.0;"),
+    "wide_matrix_product_order": ("out[2 * j + k] = r[2 * j + 0] * l[0 + k] + r[2 * j + 1] * l[2 + k];",
+                                  "out[2 * j + k] = l[2 * j + 0] * r[0 + k] + l[2 * j + 1] * r[2 + k];"),
+    "wide_jleft_transposed": ("Jl->v[2 * j + k][2 * m + k] = x[2 * j + m];",
+                              "Jl->v[2 * j + k][2 * m + k] = x[2 * m + j];"),
+    "wide_jright_wrong_column": ("Jr->v[4 + j][2 * j + m] = prev[4 + m];", "Jr->v[4 + j][2 * m + j] = prev[4 + m];"),
+    "wide_linrec_jright_transposed": ("{ { prev[0], 0.0 }, { prev[1], 1.0 } }", "{ { prev[0], prev[1] }, { 0.0, 1.0 } }"),
+    "wide_first_element_dropped": ("for (int c = 0; c < d; ++c) abar[c] += rsb[c];",
+                                   "for (int c = 0; c < d; ++c) abar[c] += 0.0 * rsb[c];"),
 }
 
 

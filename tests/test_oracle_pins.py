@@ -512,6 +512,91 @@ def test_hist_minmax_equal_reduce_with_one_bin(oracle):
 
 
 # ------------------------------------------------------------------- scatter
+def test_scan_wide_matrec_primal_fibonacci(oracle):
+    """The companion matrix [[1, 1], [1, 0]] with h_0 = (1, 0) makes the
+    affine-map scan the Fibonacci recurrence: h_i = (F_{i+1}, F_i) exactly,
+    and the matrix part is the matrix power [[F_{i+1}, F_i], [F_i, F_{i-1}]]."""
+    n = 30
+    a = np.tile([1.0, 1.0, 1.0, 0.0, 0.0, 0.0], (n, 1))
+    a[0, 4:] = [1.0, 0.0]
+    _, ys = oracle.scan_wide_vjp("matrec2", a, np.zeros((n, 6)))
+    F = [0, 1]
+    while len(F) < n + 3:
+        F.append(F[-1] + F[-2])
+    for i in range(n):
+        assert list(ys[i, 4:]) == [F[i + 1], F[i]]
+        assert list(ys[i, :4]) == [F[i + 2], F[i + 1], F[i + 1], F[i]]
+
+
+def test_scan_wide_matrec_finite_differences(oracle):
+    """Every output of the matrix recurrence is linear in each single input
+    scalar, so central differences of a plain loop of 2x2 matrix products are
+    exact up to rounding for every component of every element."""
+    g = synth.rng(51)
+    n = 12
+    a = np.concatenate([np.eye(2).ravel() + 0.4 * g.normal(size=(n, 4)), g.normal(size=(n, 2))], axis=1)
+    yb = g.normal(size=(n, 6))
+
+    def loss(x):
+        P = x[0, :4].reshape(2, 2).copy()
+        h = x[0, 4:].copy()
+        tot = yb[0, :4] @ P.ravel() + yb[0, 4:] @ h
+        for i in range(1, n):
+            M = x[i, :4].reshape(2, 2)
+            P = M @ P
+            h = M @ h + x[i, 4:]
+            tot += yb[i, :4] @ P.ravel() + yb[i, 4:] @ h
+        return tot
+
+    ab, _ = oracle.scan_wide_vjp("matrec2", a, yb)
+    step = 0.125
+    for i in range(n):
+        for c in range(6):
+            e = np.zeros_like(a)
+            e[i, c] = step
+            fd = (loss(a + e) - loss(a - e)) / (2 * step)
+            assert abs(fd - ab[i, c]) <= 1e-10 * (1 + abs(fd)), (i, c, fd, ab[i, c])
+
+
+def test_scan_wide_matrec_diagonal_is_two_linrecs(oracle):
+    """With diagonal matrices the recurrence splits into two scalar linear
+    recurrences (a = M00, b = v0) and (a = M11, b = v1); with cotangents only
+    on (P00, h0, P11, h1) their adjoints are the separately pinned LINREC
+    sweep's."""
+    g = synth.rng(52)
+    n = 40
+    a0, a1 = g.uniform(0.8, 1.2, n), g.uniform(0.8, 1.2, n)
+    b0, b1 = g.normal(size=n), g.normal(size=n)
+    y = g.normal(size=(4, n))
+    a = np.zeros((n, 6))
+    a[:, 0], a[:, 3], a[:, 4], a[:, 5] = a0, a1, b0, b1
+    yb = np.zeros((n, 6))
+    yb[:, 0], yb[:, 4], yb[:, 3], yb[:, 5] = y[0], y[1], y[2], y[3]
+    ab, _ = oracle.scan_wide_vjp("matrec2", a, yb)
+    ra0, rb0, _, _ = oracle.scan_vjp("linrec", a0, y[0], b0, y[1])
+    ra1, rb1, _, _ = oracle.scan_vjp("linrec", a1, y[2], b1, y[3])
+    for got, ref in ((ab[:, 0], ra0), (ab[:, 4], rb0), (ab[:, 3], ra1), (ab[:, 5], rb1)):
+        np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-14)
+
+
+def test_scan_wide_linrec_equals_linrec_scan(oracle):
+    """The width-2 element (a, b) with the full 2x2 Jacobians is the linear
+    recurrence of the scalar-coefficient sweep; accumulation adds on."""
+    g = synth.rng(53)
+    n = 37
+    a, b = g.uniform(0.9, 1.1, n), g.normal(size=n)
+    ya, yb = g.normal(size=n), g.normal(size=n)
+    base = g.normal(size=(n, 2))
+    ab, ys = oracle.scan_wide_vjp("linrec", np.stack([a, b], 1), np.stack([ya, yb], 1), abar=base)
+    ra, rb, rya, ryb = oracle.scan_vjp("linrec", a, ya, b, yb)
+    np.testing.assert_allclose(ab[:, 0] - base[:, 0], ra, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(ab[:, 1] - base[:, 1], rb, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(ys[:, 0], rya, rtol=1e-14)
+    np.testing.assert_allclose(ys[:, 1], ryb, rtol=1e-14)
+    ab, _ = oracle.scan_wide_vjp("matrec2", np.ones((1, 6)), np.arange(6.0).reshape(1, 6))
+    np.testing.assert_array_equal(ab, np.arange(6.0).reshape(1, 6))  # n = 1: abar = ybar
+
+
 def _bins_of(inds, m):
     return [np.flatnonzero(inds == k) for k in range(m)]
 

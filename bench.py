@@ -35,6 +35,9 @@ JSON line each; these are measurements, not the headline line):
            rules for +, max and * at 2^28 FP32
   scan_vec vectorised scan VJP (d column scans of row-major [n][d]): linear
            recurrence and max over [2^14, 2^12]
+  scan_wide scan VJP over wide elements by the general d x d lin_o: the 2x2
+           matrix linear recurrence at n = 2^24 FP32/FP64; the linear
+           recurrence as a 2-wide element vs the scalar rule at 2^26
   jvp      forward-mode scan rule: linear recurrence 2^26 FP32/FP64, max scan
            2^28 FP32, against the primal forward scan
   serve    Poisson arrivals of mixed-operator requests sized 2^10..2^24:
@@ -721,6 +724,50 @@ def row_hist_general(args):
                                             "sample": "hist LINREC, n = 2^20, m = 2^16, Zipf"})
 
 
+def row_scan_wide(args):
+    """Scan VJP over wide elements by the general d x d lin_o (Sec. 5.2): the
+    2x2 matrix linear recurrence (D = 6) at n = 2^24 FP32 and FP64, and the
+    linear recurrence as a D = 2 element beside the scalar-coefficient rule."""
+    import torch
+    from oracle import oracle as O
+    from paper_2202_10297_gb300 import adpar as A
+    from paper_2202_10297_gb300 import synth
+    hbm, _ = measured_peaks()
+    cases = {}
+    n = 1 << 24
+    for dt, tdt in ((np.float32, torch.float32), (np.float64, torch.float64)):
+        g = synth.rng(synth.SEED_BASE + 7)
+        M = 0.95 * np.eye(2).ravel() + 0.03 * g.standard_normal((n, 4))
+        a = _dev(np.concatenate([M, g.standard_normal((n, 2))], 1).astype(dt))
+        yb = torch.randn(n, 6, dtype=tdt, device="cuda")
+        ab = torch.empty_like(a)
+        wk = A.workspace(A.adpar_workspace_size(A.RULE_SCAN_WIDE, A.OP_MATREC2, A.F32 if dt == np.float32 else A.F64,
+                                                n, 0, width=6), "cuda")
+        t = _cuda_ms(lambda: A.adpar_vjp_scan_wide("matrec2", a, yb, abar=ab, work=wk), 5, 2)
+        alg = 3 * 6 * np.dtype(dt).itemsize  # a, ybar in; abar out
+        cases["matrec2_%s_n2p24" % ("f32" if dt == np.float32 else "f64")] = {
+            "ms": t, "elements_per_s": n / t * 1e3, "gbs": alg * n / t / 1e6,
+            "hbm_frac_of_measured": alg * n / t / 1e6 / hbm}
+        del a, yb, ab, wk
+    n = 1 << 26
+    a, b, ya, ybb = (_dev(v) for v in synth.linrec(n, np.float32, seed=synth.SEED_BASE + 1))
+    aw, yw = torch.stack([a, b], 1).contiguous(), torch.stack([ya, ybb], 1).contiguous()
+    abw = torch.empty_like(aw)
+    wk = A.workspace(A.adpar_workspace_size(A.RULE_SCAN_WIDE, A.OP_LINREC, A.F32, n, 0, width=2), "cuda")
+    t = _cuda_ms(lambda: A.adpar_vjp_scan_wide("linrec", aw, yw, abar=abw, work=wk), 5, 2)
+    ts = _cuda_ms(lambda: A.adpar_vjp_scan("linrec", a, ya, b=b, ybar_b=ybb), 5, 2)
+    cases["linrec_as_d2_f32_n2p26"] = {"ms": t, "scalar_rule_ms": ts, "gbs": 24 * n / t / 1e6,
+                                       "hbm_frac_of_measured": 24 * n / t / 1e6 / hbm}
+    g = synth.rng(3)
+    sa = np.concatenate([0.95 * np.eye(2).ravel() + 0.03 * g.standard_normal((1 << 18, 4)),
+                         g.standard_normal((1 << 18, 2))], 1)
+    syb = g.standard_normal(sa.shape)
+    orate = _oracle_rate(lambda: O.scan_wide_vjp("matrec2", sa, syb), 1 << 18, 2.0)
+    return _line("scan_wide", metric="VJP elements/s and % of HBM", cases=cases,
+                 cpu_baseline={"value": orate, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                               "sample": "2x2 matrix recurrence, n = 2^18"})
+
+
 def row_scatter(args):
     """Scatter VJP (Sec. 5.3) and map-accumulator VJPs (Sec. 5.4)."""
     import torch
@@ -925,7 +972,7 @@ def row_call(args):
 
 
 ROWS = {"prod": row_prod, "hist": row_hist, "hist_general": row_hist_general, "scatter": row_scatter,
-        "kmeans": row_kmeans, "batch": row_batch, "serve": row_serve, "call": row_call, "reduce_general": row_reduce_general, "jvp": row_jvp,
+        "scan_wide": row_scan_wide, "kmeans": row_kmeans, "batch": row_batch, "serve": row_serve, "call": row_call, "reduce_general": row_reduce_general, "jvp": row_jvp,
         "scan_vec": row_scan_vec}
 
 
@@ -936,7 +983,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="adpar", choices=["adpar", "reference"])
     ap.add_argument("--workload", default="scan",
-                    choices=["scan", "prod", "hist", "hist_general", "scatter", "kmeans", "batch", "serve", "call",
+                    choices=["scan", "prod", "hist", "hist_general", "scan_wide", "scatter", "kmeans", "batch", "serve", "call",
                              "reduce_general", "jvp", "scan_vec"])
     ap.add_argument("--call", default="scan-linrec-f64", choices=sorted(CALLS_ONE))
     ap.add_argument("--log2n", type=int, default=24)

@@ -56,7 +56,8 @@ typedef enum {
     ADPAR_OP_MUL = 1,
     ADPAR_OP_MIN = 2,
     ADPAR_OP_MAX = 3,
-    ADPAR_OP_LINREC = 4
+    ADPAR_OP_LINREC = 4,
+    ADPAR_OP_MATREC2 = 5   /* 2x2 matrix linear recurrence: adpar_vjp_scan_wide only */
 } adpar_op;
 
 /* map bodies g for adpar_vjp_map_acc (Sec. 5.4) */
@@ -76,7 +77,8 @@ typedef enum {
     ADPAR_RULE_KMEANS = 5,
     ADPAR_RULE_REDUCE_GENERAL = 6,
     ADPAR_RULE_SCAN_VEC = 7,  /* m = the vector length d */
-    ADPAR_RULE_HIST_GENERAL = 8
+    ADPAR_RULE_HIST_GENERAL = 8,
+    ADPAR_RULE_SCAN_WIDE = 9
 } adpar_rule;
 
 /* or'ed into the rule of adpar_workspace_size: the smallest workspace the
@@ -217,6 +219,33 @@ int adpar_vjp_scan(adpar_opdesc desc, int64_t n, const void *a, const void *b,
                    const void *ybar_a, const void *ybar_b, void *abar, void *bbar,
                    void *ys_a, void *ys_b, uint32_t flags, void *work,
                    size_t work_bytes, void *stream);
+
+/* VJP of an inclusive scan whose element is a vector of D scalars, by the
+ * general lin_o of Sec. 5.2: J_left and J_right are D x D matrices and the
+ * return sweep's recurrence rs_bar_i = ybar_i + J_left(i+1)^T rs_bar_{i+1}
+ * is a reverse scan of affine maps (d, C) whose combine multiplies two
+ * D x D matrices (neutral element (0, I)); then
+ *   as_bar_i (+)= J_right(i)^T rs_bar_i (i >= 1),  as_bar_0 (+)= rs_bar_0.
+ * Operators (desc.op, desc.width = D):
+ *   ADPAR_OP_LINREC  D = 2: the element (a, b); the same recurrence as
+ *                    adpar_vjp_scan's LINREC, through full 2x2 Jacobians.
+ *   ADPAR_OP_MATREC2 D = 6: the element (M, v), M a row-major 2x2 matrix in
+ *                    the first four scalars and v a 2-vector in the last
+ *                    two; (M1, v1) (.) (M2, v2) = (M2 M1, M2 v1 + v2), the
+ *                    affine maps h -> M h + v composed in scan order (the
+ *                    second entry of ys_i is h_i = M_i h_{i-1} + v_i with
+ *                    h_{-1} = 0; companion matrices give second-order
+ *                    recurrences).
+ * Arguments:
+ *   n        elements (0 allowed).
+ *   a        [n][D] row-major elements, dtype.
+ *   ybar     [n][D] cotangent of the inclusive scan ys.
+ *   abar     [n][D] output adjoint (overwritten, or += with ADPAR_ACCUMULATE).
+ *   ys_out   nullable [n][D]: the recomputed inclusive scan.
+ * Every non-null array must start on a 16-byte boundary (ADPAR_ERR_ALIGN).
+ * Workspace: adpar_workspace_size(ADPAR_RULE_SCAN_WIDE, desc, n, 0). */
+int adpar_vjp_scan_wide(adpar_opdesc desc, int64_t n, const void *a, const void *ybar, void *abar,
+                        void *ys_out, uint32_t flags, void *work, size_t work_bytes, void *stream);
 
 /* Reduce by the GENERAL rule of Sec. 5.1.1, for any operator of this
  * library (ADD, MUL, MIN, MAX, and LINREC, which has no special rule):

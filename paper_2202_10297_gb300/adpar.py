@@ -18,12 +18,13 @@ LIB_PATH = os.path.join(_HERE, "libadpar.so")
 
 F32, F64 = 0, 1
 I32, I64 = 0, 1
-OP_ADD, OP_MUL, OP_MIN, OP_MAX, OP_LINREC = 0, 1, 2, 3, 4
-OPS = {"add": OP_ADD, "mul": OP_MUL, "min": OP_MIN, "max": OP_MAX, "linrec": OP_LINREC}
+OP_ADD, OP_MUL, OP_MIN, OP_MAX, OP_LINREC, OP_MATREC2 = 0, 1, 2, 3, 4, 5
+OPS = {"add": OP_ADD, "mul": OP_MUL, "min": OP_MIN, "max": OP_MAX, "linrec": OP_LINREC, "matrec2": OP_MATREC2}
+WIDE = {OP_LINREC: 2, OP_MATREC2: 6}  # element width D of adpar_vjp_scan_wide
 G_GATHER, G_SCALE, G_SQDIST_ROW = 0, 1, 2
 GFUNS = {"gather": G_GATHER, "scale": G_SCALE, "sqdist_row": G_SQDIST_ROW}
 RULE_REDUCE, RULE_SCAN, RULE_HIST, RULE_SCATTER, RULE_MAP_ACC, RULE_KMEANS, RULE_REDUCE_GENERAL, RULE_SCAN_VEC, \
-    RULE_HIST_GENERAL = range(9)
+    RULE_HIST_GENERAL, RULE_SCAN_WIDE = range(10)
 WS_MINIMAL = 0x100  # or'ed into a rule: the smallest accepted workspace
 ACCUMULATE, PROD_LOGDOMAIN, SCATTER_RESTORE = 0x1, 0x4, 0x8
 OK, ERR_TIMEOUT, ERR_TOO_LARGE = 0, 6, 7
@@ -78,6 +79,8 @@ def lib():
         L.adpar_vjp_scan_vec.argtypes = [OpDesc, C.c_int64, C.c_int64] + [_VP] * 6 + [C.c_uint32, _VP, C.c_size_t, _VP]
         L.adpar_jvp_scan.restype = C.c_int
         L.adpar_jvp_scan.argtypes = [OpDesc, C.c_int64] + [_VP] * 8 + [_VP, C.c_size_t, _VP]
+        L.adpar_vjp_scan_wide.restype = C.c_int
+        L.adpar_vjp_scan_wide.argtypes = [OpDesc, C.c_int64] + [_VP] * 4 + [C.c_uint32, _VP, C.c_size_t, _VP]
         L.adpar_vjp_hist_general.restype = C.c_int
         L.adpar_vjp_hist_general.argtypes = [OpDesc, C.c_int64, C.c_int64, _VP, _VP, _VP, C.c_int] + [_VP] * 6 + \
             [C.c_uint32, _VP, C.c_size_t, _VP]
@@ -247,6 +250,30 @@ def adpar_vjp_reduce_general(op, a, ybar_a, b=None, ybar_b=None, abar=None, bbar
                                         _stream(stream))
     _check("adpar_vjp_reduce_general", st)
     return abar, bbar, y
+
+
+def adpar_vjp_scan_wide(op, a, ybar, abar=None, want_ys=False, accumulate=False, work=None, stream=None):
+    """VJP of a scan over [n, D] rows by the general d x d lin_o (C: adpar_vjp_scan_wide).
+
+    ``op`` is "linrec" (D = 2) or "matrec2" (D = 6).  Returns (abar, ys), ys
+    only with ``want_ys``.
+    """
+    opc = OPS[op] if isinstance(op, str) else int(op)
+    D = WIDE[opc]
+    if a.dim() != 2 or a.shape[1] != D or ybar.shape != a.shape:
+        raise ValueError("a and ybar must be [n, %d]" % D)
+    n = a.shape[0]
+    dt = _dtype_code(a)
+    if abar is None:
+        abar = torch.zeros_like(a) if accumulate else torch.empty_like(a)
+    ys = torch.empty_like(a) if want_ys else None
+    need = adpar_workspace_size(RULE_SCAN_WIDE, opc, dt, n, 0, width=D)
+    if work is None or work.numel() < need:
+        work = workspace(need, a.device)
+    st = lib().adpar_vjp_scan_wide(OpDesc(opc, dt, D), n, _ptr(a), _ptr(ybar), _ptr(abar), _ptr(ys),
+                                   ACCUMULATE if accumulate else 0, _ptr(work), work.numel(), _stream(stream))
+    _check("adpar_vjp_scan_wide", st)
+    return abar, ys
 
 
 def adpar_vjp_hist_general(op, a, inds, m, hsbar_a, b=None, hsbar_b=None, abar=None, bbar=None, want_hs=False,

@@ -9,6 +9,7 @@ size_t hist_workspace_size(adpar_opdesc d, int64_t m);
 size_t kmeans_workspace_size(int64_t k);
 size_t scan_vec_workspace_size(adpar_opdesc d, int64_t n, int64_t m);
 size_t hist_general_workspace_size(adpar_opdesc d, int64_t n, int64_t m);
+size_t scan_wide_workspace_size(adpar_opdesc d, int64_t n);
 }
 
 extern "C" const char* adpar_status_string(int status) {
@@ -35,6 +36,7 @@ extern "C" size_t adpar_workspace_size(int rule, adpar_opdesc d, int64_t n, int6
     case ADPAR_RULE_REDUCE_GENERAL: return adpar::scan_workspace_size(d, n, true);  // the scan's slots
     case ADPAR_RULE_SCAN_VEC: return adpar::scan_vec_workspace_size(d, n, m);
     case ADPAR_RULE_HIST_GENERAL: return adpar::hist_general_workspace_size(d, n, m);
+    case ADPAR_RULE_SCAN_WIDE: return adpar::scan_wide_workspace_size(d, n);
     case ADPAR_RULE_REDUCE: return n < 0 ? (size_t)-1 : adpar::reduce_workspace_size(d);
     case ADPAR_RULE_HIST: return n < 0 ? (size_t)-1 : adpar::hist_workspace_size(d, m);
     case ADPAR_RULE_KMEANS: return n < 0 ? (size_t)-1 : adpar::kmeans_workspace_size(m);

@@ -74,8 +74,10 @@ CALLS = [
     ("add_f32", "add", np.float32, LOG2_SCAN, 8, 8),
     ("max_f32", "max", np.float32, LOG2_SCAN, 12, 8),
 ]
-# kernel launches of one call: init + (primal pass) + adjoint pass
-LAUNCHES = {"linrec": 3, "max": 3, "add": 2, "mul": 3, "min": 3}
+# kernel launches of one call: init + (primal pass) + adjoint pass; min/max:
+# init + tile extrema + carry scan + record-free tiles + tiles with records +
+# the runs across tiles
+LAUNCHES = {"linrec": 3, "max": 6, "add": 2, "mul": 3, "min": 6}
 
 # FP64 arithmetic of the linear-recurrence VJP per pair, counted on the
 # sequential definition (an FMA is 2 flops): forward A_i = a_i A_{i-1} (1)

@@ -53,6 +53,346 @@ __global__ void __launch_bounds__(kScanBlock) scan_primal_kernel(ScanArgs A) {
     scan_primal_tile<Op, T, Cfg::K, Cfg::E>(A, (int64_t)s_tile);
 }
 
+// MIN/MAX scans: the return sweep fused into the forward pass.  For these
+// operators J_left(i) = c_i is 0 exactly when a_{i+1} is a record (strictly
+// beyond the running extremum; the tie rule keeps the earlier element), so
+// the lin_o recurrence rs_bar_i = ybar_i + c_i rs_bar_{i+1} restarts at
+// every record, and as_bar_i = J_right(i) rs_bar_i is nonzero only at
+// records (and at element 0, which takes rs_bar_0): a record's adjoint is
+// the sum of ybar from it to the element before the next record.  No tile
+// waits on another: the tile extrema (scan_minmax_tile_kernel) and their
+// exclusive scan (one block) give every tile its carry, hence its records;
+// a reverse segmented sum inside the tile gives each record's part of that
+// sum, and the adjoint is written once.  The part of the last record's sum
+// that lies in later tiles is added by scan_minmax_fixup_kernel from
+// per-tile metadata: the sum of ybar before the tile's first record (lead)
+// and the tile's last record (last).
+template <class T>
+struct RunSum {
+    T x;         // ybar from the element to the end of its run
+    uint32_t f;  // the run ends inside (a record follows)
+};
+
+template <class Op, class T, bool WYS>
+__global__ void __launch_bounds__(kScanBlock) scan_minmax_fused_kernel(ScanArgs A, const typename Op::P* tmax,
+                                                                       double* lead, int64_t* last) {
+    using Cfg = ScanCfg<Op, T>;
+    using P = typename Op::P;
+    using R = RunSum<T>;
+    constexpr int K = Cfg::K, E = Cfg::E, NW = kScanBlock / 32;
+    __shared__ P s_tot[K * NW];
+    __shared__ R s_totR[K * NW];
+    __shared__ P s_pre;
+    __shared__ uint32_t s_rec[K][kScanBlock];  // record bits of each thread's E elements
+    __shared__ unsigned long long s_last1;      // 1 + the tile's last record (0: none)
+    __shared__ uint32_t s_has;  // the tile holds a record
+    const int64_t t = blockIdx.x;
+    if (threadIdx.x == 0) {
+        s_last1 = 0ull;
+        const P pre = static_cast<const P*>(A.carry)[t];  // the extremum before the tile
+        s_pre = pre;
+        T on = T(0), dummy = T(0);
+        Op::vjp_right(pre, Op::out_a(tmax[t]), T(0), T(1), T(0), on, dummy);
+        s_has = (t == 0 || on != T(0)) ? 1u : 0u;
+    }
+    __syncthreads();
+    const int64_t base = t * Cfg::TILE;
+    const T* a = static_cast<const T*>(A.a);
+    const T* yb = static_cast<const T*>(A.ya);
+    if (!s_has) return;  // scan_minmax_zero_kernel takes it
+    T av[K][E], yv[K][E];
+    P agg[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int64_t e = base + (int64_t)k * kScanBlock * E + threadIdx.x * E;
+        load_chunk(a, e, A.n, Op::pad_a(), av[k]);
+        load_chunk(yb, e, A.n, T(0), yv[k]);
+        P acc = Op::pelem(av[k][0], T(0));
+#pragma unroll
+        for (int j = 1; j < E; ++j) acc = Op::pcomb(acc, Op::pelem(av[k][j], T(0)));
+        agg[k] = acc;
+    }
+    auto fc = [](const P& l, const P& r) { return Op::pcomb(l, r); };
+    P wex[K];
+    (void)block_scan_part1<P, false, K, NW>(agg, wex, s_tot, Op::pid(), fc);
+    __syncthreads();
+    // records: J_right(i) = 1 (a_i strictly beyond everything before it), and element 0
+    uint32_t rec[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int64_t e = base + (int64_t)k * kScanBlock * E + threadIdx.x * E;
+        P prev = block_scan_excl<P, false, K, NW>(k, wex, s_tot, s_pre, fc);
+        uint32_t bits = 0;
+        T ys[E];
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            T on = T(0), dummy = T(0);
+            Op::vjp_right(prev, av[k][j], T(0), T(1), T(0), on, dummy);
+            if (e + j < A.n && (e + j == 0 || on != T(0))) bits |= 1u << j;
+            prev = Op::pcomb(prev, Op::pelem(av[k][j], T(0)));
+            ys[j] = Op::out_a(prev);
+        }
+        rec[k] = bits;
+        s_rec[k][threadIdx.x] = bits;
+        if constexpr (WYS) {
+            if (e < A.n) store_chunk(static_cast<T*>(A.ys_a), e, A.n, ys);
+        }
+    }
+    __syncthreads();
+    // in-tile runs: element i's run ends where element i+1 is a record
+    R aggR[K];
+    uint32_t nextrec[K];  // record bit of the element after each thread's last one
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int tn = threadIdx.x + 1;
+        nextrec[k] = tn < kScanBlock ? (s_rec[k][tn] & 1u) : (k + 1 < K ? (s_rec[k + 1 < K ? k + 1 : k][0] & 1u) : 0u);
+        R acc{T(0), 0u};
+        uint32_t nxt = nextrec[k];
+#pragma unroll
+        for (int j = E - 1; j >= 0; --j) {
+            const R el{yv[k][j], nxt};
+            acc = el.f ? el : R{el.x + acc.x, acc.f};
+            nxt = (rec[k] >> j) & 1u;
+        }
+        aggR[k] = acc;
+    }
+    auto rc = [](const R& later, const R& earlier) { return earlier.f ? earlier : R{earlier.x + later.x, later.f}; };
+    R wexR[K];
+    (void)block_scan_part1<R, true, K, NW>(aggR, wexR, s_totR, R{T(0), 0u}, rc);
+    __syncthreads();
+    T* abar = static_cast<T*>(A.abar);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int64_t e = base + (int64_t)k * kScanBlock * E + threadIdx.x * E;
+        if (e >= A.n) continue;
+        R after = block_scan_excl<R, true, K, NW>(k, wexR, s_totR, R{T(0), 0u}, rc);
+        T out[E];
+        uint32_t nxt = nextrec[k];
+#pragma unroll
+        for (int j = E - 1; j >= 0; --j) {
+            const R el{yv[k][j], nxt};
+            after = el.f ? el : R{el.x + after.x, after.f};  // after.x = the run sum from element j
+            nxt = (rec[k] >> j) & 1u;
+            out[j] = nxt ? after.x : T(0);
+        }
+        if (e == base && k == 0) lead[t] = rec[0] & 1u ? 0.0 : (double)after.x;  // after the loop: element base
+        if (rec[k]) atomicMax(&s_last1, (unsigned long long)(e + 31 - __clz(rec[k]) + 1));
+        if (A.accumulate) {
+            T old[E];
+            load_chunk_keep(static_cast<const T*>(A.abar), e, A.n, T(0), old);
+#pragma unroll
+            for (int j = 0; j < E; ++j) out[j] += old[j];
+        }
+        store_chunk(abar, e, A.n, out);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) last[t] = (int64_t)s_last1 - 1;
+}
+
+// Tiles without a record (nothing beyond the carry): the adjoint is 0, the
+// primal is the carry, and all of the tile's ybar belongs to the run of the
+// last record before it, so only ybar is read.  A small kernel of its own
+// (few registers, many blocks per SM); scan_minmax_fused_kernel skips these
+// tiles.
+template <class Op, class T, bool WYS>
+__global__ void __launch_bounds__(kScanBlock) scan_minmax_zero_kernel(ScanArgs A, const typename Op::P* tmax,
+                                                                      double* lead, int64_t* last) {
+    using Cfg = ScanCfg<Op, T>;
+    using P = typename Op::P;
+    constexpr int K = Cfg::K, E = Cfg::E, NW = kScanBlock / 32;
+    __shared__ P s_pre;
+    __shared__ uint32_t s_has;
+    __shared__ double s_sum[NW];
+    const int64_t t = blockIdx.x;
+    if (threadIdx.x == 0) {
+        const P pre = static_cast<const P*>(A.carry)[t];
+        s_pre = pre;
+        T on = T(0), dummy = T(0);
+        Op::vjp_right(pre, Op::out_a(tmax[t]), T(0), T(1), T(0), on, dummy);
+        s_has = (t == 0 || on != T(0)) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (s_has) return;
+    const int64_t base = t * Cfg::TILE;
+    const T* yb = static_cast<const T*>(A.ya);
+    double sum = 0.0;
+    T zero[E], ysv[E];
+#pragma unroll
+    for (int j = 0; j < E; ++j) {
+        zero[j] = T(0);
+        ysv[j] = Op::out_a(s_pre);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int64_t e = base + (int64_t)k * kScanBlock * E + threadIdx.x * E;
+        T yv[E];
+        load_chunk(yb, e, A.n, T(0), yv);
+        T ps = T(0);
+#pragma unroll
+        for (int j = 0; j < E; ++j) ps += yv[j];
+        sum += (double)ps;
+        if (e < A.n) {
+            if (!A.accumulate) store_chunk(static_cast<T*>(A.abar), e, A.n, zero);
+            if constexpr (WYS) store_chunk(static_cast<T*>(A.ys_a), e, A.n, ysv);
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, off);
+    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < NW; ++w) tot += s_sum[w];
+        lead[t] = tot;
+        last[t] = -1;
+    }
+}
+
+// Each tile's extremum (no dependence between tiles).
+template <class Op, class T>
+__global__ void __launch_bounds__(kScanBlock) scan_minmax_tile_kernel(ScanArgs A, typename Op::P* tmax) {
+    using Cfg = ScanCfg<Op, T>;
+    using P = typename Op::P;
+    constexpr int K = Cfg::K, E = Cfg::E;
+    __shared__ P s_w[kScanBlock / 32];
+    const int64_t base = (int64_t)blockIdx.x * Cfg::TILE;
+    const T* a = static_cast<const T*>(A.a);
+    P acc = Op::pid();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        T av[E];
+        load_chunk(a, base + (int64_t)k * kScanBlock * E + threadIdx.x * E, A.n, Op::pad_a(), av);
+#pragma unroll
+        for (int j = 0; j < E; ++j) acc = Op::pcomb(acc, Op::pelem(av[j], T(0)));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc = Op::pcomb(acc, shfl_down_s(acc, off));
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        P r = s_w[0];
+        for (int w = 1; w < kScanBlock / 32; ++w) r = Op::pcomb(r, s_w[w]);
+        tmax[blockIdx.x] = r;
+    }
+}
+
+// Exclusive scan of the tile extrema in place (one block; the extremum is
+// exact in any order, so the block-level order does not matter).
+template <class Op, class T>
+__global__ void __launch_bounds__(1024) scan_minmax_carry_kernel(int64_t tiles, const typename Op::P* tmax,
+                                                                 void* carry) {
+    using P = typename Op::P;
+    constexpr int NT = 1024;
+    __shared__ P s_w[NT / 32];
+    P* c = static_cast<P*>(carry);
+    const int64_t per = (tiles + NT - 1) / NT;
+    const int64_t t0 = threadIdx.x * per, t1 = t0 + per < tiles ? t0 + per : tiles;
+    P agg = Op::pid();
+    for (int64_t u = t0; u < t1; ++u) agg = Op::pcomb(agg, tmax[u]);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    P inc = agg;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const P o = shfl_up_s(inc, off);
+        if (lane >= off) inc = Op::pcomb(o, inc);
+    }
+    if (lane == 31) s_w[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        P w = s_w[lane], wi = w;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const P o = shfl_up_s(wi, off);
+            if (lane >= off) wi = Op::pcomb(o, wi);
+        }
+        P ex = shfl_up_s(wi, 1);
+        if (lane == 0) ex = Op::pid();
+        __syncwarp();
+        s_w[lane] = ex;
+    }
+    __syncthreads();
+    P ex = shfl_up_s(inc, 1);
+    if (lane == 0) ex = Op::pid();
+    P run = Op::pcomb(s_w[warp], ex);
+    for (int64_t u = t0; u < t1; ++u) {
+        c[u] = run;
+        run = Op::pcomb(run, tmax[u]);
+    }
+}
+
+// Adds to each tile's last record the part of its run in later tiles:
+// R_t = lead_{t+1} + (tile t+1 has a record ? 0 : R_{t+1}), a reverse
+// segmented sum over the tiles in FP64 (one block; tiles are few).
+template <class T>
+__global__ void __launch_bounds__(1024) scan_minmax_fixup_kernel(int64_t tiles, const double* lead, const int64_t* last,
+                                                                T* abar) {
+    constexpr int NT = 1024;
+    __shared__ double s_x[NT / 32];
+    __shared__ uint32_t s_f[NT / 32];
+    const int64_t per = (tiles + NT - 1) / NT;
+    const int64_t t0 = threadIdx.x * per, t1 = t0 + per < tiles ? t0 + per : tiles;
+    // this thread's part as a run: (sum of leads up to its first record tile, saw one)
+    double x = 0.0;
+    uint32_t f = 0;
+    for (int64_t u = t1 - 1; u >= t0; --u) {
+        const bool has = last[u] >= 0;
+        x = has ? lead[u] : lead[u] + x;
+        f = has ? 1u : f;
+    }
+    // reverse exclusive scan over the threads (later threads first)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double ix = x;
+    uint32_t iff = f;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const double ox = __shfl_down_sync(0xffffffffu, ix, off);
+        const uint32_t of = __shfl_down_sync(0xffffffffu, iff, off);
+        if (lane + off < 32 && !iff) {
+            ix += ox;
+            iff = of;
+        }
+    }
+    if (lane == 0) {
+        s_x[warp] = ix;
+        s_f[warp] = iff;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        double wx = s_x[lane];
+        uint32_t wf = s_f[lane];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const double ox = __shfl_down_sync(0xffffffffu, wx, off);
+            const uint32_t of = __shfl_down_sync(0xffffffffu, wf, off);
+            if (lane + off < 32 && !wf) {
+                wx += ox;
+                wf = of;
+            }
+        }
+        // exclusive: the warps after this one
+        const double ex = __shfl_down_sync(0xffffffffu, wx, 1);
+        const uint32_t ef = __shfl_down_sync(0xffffffffu, wf, 1);
+        __syncwarp();
+        s_x[lane] = lane < 31 ? ex : 0.0;
+        s_f[lane] = lane < 31 ? ef : 0u;
+    }
+    __syncthreads();
+    // after this thread: the later lanes of its warp, then the later warps
+    double ax = __shfl_down_sync(0xffffffffu, ix, 1);
+    uint32_t af = __shfl_down_sync(0xffffffffu, iff, 1);
+    if (lane == 31) {
+        ax = 0.0;
+        af = 0u;
+    }
+    if (!af) ax += s_x[warp];
+    // walk the thread's tiles right to left; ax is R of the tile before
+    for (int64_t u = t1 - 1; u >= t0; --u) {
+        const int64_t p = last[u];
+        if (p >= 0) abar[p] += (T)ax;  // R_u: the leads after tile u up to the next record
+        ax = p >= 0 ? lead[u] : lead[u] + ax;
+    }
+}
+
 // The factored path (FP64 operators with J_left = a_i): the return sweep's
 // tiles are kScanBlock runs of kFacV elements; the primal pass takes
 // kFacKP of them per tile (its carries keep the return sweep's indexing),
@@ -110,6 +450,10 @@ struct ScanLayout {
 // (scan_primal_fac_tile) when the workspace holds it.
 template <class Op, class T>
 constexpr bool kFactored = Op::kCoefIsA && sizeof(T) == 8;
+
+// MIN/MAX take the fused single-pass rule (scan_minmax_fused_kernel).
+template <class Op, class T>
+constexpr bool kMinMax = std::is_same<Op, OpMax<T>>::value || std::is_same<Op, OpMin<T>>::value;
 
 // header | carry[tiles] | look-back slots (primal agg, primal incl,
 // adjoint agg, adjoint incl), the slots contiguous so one kernel zeroes
@@ -196,6 +540,27 @@ int run_scan(int64_t n, const void* a, const void* b, const void* ya, const void
             else scan_adjoint_fac_kernel<Op, false><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
             return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
         }
+    }
+    if constexpr (kMinMax<Op, T>) {
+        // the return sweep fused into the forward pass; the per-tile
+        // metadata take the return sweep's (unused) slot regions
+        double* lead = reinterpret_cast<double*>(A.lbR_agg);
+        int64_t* last = reinterpret_cast<int64_t*>(A.lbR_incl);
+        static_assert(lb_words<Lin<T, 1, true>>() * 4 >= 8, "8 bytes of metadata per tile");
+        using P = typename Op::P;
+        P* tmax = reinterpret_cast<P*>(A.lbP_agg);  // the primal slots are unused on this path
+        static_assert(lb_words<P>() * 4 >= sizeof(P), "one extremum per tile");
+        scan_minmax_tile_kernel<Op, T><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A, tmax);
+        scan_minmax_carry_kernel<Op, T><<<1, 1024, 0, stream>>>(A.tiles, tmax, A.carry);
+        if (ys_a) {
+            scan_minmax_zero_kernel<Op, T, true><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A, tmax, lead, last);
+            scan_minmax_fused_kernel<Op, T, true><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A, tmax, lead, last);
+        } else {
+            scan_minmax_zero_kernel<Op, T, false><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A, tmax, lead, last);
+            scan_minmax_fused_kernel<Op, T, false><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A, tmax, lead, last);
+        }
+        scan_minmax_fixup_kernel<T><<<1, 1024, 0, stream>>>(A.tiles, lead, last, static_cast<T*>(A.abar));
+        return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
     }
     if (need_primal) scan_primal_kernel<Op, T><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
     if (ys_a) scan_adjoint_kernel<Op, T, true><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);

@@ -161,6 +161,45 @@ def test_fp64_factored_and_minimal_workspace_paths(A, oracle, op, n):
             assert rel_l2(ysb.cpu().numpy(), ryb) < 1e-12
 
 
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+@pytest.mark.parametrize("op", ["min", "max"])
+@pytest.mark.parametrize("pattern", ["increasing", "decreasing", "sawtooth", "tile_edges", "plateaus"])
+def test_minmax_scan_record_patterns(A, oracle, op, dt, pattern):
+    """Record structure of the min/max rule: the adjoint is nonzero only at
+    records (strictly beyond everything before; ties stay with the earlier
+    element) and element 0.  Every element a record, none after the first,
+    records in some tiles only, records on tile boundaries and long ties;
+    the nonzero pattern is compared exactly."""
+    n = 5 * 8192 + 77
+    g = synth.rng(17)
+    i = np.arange(n, dtype=np.float64)
+    if pattern == "increasing":
+        a = i
+    elif pattern == "decreasing":
+        a = -i
+    elif pattern == "sawtooth":
+        a = (i % 3000) + np.floor(i / 20000) * 4000  # a new high every 20000 elements
+    elif pattern == "tile_edges":
+        a = np.full(n, -1e6)
+        for t, e in enumerate(range(0, n, 4096)):
+            a[e] = t  # a record on every 4096-element boundary
+    else:
+        a = np.floor(i / 5000)  # plateaus: only each plateau's first element is a record
+    if op == "min":
+        a = -a
+    a = a.astype(dt)
+    y = g.standard_normal(n).astype(dt)
+    ys = torch.empty(n, dtype=torch.float32 if dt == np.float32 else torch.float64, device="cuda")
+    ab, _, work = A.adpar_vjp_scan(op, dev(a), dev(y), ys_a=ys)
+    torch.cuda.synchronize()
+    assert A.adpar_workspace_status(work) == A.OK
+    ref, _, rys, _ = oracle.scan_vjp(op, a, y)
+    got = ab.cpu().numpy()
+    np.testing.assert_array_equal(got != 0, ref != 0)
+    assert rel_l2(got, ref) < tol(dt, n)
+    np.testing.assert_array_equal(ys.cpu().numpy(), rys.astype(dt))
+
+
 def test_scan_zero_length_and_errors(A):
     e = torch.empty(0, device="cuda")
     ab, _, _ = A.adpar_vjp_scan("add", e, e)

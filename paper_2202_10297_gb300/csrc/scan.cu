@@ -74,8 +74,9 @@ struct RunSum {
 };
 
 template <class Op, class T, bool WYS>
-__global__ void __launch_bounds__(kScanBlock) scan_minmax_fused_kernel(ScanArgs A, const typename Op::P* tmax,
-                                                                       double* lead, int64_t* last) {
+__global__ void __launch_bounds__(kScanBlock) scan_minmax_fused_kernel(ScanArgs A, const uint32_t* rec_list,
+                                                                       const uint32_t* n_rec, double* lead,
+                                                                       int64_t* last) {
     using Cfg = ScanCfg<Op, T>;
     using P = typename Op::P;
     using R = RunSum<T>;
@@ -85,108 +86,107 @@ __global__ void __launch_bounds__(kScanBlock) scan_minmax_fused_kernel(ScanArgs 
     __shared__ P s_pre;
     __shared__ uint32_t s_rec[K][kScanBlock];  // record bits of each thread's E elements
     __shared__ unsigned long long s_last1;      // 1 + the tile's last record (0: none)
-    __shared__ uint32_t s_has;  // the tile holds a record
-    const int64_t t = blockIdx.x;
-    if (threadIdx.x == 0) {
-        s_last1 = 0ull;
-        const P pre = static_cast<const P*>(A.carry)[t];  // the extremum before the tile
-        s_pre = pre;
-        T on = T(0), dummy = T(0);
-        Op::vjp_right(pre, Op::out_a(tmax[t]), T(0), T(1), T(0), on, dummy);
-        s_has = (t == 0 || on != T(0)) ? 1u : 0u;
-    }
-    __syncthreads();
-    const int64_t base = t * Cfg::TILE;
     const T* a = static_cast<const T*>(A.a);
     const T* yb = static_cast<const T*>(A.ya);
-    if (!s_has) return;  // scan_minmax_zero_kernel takes it
-    T av[K][E], yv[K][E];
-    P agg[K];
+    // persistent over the tiles holding a record (listed by the carry scan)
+    const uint32_t nrec = *n_rec;
+    for (uint32_t q = blockIdx.x; q < nrec; q += gridDim.x) {
+        const int64_t t = rec_list[q];
+        if (threadIdx.x == 0) {
+            s_last1 = 0ull;
+            s_pre = static_cast<const P*>(A.carry)[t];  // the extremum before the tile
+        }
+        __syncthreads();
+        const int64_t base = t * Cfg::TILE;
+        T av[K][E], yv[K][E];
+        P agg[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int64_t e = base + (int64_t)k * kScanBlock * E + threadIdx.x * E;
-        load_chunk(a, e, A.n, Op::pad_a(), av[k]);
-        load_chunk(yb, e, A.n, T(0), yv[k]);
-        P acc = Op::pelem(av[k][0], T(0));
+        for (int k = 0; k < K; ++k) {
+            const int64_t e = base + (int64_t)k * kScanBlock * E + threadIdx.x * E;
+            load_chunk(a, e, A.n, Op::pad_a(), av[k]);
+            load_chunk(yb, e, A.n, T(0), yv[k]);
+            P acc = Op::pelem(av[k][0], T(0));
 #pragma unroll
-        for (int j = 1; j < E; ++j) acc = Op::pcomb(acc, Op::pelem(av[k][j], T(0)));
-        agg[k] = acc;
+            for (int j = 1; j < E; ++j) acc = Op::pcomb(acc, Op::pelem(av[k][j], T(0)));
+            agg[k] = acc;
+        }
+        auto fc = [](const P& l, const P& r) { return Op::pcomb(l, r); };
+        P wex[K];
+        (void)block_scan_part1<P, false, K, NW>(agg, wex, s_tot, Op::pid(), fc);
+        __syncthreads();
+        // records: J_right(i) = 1 (a_i strictly beyond everything before it), and element 0
+        uint32_t rec[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int64_t e = base + (int64_t)k * kScanBlock * E + threadIdx.x * E;
+            P prev = block_scan_excl<P, false, K, NW>(k, wex, s_tot, s_pre, fc);
+            uint32_t bits = 0;
+            T ys[E];
+#pragma unroll
+            for (int j = 0; j < E; ++j) {
+                T on = T(0), dummy = T(0);
+                Op::vjp_right(prev, av[k][j], T(0), T(1), T(0), on, dummy);
+                if (e + j < A.n && (e + j == 0 || on != T(0))) bits |= 1u << j;
+                prev = Op::pcomb(prev, Op::pelem(av[k][j], T(0)));
+                ys[j] = Op::out_a(prev);
+            }
+            rec[k] = bits;
+            s_rec[k][threadIdx.x] = bits;
+            if constexpr (WYS) {
+                if (e < A.n) store_chunk(static_cast<T*>(A.ys_a), e, A.n, ys);
+            }
+        }
+        __syncthreads();
+        // in-tile runs: element i's run ends where element i+1 is a record
+        R aggR[K];
+        uint32_t nextrec[K];  // record bit of the element after each thread's last one
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int tn = threadIdx.x + 1;
+            nextrec[k] = tn < kScanBlock ? (s_rec[k][tn] & 1u) : (k + 1 < K ? (s_rec[k + 1 < K ? k + 1 : k][0] & 1u) : 0u);
+            R acc{T(0), 0u};
+            uint32_t nxt = nextrec[k];
+#pragma unroll
+            for (int j = E - 1; j >= 0; --j) {
+                const R el{yv[k][j], nxt};
+                acc = el.f ? el : R{el.x + acc.x, acc.f};
+                nxt = (rec[k] >> j) & 1u;
+            }
+            aggR[k] = acc;
+        }
+        auto rc = [](const R& later, const R& earlier) { return earlier.f ? earlier : R{earlier.x + later.x, later.f}; };
+        R wexR[K];
+        (void)block_scan_part1<R, true, K, NW>(aggR, wexR, s_totR, R{T(0), 0u}, rc);
+        __syncthreads();
+        T* abar = static_cast<T*>(A.abar);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int64_t e = base + (int64_t)k * kScanBlock * E + threadIdx.x * E;
+            if (e >= A.n) continue;
+            R after = block_scan_excl<R, true, K, NW>(k, wexR, s_totR, R{T(0), 0u}, rc);
+            T out[E];
+            uint32_t nxt = nextrec[k];
+#pragma unroll
+            for (int j = E - 1; j >= 0; --j) {
+                const R el{yv[k][j], nxt};
+                after = el.f ? el : R{el.x + after.x, after.f};  // after.x = the run sum from element j
+                nxt = (rec[k] >> j) & 1u;
+                out[j] = nxt ? after.x : T(0);
+            }
+            if (e == base && k == 0) lead[t] = rec[0] & 1u ? 0.0 : (double)after.x;  // after the loop: element base
+            if (rec[k]) atomicMax(&s_last1, (unsigned long long)(e + 31 - __clz(rec[k]) + 1));
+            if (A.accumulate) {
+                T old[E];
+                load_chunk_keep(static_cast<const T*>(A.abar), e, A.n, T(0), old);
+#pragma unroll
+                for (int j = 0; j < E; ++j) out[j] += old[j];
+            }
+            store_chunk(abar, e, A.n, out);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) last[t] = (int64_t)s_last1 - 1;
+        __syncthreads();  // the shared state is reused by the next tile
     }
-    auto fc = [](const P& l, const P& r) { return Op::pcomb(l, r); };
-    P wex[K];
-    (void)block_scan_part1<P, false, K, NW>(agg, wex, s_tot, Op::pid(), fc);
-    __syncthreads();
-    // records: J_right(i) = 1 (a_i strictly beyond everything before it), and element 0
-    uint32_t rec[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int64_t e = base + (int64_t)k * kScanBlock * E + threadIdx.x * E;
-        P prev = block_scan_excl<P, false, K, NW>(k, wex, s_tot, s_pre, fc);
-        uint32_t bits = 0;
-        T ys[E];
-#pragma unroll
-        for (int j = 0; j < E; ++j) {
-            T on = T(0), dummy = T(0);
-            Op::vjp_right(prev, av[k][j], T(0), T(1), T(0), on, dummy);
-            if (e + j < A.n && (e + j == 0 || on != T(0))) bits |= 1u << j;
-            prev = Op::pcomb(prev, Op::pelem(av[k][j], T(0)));
-            ys[j] = Op::out_a(prev);
-        }
-        rec[k] = bits;
-        s_rec[k][threadIdx.x] = bits;
-        if constexpr (WYS) {
-            if (e < A.n) store_chunk(static_cast<T*>(A.ys_a), e, A.n, ys);
-        }
-    }
-    __syncthreads();
-    // in-tile runs: element i's run ends where element i+1 is a record
-    R aggR[K];
-    uint32_t nextrec[K];  // record bit of the element after each thread's last one
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int tn = threadIdx.x + 1;
-        nextrec[k] = tn < kScanBlock ? (s_rec[k][tn] & 1u) : (k + 1 < K ? (s_rec[k + 1 < K ? k + 1 : k][0] & 1u) : 0u);
-        R acc{T(0), 0u};
-        uint32_t nxt = nextrec[k];
-#pragma unroll
-        for (int j = E - 1; j >= 0; --j) {
-            const R el{yv[k][j], nxt};
-            acc = el.f ? el : R{el.x + acc.x, acc.f};
-            nxt = (rec[k] >> j) & 1u;
-        }
-        aggR[k] = acc;
-    }
-    auto rc = [](const R& later, const R& earlier) { return earlier.f ? earlier : R{earlier.x + later.x, later.f}; };
-    R wexR[K];
-    (void)block_scan_part1<R, true, K, NW>(aggR, wexR, s_totR, R{T(0), 0u}, rc);
-    __syncthreads();
-    T* abar = static_cast<T*>(A.abar);
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int64_t e = base + (int64_t)k * kScanBlock * E + threadIdx.x * E;
-        if (e >= A.n) continue;
-        R after = block_scan_excl<R, true, K, NW>(k, wexR, s_totR, R{T(0), 0u}, rc);
-        T out[E];
-        uint32_t nxt = nextrec[k];
-#pragma unroll
-        for (int j = E - 1; j >= 0; --j) {
-            const R el{yv[k][j], nxt};
-            after = el.f ? el : R{el.x + after.x, after.f};  // after.x = the run sum from element j
-            nxt = (rec[k] >> j) & 1u;
-            out[j] = nxt ? after.x : T(0);
-        }
-        if (e == base && k == 0) lead[t] = rec[0] & 1u ? 0.0 : (double)after.x;  // after the loop: element base
-        if (rec[k]) atomicMax(&s_last1, (unsigned long long)(e + 31 - __clz(rec[k]) + 1));
-        if (A.accumulate) {
-            T old[E];
-            load_chunk_keep(static_cast<const T*>(A.abar), e, A.n, T(0), old);
-#pragma unroll
-            for (int j = 0; j < E; ++j) out[j] += old[j];
-        }
-        store_chunk(abar, e, A.n, out);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) last[t] = (int64_t)s_last1 - 1;
 }
 
 // Tiles without a record (nothing beyond the carry): the adjoint is 0, the
@@ -280,15 +280,21 @@ __global__ void __launch_bounds__(kScanBlock) scan_minmax_tile_kernel(ScanArgs A
 // exact in any order, so the block-level order does not matter).
 template <class Op, class T>
 __global__ void __launch_bounds__(1024) scan_minmax_carry_kernel(int64_t tiles, const typename Op::P* tmax,
-                                                                 void* carry) {
+                                                                 void* carry, uint32_t* rec_list, uint32_t* n_rec) {
     using P = typename Op::P;
-    constexpr int NT = 1024;
+    constexpr int NT = 1024, B = 8;  // loads issued B at a time
     __shared__ P s_w[NT / 32];
     P* c = static_cast<P*>(carry);
     const int64_t per = (tiles + NT - 1) / NT;
     const int64_t t0 = threadIdx.x * per, t1 = t0 + per < tiles ? t0 + per : tiles;
     P agg = Op::pid();
-    for (int64_t u = t0; u < t1; ++u) agg = Op::pcomb(agg, tmax[u]);
+    for (int64_t u0 = t0; u0 < t1; u0 += B) {
+        P v[B];
+#pragma unroll
+        for (int j = 0; j < B; ++j) v[j] = u0 + j < t1 ? tmax[u0 + j] : Op::pid();
+#pragma unroll
+        for (int j = 0; j < B; ++j) agg = Op::pcomb(agg, v[j]);
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     P inc = agg;
 #pragma unroll
@@ -299,7 +305,7 @@ __global__ void __launch_bounds__(1024) scan_minmax_carry_kernel(int64_t tiles, 
     if (lane == 31) s_w[warp] = inc;
     __syncthreads();
     if (warp == 0) {
-        P w = s_w[lane], wi = w;
+        P wi = s_w[lane];
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const P o = shfl_up_s(wi, off);
@@ -314,9 +320,22 @@ __global__ void __launch_bounds__(1024) scan_minmax_carry_kernel(int64_t tiles, 
     P ex = shfl_up_s(inc, 1);
     if (lane == 0) ex = Op::pid();
     P run = Op::pcomb(s_w[warp], ex);
-    for (int64_t u = t0; u < t1; ++u) {
-        c[u] = run;
-        run = Op::pcomb(run, tmax[u]);
+    // carries, and the tiles holding a record (the same test as
+    // scan_minmax_zero_kernel's) listed for scan_minmax_fused_kernel
+    for (int64_t u0 = t0; u0 < t1; u0 += B) {
+        P v[B];
+#pragma unroll
+        for (int j = 0; j < B; ++j) v[j] = u0 + j < t1 ? tmax[u0 + j] : Op::pid();
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            const int64_t u = u0 + j;
+            if (u >= t1) break;
+            c[u] = run;
+            T on = T(0), dummy = T(0);
+            Op::vjp_right(run, Op::out_a(v[j]), T(0), T(1), T(0), on, dummy);
+            if (u == 0 || on != T(0)) rec_list[atomicAdd(n_rec, 1u)] = (uint32_t)u;
+            run = Op::pcomb(run, v[j]);
+        }
     }
 }
 
@@ -332,12 +351,24 @@ __global__ void __launch_bounds__(1024) scan_minmax_fixup_kernel(int64_t tiles, 
     const int64_t per = (tiles + NT - 1) / NT;
     const int64_t t0 = threadIdx.x * per, t1 = t0 + per < tiles ? t0 + per : tiles;
     // this thread's part as a run: (sum of leads up to its first record tile, saw one)
+    constexpr int B = 8;  // loads issued B at a time
     double x = 0.0;
     uint32_t f = 0;
-    for (int64_t u = t1 - 1; u >= t0; --u) {
-        const bool has = last[u] >= 0;
-        x = has ? lead[u] : lead[u] + x;
-        f = has ? 1u : f;
+    for (int64_t u0 = t1 - 1; u0 >= t0; u0 -= B) {
+        double ld[B];
+        int64_t ls[B];
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            ld[j] = u0 - j >= t0 ? lead[u0 - j] : 0.0;
+            ls[j] = u0 - j >= t0 ? last[u0 - j] : -1;
+        }
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            if (u0 - j < t0) break;
+            const bool has = ls[j] >= 0;
+            x = has ? ld[j] : ld[j] + x;
+            f = has ? 1u : f;
+        }
     }
     // reverse exclusive scan over the threads (later threads first)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -386,10 +417,21 @@ __global__ void __launch_bounds__(1024) scan_minmax_fixup_kernel(int64_t tiles, 
     }
     if (!af) ax += s_x[warp];
     // walk the thread's tiles right to left; ax is R of the tile before
-    for (int64_t u = t1 - 1; u >= t0; --u) {
-        const int64_t p = last[u];
-        if (p >= 0) abar[p] += (T)ax;  // R_u: the leads after tile u up to the next record
-        ax = p >= 0 ? lead[u] : lead[u] + ax;
+    for (int64_t u0 = t1 - 1; u0 >= t0; u0 -= B) {
+        double ld[B];
+        int64_t ls[B];
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            ld[j] = u0 - j >= t0 ? lead[u0 - j] : 0.0;
+            ls[j] = u0 - j >= t0 ? last[u0 - j] : -1;
+        }
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            if (u0 - j < t0) break;
+            const int64_t p = ls[j];
+            if (p >= 0) abar[p] += (T)ax;  // R_u: the leads after tile u up to the next record
+            ax = p >= 0 ? ld[j] : ld[j] + ax;
+        }
     }
 }
 
@@ -507,6 +549,18 @@ inline void launch_init(const ScanArgs& A, char* w, const ScanLayout& L, cudaStr
                                                  words);
 }
 
+// blocks of the persistent min/max pass: two per SM (its register use)
+inline int fused_grid() {
+    static int g = 0;
+    if (g == 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        g = 2 * (sms > 0 ? sms : 1);
+    }
+    return g;
+}
+
 template <class Op, class T>
 int run_scan(int64_t n, const void* a, const void* b, const void* ya, const void* yb, void* abar,
              void* bbar, void* ys_a, void* ys_b, uint32_t flags, void* work, size_t work_bytes,
@@ -551,13 +605,17 @@ int run_scan(int64_t n, const void* a, const void* b, const void* ya, const void
         P* tmax = reinterpret_cast<P*>(A.lbP_agg);  // the primal slots are unused on this path
         static_assert(lb_words<P>() * 4 >= sizeof(P), "one extremum per tile");
         scan_minmax_tile_kernel<Op, T><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A, tmax);
-        scan_minmax_carry_kernel<Op, T><<<1, 1024, 0, stream>>>(A.tiles, tmax, A.carry);
+        uint32_t* rec_list = reinterpret_cast<uint32_t*>(A.lbP_incl);  // [tiles], unused slots too
+        uint32_t* n_rec = &A.hdr->done[1];                               // zeroed by the init kernel
+        static_assert(lb_words<P>() * 4 >= sizeof(uint32_t), "one list entry per tile");
+        scan_minmax_carry_kernel<Op, T><<<1, 1024, 0, stream>>>(A.tiles, tmax, A.carry, rec_list, n_rec);
+        const unsigned fgrid = (unsigned)std::min<int64_t>(A.tiles, (int64_t)fused_grid());
         if (ys_a) {
             scan_minmax_zero_kernel<Op, T, true><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A, tmax, lead, last);
-            scan_minmax_fused_kernel<Op, T, true><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A, tmax, lead, last);
+            scan_minmax_fused_kernel<Op, T, true><<<fgrid, kScanBlock, 0, stream>>>(A, rec_list, n_rec, lead, last);
         } else {
             scan_minmax_zero_kernel<Op, T, false><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A, tmax, lead, last);
-            scan_minmax_fused_kernel<Op, T, false><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A, tmax, lead, last);
+            scan_minmax_fused_kernel<Op, T, false><<<fgrid, kScanBlock, 0, stream>>>(A, rec_list, n_rec, lead, last);
         }
         scan_minmax_fixup_kernel<T><<<1, 1024, 0, stream>>>(A.tiles, lead, last, static_cast<T*>(A.abar));
         return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;

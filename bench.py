@@ -746,10 +746,11 @@ def row_scan_wide(args):
         wk = A.workspace(A.adpar_workspace_size(A.RULE_SCAN_WIDE, A.OP_MATREC2, A.F32 if dt == np.float32 else A.F64,
                                                 n, 0, width=6), "cuda")
         t = _cuda_ms(lambda: A.adpar_vjp_scan_wide("matrec2", a, yb, abar=ab, work=wk), 5, 2)
+        tf = _cuda_ms(lambda: A.adpar_vjp_scan_wide("matrec2", a, yb, abar=ab, work=wk, full_lin_o=True), 3, 1)
         alg = 3 * 6 * np.dtype(dt).itemsize  # a, ybar in; abar out
         cases["matrec2_%s_n2p24" % ("f32" if dt == np.float32 else "f64")] = {
             "ms": t, "elements_per_s": n / t * 1e3, "gbs": alg * n / t / 1e6,
-            "hbm_frac_of_measured": alg * n / t / 1e6 / hbm}
+            "hbm_frac_of_measured": alg * n / t / 1e6 / hbm, "full_lin_o_ms": tf}
         del a, yb, ab, wk
     n = 1 << 26
     a, b, ya, ybb = (_dev(v) for v in synth.linrec(n, np.float32, seed=synth.SEED_BASE + 1))

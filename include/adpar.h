@@ -101,6 +101,7 @@ typedef enum {
 #define ADPAR_ACCUMULATE      0x1u /* x_bar += contribution (else x_bar = contribution) */
 #define ADPAR_PROD_LOGDOMAIN  0x4u /* * rules: write ln|contribution| and its sign      */
 #define ADPAR_SCATTER_RESTORE 0x8u /* scatter: also restore ys[is_j] = xs_saved[j]      */
+#define ADPAR_FULL_LIN_O      0x10u /* wide scans: the return sweep on full d x d lin_o   */
 
 /* operator descriptor: op (adpar_op), dtype (adpar_dtype) of the values,
  * width = number of arrays per element (1, or 2 for ADPAR_OP_LINREC). */
@@ -242,8 +243,15 @@ int adpar_vjp_scan(adpar_opdesc desc, int64_t n, const void *a, const void *b,
  *   ybar     [n][D] cotangent of the inclusive scan ys.
  *   abar     [n][D] output adjoint (overwritten, or += with ADPAR_ACCUMULATE).
  *   ys_out   nullable [n][D]: the recomputed inclusive scan.
+ * The 2x2 matrix recurrence's J_left is I_3 (x) M (M acts on the two
+ * columns of the matrix part and on the vector part alike), so by default
+ * its return sweep carries C = I_3 (x) N with N a 2x2 matrix (10 scalars a
+ * state instead of 42); ADPAR_FULL_LIN_O forces the full d x d lin_o for
+ * either operator (same results up to rounding).
  * Every non-null array must start on a 16-byte boundary (ADPAR_ERR_ALIGN).
- * Workspace: adpar_workspace_size(ADPAR_RULE_SCAN_WIDE, desc, n, 0). */
+ * Flags: ADPAR_ACCUMULATE, ADPAR_FULL_LIN_O.
+ * Workspace: adpar_workspace_size(ADPAR_RULE_SCAN_WIDE, desc, n, 0) (the
+ * full lin_o's size, which covers both forms). */
 int adpar_vjp_scan_wide(adpar_opdesc desc, int64_t n, const void *a, const void *ybar, void *abar,
                         void *ys_out, uint32_t flags, void *work, size_t work_bytes, void *stream);
 

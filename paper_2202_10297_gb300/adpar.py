@@ -26,7 +26,7 @@ GFUNS = {"gather": G_GATHER, "scale": G_SCALE, "sqdist_row": G_SQDIST_ROW}
 RULE_REDUCE, RULE_SCAN, RULE_HIST, RULE_SCATTER, RULE_MAP_ACC, RULE_KMEANS, RULE_REDUCE_GENERAL, RULE_SCAN_VEC, \
     RULE_HIST_GENERAL, RULE_SCAN_WIDE = range(10)
 WS_MINIMAL = 0x100  # or'ed into a rule: the smallest accepted workspace
-ACCUMULATE, PROD_LOGDOMAIN, SCATTER_RESTORE = 0x1, 0x4, 0x8
+ACCUMULATE, PROD_LOGDOMAIN, SCATTER_RESTORE, FULL_LIN_O = 0x1, 0x4, 0x8, 0x10
 OK, ERR_TIMEOUT, ERR_TOO_LARGE = 0, 6, 7
 
 
@@ -252,11 +252,13 @@ def adpar_vjp_reduce_general(op, a, ybar_a, b=None, ybar_b=None, abar=None, bbar
     return abar, bbar, y
 
 
-def adpar_vjp_scan_wide(op, a, ybar, abar=None, want_ys=False, accumulate=False, work=None, stream=None):
-    """VJP of a scan over [n, D] rows by the general d x d lin_o (C: adpar_vjp_scan_wide).
+def adpar_vjp_scan_wide(op, a, ybar, abar=None, want_ys=False, accumulate=False, full_lin_o=False, work=None,
+                        stream=None):
+    """VJP of a scan over [n, D] rows by the d x d lin_o (C: adpar_vjp_scan_wide).
 
-    ``op`` is "linrec" (D = 2) or "matrec2" (D = 6).  Returns (abar, ys), ys
-    only with ``want_ys``.
+    ``op`` is "linrec" (D = 2) or "matrec2" (D = 6); ``full_lin_o`` forces
+    the full d x d lin_o where a blockwise one applies.  Returns (abar, ys),
+    ys only with ``want_ys``.
     """
     opc = OPS[op] if isinstance(op, str) else int(op)
     D = WIDE[opc]
@@ -270,8 +272,9 @@ def adpar_vjp_scan_wide(op, a, ybar, abar=None, want_ys=False, accumulate=False,
     need = adpar_workspace_size(RULE_SCAN_WIDE, opc, dt, n, 0, width=D)
     if work is None or work.numel() < need:
         work = workspace(need, a.device)
-    st = lib().adpar_vjp_scan_wide(OpDesc(opc, dt, D), n, _ptr(a), _ptr(ybar), _ptr(abar), _ptr(ys),
-                                   ACCUMULATE if accumulate else 0, _ptr(work), work.numel(), _stream(stream))
+    flags = (ACCUMULATE if accumulate else 0) | (FULL_LIN_O if full_lin_o else 0)
+    st = lib().adpar_vjp_scan_wide(OpDesc(opc, dt, D), n, _ptr(a), _ptr(ybar), _ptr(abar), _ptr(ys), flags,
+                                   _ptr(work), work.numel(), _stream(stream))
     _check("adpar_vjp_scan_wide", st)
     return abar, ys
 

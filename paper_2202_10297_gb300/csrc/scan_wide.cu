@@ -14,6 +14,12 @@
 // tile's primal carry (and writes ys when asked); the reverse pass re-forms
 // the primal inside the tile from that carry, forms (ybar_i, J_left(i+1)^T)
 // per element, scans the affine maps right to left and applies J_right^T.
+// Where J_left acts alike on blocks of the element (the matrix recurrence:
+// M on both columns of the matrix part and on the vector part), C stays
+// I (x) N with a small N, and that lin_o (LinBlock) replaces the full one
+// (LinFull) unless ADPAR_FULL_LIN_O asks for it.
+#include <type_traits>
+
 #include "common.cuh"
 #include "scan_engine.cuh"
 
@@ -89,6 +95,11 @@ struct WMatrec2 {
                 J[4 + j][4 + m] = x.v[2 * j + m];
             }
     }
+    // J_left = I_3 (x) M on three 2-vectors: block j < 2 is column j of the
+    // matrix part (components j, 2 + j), block 2 the vector part (4, 5)
+    static constexpr int kB = 2;
+    __device__ static int blk(int j, int i) { return j < 2 ? 2 * i + j : 4 + i; }
+    __device__ static T block_m(const S& x, int r, int m) { return x.v[2 * r + m]; }
     __device__ static void vjp_right(const S& prev, const S&, const T (&g)[D], T (&o)[D]) {
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
@@ -132,6 +143,108 @@ __device__ __forceinline__ WLin<T, D> wlin_comb(const WLin<T, D>& e, const WLin<
     }
     return r;
 }
+
+// The return sweep's lin_o, in full: C = J_left^T as a D x D matrix.
+template <class Op, class T>
+struct LinFull {
+    static constexpr int D = Op::D;
+    using S = typename Op::S;
+    using L = WLin<T, D>;
+    __device__ static L id() { return wlin_id<T, D>(); }
+    __device__ static L comb(const L& later, const L& earlier) { return wlin_comb<T, D>(later, earlier); }
+    // (ybar_i, J_left(i+1)^T) from rs_i and a_{i+1}
+    __device__ static L elem(const S& prev, const S& xn, const S& y) {
+        L el;
+        T J[D][D];
+        Op::jleft(prev, xn, J);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            el.d[i] = y.v[i];
+#pragma unroll
+            for (int j = 0; j < D; ++j) el.c[i][j] = J[j][i];
+        }
+        return el;
+    }
+    // o = el.d + el.C g
+    __device__ static void apply(const L& el, const T (&g)[D], T (&o)[D]) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            T s = el.d[i];
+#pragma unroll
+            for (int k = 0; k < D; ++k) s = fma(el.c[i][k], g[k], s);
+            o[i] = s;
+        }
+    }
+};
+
+// The same lin_o when J_left = I (x) M acts alike on D / B blocks of B
+// components (Op::blk), so C = I (x) N with N = M^T a B x B matrix and the
+// maps compose blockwise: (d1, N1) after (d2, N2) = (d1 + N1 d2, N1 N2).
+template <class T, int D, int B>
+struct WLinB {
+    T d[D];
+    T n[B][B];
+};
+
+template <class Op, class T>
+struct LinBlock {
+    static constexpr int D = Op::D, B = Op::kB, NB = D / B;
+    using S = typename Op::S;
+    using L = WLinB<T, D, B>;
+    __device__ static L id() {
+        L r;
+#pragma unroll
+        for (int i = 0; i < D; ++i) r.d[i] = T(0);
+#pragma unroll
+        for (int i = 0; i < B; ++i)
+#pragma unroll
+            for (int m = 0; m < B; ++m) r.n[i][m] = i == m ? T(1) : T(0);
+        return r;
+    }
+    __device__ static L comb(const L& e, const L& l) {  // e later, l earlier
+        L r;
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+#pragma unroll
+            for (int i = 0; i < B; ++i) {
+                T s = l.d[Op::blk(j, i)];
+#pragma unroll
+                for (int m = 0; m < B; ++m) s = fma(l.n[i][m], e.d[Op::blk(j, m)], s);
+                r.d[Op::blk(j, i)] = s;
+            }
+#pragma unroll
+        for (int i = 0; i < B; ++i)
+#pragma unroll
+            for (int m = 0; m < B; ++m) {
+                T s = T(0);
+#pragma unroll
+                for (int k = 0; k < B; ++k) s = fma(l.n[i][k], e.n[k][m], s);
+                r.n[i][m] = s;
+            }
+        return r;
+    }
+    __device__ static L elem(const S&, const S& xn, const S& y) {
+        L el;
+#pragma unroll
+        for (int i = 0; i < D; ++i) el.d[i] = y.v[i];
+#pragma unroll
+        for (int i = 0; i < B; ++i)
+#pragma unroll
+            for (int m = 0; m < B; ++m) el.n[i][m] = Op::block_m(xn, m, i);  // N = M^T
+        return el;
+    }
+    __device__ static void apply(const L& el, const T (&g)[D], T (&o)[D]) {
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+#pragma unroll
+            for (int i = 0; i < B; ++i) {
+                T s = el.d[Op::blk(j, i)];
+#pragma unroll
+                for (int m = 0; m < B; ++m) s = fma(el.n[i][m], g[Op::blk(j, m)], s);
+                o[Op::blk(j, i)] = s;
+            }
+    }
+};
 
 template <class T, int D>
 struct WideArgs {
@@ -232,11 +345,11 @@ __global__ void __launch_bounds__(kWideBlock) wide_primal_kernel(WideArgs<T, Op:
 }
 
 // Reverse pass (tiles right to left).
-template <class Op, class T>
+template <class Op, class T, class LP>
 __global__ void __launch_bounds__(kWideBlock) wide_adjoint_kernel(WideArgs<T, Op::D> A) {
     constexpr int D = Op::D, NW = kWideBlock / 32;
     using S = typename Op::S;
-    using L = WLin<T, D>;
+    using L = typename LP::L;
     __shared__ uint32_t s_tile;
     __shared__ S s_totP[NW];
     __shared__ L s_totR[NW];
@@ -270,28 +383,17 @@ __global__ void __launch_bounds__(kWideBlock) wide_adjoint_kernel(WideArgs<T, Op
 #pragma unroll
     for (int r = 0; r < kWideV; ++r) prev[r + 1] = Op::comb(prev[r], x[r]);
     // lin_o element of row r: (ybar_r, J_left(r+1)^T), formed when needed
-    auto element = [&](int r) {
-        L el;
-        T J[D][D];
-        Op::jleft(prev[r + 1], r + 1 < kWideV ? x[r + 1] : xnext, J);
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            el.d[i] = yb[r].v[i];
-#pragma unroll
-            for (int j = 0; j < D; ++j) el.c[i][j] = J[j][i];
-        }
-        return el;
-    };
+    auto element = [&](int r) { return LP::elem(prev[r + 1], r + 1 < kWideV ? x[r + 1] : xnext, yb[r]); };
     L agg[1];
     agg[0] = element(kWideV - 1);
 #pragma unroll
-    for (int r = kWideV - 2; r >= 0; --r) agg[0] = wlin_comb<T, D>(agg[0], element(r));
-    auto rc = [](const L& later, const L& earlier) { return wlin_comb<T, D>(later, earlier); };
+    for (int r = kWideV - 2; r >= 0; --r) agg[0] = LP::comb(agg[0], element(r));
+    auto rc = [](const L& later, const L& earlier) { return LP::comb(later, earlier); };
     L wexR[1];
-    const L totR = block_scan_part1<L, true, 1, NW>(agg, wexR, s_totR, wlin_id<T, D>(), rc);
+    const L totR = block_scan_part1<L, true, 1, NW>(agg, wexR, s_totR, LP::id(), rc);
     if ((threadIdx.x >> 5) == 0) {
         LookbackState<L> st{A.lbR_agg, A.lbR_incl};
-        const L suf = lookback(t_log, st, totR, wlin_id<T, D>(), rc, A.hdr);
+        const L suf = lookback(t_log, st, totR, LP::id(), rc, A.hdr);
         if ((threadIdx.x & 31) == 0) s_suf = suf;
     }
     __syncthreads();
@@ -305,16 +407,8 @@ __global__ void __launch_bounds__(kWideBlock) wide_adjoint_kernel(WideArgs<T, Op
 #pragma unroll
     for (int r = kWideV - 1; r >= 0; --r) {
         // rs_bar_r = ybar_r + J_left(r+1)^T rs_bar_{r+1}
-        T J[D][D];
-        Op::jleft(prev[r + 1], r + 1 < kWideV ? x[r + 1] : xnext, J);
         T ng[D];
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            T s = yb[r].v[i];
-#pragma unroll
-            for (int k = 0; k < D; ++k) s = fma(J[k][i], g[k], s);
-            ng[i] = s;
-        }
+        LP::apply(element(r), g, ng);
 #pragma unroll
         for (int i = 0; i < D; ++i) g[i] = ng[i];
         if (e + r == 0) {
@@ -326,6 +420,14 @@ __global__ void __launch_bounds__(kWideBlock) wide_adjoint_kernel(WideArgs<T, Op
     }
     st_rows<T, D>(A.abar, e, A.n, out, A.accumulate != 0);
 }
+
+// operators whose J_left acts blockwise (Op::kB, Op::blk, Op::block_m)
+template <class Op, class = void>
+struct HasBlocks : std::false_type {};
+template <class Op>
+struct HasBlocks<Op, std::void_t<decltype(Op::kB)>> : std::true_type {};
+template <class Op>
+constexpr bool kHasBlocks = HasBlocks<Op>::value;
 
 template <class Op, class T>
 struct WideLayout {
@@ -380,7 +482,13 @@ int run_wide(int64_t n, const void* a, const void* ybar, void* abar, void* ys, u
     A.hdr = reinterpret_cast<WsHeader*>(w);
     A.accumulate = (flags & ADPAR_ACCUMULATE) ? 1 : 0;
     wide_primal_kernel<Op, T><<<(unsigned)W.tiles, kWideBlock, 0, s>>>(A);
-    wide_adjoint_kernel<Op, T><<<(unsigned)W.tiles, kWideBlock, 0, s>>>(A);
+    if constexpr (kHasBlocks<Op>) {
+        if (!(flags & ADPAR_FULL_LIN_O)) {
+            wide_adjoint_kernel<Op, T, LinBlock<Op, T>><<<(unsigned)W.tiles, kWideBlock, 0, s>>>(A);
+            return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
+        }
+    }
+    wide_adjoint_kernel<Op, T, LinFull<Op, T>><<<(unsigned)W.tiles, kWideBlock, 0, s>>>(A);
     return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
 }
 
@@ -408,7 +516,7 @@ extern "C" int adpar_vjp_scan_wide(adpar_opdesc d, int64_t n, const void* a, con
     const int D = wide_width(d.op);
     if (D == 0 || d.width != D) return ADPAR_ERR_INVALID;
     if (d.dtype != ADPAR_F32 && d.dtype != ADPAR_F64) return ADPAR_ERR_INVALID;
-    if (flags & ~(uint32_t)ADPAR_ACCUMULATE) return ADPAR_ERR_UNSUPPORTED;
+    if (flags & ~(uint32_t)(ADPAR_ACCUMULATE | ADPAR_FULL_LIN_O)) return ADPAR_ERR_UNSUPPORTED;
     if (n > 0) {
         if (!a || !ybar || !abar) return ADPAR_ERR_INVALID;
         const void* ptrs[] = {a, ybar, abar, ys_out};

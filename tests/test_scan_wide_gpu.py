@@ -60,12 +60,15 @@ def inputs(op, n, dt, seed):
     return a.astype(dt), yb.astype(dt)
 
 
+@pytest.mark.parametrize("full", [False, True])
 @pytest.mark.parametrize("dt", [np.float32, np.float64])
 @pytest.mark.parametrize("op", ["linrec", "matrec2"])
 @pytest.mark.parametrize("n", SIZES)
-def test_scan_wide_matches_oracle(A, O, op, dt, n):
+def test_scan_wide_matches_oracle(A, O, op, dt, n, full):
+    """Both forms of the lin_o: blockwise C = I (x) N where the operator
+    allows it (the default) and the full d x d matrix (ADPAR_FULL_LIN_O)."""
     a, yb = inputs(op, n, dt, seed=n % 89 + 3)
-    ab, ys = A.adpar_vjp_scan_wide(op, dev(a), dev(yb), want_ys=True)
+    ab, ys = A.adpar_vjp_scan_wide(op, dev(a), dev(yb), want_ys=True, full_lin_o=full)
     torch.cuda.synchronize()
     rab, rys = O.scan_wide_vjp(op, a, yb)
     assert rel_l2(ab.cpu().numpy(), rab) <= tol(dt), rel_l2(ab.cpu().numpy(), rab)
@@ -103,11 +106,12 @@ def test_scan_wide_edges(A):
     assert L.adpar_vjp_scan_wide(d, 4, None, None, None, None, 0, None, 0, None) == 1
 
 
-def test_scan_wide_full_size_matrec(A, O):
+@pytest.mark.parametrize("full", [False, True])
+def test_scan_wide_full_size_matrec(A, O, full):
     """The benchmark's case, n = 2^24 2x2-matrix elements FP32, against the
-    oracle on every output."""
+    oracle on every output, with both forms of the lin_o."""
     n = 1 << 24
     a, yb = inputs("matrec2", n, np.float32, seed=synth.SEED_BASE + 7)
-    ab, ys = A.adpar_vjp_scan_wide("matrec2", dev(a), dev(yb), want_ys=True)
+    ab, ys = A.adpar_vjp_scan_wide("matrec2", dev(a), dev(yb), want_ys=True, full_lin_o=full)
     rab, rys = O.scan_wide_vjp("matrec2", a, yb)
     assert rel_l2(ab.cpu().numpy(), rab) <= 1e-4 and rel_l2(ys.cpu().numpy(), rys) <= 1e-4

@@ -76,3 +76,40 @@ def test_host_side_validation_without_gpu():
     for op in (A.OP_ADD, A.OP_MIN, A.OP_MAX):
         assert A.adpar_workspace_size(A.RULE_SCAN, op, A.F64, n) == A.adpar_workspace_size(
             A.RULE_SCAN | A.WS_MINIMAL, op, A.F64, n)
+
+
+def test_new_rules_validate_and_size_without_gpu():
+    """The general reduce_by_index rule and the wide-element scan refuse bad
+    arguments and a missing workspace before any CUDA call; their workspace
+    sizes are host arithmetic (two sort buffers plus one destination record
+    per radix pass; the full d x d lin_o's slots)."""
+    from paper_2202_10297_gb300 import adpar as A
+    L = A.lib()
+    V = None
+    # general reduce_by_index: LINREC needs width 2; negative sizes; too many elements; no workspace
+    d = A.OpDesc(A.OP_LINREC, A.F32, 1)
+    assert L.adpar_vjp_hist_general(d, 10, 4, V, V, V, A.I32, V, V, V, V, V, V, 0, V, 0, V) == 1
+    d = A.OpDesc(A.OP_ADD, A.F32, 1)
+    assert L.adpar_vjp_hist_general(d, 10, -1, V, V, V, A.I32, V, V, V, V, V, V, 0, V, 0, V) == 1
+    assert L.adpar_vjp_hist_general(d, 1 << 33, 4, V, V, V, A.I32, V, V, V, V, V, V, 0, V, 0, V) == 2
+    assert L.adpar_vjp_hist_general(d, 10, 4, 0x1000, V, 0x2000, A.I32, 0x3000, V, 0x4000, V, V, V, 0, V, 0,
+                                    V) == 4
+    assert L.adpar_vjp_hist_general(d, 10, 4, 0x1000, V, 0x2000, A.I32, 0x3000, V, 0x4000, V, V, V, 0x2, V, 0,
+                                    V) == 2  # unknown flag
+    n = 1 << 20
+    small = A.adpar_workspace_size(A.RULE_HIST_GENERAL, A.OP_ADD, A.F32, n, 256)
+    wide_m = A.adpar_workspace_size(A.RULE_HIST_GENERAL, A.OP_ADD, A.F32, n, 1 << 22)
+    pair = A.adpar_workspace_size(A.RULE_HIST_GENERAL, A.OP_LINREC, A.F64, n, 256)
+    assert small >= 2 * 8 * n + 4 * n          # keys and values twice, one pass of destinations
+    assert wide_m - small >= 2 * 4 * n         # three passes instead of one
+    assert pair >= 2 * (4 + 16) * n + 4 * n    # FP64 pairs travel with the keys
+    # wide-element scan: MATREC2 is width 6; MAX is not a wide operator; unknown flag; misaligned; no workspace
+    assert L.adpar_vjp_scan_wide(A.OpDesc(A.OP_MATREC2, A.F32, 2), 4, V, V, V, V, 0, V, 0, V) == 1
+    assert L.adpar_vjp_scan_wide(A.OpDesc(A.OP_MAX, A.F32, 1), 4, V, V, V, V, 0, V, 0, V) == 1
+    d = A.OpDesc(A.OP_MATREC2, A.F32, 6)
+    assert L.adpar_vjp_scan_wide(d, 4, 0x1000, 0x2000, 0x3000, V, 0x2, V, 0, V) == 2
+    assert L.adpar_vjp_scan_wide(d, 4, 0x1004, 0x2000, 0x3000, V, 0, V, 0, V) == 3
+    assert L.adpar_vjp_scan_wide(d, 4, 0x1000, 0x2000, 0x3000, V, A.FULL_LIN_O, V, 0, V) == 4
+    w6 = A.adpar_workspace_size(A.RULE_SCAN_WIDE, A.OP_MATREC2, A.F32, n, 0, width=6)
+    w2 = A.adpar_workspace_size(A.RULE_SCAN_WIDE, A.OP_LINREC, A.F32, n, 0, width=2)
+    assert w6 > w2 > 0

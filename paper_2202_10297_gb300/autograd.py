@@ -8,7 +8,9 @@ intermediate) and returns the adjoints the paper's rule gives.
     scan(op, a, b=None)           inclusive scan; LINREC returns (A, B); reverse
                                   and forward mode (torch.autograd.forward_ad)
     reduce(op, a)                 0-dim result
-    reduce_by_index(op, vals, inds, m)
+    reduce_by_index(op, vals, inds, m, b=None)
+                                  LINREC (b given) by the general rule
+    scan_wide(op, a)              scan over [n, d] elements ("linrec", "matrec2")
     scatter(xs, is_, vs)          out of place: xs is not modified
     map_acc(g, as_, is_, ws=None, width=1)
     kmeans_loss(X, C)             gradient with respect to C only
@@ -95,9 +97,58 @@ class _Hist(torch.autograd.Function):
         return None, out["valsbar"], None, None
 
 
-def reduce_by_index(op, vals, inds, m):
-    """reduce_by_index with op in {add, mul, min, max} (Sec. 5.1.2)."""
+class _HistGeneral(torch.autograd.Function):
+    """reduce_by_index by the general rule (radix sort by bin, segmented
+    scans); its forward is the same call with a zero cotangent, which
+    recomputes the bins."""
+
+    @staticmethod
+    def forward(ctx, op, a, b, inds, m):
+        z = torch.zeros(m, dtype=a.dtype, device=a.device)
+        _, _, hs_a, hs_b = A.adpar_vjp_hist_general(op, a, inds, m, z, b=b, hsbar_b=z, want_hs=True)
+        ctx.op, ctx.m = op, m
+        ctx.save_for_backward(a, b, inds)
+        return hs_a, hs_b
+
+    @staticmethod
+    def backward(ctx, ga, gb):
+        a, b, inds = ctx.saved_tensors
+        ga = torch.zeros(ctx.m, dtype=a.dtype, device=a.device) if ga is None else ga.contiguous()
+        gb = torch.zeros(ctx.m, dtype=a.dtype, device=a.device) if gb is None else gb.contiguous()
+        ab, bb, _, _ = A.adpar_vjp_hist_general(ctx.op, a, inds, ctx.m, ga, b=b, hsbar_b=gb)
+        return None, ab, bb, None, None
+
+
+def reduce_by_index(op, vals, inds, m, b=None):
+    """reduce_by_index (Sec. 5.1.2): op in {add, mul, min, max} by the special
+    rules; "linrec" (b given) by the general rule, returning the bins (A, B)."""
+    if op == "linrec":
+        return _HistGeneral.apply(op, _c(vals), _c(b), _c(inds), int(m))
     return _Hist.apply(op, _c(vals), _c(inds), int(m))
+
+
+class _ScanWide(torch.autograd.Function):
+    """Scan over [n, d] elements (the d x d lin_o rule); the forward is the
+    same call with a zero cotangent, which recomputes the scan."""
+
+    @staticmethod
+    def forward(ctx, op, a):
+        _, ys = A.adpar_vjp_scan_wide(op, a, torch.zeros_like(a), want_ys=True)
+        ctx.op = op
+        ctx.save_for_backward(a)
+        return ys
+
+    @staticmethod
+    def backward(ctx, g):
+        (a,) = ctx.saved_tensors
+        ab, _ = A.adpar_vjp_scan_wide(ctx.op, a, g.contiguous())
+        return None, ab
+
+
+def scan_wide(op, a):
+    """Inclusive scan over the rows of a [n, d] array: "linrec" (d = 2) or
+    "matrec2" (d = 6, the 2x2 matrix linear recurrence)."""
+    return _ScanWide.apply(op, _c(a))
 
 
 class _Scatter(torch.autograd.Function):

@@ -197,3 +197,34 @@ def test_primal_operators(oracle):
     ref[is2] = vs
     np.testing.assert_array_equal(ys.cpu().numpy(), ref)
     np.testing.assert_array_equal(saved.cpu().numpy(), xs0[is2])
+
+
+def test_gradcheck_reduce_by_index_linrec_general_rule():
+    """torch's gradcheck of the general reduce_by_index rule (LINREC bins,
+    out-of-range indices included) in FP64."""
+    from paper_2202_10297_gb300 import autograd as AG
+    g = torch.Generator().manual_seed(7)
+    n, m = 300, 7
+    a = (0.9 + 0.2 * torch.rand(n, generator=g, dtype=torch.float64)).cuda().requires_grad_()
+    b = torch.randn(n, generator=g, dtype=torch.float64).cuda().requires_grad_()
+    inds = torch.randint(-1, m + 1, (n,), generator=g).to(torch.int32).cuda()
+    assert torch.autograd.gradcheck(lambda x, y: AG.reduce_by_index("linrec", x, inds, m, b=y), (a, b),
+                                    eps=1e-6, atol=1e-7, rtol=1e-6)
+
+
+@pytest.mark.parametrize("op", ["linrec", "matrec2"])
+def test_gradcheck_scan_wide(op):
+    """torch's gradcheck of the wide-element scan (block and full lin_o give
+    the same numbers) in FP64."""
+    from paper_2202_10297_gb300 import autograd as AG
+    g = torch.Generator().manual_seed(8)
+    n = 700
+    if op == "linrec":
+        a = torch.stack([0.9 + 0.1 * torch.rand(n, generator=g, dtype=torch.float64),
+                         torch.randn(n, generator=g, dtype=torch.float64)], 1)
+    else:
+        M = torch.eye(2, dtype=torch.float64).reshape(1, 4) * 0.95 + 0.03 * torch.randn(n, 4, generator=g,
+                                                                                      dtype=torch.float64)
+        a = torch.cat([M, torch.randn(n, 2, generator=g, dtype=torch.float64)], 1)
+    a = a.cuda().requires_grad_()
+    assert torch.autograd.gradcheck(lambda x: AG.scan_wide(op, x), (a,), eps=1e-6, atol=1e-7, rtol=1e-6)

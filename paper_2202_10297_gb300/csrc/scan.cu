@@ -618,11 +618,11 @@ int run_scan(int64_t n, const void* a, const void* b, const void* ya, const void
             scan_minmax_fused_kernel<Op, T, false><<<fgrid, kScanBlock, 0, stream>>>(A, rec_list, n_rec, lead, last);
         }
         scan_minmax_fixup_kernel<T><<<1, 1024, 0, stream>>>(A.tiles, lead, last, static_cast<T*>(A.abar));
-        return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
+    } else {
+        if (need_primal) scan_primal_kernel<Op, T><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
+        if (ys_a) scan_adjoint_kernel<Op, T, true><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
+        else scan_adjoint_kernel<Op, T, false><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
     }
-    if (need_primal) scan_primal_kernel<Op, T><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
-    if (ys_a) scan_adjoint_kernel<Op, T, true><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
-    else scan_adjoint_kernel<Op, T, false><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
     return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
 }
 

@@ -805,3 +805,36 @@ int oracle_scan_wide_vjp(int op, int64_t n, int d, const double *a, const double
     free(rs); free(rsb);
     return 0;
 }
+
+/* ---------------------------------------------------------------------
+ * Hessian diagonal of the k-means cost in C (Sec. 7.3, the second-order
+ * information the paper obtains by nesting forward mode over the VJP):
+ * with every point's argmin held fixed (the cost is piecewise quadratic in
+ * C and the argmin changes only on measure-zero ties),
+ *   d^2/dc_kj^2 ybar sum_{i: argmin_i = k} (x_ij - c_kj)^2 = 2 ybar |{i: argmin_i = k}|.
+ * The argmin is the one oracle_kmeans takes (FP64, lowest k on ties).
+ * H is [k*d], overwritten.
+ * ------------------------------------------------------------------- */
+int oracle_kmeans_hessdiag(int64_t N, int d, int k, const double *X, const double *C,
+                           double ybar, double *H)
+{
+    int64_t *cnt = (int64_t *)calloc((size_t)(k > 0 ? k : 1), sizeof(int64_t));
+    if (!cnt) return 2;
+    for (int64_t i = 0; i < N; ++i) {
+        double best = INFINITY;
+        int64_t arg = -1;
+        for (int c = 0; c < k; ++c) {
+            double s = 0.0;
+            for (int j = 0; j < d; ++j) {
+                double diff = X[i * d + j] - C[(int64_t)c * d + j];
+                s += diff * diff;
+            }
+            if (s < best) { best = s; arg = c; }
+        }
+        if (arg >= 0) ++cnt[arg];
+    }
+    for (int c = 0; c < k; ++c)
+        for (int j = 0; j < d; ++j) H[(int64_t)c * d + j] = 2.0 * ybar * (double)cnt[c];
+    free(cnt);
+    return 0;
+}

@@ -50,10 +50,11 @@ def lib():
         L.oracle_hist_general_vjp.argtypes = [C.c_int, i64, i64, _D, _D, _I64, _D, _D, _D, _D,
                                               _D, _D]
         L.oracle_scan_wide_vjp.argtypes = [C.c_int, i64, C.c_int, _D, _D, _D, _D]
+        L.oracle_kmeans_hessdiag.argtypes = [i64, C.c_int, C.c_int, _D, _D, dbl, _D]
         for f in ("oracle_reduce_vjp", "oracle_prod_reduce_vjp", "oracle_scan_vjp",
                   "oracle_hist_vjp", "oracle_hist_prod_vjp", "oracle_scatter_vjp",
                   "oracle_map_acc_vjp", "oracle_kmeans", "oracle_reduce_general_vjp", "oracle_scan_jvp",
-                  "oracle_hist_general_vjp", "oracle_scan_wide_vjp"):
+                  "oracle_hist_general_vjp", "oracle_scan_wide_vjp", "oracle_kmeans_hessdiag"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -269,6 +270,18 @@ def map_acc_vjp(g, as_, is_, xsbar, ws=None, width=1, asbar=None, wsbar=None):
     _check(lib().oracle_map_acc_vjp(GFUNS[g], nj, na, width, _p(a), _p(ix, _I64),
                                     _p(w), _p(xb), _p(ab), _p(wb)), "map_acc_vjp")
     return ab, wb
+
+
+def kmeans_hessdiag(X, Cm, ybar=1.0):
+    """Hessian diagonal of the k-means cost in C with the argmins held fixed
+    (Sec. 7.3): 2 ybar times each centroid's count, [k, d]."""
+    X = _f64(X)
+    Cm = _f64(Cm)
+    N, d = X.shape
+    k = Cm.shape[0]
+    H = np.empty((k, d))
+    _check(lib().oracle_kmeans_hessdiag(N, d, k, _p(X), _p(Cm), float(ybar), _p(H)), "kmeans_hessdiag")
+    return H
 
 
 def kmeans(X, Cm, ybar=1.0):

@@ -57,6 +57,8 @@ MUTANTS = {
                               "Jl->v[2 * j + k][2 * m + k] = x[2 * m + j];"),
     "wide_jright_wrong_column": ("Jr->v[4 + j][2 * j + m] = prev[4 + m];", "Jr->v[4 + j][2 * m + j] = prev[4 + m];"),
     "wide_linrec_jright_transposed": ("{ { prev[0], 0.0 }, { prev[1], 1.0 } }", "{ { prev[0], prev[1] }, { 0.0, 1.0 } }"),
+    "kmeans_hessdiag_factor": ("H[(int64_t)c * d + j] = 2.0 * ybar * (double)cnt[c];",
+                               "H[(int64_t)c * d + j] = ybar * (double)cnt[c];"),
     "wide_first_element_dropped": ("for (int c = 0; c < d; ++c) abar[c] += rsb[c];",
                                    "for (int c = 0; c < d; ++c) abar[c] += 0.0 * rsb[c];"),
 }

@@ -804,3 +804,31 @@ def test_kmeans_closed_form_and_fd(oracle):
         Cn[k, j] -= h
         fd = 1.5 * (oracle.kmeans(X, Cp)[0] - oracle.kmeans(X, Cn)[0]) / (2 * h)
         assert abs(fd - cb[k, j]) < 1e-5 * (1 + abs(fd))
+
+
+def test_kmeans_hessdiag_is_derivative_of_gradient(oracle):
+    """The Hessian diagonal in C equals central differences of the oracle's
+    own gradient (Cbar) along each coordinate of C: with the steps far from
+    any argmin tie the gradient is affine in C, so the differences are exact
+    up to rounding.  Also the closed form 2 ybar cnt_k against argmin counts."""
+    g = synth.rng(61)
+    N, d, k = 400, 4, 5
+    X = g.normal(size=(N, d))
+    Cm = g.normal(size=(k, d)) * 1.5
+    H = oracle.kmeans_hessdiag(X, Cm, ybar=0.7)
+    _, arg, mind, _ = oracle.kmeans(X, Cm)
+    # the step must not move any point across a tie
+    dist = ((X[:, None, :] - Cm[None, :, :]) ** 2).sum(-1)
+    srt = np.sort(dist, axis=1)
+    step = 1e-4
+    assert (srt[:, 1] - srt[:, 0]).min() > 10 * step * (np.abs(X).max() + np.abs(Cm).max())
+    for c in range(k):
+        for j in range(d):
+            e = np.zeros_like(Cm)
+            e[c, j] = step
+            gp = oracle.kmeans(X, Cm + e, ybar=0.7)[3]
+            gm = oracle.kmeans(X, Cm - e, ybar=0.7)[3]
+            fd = (gp[c, j] - gm[c, j]) / (2 * step)
+            assert abs(fd - H[c, j]) <= 1e-6 * (1 + abs(fd))
+    cnt = np.bincount(arg, minlength=k)
+    np.testing.assert_array_equal(H, 2 * 0.7 * cnt[:, None] * np.ones((1, d)))

@@ -824,6 +824,12 @@ def row_kmeans(args):
     yb = torch.ones(1, device="cuda")
     t_vjp = _cuda_ms(lambda: A.adpar_kmeans_vjp(Xt, Ct, ybar=yb, Cbar=cb, work=wk), 20, 5)
     t_fwd = _cuda_ms(lambda: A.adpar_kmeans_vjp(Xt, Ct, want_grad=False, work=wk), 20, 5)
+    hd = torch.empty_like(Ct)
+
+    def grad_and_hessdiag():
+        A.adpar_kmeans_vjp(Xt, Ct, ybar=yb, Cbar=cb, work=wk)
+        A.adpar_kmeans_hessdiag(k, yb, wk, Hdiag=hd)
+    t_gh = _cuda_ms(grad_and_hessdiag, 20, 5)  # the paper's "Jacobian + Hessian diagonal" measurement
     flops = 2.0 * N * k * d
     bf16 = 1933.0
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -834,6 +840,7 @@ def row_kmeans(args):
     hbm, _ = measured_peaks()
     orate = _oracle_rate(lambda: O.kmeans(X[:2048], Cm, 1.0), 2048, 2.0)
     return _line("kmeans", metric="k-means VJP time", N=N, d=d, k=k, vjp_ms=t_vjp, forward_ms=t_fwd,
+                 grad_and_hessdiag_ms=t_gh,
                  vjp_primal_ratio=t_vjp / t_fwd, points_per_s=N / t_vjp * 1e3,
                  roofline={"bound": "tensor", "achieved": flops / t_vjp / 1e9, "peak": tf32_peak, "unit": "TFLOP/s",
                            "frac": flops / t_vjp / 1e9 / tf32_peak,

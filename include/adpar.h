@@ -448,6 +448,20 @@ int adpar_kmeans_vjp(int64_t N, int d, int k, const float *X, const float *C, co
                      float *loss_out, int32_t *argmin_out, float *Cbar, uint32_t flags, void *work,
                      size_t work_bytes, void *stream);
 
+/* Hessian diagonal of the same cost in C, the second-order information of
+ * Sec. 7.3 (the paper nests forward mode over this VJP): with every point's
+ * argmin held fixed (the cost is piecewise quadratic in C),
+ *   Hdiag[k][j] = d^2 loss / dc_kj^2 = 2 ybar cnt_k,
+ * cnt_k the number of points whose argmin is k.  It reads the counts that
+ * the preceding adpar_kmeans_vjp call (Cbar requested) left in its
+ * workspace: call it on the same stream with the same workspace, before
+ * the workspace is reused.
+ * Arguments: k (as for adpar_kmeans_vjp); ybar device FP32 scalar; work,
+ * work_bytes that call's workspace; Hdiag [k*32] FP32 output.
+ * Flags: ADPAR_ACCUMULATE (Hdiag += ...). */
+int adpar_kmeans_hessdiag(int k, const float *ybar, const void *work, size_t work_bytes, float *Hdiag,
+                          uint32_t flags, void *stream);
+
 /* ------------------------------------------------------------------ */
 /* batched VJPs: many instances in one persistent launch               */
 /* ------------------------------------------------------------------ */

@@ -79,6 +79,8 @@ def lib():
         L.adpar_vjp_scan_vec.argtypes = [OpDesc, C.c_int64, C.c_int64] + [_VP] * 6 + [C.c_uint32, _VP, C.c_size_t, _VP]
         L.adpar_jvp_scan.restype = C.c_int
         L.adpar_jvp_scan.argtypes = [OpDesc, C.c_int64] + [_VP] * 8 + [_VP, C.c_size_t, _VP]
+        L.adpar_kmeans_hessdiag.restype = C.c_int
+        L.adpar_kmeans_hessdiag.argtypes = [C.c_int, _VP, _VP, C.c_size_t, _VP, C.c_uint32, _VP]
         L.adpar_vjp_scan_wide.restype = C.c_int
         L.adpar_vjp_scan_wide.argtypes = [OpDesc, C.c_int64] + [_VP] * 4 + [C.c_uint32, _VP, C.c_size_t, _VP]
         L.adpar_vjp_hist_general.restype = C.c_int
@@ -536,6 +538,19 @@ def adpar_vjp_map_acc(g, as_, is_, xsbar, ws=None, width=1, asbar=None, wsbar=No
                                  _stream(stream))
     _check("adpar_vjp_map_acc", st)
     return asbar, wsbar
+
+
+def adpar_kmeans_hessdiag(k, ybar, work, Hdiag=None, accumulate=False, stream=None):
+    """Hessian diagonal [k, 32] of the k-means cost in C (C: adpar_kmeans_hessdiag), from the
+    counts that the preceding adpar_kmeans_vjp call (gradient requested) left in ``work``."""
+    dev = work.device
+    yb = _scalar_dev(1.0 if ybar is None else ybar, torch.empty(0, device=dev))
+    if Hdiag is None:
+        Hdiag = (torch.zeros if accumulate else torch.empty)(k, 32, dtype=torch.float32, device=dev)
+    st = lib().adpar_kmeans_hessdiag(int(k), _ptr(yb), _ptr(work), work.numel(), _ptr(Hdiag),
+                                     ACCUMULATE if accumulate else 0, _stream(stream))
+    _check("adpar_kmeans_hessdiag", st)
+    return Hdiag
 
 
 def adpar_kmeans_vjp(X, C, ybar=None, want_grad=True, want_argmin=False, Cbar=None, accumulate=False,

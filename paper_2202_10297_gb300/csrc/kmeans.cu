@@ -510,6 +510,15 @@ bool make_map(CUtensorMap* m, const float* ptr, int64_t rows, uint32_t box_rows)
 constexpr int kMaxDev = 64;
 bool km_configured[kMaxDev] = {};
 
+// Hessian diagonal in C from the counts a gradient call left in the
+// workspace: d^2 loss / dc_kj^2 = 2 ybar cnt_k (argmins held fixed).
+__global__ void km_hessdiag_kernel(int kd, const float* ybar, const float* gcnt, float* H, int accumulate) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= kd) return;
+    const float h = 2.f * *ybar * gcnt[q / KM_D];
+    H[q] = accumulate ? H[q] + h : h;
+}
+
 }  // namespace
 
 size_t kmeans_workspace_size(int64_t k) {
@@ -570,5 +579,22 @@ extern "C" int adpar_kmeans_vjp(int64_t N, int d, int k, const float* X, const f
     if (!make_map(&tmX, X, N, KM_TILE) || !make_map(&tmC, C, k, (uint32_t)k)) return ADPAR_ERR_CUDA;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(A.ntiles, sms));
     kmeans_kernel<<<grid, KM_THREADS, KM_SMEM, s>>>(tmX, tmC, A);
+    return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
+}
+
+extern "C" int adpar_kmeans_hessdiag(int k, const float* ybar, const void* work, size_t work_bytes, float* Hdiag,
+                                     uint32_t flags, void* stream) {
+    using namespace adpar;
+    if (k <= 0 || !ybar || !Hdiag) return ADPAR_ERR_INVALID;
+    if (k > KM_KMAX || k % 32 != 0) return ADPAR_ERR_UNSUPPORTED;
+    if (flags & ~(uint32_t)ADPAR_ACCUMULATE) return ADPAR_ERR_UNSUPPORTED;
+    const size_t need = kmeans_workspace_size(k);
+    if (!work || work_bytes < need || (reinterpret_cast<uintptr_t>(work) & 255u)) return ADPAR_ERR_WORKSPACE;
+    const char* w = static_cast<const char*>(work);
+    const float* gcnt =
+        reinterpret_cast<const float*>(w + sizeof(WsHeader) + 256 + round_up((size_t)k * KM_D * 4, 256));
+    const int kd = k * KM_D;
+    km_hessdiag_kernel<<<(kd + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        kd, ybar, gcnt, Hdiag, (flags & ADPAR_ACCUMULATE) ? 1 : 0);
     return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
 }

@@ -81,3 +81,18 @@ def test_kmeans_full_size(A, oracle):
     """N = 2^20, d = 32, k = 256 (the workload size): every argmin bit-exact."""
     X, Cm = synth.kmeans(1 << 20, 32, 256, seed=synth.SEED_BASE + 4)
     run_and_check(A, oracle, X, Cm, ybar=1.0)
+
+
+@pytest.mark.parametrize("N,k", [(1000, 32), (20000, 256), (50001, 128)])
+def test_kmeans_hessdiag(A, oracle, N, k):
+    """Hessian diagonal in C (argmins held fixed) from the gradient call's
+    counts: exactly 2 ybar cnt_k, as the FP64 oracle gives it (the certified
+    argmin matches the oracle's, and counts are exact integers in FP32)."""
+    X, Cm = synth.kmeans(N, 32, k, seed=N + 2 * k)
+    out = A.adpar_kmeans_vjp(dev(X), dev(Cm), ybar=1.5)
+    H = A.adpar_kmeans_hessdiag(k, 1.5, out["work"])
+    ref = oracle.kmeans_hessdiag(X, Cm, ybar=1.5)
+    np.testing.assert_array_equal(H.cpu().numpy(), ref.astype(np.float32))
+    base = torch.ones(k, 32, device="cuda")
+    H2 = A.adpar_kmeans_hessdiag(k, 1.5, out["work"], Hdiag=base, accumulate=True)
+    np.testing.assert_array_equal(H2.cpu().numpy(), ref.astype(np.float32) + 1)

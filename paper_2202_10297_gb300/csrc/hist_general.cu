@@ -13,8 +13,8 @@
 // per digit, a stable scatter that ranks each tile by digit, stages it in
 // shared memory in digit order and writes every digit's run contiguously).
 // The values travel with their keys, so every read of a and b is
-// coalesced, and each pass records where every element went.  Elements whose index is outside [0, m) leave in the first
-// pass.
+// coalesced, and each pass records where every element went.  Elements
+// whose index is outside [0, m) leave in the first pass.
 // Segmented scans: a segmented scan is a plain scan of (state, flag) pairs,
 //   forward  (x1,f1) + (x2,f2) = f2 ? (x2,f2) : (x1 (.) x2, f1)
 // with f = "a bin starts here", and its mirror image for the reverse scan

@@ -75,9 +75,9 @@ CALLS = [
     ("max_f32", "max", np.float32, LOG2_SCAN, 12, 8),
 ]
 # kernel launches of one call: init + (primal pass) + adjoint pass; min/max:
-# init + tile extrema + carry scan + record-free tiles + tiles with records +
-# the runs across tiles
-LAUNCHES = {"linrec": 3, "max": 6, "add": 2, "mul": 3, "min": 6}
+# init + tile extrema + group scan + record-free tiles + tiles with records +
+# runs by group + runs across groups
+LAUNCHES = {"linrec": 3, "max": 7, "add": 2, "mul": 3, "min": 7}
 
 # FP64 arithmetic of the linear-recurrence VJP per pair, counted on the
 # sequential definition (an FMA is 2 flops): forward A_i = a_i A_{i-1} (1)

@@ -64,9 +64,44 @@ __global__ void __launch_bounds__(kScanBlock) scan_primal_kernel(ScanArgs A) {
 // exclusive scan (one block) give every tile its carry, hence its records;
 // a reverse segmented sum inside the tile gives each record's part of that
 // sum, and the adjoint is written once.  The part of the last record's sum
-// that lies in later tiles is added by scan_minmax_fixup_kernel from
-// per-tile metadata: the sum of ybar before the tile's first record (lead)
-// and the tile's last record (last).
+// that lies in later tiles is added by scan_minmax_runs_kernel and
+// scan_minmax_fixup_kernel from per-tile data: the sum of ybar before the
+// tile's first record (lead) and the tile's last record (last).
+// Per-tile data of the min/max rule, in the scan workspace.  Tiles form
+// groups of kMmGroup; each small scan over the tiles runs as one block per
+// group plus a combine of the (few) group aggregates by its consumer.
+constexpr int kMmGroup = 1024;
+
+template <class P>
+struct MinMaxWs {
+    P* tmax;             // [tiles] the tile's extremum
+    P* carry;            // [tiles] exclusive within the group; record tiles: the whole carry
+    P* gagg;             // [groups] group extremum
+    uint32_t* rec_list;  // [tiles] the tiles holding a record
+    uint32_t* n_rec;     // their count (zeroed with the workspace header)
+    double* lead;        // [tiles] ybar of the tile before its first record
+    int64_t* last;       // [tiles] the tile's last record, -1 if none
+    double* xloc;        // [tiles] run sum from the tile to its group's end or the first record tile
+    uint32_t* floc;      // [tiles] a record tile lies in [tile, group end]
+    double* fx;          // [groups] the same for the group's first tile
+    uint32_t* ff;
+    int64_t tiles;
+    int groups;
+};
+
+// Extremum of the groups before g (warp 0 of the block; any order: the
+// extremum is exact)
+template <class Op>
+__device__ __forceinline__ typename Op::P mm_group_prefix(const typename Op::P* gagg, int g) {
+    using P = typename Op::P;
+    const int lane = threadIdx.x & 31;
+    P acc = Op::pid();
+    for (int h = lane; h < g; h += 32) acc = Op::pcomb(acc, gagg[h]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc = Op::pcomb(acc, shfl_down_s(acc, off));
+    return acc;  // lane 0
+}
+
 template <class T>
 struct RunSum {
     T x;         // ybar from the element to the end of its run
@@ -195,8 +230,7 @@ __global__ void __launch_bounds__(kScanBlock) scan_minmax_fused_kernel(ScanArgs 
 // (few registers, many blocks per SM); scan_minmax_fused_kernel skips these
 // tiles.
 template <class Op, class T, bool WYS>
-__global__ void __launch_bounds__(kScanBlock) scan_minmax_zero_kernel(ScanArgs A, const typename Op::P* tmax,
-                                                                      double* lead, int64_t* last) {
+__global__ void __launch_bounds__(kScanBlock) scan_minmax_zero_kernel(ScanArgs A, MinMaxWs<typename Op::P> M) {
     using Cfg = ScanCfg<Op, T>;
     using P = typename Op::P;
     constexpr int K = Cfg::K, E = Cfg::E, NW = kScanBlock / 32;
@@ -204,12 +238,22 @@ __global__ void __launch_bounds__(kScanBlock) scan_minmax_zero_kernel(ScanArgs A
     __shared__ uint32_t s_has;
     __shared__ double s_sum[NW];
     const int64_t t = blockIdx.x;
-    if (threadIdx.x == 0) {
-        const P pre = static_cast<const P*>(A.carry)[t];
-        s_pre = pre;
-        T on = T(0), dummy = T(0);
-        Op::vjp_right(pre, Op::out_a(tmax[t]), T(0), T(1), T(0), on, dummy);
-        s_has = (t == 0 || on != T(0)) ? 1u : 0u;
+    double* lead = M.lead;
+    int64_t* last = M.last;
+    if (threadIdx.x < 32) {
+        const P gp = mm_group_prefix<Op>(M.gagg, (int)(t / kMmGroup));
+        if (threadIdx.x == 0) {
+            const P pre = Op::pcomb(gp, M.carry[t]);  // the extremum before the tile
+            s_pre = pre;
+            T on = T(0), dummy = T(0);
+            Op::vjp_right(pre, Op::out_a(M.tmax[t]), T(0), T(1), T(0), on, dummy);
+            const bool has = t == 0 || on != T(0);
+            s_has = has ? 1u : 0u;
+            if (has) {  // scan_minmax_fused_kernel takes the tile, with its whole carry
+                M.carry[t] = pre;
+                M.rec_list[atomicAdd(M.n_rec, 1u)] = (uint32_t)t;
+            }
+        }
     }
     __syncthreads();
     if (s_has) return;
@@ -276,27 +320,16 @@ __global__ void __launch_bounds__(kScanBlock) scan_minmax_tile_kernel(ScanArgs A
     }
 }
 
-// Exclusive scan of the tile extrema in place (one block; the extremum is
-// exact in any order, so the block-level order does not matter).
+// Exclusive extremum of the tiles within each group (one block per group,
+// one tile per thread) and each group's extremum.
 template <class Op, class T>
-__global__ void __launch_bounds__(1024) scan_minmax_carry_kernel(int64_t tiles, const typename Op::P* tmax,
-                                                                 void* carry, uint32_t* rec_list, uint32_t* n_rec) {
+__global__ void __launch_bounds__(kMmGroup) scan_minmax_group_kernel(MinMaxWs<typename Op::P> M) {
     using P = typename Op::P;
-    constexpr int NT = 1024, B = 8;  // loads issued B at a time
-    __shared__ P s_w[NT / 32];
-    P* c = static_cast<P*>(carry);
-    const int64_t per = (tiles + NT - 1) / NT;
-    const int64_t t0 = threadIdx.x * per, t1 = t0 + per < tiles ? t0 + per : tiles;
-    P agg = Op::pid();
-    for (int64_t u0 = t0; u0 < t1; u0 += B) {
-        P v[B];
-#pragma unroll
-        for (int j = 0; j < B; ++j) v[j] = u0 + j < t1 ? tmax[u0 + j] : Op::pid();
-#pragma unroll
-        for (int j = 0; j < B; ++j) agg = Op::pcomb(agg, v[j]);
-    }
+    __shared__ P s_w[kMmGroup / 32];
+    const int64_t u = (int64_t)blockIdx.x * kMmGroup + threadIdx.x;
+    const P v = u < M.tiles ? M.tmax[u] : Op::pid();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    P inc = agg;
+    P inc = v;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
         const P o = shfl_up_s(inc, off);
@@ -311,6 +344,7 @@ __global__ void __launch_bounds__(1024) scan_minmax_carry_kernel(int64_t tiles, 
             const P o = shfl_up_s(wi, off);
             if (lane >= off) wi = Op::pcomb(o, wi);
         }
+        if (lane == 31) M.gagg[blockIdx.x] = wi;
         P ex = shfl_up_s(wi, 1);
         if (lane == 0) ex = Op::pid();
         __syncwarp();
@@ -319,73 +353,39 @@ __global__ void __launch_bounds__(1024) scan_minmax_carry_kernel(int64_t tiles, 
     __syncthreads();
     P ex = shfl_up_s(inc, 1);
     if (lane == 0) ex = Op::pid();
-    P run = Op::pcomb(s_w[warp], ex);
-    // carries, and the tiles holding a record (the same test as
-    // scan_minmax_zero_kernel's) listed for scan_minmax_fused_kernel
-    for (int64_t u0 = t0; u0 < t1; u0 += B) {
-        P v[B];
-#pragma unroll
-        for (int j = 0; j < B; ++j) v[j] = u0 + j < t1 ? tmax[u0 + j] : Op::pid();
-#pragma unroll
-        for (int j = 0; j < B; ++j) {
-            const int64_t u = u0 + j;
-            if (u >= t1) break;
-            c[u] = run;
-            T on = T(0), dummy = T(0);
-            Op::vjp_right(run, Op::out_a(v[j]), T(0), T(1), T(0), on, dummy);
-            if (u == 0 || on != T(0)) rec_list[atomicAdd(n_rec, 1u)] = (uint32_t)u;
-            run = Op::pcomb(run, v[j]);
-        }
-    }
+    if (u < M.tiles) M.carry[u] = Op::pcomb(s_w[warp], ex);
 }
 
-// Adds to each tile's last record the part of its run in later tiles:
-// R_t = lead_{t+1} + (tile t+1 has a record ? 0 : R_{t+1}), a reverse
-// segmented sum over the tiles in FP64 (one block; tiles are few).
-template <class T>
-__global__ void __launch_bounds__(1024) scan_minmax_fixup_kernel(int64_t tiles, const double* lead, const int64_t* last,
-                                                                T* abar) {
-    constexpr int NT = 1024;
-    __shared__ double s_x[NT / 32];
-    __shared__ uint32_t s_f[NT / 32];
-    const int64_t per = (tiles + NT - 1) / NT;
-    const int64_t t0 = threadIdx.x * per, t1 = t0 + per < tiles ? t0 + per : tiles;
-    // this thread's part as a run: (sum of leads up to its first record tile, saw one)
-    constexpr int B = 8;  // loads issued B at a time
+// The run across tiles, R_t = lead_{t+1} + (tile t+1 has a record ? 0 :
+// R_{t+1}), is a reverse segmented sum over the tiles.  Pass 1: within
+// each group (one block, one tile per thread, FP64), S(u) = lead_u +
+// (u has a record ? 0 : S(u+1)) up to the group's end, whether a record
+// tile lies in [u, group end], and the same for the group's first tile.
+template <class P>
+__global__ void __launch_bounds__(kMmGroup) scan_minmax_runs_kernel(MinMaxWs<P> M) {
+    __shared__ double s_x[kMmGroup / 32];
+    __shared__ uint32_t s_f[kMmGroup / 32];
+    const int64_t u = (int64_t)blockIdx.x * kMmGroup + threadIdx.x;
     double x = 0.0;
-    uint32_t f = 0;
-    for (int64_t u0 = t1 - 1; u0 >= t0; u0 -= B) {
-        double ld[B];
-        int64_t ls[B];
-#pragma unroll
-        for (int j = 0; j < B; ++j) {
-            ld[j] = u0 - j >= t0 ? lead[u0 - j] : 0.0;
-            ls[j] = u0 - j >= t0 ? last[u0 - j] : -1;
-        }
-#pragma unroll
-        for (int j = 0; j < B; ++j) {
-            if (u0 - j < t0) break;
-            const bool has = ls[j] >= 0;
-            x = has ? ld[j] : ld[j] + x;
-            f = has ? 1u : f;
-        }
+    uint32_t f = 0u;
+    if (u < M.tiles) {
+        x = M.lead[u];
+        f = M.last[u] >= 0 ? 1u : 0u;
     }
-    // reverse exclusive scan over the threads (later threads first)
+    // inclusive reverse scan: (x, f) over [u, group end], later lanes first
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double ix = x;
-    uint32_t iff = f;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-        const double ox = __shfl_down_sync(0xffffffffu, ix, off);
-        const uint32_t of = __shfl_down_sync(0xffffffffu, iff, off);
-        if (lane + off < 32 && !iff) {
-            ix += ox;
-            iff = of;
+        const double ox = __shfl_down_sync(0xffffffffu, x, off);
+        const uint32_t of = __shfl_down_sync(0xffffffffu, f, off);
+        if (lane + off < 32 && !f) {
+            x += ox;
+            f = of;
         }
     }
     if (lane == 0) {
-        s_x[warp] = ix;
-        s_f[warp] = iff;
+        s_x[warp] = x;
+        s_f[warp] = f;
     }
     __syncthreads();
     if (warp == 0) {
@@ -400,39 +400,69 @@ __global__ void __launch_bounds__(1024) scan_minmax_fixup_kernel(int64_t tiles, 
                 wf = of;
             }
         }
-        // exclusive: the warps after this one
-        const double ex = __shfl_down_sync(0xffffffffu, wx, 1);
+        if (lane == 0) {
+            M.fx[blockIdx.x] = wx;
+            M.ff[blockIdx.x] = wf;
+        }
+        const double ex = __shfl_down_sync(0xffffffffu, wx, 1);  // the warps after this one
         const uint32_t ef = __shfl_down_sync(0xffffffffu, wf, 1);
         __syncwarp();
         s_x[lane] = lane < 31 ? ex : 0.0;
         s_f[lane] = lane < 31 ? ef : 0u;
     }
     __syncthreads();
-    // after this thread: the later lanes of its warp, then the later warps
-    double ax = __shfl_down_sync(0xffffffffu, ix, 1);
-    uint32_t af = __shfl_down_sync(0xffffffffu, iff, 1);
-    if (lane == 31) {
-        ax = 0.0;
-        af = 0u;
+    if (!f) {
+        x += s_x[warp];
+        f = s_f[warp];
     }
-    if (!af) ax += s_x[warp];
-    // walk the thread's tiles right to left; ax is R of the tile before
-    for (int64_t u0 = t1 - 1; u0 >= t0; u0 -= B) {
-        double ld[B];
-        int64_t ls[B];
-#pragma unroll
-        for (int j = 0; j < B; ++j) {
-            ld[j] = u0 - j >= t0 ? lead[u0 - j] : 0.0;
-            ls[j] = u0 - j >= t0 ? last[u0 - j] : -1;
+    if (u < M.tiles) {
+        M.xloc[u] = x;
+        M.floc[u] = f;
+    }
+}
+
+// Pass 2: adds R_t to each tile's last record; R_t comes from tile t+1's
+// group-local value and, where its run leaves the group, the groups after.
+template <class P, class T>
+__global__ void __launch_bounds__(kMmGroup) scan_minmax_fixup_kernel(MinMaxWs<P> M, T* abar) {
+    __shared__ double s_after;  // S of the first tile after this group
+    const int g = blockIdx.x;
+    if (threadIdx.x < 32) {
+        // reverse combine of the groups after g: each lane folds a
+        // contiguous part, then the lanes combine right to left
+        const int lane = threadIdx.x;
+        const int cnt = M.groups - 1 - g;
+        const int per = (cnt + 31) / 32;
+        const int h0 = g + 1 + lane * per, h1 = min(h0 + per, M.groups);
+        double x = 0.0;
+        uint32_t f = 0u;
+        for (int h = h1 - 1; h >= h0; --h) {
+            const double hx = M.fx[h];
+            const uint32_t hf = M.ff[h];
+            x = hf ? hx : hx + x;
+            f = hf ? 1u : f;
         }
 #pragma unroll
-        for (int j = 0; j < B; ++j) {
-            if (u0 - j < t0) break;
-            const int64_t p = ls[j];
-            if (p >= 0) abar[p] += (T)ax;  // R_u: the leads after tile u up to the next record
-            ax = p >= 0 ? ld[j] : ld[j] + ax;
+        for (int off = 1; off < 32; off <<= 1) {
+            const double ox = __shfl_down_sync(0xffffffffu, x, off);
+            const uint32_t of = __shfl_down_sync(0xffffffffu, f, off);
+            if (lane + off < 32 && !f) {
+                x += ox;
+                f = of;
+            }
         }
+        if (lane == 0) s_after = x;
     }
+    __syncthreads();
+    const int64_t t = (int64_t)g * kMmGroup + threadIdx.x;
+    if (t >= M.tiles) return;
+    const int64_t p = M.last[t];
+    if (p < 0) return;
+    double r;
+    if (t + 1 >= M.tiles) r = 0.0;
+    else if ((t + 1) / kMmGroup == g) r = M.floc[t + 1] ? M.xloc[t + 1] : M.xloc[t + 1] + s_after;
+    else r = s_after;
+    abar[p] += (T)r;
 }
 
 // The factored path (FP64 operators with J_left = a_i): the return sweep's
@@ -486,6 +516,7 @@ __global__ void __launch_bounds__(kScanBlock) scan_forward_kernel(ScanArgs A) {
 struct ScanLayout {
     size_t off_carry, off_slots, off_pA, off_pI, off_rA, off_rI, slot_words, total_min;
     size_t off_loc_a, off_loc_b, off_thc, total;
+    size_t off_xloc, off_floc, off_gagg, off_fx, off_ff;  // min/max rule only
 };
 
 // The FP64 operators with J_left = a_i take the factored forward result
@@ -516,6 +547,16 @@ ScanLayout scan_layout(int64_t n) {
     s.off_rA = o; o += wr * 8;
     s.off_rI = o; o += wr * 8;
     s.slot_words = (o - s.off_slots) / 8;
+    s.off_xloc = s.off_floc = s.off_gagg = s.off_fx = s.off_ff = 0;
+    if constexpr (kMinMax<Op, T>) {
+        const size_t groups = (tiles + kMmGroup - 1) / kMmGroup;
+        o = round_up(o, 256);
+        s.off_xloc = o; o = round_up(o + tiles * 8, 256);
+        s.off_floc = o; o = round_up(o + tiles * 4, 256);
+        s.off_gagg = o; o = round_up(o + groups * sizeof(P), 256);
+        s.off_fx = o; o = round_up(o + groups * 8, 256);
+        s.off_ff = o; o += groups * 4;
+    }
     s.total_min = round_up(o, 256);
     o = s.total_min;
     s.off_loc_a = s.off_loc_b = s.off_thc = 0;
@@ -596,28 +637,40 @@ int run_scan(int64_t n, const void* a, const void* b, const void* ya, const void
         }
     }
     if constexpr (kMinMax<Op, T>) {
-        // the return sweep fused into the forward pass; the per-tile
-        // metadata take the return sweep's (unused) slot regions
-        double* lead = reinterpret_cast<double*>(A.lbR_agg);
-        int64_t* last = reinterpret_cast<int64_t*>(A.lbR_incl);
-        static_assert(lb_words<Lin<T, 1, true>>() * 4 >= 8, "8 bytes of metadata per tile");
+        // tile extrema, their scan by groups, record-free tiles, tiles with
+        // records, and the runs across tiles; the per-tile data take the
+        // look-back slots (unused on this path) and the rule's own region
         using P = typename Op::P;
-        P* tmax = reinterpret_cast<P*>(A.lbP_agg);  // the primal slots are unused on this path
-        static_assert(lb_words<P>() * 4 >= sizeof(P), "one extremum per tile");
-        scan_minmax_tile_kernel<Op, T><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A, tmax);
-        uint32_t* rec_list = reinterpret_cast<uint32_t*>(A.lbP_incl);  // [tiles], unused slots too
-        uint32_t* n_rec = &A.hdr->done[1];                               // zeroed by the init kernel
-        static_assert(lb_words<P>() * 4 >= sizeof(uint32_t), "one list entry per tile");
-        scan_minmax_carry_kernel<Op, T><<<1, 1024, 0, stream>>>(A.tiles, tmax, A.carry, rec_list, n_rec);
+        static_assert(lb_words<P>() * 4 >= sizeof(P) && lb_words<P>() * 4 >= sizeof(uint32_t), "slot size");
+        static_assert(lb_words<Lin<T, 1, true>>() * 4 >= 8, "8 bytes of metadata per tile");
+        MinMaxWs<P> M;
+        M.tmax = reinterpret_cast<P*>(A.lbP_agg);
+        M.carry = static_cast<P*>(A.carry);
+        M.gagg = reinterpret_cast<P*>(w + L.off_gagg);
+        M.rec_list = reinterpret_cast<uint32_t*>(A.lbP_incl);
+        M.n_rec = &A.hdr->done[1];  // zeroed by the init kernel
+        M.lead = reinterpret_cast<double*>(A.lbR_agg);
+        M.last = reinterpret_cast<int64_t*>(A.lbR_incl);
+        M.xloc = reinterpret_cast<double*>(w + L.off_xloc);
+        M.floc = reinterpret_cast<uint32_t*>(w + L.off_floc);
+        M.fx = reinterpret_cast<double*>(w + L.off_fx);
+        M.ff = reinterpret_cast<uint32_t*>(w + L.off_ff);
+        M.tiles = A.tiles;
+        M.groups = (int)((A.tiles + kMmGroup - 1) / kMmGroup);
         const unsigned fgrid = (unsigned)std::min<int64_t>(A.tiles, (int64_t)fused_grid());
+        scan_minmax_tile_kernel<Op, T><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A, M.tmax);
+        scan_minmax_group_kernel<Op, T><<<M.groups, kMmGroup, 0, stream>>>(M);
         if (ys_a) {
-            scan_minmax_zero_kernel<Op, T, true><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A, tmax, lead, last);
-            scan_minmax_fused_kernel<Op, T, true><<<fgrid, kScanBlock, 0, stream>>>(A, rec_list, n_rec, lead, last);
+            scan_minmax_zero_kernel<Op, T, true><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A, M);
+            scan_minmax_fused_kernel<Op, T, true><<<fgrid, kScanBlock, 0, stream>>>(A, M.rec_list, M.n_rec, M.lead,
+                                                                                     M.last);
         } else {
-            scan_minmax_zero_kernel<Op, T, false><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A, tmax, lead, last);
-            scan_minmax_fused_kernel<Op, T, false><<<fgrid, kScanBlock, 0, stream>>>(A, rec_list, n_rec, lead, last);
+            scan_minmax_zero_kernel<Op, T, false><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A, M);
+            scan_minmax_fused_kernel<Op, T, false><<<fgrid, kScanBlock, 0, stream>>>(A, M.rec_list, M.n_rec, M.lead,
+                                                                                      M.last);
         }
-        scan_minmax_fixup_kernel<T><<<1, 1024, 0, stream>>>(A.tiles, lead, last, static_cast<T*>(A.abar));
+        scan_minmax_runs_kernel<P><<<M.groups, kMmGroup, 0, stream>>>(M);
+        scan_minmax_fixup_kernel<P, T><<<M.groups, kMmGroup, 0, stream>>>(M, static_cast<T*>(A.abar));
     } else {
         if (need_primal) scan_primal_kernel<Op, T><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
         if (ys_a) scan_adjoint_kernel<Op, T, true><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);

@@ -113,3 +113,41 @@ def test_new_rules_validate_and_size_without_gpu():
     w6 = A.adpar_workspace_size(A.RULE_SCAN_WIDE, A.OP_MATREC2, A.F32, n, 0, width=6)
     w2 = A.adpar_workspace_size(A.RULE_SCAN_WIDE, A.OP_LINREC, A.F32, n, 0, width=2)
     assert w6 > w2 > 0
+
+
+def test_older_entry_points_validate_without_gpu(lib):
+    """reduce, reduce_by_index, scatter, map-accumulator and k-means refuse bad
+    arguments before any CUDA call (C status codes, no GPU needed)."""
+    from paper_2202_10297_gb300 import adpar as A
+    C = ctypes
+    VP, I64 = C.c_void_p, C.c_int64
+    lib.adpar_vjp_reduce.argtypes = [A.OpDesc, I64] + [VP] * 7 + [C.c_uint32, VP, C.c_size_t, VP]
+    lib.adpar_vjp_reduce.restype = C.c_int
+    V = None
+    # LINREC has no special reduce rule; width must be 1; log domain is for * only
+    assert lib.adpar_vjp_reduce(A.OpDesc(A.OP_LINREC, A.F32, 2), 8, V, V, V, V, V, V, V, 0, V, 0, V) == 1
+    assert lib.adpar_vjp_reduce(A.OpDesc(A.OP_ADD, A.F32, 2), 8, V, V, V, V, V, V, V, 0, V, 0, V) == 1
+    assert lib.adpar_vjp_reduce(A.OpDesc(A.OP_ADD, A.F32, 1), 8, V, 0x1000, 0x2000, V, V, V, V, A.PROD_LOGDOMAIN,
+                                V, 0, V) == 2
+    assert lib.adpar_vjp_reduce(A.OpDesc(A.OP_MAX, A.F32, 1), 8, 0x1004, 0x1000, 0x2000, V, V, V, V, 0,
+                                V, 0, V) == 3
+    lib.adpar_vjp_scatter.argtypes = [C.c_int, I64, I64, VP, C.c_int, VP, VP, VP, VP, C.c_uint32, VP]
+    lib.adpar_vjp_scatter.restype = C.c_int
+    assert lib.adpar_vjp_scatter(7, 10, 4, V, A.I32, V, V, V, V, 0, V) == 1          # bad dtype
+    assert lib.adpar_vjp_scatter(A.F32, 10, 4, V, 9, V, V, V, V, 0, V) == 1          # bad itype
+    assert lib.adpar_vjp_scatter(A.F32, -1, 4, V, A.I32, V, V, V, V, 0, V) == 1      # negative size
+    lib.adpar_vjp_map_acc.argtypes = [C.c_int, C.c_int, I64, I64, C.c_int, VP, VP, C.c_int, VP, VP, VP, VP,
+                                      C.c_uint32, VP, C.c_size_t, VP]
+    lib.adpar_vjp_map_acc.restype = C.c_int
+    assert lib.adpar_vjp_map_acc(9, A.F32, 10, 4, 1, V, V, A.I32, V, V, V, V, 0, V, 0, V) == 1   # bad g
+    assert lib.adpar_vjp_map_acc(A.G_GATHER, A.F32, 10, 4, 3, V, V, A.I32, V, V, V, V, 0, V, 0, V) == 1  # width
+    lib.adpar_kmeans_vjp.argtypes = [I64, C.c_int, C.c_int] + [VP] * 6 + [C.c_uint32, VP, C.c_size_t, VP]
+    lib.adpar_kmeans_vjp.restype = C.c_int
+    assert lib.adpar_kmeans_vjp(100, 32, 48, V, V, V, V, V, V, 0, V, 0, V) == 2   # k not a multiple of 32
+    assert lib.adpar_kmeans_vjp(100, 16, 64, V, V, V, V, V, V, 0, V, 0, V) == 2   # d != 32
+    assert lib.adpar_kmeans_vjp(100, 32, 64, V, V, V, V, V, V, 0, V, 0, V) == 1   # X, C missing
+    lib.adpar_kmeans_hessdiag.argtypes = [C.c_int, VP, VP, C.c_size_t, VP, C.c_uint32, VP]
+    lib.adpar_kmeans_hessdiag.restype = C.c_int
+    assert lib.adpar_kmeans_hessdiag(64, V, V, 0, V, 0, V) == 1                    # ybar, Hdiag missing
+    assert lib.adpar_kmeans_hessdiag(48, 0x1000, V, 0, 0x2000, 0, V) == 2          # k not a multiple of 32
+    assert lib.adpar_kmeans_hessdiag(64, 0x1000, V, 0, 0x2000, 0, V) == 4          # workspace missing

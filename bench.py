@@ -89,8 +89,7 @@ LINREC_FLOP_PER_PAIR = 10
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes per call of the FP64 linear-recurrence VJP (init + primal pass +
 # adjoint pass), from the ncu capture at n = 2^24 scaled by 4 to 2^26
-# (traffic grows in proportion to n); the capture is summarised in
-# profiles/scan_linrec_f64_n2p24.md
+# (traffic grows in proportion to n)
 LINREC_F64_TRAFFIC_PER_CALL = 4 * 1798297088
 
 WORKLOAD = ("scan VJPs: linear-recurrence n=2^26 pairs FP32 and FP64 (a~U[0.9,1], b,ybar~N(0,1)); "
@@ -811,7 +810,7 @@ def row_scatter(args):
 
 
 def row_kmeans(args):
-    """k-means loss and C-gradient (Sec. 7.3), N = 2^20, d = 32, k = 256."""
+    """k-means loss and C-gradient (Sec. 7.4), N = 2^20, d = 32, k = 256."""
     import torch
     from oracle import oracle as O
     from paper_2202_10297_gb300 import adpar as A

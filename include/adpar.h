@@ -255,7 +255,7 @@ int adpar_vjp_scan(adpar_opdesc desc, int64_t n, const void *a, const void *b,
 int adpar_vjp_scan_wide(adpar_opdesc desc, int64_t n, const void *a, const void *ybar, void *abar,
                         void *ys_out, uint32_t flags, void *work, size_t work_bytes, void *stream);
 
-/* Reduce by the GENERAL rule of Sec. 5.1.1, for any operator of this
+/* Reduce by the GENERAL rule of Sec. 5.1, for any operator of this
  * library (ADD, MUL, MIN, MAX, and LINREC, which has no special rule):
  *   y = a_0 (.) a_1 (.) ... (.) a_{n-1},
  *   a_bar_i (+)= d(l_i (.) a_i (.) r_i)/d a_i ^T y_bar,
@@ -264,7 +264,10 @@ int adpar_vjp_scan_wide(adpar_opdesc desc, int64_t n, const void *a, const void 
  * ends).  For LINREC that is (abar, bbar)_i = (rA (lA ybar_A + lB ybar_B),
  * rA ybar_B); for MUL the product of all other elements (no division, so
  * zeros are safe; values may underflow where adpar_vjp_reduce's scaled
- * rule would not); for MIN/MAX the lowest index of the extremum.  Two
+ * rule would not: with factors of magnitude about 1/2..3/2 an FP32 product
+ * underflows beyond a few thousand factors and an FP64 one beyond about
+ * 16000, and every adjoint then rounds to 0; use adpar_vjp_reduce for long
+ * products); for MIN/MAX the lowest index of the extremum.  Two
  * single-pass kernels: the forward carries, then the reverse pass.
  * Arguments (as for adpar_vjp_scan; b, ybar_b, bbar, y_out_b for LINREC):
  *   n            number of elements (0 allowed: y = neutral element).
@@ -424,7 +427,7 @@ int adpar_vjp_map_acc(int gfun, int dtype, int64_t nj, int64_t na, int width, co
                       void *wsbar, uint32_t flags, void *work, size_t work_bytes, void *stream);
 
 /* ------------------------------------------------------------------ */
-/* k-means cost and its gradient (Sec. 7.3)                            */
+/* k-means cost and its gradient (Sec. 7.4)                            */
 /* ------------------------------------------------------------------ */
 /* loss = sum_i min_k ||x_i - c_k||^2 over N points x_i (rows of X, d = 32
  * FP32) and k centroids (rows of C), and its VJP in C:
@@ -449,7 +452,7 @@ int adpar_kmeans_vjp(int64_t N, int d, int k, const float *X, const float *C, co
                      size_t work_bytes, void *stream);
 
 /* Hessian diagonal of the same cost in C, the second-order information of
- * Sec. 7.3 (the paper nests forward mode over this VJP): with every point's
+ * Sec. 7.4 (the paper nests forward mode over this VJP): with every point's
  * argmin held fixed (the cost is piecewise quadratic in C),
  *   Hdiag[k][j] = d^2 loss / dc_kj^2 = 2 ybar cnt_k,
  * cnt_k the number of points whose argmin is k.  It reads the counts that
@@ -561,21 +564,39 @@ int adpar_map_acc(int gfun, int dtype, int64_t nj, int64_t na, int width, const 
  *   - Sizes whose scan workspace exceeds the array are refused with
  *     ADPAR_ERR_TOO_LARGE before anything is enqueued (up to 2^28 FP32
  *     elements of a width-1 operator and 2^26 FP64 LINREC pairs fit).
- *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress, with that device current) and caches it; make
- *     that first call before any stream capture on the device.
+ *   - Every call looks up the array's device address on the current device
+ *     (cudaGetSymbolAddress).  The first lookup on a device also loads the
+ *     library's module there; make that first call before any stream
+ *     capture on the device.
  *   - All calls on one device share the array.  Each call clears the parts
  *     that must start at zero, but two calls that overlap on the GPU (on
  *     different streams, or from different threads) race on it and give
  *     wrong results: serialise them.
- *   - The device status word of adpar_workspace_status lives in the same
- *     array and is not exposed here. */
+ *   - A device-side wait that gives up records ADPAR_ERR_TIMEOUT in the
+ *     array's status word while the call itself has returned ADPAR_OK; read
+ *     it with adpar_noalloc_status after the call.  The next call clears it. */
 int adpar_vjp_scan_noalloc(adpar_opdesc desc, int64_t n, const void *a, const void *b,
                            const void *ybar_a, const void *ybar_b, void *abar, void *bbar,
                            void *ys_a, void *ys_b, uint32_t flags, void *stream);
 
 /* Size in bytes of the static scratch array of adpar_vjp_scan_noalloc. */
 size_t adpar_noalloc_scratch_bytes(void);
+
+/* Device status of the last adpar_vjp_scan_noalloc call on the current
+ * device, as adpar_workspace_status gives it for a caller workspace: waits
+ * for `stream` (cudaStreamSynchronize), then copies the status word out of
+ * the static array into *device_status (ADPAR_OK, or ADPAR_ERR_TIMEOUT when
+ * a bounded wait gave up and the adjoints are wrong).  Allocates nothing.
+ * Returns ADPAR_ERR_INVALID for a null device_status, ADPAR_ERR_CUDA when
+ * the synchronisation or the copy fails. */
+int adpar_noalloc_status(void *stream, int *device_status);
+
+/* Failure-detection self-test on the static array: the same bounded wait on
+ * a flag that nothing sets as adpar_selftest_timeout, run in the static
+ * array instead of a caller workspace, so that adpar_noalloc_status then
+ * reports ADPAR_ERR_TIMEOUT.  Takes about a second on the GPU; the GPU
+ * context stays usable.  Allocates nothing. */
+int adpar_noalloc_selftest_timeout(void *stream);
 
 #ifdef __cplusplus
 }

@@ -593,7 +593,7 @@ int oracle_map_acc_vjp(int gfun, int64_t nj, int64_t na, int width,
 }
 
 /* ---------------------------------------------------------------------
- * k-means cost (Sec. 7.3, with the squared distance):
+ * k-means cost (Sec. 7.4, with the squared distance):
  *   loss = sum_i min_k sum_j (x_ij - c_kj)^2.
  * Forward: all distances in FP64, argmin with the lowest k on ties
  * (the min-reduce rule of Sec. 5.1.1).  Reverse: the min-reduce adjoint
@@ -807,7 +807,7 @@ int oracle_scan_wide_vjp(int op, int64_t n, int d, const double *a, const double
 }
 
 /* ---------------------------------------------------------------------
- * Hessian diagonal of the k-means cost in C (Sec. 7.3, the second-order
+ * Hessian diagonal of the k-means cost in C (Sec. 7.4, the second-order
  * information the paper obtains by nesting forward mode over the VJP):
  * with every point's argmin held fixed (the cost is piecewise quadratic in
  * C and the argmin changes only on measure-zero ties),

@@ -274,7 +274,7 @@ def map_acc_vjp(g, as_, is_, xsbar, ws=None, width=1, asbar=None, wsbar=None):
 
 def kmeans_hessdiag(X, Cm, ybar=1.0):
     """Hessian diagonal of the k-means cost in C with the argmins held fixed
-    (Sec. 7.3): 2 ybar times each centroid's count, [k, d]."""
+    (Sec. 7.4): 2 ybar times each centroid's count, [k, d]."""
     X = _f64(X)
     Cm = _f64(Cm)
     N, d = X.shape
@@ -285,7 +285,7 @@ def kmeans_hessdiag(X, Cm, ybar=1.0):
 
 
 def kmeans(X, Cm, ybar=1.0):
-    """k-means cost with squared distances and its gradient in C (Sec. 7.3).
+    """k-means cost with squared distances and its gradient in C (Sec. 7.4).
 
     Returns (loss, argmin[N], mind[N], Cbar[k, d]).
     """

@@ -27,7 +27,7 @@ RULE_REDUCE, RULE_SCAN, RULE_HIST, RULE_SCATTER, RULE_MAP_ACC, RULE_KMEANS, RULE
     RULE_HIST_GENERAL, RULE_SCAN_WIDE = range(10)
 WS_MINIMAL = 0x100  # or'ed into a rule: the smallest accepted workspace
 ACCUMULATE, PROD_LOGDOMAIN, SCATTER_RESTORE, FULL_LIN_O = 0x1, 0x4, 0x8, 0x10
-OK, ERR_TIMEOUT, ERR_TOO_LARGE = 0, 6, 7
+OK, ERR_INVALID, ERR_TIMEOUT, ERR_TOO_LARGE = 0, 1, 6, 7
 
 
 class AdparError(RuntimeError):
@@ -73,6 +73,10 @@ def lib():
         L.adpar_vjp_scan_noalloc.argtypes = [OpDesc, C.c_int64] + [_VP] * 8 + [C.c_uint32, _VP]
         L.adpar_noalloc_scratch_bytes.restype = C.c_size_t
         L.adpar_noalloc_scratch_bytes.argtypes = []
+        L.adpar_noalloc_status.restype = C.c_int
+        L.adpar_noalloc_status.argtypes = [_VP, C.POINTER(C.c_int)]
+        L.adpar_noalloc_selftest_timeout.restype = C.c_int
+        L.adpar_noalloc_selftest_timeout.argtypes = [_VP]
         L.adpar_scan.restype = C.c_int
         L.adpar_scan.argtypes = [OpDesc, C.c_int64] + [_VP] * 4 + [_VP, C.c_size_t, _VP]
         L.adpar_vjp_scan_vec.restype = C.c_int
@@ -403,6 +407,18 @@ def adpar_vjp_scan_noalloc(op, a, ybar_a, b=None, ybar_b=None, abar=None, bbar=N
         raise ValueError("pass the output adjoint tensors: this entry point allocates nothing")
     n = ybar_a.numel()
     dt = _dtype_code(ybar_a)
+    # every array is read or written over n elements on the device: one of
+    # another dtype or length, or one in host memory, would be overrun
+    given = [(name, t) for name, t in (("a", a), ("b", b), ("ybar_a", ybar_a), ("ybar_b", ybar_b),
+                                       ("abar", abar), ("bbar", bbar), ("ys_a", ys_a), ("ys_b", ys_b))
+             if t is not None]
+    for name, t in given:
+        if t.dtype != ybar_a.dtype or t.numel() != n:
+            raise ValueError("%s must have ybar_a's dtype and length (%s, %d), got (%s, %d)"
+                             % (name, ybar_a.dtype, n, t.dtype, t.numel()))
+    for name, t in given:
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous CUDA tensor" % name)
     st = lib().adpar_vjp_scan_noalloc(OpDesc(opc, dt, w), n, _ptr(a), _ptr(b), _ptr(ybar_a),
                                       _ptr(ybar_b), _ptr(abar), _ptr(bbar), _ptr(ys_a), _ptr(ys_b),
                                       ACCUMULATE if accumulate else 0, _stream(stream))
@@ -413,6 +429,20 @@ def adpar_vjp_scan_noalloc(op, a, ybar_a, b=None, ybar_b=None, abar=None, bbar=N
 def adpar_noalloc_scratch_bytes():
     """Bytes of the static scratch behind adpar_vjp_scan_noalloc."""
     return lib().adpar_noalloc_scratch_bytes()
+
+
+def adpar_noalloc_status(stream=None):
+    """Device status word of the last adpar_vjp_scan_noalloc call on the
+    current device (C: adpar_noalloc_status; synchronises the stream)."""
+    st = C.c_int(0)
+    _check("adpar_noalloc_status", lib().adpar_noalloc_status(_stream(stream), C.byref(st)))
+    return st.value
+
+
+def adpar_noalloc_selftest_timeout(stream=None):
+    """Bounded-wait timeout diagnostic in the static scratch
+    (C: adpar_noalloc_selftest_timeout)."""
+    _check("adpar_noalloc_selftest_timeout", lib().adpar_noalloc_selftest_timeout(_stream(stream)))
 
 
 def _scalar_dev(x, like):

@@ -210,5 +210,5 @@ class _KMeans(torch.autograd.Function):
 
 
 def kmeans_loss(X, C):
-    """sum_i min_k ||x_i - c_k||^2 (Sec. 7.3, squared distances); gradient in C."""
+    """sum_i min_k ||x_i - c_k||^2 (Sec. 7.4, squared distances); gradient in C."""
     return _KMeans.apply(_c(X), _c(C))

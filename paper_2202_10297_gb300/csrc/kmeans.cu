@@ -1,5 +1,5 @@
 // k-means cost and its gradient in C, the nested-parallel program of
-// Sec. 7.3 with squared distances:
+// Sec. 7.4 with squared distances:
 //   loss = sum_i min_k ||x_i - c_k||^2,
 //   Cbar[k] = 2 ybar (cnt_k c_k - sum_{i: argmin_i = k} x_i).
 // Its VJP is the min-reduce rule of Sec. 5.1.1 (the adjoint goes to the

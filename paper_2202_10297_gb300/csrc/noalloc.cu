@@ -10,10 +10,9 @@
 // every GPU loading the library holds from module load until process exit.
 //
 // The array's name is a host-side stand-in in host code, not a device
-// address, so its device address is looked up once per device with
-// cudaGetSymbolAddress (with that device current) and cached.
-#include <mutex>
-
+// address, so every call looks up its device address on the current device
+// with cudaGetSymbolAddress.  Nothing is cached: a context that is torn down
+// and re-created (cudaDeviceReset) may load the module at another address.
 #include "common.cuh"
 
 namespace adpar {
@@ -25,25 +24,15 @@ namespace {
 // 8 MiB: enough for every scan VJP up to 2^28 FP32 elements of a width-1
 // operator and 2^26 FP64 pairs of the linear recurrence.
 constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_scan_scratch[kNoAllocScratchBytes];
 
-std::mutex g_mu;
-void* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the static scratch on the current device (set up on
-// the first call per device).
+// Device address of the static scratch on the current device.  The first
+// lookup on a device loads the module there; later ones are cheap.
 int scratch_on_current_device(void** out) {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ADPAR_ERR_CUDA;
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (g_scratch_ptr[dev] == nullptr) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_scan_scratch) != cudaSuccess || p == nullptr) return ADPAR_ERR_CUDA;
-        g_scratch_ptr[dev] = p;
-    }
-    *out = g_scratch_ptr[dev];
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_scan_scratch) != cudaSuccess || p == nullptr) return ADPAR_ERR_CUDA;
+    *out = p;
     return ADPAR_OK;
 }
 
@@ -66,4 +55,21 @@ extern "C" int adpar_vjp_scan_noalloc(adpar_opdesc d, int64_t n, const void* a, 
     // call, so stale contents from the previous call do no harm
     return adpar_vjp_scan(d, n, a, b, ybar_a, ybar_b, abar, bbar, ys_a, ys_b, flags, scratch,
                           kNoAllocScratchBytes, stream);
+}
+
+extern "C" int adpar_noalloc_status(void* stream, int* device_status) {
+    if (!device_status) return ADPAR_ERR_INVALID;
+    void* scratch = nullptr;
+    const int st = scratch_on_current_device(&scratch);
+    if (st != ADPAR_OK) return st;
+    // the status word is the first word of the scan's workspace header,
+    // which adpar_vjp_scan_noalloc places at the start of the static array
+    return adpar_workspace_status(scratch, stream, device_status);
+}
+
+extern "C" int adpar_noalloc_selftest_timeout(void* stream) {
+    void* scratch = nullptr;
+    const int st = scratch_on_current_device(&scratch);
+    if (st != ADPAR_OK) return st;
+    return adpar_selftest_timeout(scratch, kNoAllocScratchBytes, stream);
 }

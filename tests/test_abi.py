@@ -151,3 +151,26 @@ def test_older_entry_points_validate_without_gpu(lib):
     assert lib.adpar_kmeans_hessdiag(64, V, V, 0, V, 0, V) == 1                    # ybar, Hdiag missing
     assert lib.adpar_kmeans_hessdiag(48, 0x1000, V, 0, 0x2000, 0, V) == 2          # k not a multiple of 32
     assert lib.adpar_kmeans_hessdiag(64, 0x1000, V, 0, 0x2000, 0, V) == 4          # workspace missing
+
+
+def test_noalloc_binding_checks_every_array_without_gpu():
+    """The allocation-free scan VJP reads and writes n elements of every array
+    it is given, n taken from ybar_a: an array of another length or dtype
+    would be overrun on the device, so the binding refuses it on the host."""
+    import torch
+    from paper_2202_10297_gb300 import adpar as A
+    n = 64
+    f64 = lambda k=n: torch.zeros(k, dtype=torch.float64)  # noqa: E731
+    with pytest.raises(ValueError, match="abar"):
+        A.adpar_vjp_scan_noalloc("linrec", f64(), f64(), b=f64(), ybar_b=f64(), abar=f64(n - 1), bbar=f64())
+    with pytest.raises(ValueError, match="bbar"):
+        A.adpar_vjp_scan_noalloc("linrec", f64(), f64(), b=f64(), ybar_b=f64(), abar=f64(),
+                                 bbar=torch.zeros(n, dtype=torch.float32))
+    with pytest.raises(ValueError, match="ys_b"):
+        A.adpar_vjp_scan_noalloc("linrec", f64(), f64(), b=f64(), ybar_b=f64(), abar=f64(), bbar=f64(),
+                                 ys_a=f64(), ys_b=f64(2 * n))
+    # right shapes, but host tensors: refused before the library is called
+    with pytest.raises(ValueError, match="CUDA"):
+        A.adpar_vjp_scan_noalloc("add", None, f64(), abar=f64())
+    # the status reader checks its output pointer before any CUDA call
+    assert A.lib().adpar_noalloc_status(None, None) == A.ERR_INVALID

@@ -1,4 +1,4 @@
-"""GPU parity of the k-means cost and gradient (Sec. 7.3, squared distances).
+"""GPU parity of the k-means cost and gradient (Sec. 7.4, squared distances).
 
 The argmin from the TF32 tensor-core distances is certified, so it must
 equal the FP64 oracle's argmin (lowest k on ties) bit-exactly on every

@@ -59,6 +59,10 @@ MUTANTS = {
     "wide_linrec_jright_transposed": ("{ { prev[0], 0.0 }, { prev[1], 1.0 } }", "{ { prev[0], prev[1] }, { 0.0, 1.0 } }"),
     "kmeans_hessdiag_factor": ("H[(int64_t)c * d + j] = 2.0 * ybar * (double)cnt[c];",
                                "H[(int64_t)c * d + j] = ybar * (double)cnt[c];"),
+    "kmeans_tie_to_highest_k": ("if (s < best) { best = s; arg = c; }\n        }\n        if (argmin_out)",
+                                "if (s <= best) { best = s; arg = c; }\n        }\n        if (argmin_out)"),
+    "kmeans_hessdiag_tie_to_highest_k": ("if (s < best) { best = s; arg = c; }\n        }\n        if (arg >= 0) ++cnt[arg];",
+                                         "if (s <= best) { best = s; arg = c; }\n        }\n        if (arg >= 0) ++cnt[arg];"),
     "wide_first_element_dropped": ("for (int c = 0; c < d; ++c) abar[c] += rsb[c];",
                                    "for (int c = 0; c < d; ++c) abar[c] += 0.0 * rsb[c];"),
 }

@@ -75,6 +75,19 @@ def test_golden_map_acc(oracle, golden):
         np.testing.assert_array_equal(ab, c["asbar"], err_msg=c["cite"])
 
 
+def test_golden_kmeans(oracle, golden):
+    for c in golden["kmeans"]:
+        X = np.array(c["X"])
+        Cm = np.array(c["C"])
+        loss, arg, mind, cb = oracle.kmeans(X, Cm, c["ybar"])
+        np.testing.assert_array_equal(arg, c["argmin"], err_msg=c["cite"])
+        np.testing.assert_array_equal(mind, c["mind"])
+        assert loss == c["loss"]
+        np.testing.assert_array_equal(cb, c["Cbar"])
+        H = oracle.kmeans_hessdiag(X, Cm, ybar=c["ybar"])
+        np.testing.assert_array_equal(H, c["hessdiag"])
+
+
 # ------------------------------------------------------------- product reduce
 def _prod_brute(a, ybar):
     """d(prod a)/d a_i = product of all other elements (O(n^2))."""

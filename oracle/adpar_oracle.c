@@ -838,3 +838,203 @@ int oracle_kmeans_hessdiag(int64_t N, int d, int k, const double *X, const doubl
     free(cnt);
     return 0;
 }
+
+/* =====================================================================
+ * Forward mode (Sec. 3): dual numbers.  Every value of the primal loop
+ * carries a tangent, and each operation is followed by its derivative
+ * applied to the tangents of its arguments:
+ *   t (.) a  ->  tdot' = d(t (.) a)/dt * tdot + d(t (.) a)/da * adot.
+ * The primal loops and the partial derivatives (combine, d_dt, d_da) are
+ * the ones of the reverse sweeps above, so the duality
+ *   <ybar, J xdot> = <J^T ybar, xdot>
+ * against the reverse sweeps checks the two directions against each other.
+ * ===================================================================== */
+
+/* extended-exponent addition, rounded once like an FP64 add */
+static xd xd_add(xd a, xd b)
+{
+    if (a.m == 0.0) return b;
+    if (b.m == 0.0) return a;
+    if (a.e < b.e) { xd t = a; a = b; b = t; }
+    int64_t d = a.e - b.e;
+    if (d > 1100) return a; /* b lies far below half an ulp of a */
+    xd r;
+    int e = 0;
+    r.m = frexp(a.m + ldexp(b.m, (int)(-d)), &e);
+    r.e = (r.m == 0.0) ? 0 : a.e + e;
+    return r;
+}
+
+/* reduce with +, min, max:  t_0 = e, tdot_0 = 0;
+ *   tdot_{i+1} = d_dt(t_i, a_i) tdot_i + d_da(t_i, a_i) adot_i,
+ *   t_{i+1}    = t_i (.) a_i.
+ * For max the tangent follows t on ties (t >= a): the first index. */
+int oracle_reduce_jvp(int op, int64_t n, const double *a, const double *adot,
+                      double *y_out, double *ydot_out)
+{
+    if (op != O_ADD && op != O_MIN && op != O_MAX) return 1;
+    double t = neutral_of(op), td = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double ft = d_dt(op, t, a[i]), fa = d_da(op, t, a[i]);
+        td = (ft != 0.0 ? ft * td : 0.0) + (fa != 0.0 ? fa * adot[i] : 0.0);
+        t = combine(op, t, a[i]);
+    }
+    if (y_out) *y_out = t;
+    if (ydot_out) *ydot_out = td;
+    return 0;
+}
+
+/* reduce with * in extended exponent: the product rule on dual numbers,
+ *   tdot_{i+1} = a_i tdot_i + t_i adot_i,   t_{i+1} = t_i a_i,
+ * with no division and no case analysis of the zeros.  Outputs the tangent
+ * of y rounded to FP64, ln|ydot| (-inf when 0) and its sign. */
+int oracle_prod_reduce_jvp(int64_t n, const double *a, const double *adot,
+                           double *ydot_val, double *ydot_log, int8_t *ydot_sign)
+{
+    xd t = xd_make(1.0), td = xd_make(0.0);
+    for (int64_t i = 0; i < n; ++i) {
+        xd ai = xd_make(a[i]);
+        td = xd_add(xd_mul(ai, td), xd_mul(t, xd_make(adot[i])));
+        t = xd_mul(t, ai);
+    }
+    if (ydot_val) *ydot_val = xd_value(td);
+    if (ydot_log) *ydot_log = xd_log(td);
+    if (ydot_sign) *ydot_sign = (int8_t)xd_sign(td);
+    return 0;
+}
+
+/* reduce_by_index with +, min, max: the semantic loop of Sec. 5.1.2 on dual
+ * numbers, one (value, tangent) per bin, elements taken in index order;
+ * out-of-range indices are skipped.  hs_out (nullable) and hsdot_out [m]. */
+int oracle_hist_jvp(int op, int64_t n, int64_t m, const double *vals, const double *vdot,
+                    const int64_t *inds, double *hs_out, double *hsdot_out)
+{
+    if (op != O_ADD && op != O_MIN && op != O_MAX) return 1;
+    double *hs = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+    double *hd = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+    if (!hs || !hd) { free(hs); free(hd); return 2; }
+    for (int64_t b = 0; b < m; ++b) { hs[b] = neutral_of(op); hd[b] = 0.0; }
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t b = inds[i];
+        if (b < 0 || b >= m) continue;
+        double t = hs[b];
+        double ft = d_dt(op, t, vals[i]), fa = d_da(op, t, vals[i]);
+        hd[b] = (ft != 0.0 ? ft * hd[b] : 0.0) + (fa != 0.0 ? fa * vdot[i] : 0.0);
+        hs[b] = combine(op, t, vals[i]);
+    }
+    for (int64_t b = 0; b < m; ++b) {
+        if (hs_out) hs_out[b] = hs[b];
+        hsdot_out[b] = hd[b];
+    }
+    free(hs); free(hd);
+    return 0;
+}
+
+/* reduce_by_index with * in extended exponent: per bin the product rule on
+ * dual numbers; per bin the tangent rounded to FP64, its log and sign. */
+int oracle_hist_prod_jvp(int64_t n, int64_t m, const double *vals, const double *vdot,
+                         const int64_t *inds, double *hsdot_val, double *hsdot_log,
+                         int8_t *hsdot_sign)
+{
+    xd *t = (xd *)malloc(sizeof(xd) * (size_t)(m > 0 ? m : 1));
+    xd *td = (xd *)malloc(sizeof(xd) * (size_t)(m > 0 ? m : 1));
+    if (!t || !td) { free(t); free(td); return 2; }
+    for (int64_t b = 0; b < m; ++b) { t[b] = xd_make(1.0); td[b] = xd_make(0.0); }
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t b = inds[i];
+        if (b < 0 || b >= m) continue;
+        xd vi = xd_make(vals[i]);
+        td[b] = xd_add(xd_mul(vi, td[b]), xd_mul(t[b], xd_make(vdot[i])));
+        t[b] = xd_mul(t[b], vi);
+    }
+    for (int64_t b = 0; b < m; ++b) {
+        if (hsdot_val) hsdot_val[b] = xd_value(td[b]);
+        if (hsdot_log) hsdot_log[b] = xd_log(td[b]);
+        if (hsdot_sign) hsdot_sign[b] = (int8_t)xd_sign(td[b]);
+    }
+    free(t); free(td);
+    return 0;
+}
+
+/* scatter (Sec. 5.3) on dual numbers: ys = xs with ys[is_j] = vs_j, so
+ * ysdot = xsdot with ysdot[is_j] = vsdot_j (in place over xsdot; indices
+ * outside [0, n) are skipped). */
+int oracle_scatter_jvp(int64_t n, int64_t m, const int64_t *is, const double *vsdot,
+                       double *xsdot_inout)
+{
+    for (int64_t j = 0; j < m; ++j) {
+        int64_t k = is[j];
+        if (k < 0 || k >= n) continue;
+        xsdot_inout[k] = vsdot[j];
+    }
+    return 0;
+}
+
+/* map with a free array (Sec. 5.4) on dual numbers:
+ *   xs_j = g(as[is_j], ws_j)  ->  xsdot_j = dg/da asdot[is_j] + dg/dw wsdot_j,
+ *   GATHER: xsdot_j = asdot_i;  SCALE: asdot_i w_j + a_i wsdot_j;
+ *   SQDIST_ROW: sum_k 2 (w_jk - a_ik)(wsdot_jk - asdot_ik).
+ * An index out of range gives xs_j = 0 and a zero tangent.  wsdot may be
+ * NULL (no tangent on ws). */
+int oracle_map_acc_jvp(int gfun, int64_t nj, int64_t na, int width,
+                       const double *as, const int64_t *is, const double *ws,
+                       const double *asdot, const double *wsdot, double *xsdot)
+{
+    for (int64_t j = 0; j < nj; ++j) {
+        int64_t i = is[j];
+        if (i < 0 || i >= na) { xsdot[j] = 0.0; continue; }
+        if (gfun == G_GATHER) {
+            xsdot[j] = asdot[i];
+        } else if (gfun == G_SCALE) {
+            xsdot[j] = asdot[i] * ws[j] + (wsdot ? as[i] * wsdot[j] : 0.0);
+        } else if (gfun == G_SQDIST_ROW) {
+            double s = 0.0;
+            for (int k = 0; k < width; ++k) {
+                double diff = ws[j * width + k] - as[i * width + k];
+                double dd = (wsdot ? wsdot[j * width + k] : 0.0) - asdot[i * width + k];
+                s += 2.0 * diff * dd;
+            }
+            xsdot[j] = s;
+        } else {
+            return 1;
+        }
+    }
+    return 0;
+}
+
+/* Forward over reverse for the k-means cost (Sec. 7.4 nests forward mode
+ * over the VJP for the Hessian diagonal): the forward and reverse sweeps of
+ * oracle_kmeans run on dual numbers whose tangent is Cdot (X and ybar carry
+ * none).  Per point: the distances and their tangents
+ *   s_c = sum_j (x_ij - c_cj)^2,   sdot_c = sum_j 2 (c_cj - x_ij) cdot_cj,
+ * the min (lowest k on ties; the argmin itself has no tangent), the loss
+ * and its tangent ydot += sdot_k*; then the reverse step
+ *   Cbar[k*, j] += ybar (-2)(x_ij - c_k*j)
+ * whose tangent is  Cbardot[k*, j] += ybar (-2)(0 - cdot_k*j).
+ * Cbardot [k*d] is overwritten; ydot_out (nullable) receives the loss's
+ * tangent. */
+int oracle_kmeans_fwd_rev(int64_t N, int d, int k, const double *X, const double *C,
+                          const double *Cdot, double ybar, double *ydot_out, double *Cbardot)
+{
+    double ydot = 0.0;
+    for (int64_t q = 0; q < (int64_t)k * d; ++q) Cbardot[q] = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        double best = INFINITY, bestdot = 0.0;
+        int64_t arg = -1;
+        for (int c = 0; c < k; ++c) {
+            double s = 0.0, sd = 0.0;
+            for (int j = 0; j < d; ++j) {
+                double diff = X[i * d + j] - C[(int64_t)c * d + j];
+                s += diff * diff;
+                sd += 2.0 * (-diff) * Cdot[(int64_t)c * d + j];
+            }
+            if (s < best) { best = s; bestdot = sd; arg = c; }
+        }
+        ydot += bestdot;
+        if (arg >= 0)
+            for (int j = 0; j < d; ++j)
+                Cbardot[arg * d + j] += ybar * (-2.0) * (0.0 - Cdot[arg * d + j]);
+    }
+    if (ydot_out) *ydot_out = ydot;
+    return 0;
+}

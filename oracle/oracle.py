@@ -51,10 +51,19 @@ def lib():
                                               _D, _D]
         L.oracle_scan_wide_vjp.argtypes = [C.c_int, i64, C.c_int, _D, _D, _D, _D]
         L.oracle_kmeans_hessdiag.argtypes = [i64, C.c_int, C.c_int, _D, _D, dbl, _D]
+        L.oracle_reduce_jvp.argtypes = [C.c_int, i64, _D, _D, _D, _D]
+        L.oracle_prod_reduce_jvp.argtypes = [i64, _D, _D, _D, _D, _I8]
+        L.oracle_hist_jvp.argtypes = [C.c_int, i64, i64, _D, _D, _I64, _D, _D]
+        L.oracle_hist_prod_jvp.argtypes = [i64, i64, _D, _D, _I64, _D, _D, _I8]
+        L.oracle_scatter_jvp.argtypes = [i64, i64, _I64, _D, _D]
+        L.oracle_map_acc_jvp.argtypes = [C.c_int, i64, i64, C.c_int, _D, _I64, _D, _D, _D, _D]
+        L.oracle_kmeans_fwd_rev.argtypes = [i64, C.c_int, C.c_int, _D, _D, _D, dbl, _D, _D]
         for f in ("oracle_reduce_vjp", "oracle_prod_reduce_vjp", "oracle_scan_vjp",
                   "oracle_hist_vjp", "oracle_hist_prod_vjp", "oracle_scatter_vjp",
                   "oracle_map_acc_vjp", "oracle_kmeans", "oracle_reduce_general_vjp", "oracle_scan_jvp",
-                  "oracle_hist_general_vjp", "oracle_scan_wide_vjp", "oracle_kmeans_hessdiag"):
+                  "oracle_hist_general_vjp", "oracle_scan_wide_vjp", "oracle_kmeans_hessdiag",
+                  "oracle_reduce_jvp", "oracle_prod_reduce_jvp", "oracle_hist_jvp", "oracle_hist_prod_jvp",
+                  "oracle_scatter_jvp", "oracle_map_acc_jvp", "oracle_kmeans_fwd_rev"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -300,3 +309,77 @@ def kmeans(X, Cm, ybar=1.0):
     _check(lib().oracle_kmeans(N, d, k, _p(X), _p(Cm), float(ybar), C.byref(loss),
                                _p(arg, _I64), _p(mind), _p(cb)), "kmeans")
     return loss.value, arg, mind, cb
+
+
+# ------------------------------------------------------------ forward mode
+def reduce_jvp(op, a, adot):
+    """Forward mode of reduce with +, min, max (Sec. 3 dual numbers over the
+    loop of Sec. 5.1).  Returns (y, ydot)."""
+    a, ad = _f64(a), _f64(adot)
+    y, yd = np.zeros(1), np.zeros(1)
+    _check(lib().oracle_reduce_jvp(OPS[op], a.size, _p(a), _p(ad), _p(y), _p(yd)), "reduce_jvp")
+    return float(y[0]), float(yd[0])
+
+
+def prod_reduce_jvp(a, adot):
+    """Forward mode of reduce with * (extended exponent).  Returns a dict:
+    ydot (FP64 value), log (ln|ydot|), sign."""
+    a, ad = _f64(a), _f64(adot)
+    v, lg = np.zeros(1), np.zeros(1)
+    sg = np.zeros(1, dtype=np.int8)
+    _check(lib().oracle_prod_reduce_jvp(a.size, _p(a), _p(ad), _p(v), _p(lg), _p(sg, _I8)), "prod_reduce_jvp")
+    return dict(ydot=float(v[0]), log=float(lg[0]), sign=int(sg[0]))
+
+
+def hist_jvp(op, vals, vdot, inds, m):
+    """Forward mode of reduce_by_index with +, min, max (Sec. 5.1.2's loop on
+    dual numbers).  Returns (hs, hsdot), each [m]."""
+    v, vd, ix = _f64(vals), _f64(vdot), _i64(inds)
+    hs, hd = np.zeros(m), np.zeros(m)
+    _check(lib().oracle_hist_jvp(OPS[op], v.size, m, _p(v), _p(vd), _p(ix, _I64), _p(hs), _p(hd)), "hist_jvp")
+    return hs, hd
+
+
+def hist_prod_jvp(vals, vdot, inds, m):
+    """Forward mode of reduce_by_index with * (extended exponent).  Returns a
+    dict of [m] arrays: hsdot (FP64 values), log, sign."""
+    v, vd, ix = _f64(vals), _f64(vdot), _i64(inds)
+    val, lg = np.zeros(m), np.zeros(m)
+    sg = np.zeros(m, dtype=np.int8)
+    _check(lib().oracle_hist_prod_jvp(v.size, m, _p(v), _p(vd), _p(ix, _I64), _p(val), _p(lg), _p(sg, _I8)),
+           "hist_prod_jvp")
+    return dict(hsdot=val, log=lg, sign=sg)
+
+
+def scatter_jvp(n, is_, vsdot, xsdot):
+    """Forward mode of scatter (Sec. 5.3): ysdot = xsdot with ysdot[is_j] = vsdot_j."""
+    ix, vd = _i64(is_), _f64(vsdot)
+    out = _f64(xsdot).copy()
+    assert out.size == n
+    _check(lib().oracle_scatter_jvp(n, ix.size, _p(ix, _I64), _p(vd), _p(out)), "scatter_jvp")
+    return out
+
+
+def map_acc_jvp(g, as_, is_, asdot, ws=None, wsdot=None, width=1):
+    """Forward mode of map with a free array (Sec. 5.4).  Returns xsdot [nj]."""
+    a, ix, ad = _f64(as_), _i64(is_), _f64(asdot)
+    w = None if ws is None else _f64(ws)
+    wd = None if wsdot is None else _f64(wsdot)
+    na = a.size // width
+    out = np.zeros(ix.size)
+    _check(lib().oracle_map_acc_jvp(GFUNS[g], ix.size, na, width, _p(a), _p(ix, _I64), _p(w), _p(ad), _p(wd),
+                                    _p(out)), "map_acc_jvp")
+    return out
+
+
+def kmeans_fwd_rev(X, Cm, Cdot, ybar=1.0):
+    """Forward over reverse for the k-means cost (Sec. 7.4): the tangent, along
+    Cdot, of the loss and of its gradient in C.  Returns (ydot, Cbardot [k, d])."""
+    X, Cm, Cd = _f64(X), _f64(Cm), _f64(Cdot)
+    N, d = X.shape
+    k = Cm.shape[0]
+    yd = np.zeros(1)
+    out = np.zeros((k, d))
+    _check(lib().oracle_kmeans_fwd_rev(N, d, k, _p(X), _p(Cm), _p(Cd), float(ybar), _p(yd), _p(out)),
+           "kmeans_fwd_rev")
+    return float(yd[0]), out

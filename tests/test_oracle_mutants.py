@@ -63,6 +63,23 @@ MUTANTS = {
                                 "if (s <= best) { best = s; arg = c; }\n        }\n        if (argmin_out)"),
     "kmeans_hessdiag_tie_to_highest_k": ("if (s < best) { best = s; arg = c; }\n        }\n        if (arg >= 0) ++cnt[arg];",
                                          "if (s <= best) { best = s; arg = c; }\n        }\n        if (arg >= 0) ++cnt[arg];"),
+    "prod_jvp_uses_updated_product": (
+        "td = xd_add(xd_mul(ai, td), xd_mul(t, xd_make(adot[i])));\n        t = xd_mul(t, ai);",
+        "t = xd_mul(t, ai);\n        td = xd_add(xd_mul(ai, td), xd_mul(t, xd_make(adot[i])));"),
+    "xd_add_exponent_dropped": ("r.e = (r.m == 0.0) ? 0 : a.e + e;", "r.e = (r.m == 0.0) ? 0 : a.e;"),
+    "hist_prod_jvp_wrong_factor": ("td[b] = xd_add(xd_mul(vi, td[b]), xd_mul(t[b], xd_make(vdot[i])));",
+                                   "td[b] = xd_add(xd_mul(t[b], td[b]), xd_mul(t[b], xd_make(vdot[i])));"),
+    "hist_jvp_chain_dropped": ("hd[b] = (ft != 0.0 ? ft * hd[b] : 0.0) + (fa != 0.0 ? fa * vdot[i] : 0.0);",
+                               "hd[b] = (fa != 0.0 ? fa * vdot[i] : 0.0);"),
+    "map_acc_jvp_scale_term_dropped": ("xsdot[j] = asdot[i] * ws[j] + (wsdot ? as[i] * wsdot[j] : 0.0);",
+                                       "xsdot[j] = asdot[i] * ws[j];"),
+    "map_acc_jvp_sqdist_sign": ("double dd = (wsdot ? wsdot[j * width + k] : 0.0) - asdot[i * width + k];",
+                                "double dd = (wsdot ? wsdot[j * width + k] : 0.0) + asdot[i * width + k];"),
+    "scatter_jvp_wrong_index": ("xsdot_inout[k] = vsdot[j];", "xsdot_inout[j] = vsdot[j];"),
+    "kmeans_fwd_rev_sign": ("Cbardot[arg * d + j] += ybar * (-2.0) * (0.0 - Cdot[arg * d + j]);",
+                            "Cbardot[arg * d + j] += ybar * (2.0) * (0.0 - Cdot[arg * d + j]);"),
+    "kmeans_fwd_rev_distance_tangent_sign": ("sd += 2.0 * (-diff) * Cdot[(int64_t)c * d + j];",
+                                             "sd += 2.0 * diff * Cdot[(int64_t)c * d + j];"),
     "wide_first_element_dropped": ("for (int c = 0; c < d; ++c) abar[c] += rsb[c];",
                                    "for (int c = 0; c < d; ++c) abar[c] += 0.0 * rsb[c];"),
 }

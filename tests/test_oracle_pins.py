@@ -845,3 +845,178 @@ def test_kmeans_hessdiag_is_derivative_of_gradient(oracle):
             assert abs(fd - H[c, j]) <= 1e-6 * (1 + abs(fd))
     cnt = np.bincount(arg, minlength=k)
     np.testing.assert_array_equal(H, 2 * 0.7 * cnt[:, None] * np.ones((1, d)))
+
+
+# ------------------------------------------------------------ forward mode
+# The dual-number sweeps (Sec. 3) are pinned by brute force and closed forms
+# on small inputs, by central differences where the function is multilinear
+# or quadratic (exact up to rounding), and by the duality
+# <ybar, J xdot> = <J^T ybar, xdot> against the reverse sweeps pinned above.
+@pytest.mark.parametrize("op", ["add", "min", "max"])
+def test_reduce_jvp_closed_form_and_duality(oracle, op):
+    g = synth.rng(101)
+    a = np.round(g.normal(size=57) * 4) / 4  # forced ties
+    ad = g.normal(size=57)
+    y, yd = oracle.reduce_jvp(op, a, ad)
+    if op == "add":
+        assert y == a.sum() or abs(y - a.sum()) < 1e-12
+        assert abs(yd - ad.sum()) < 1e-12
+    else:
+        k = int(np.argmax(a) if op == "max" else np.argmin(a))  # numpy: first index
+        assert y == a[k] and yd == ad[k]
+    ybar = 1.7
+    _, ab, _ = oracle.reduce_vjp(op, a, ybar)
+    assert abs(ybar * yd - np.dot(ab, ad)) < 1e-12 * (1 + abs(ybar * yd))
+    # n = 0: the neutral element and a zero tangent
+    y0, yd0 = oracle.reduce_jvp(op, np.zeros(0), np.zeros(0))
+    assert yd0 == 0.0
+
+
+@pytest.mark.parametrize("nz", [0, 1, 2])
+def test_prod_reduce_jvp_brute_force_fd_and_duality(oracle, nz):
+    g = synth.rng(102 + nz)
+    n = 40
+    a = g.uniform(0.5, 1.5, n)
+    a[g.choice(n, nz, replace=False)] = 0.0
+    ad = g.normal(size=n)
+    r = oracle.prod_reduce_jvp(a, ad)
+    # brute force: sum_i prod_{j != i} a_j adot_i
+    ref = sum(np.prod(np.delete(a, i)) * ad[i] for i in range(n))
+    assert abs(r["ydot"] - ref) <= 1e-13 * max(1e-300, abs(ref)) + 1e-300
+    if nz >= 2:
+        assert r["ydot"] == 0.0 and r["sign"] == 0
+    else:
+        assert r["sign"] == np.sign(ref) and abs(r["log"] - np.log(abs(ref))) < 1e-12
+    # central differences along adot: even orders cancel, the third-order
+    # terms are O(h^2)
+    h = 1e-5
+    fd = (np.prod(a + h * ad) - np.prod(a - h * ad)) / (2 * h)
+    assert abs(fd - ref) <= 1e-6 * (abs(ref) + 1e-3)
+    # duality with the reverse sweep, in the log domain for long products
+    a2 = g.uniform(0.5, 1.5, 5000)
+    ad2 = g.normal(size=5000)
+    rj = oracle.prod_reduce_jvp(a2, ad2)
+    rv = oracle.prod_reduce_vjp(a2, 1.0)
+    # <1, J adot> = sum_i abar_i adot_i with abar_i = exp(log_i) sign_i: sum in
+    # scaled form around the largest term
+    lg = rv["log"]
+    top = lg.max()
+    s = np.sum(rv["sign"] * np.exp(lg - top) * ad2)
+    assert rj["sign"] == np.sign(s)
+    assert abs(rj["log"] - (top + np.log(abs(s)))) < 1e-10
+
+
+@pytest.mark.parametrize("op", ["add", "min", "max"])
+def test_hist_jvp_brute_force_and_duality(oracle, op):
+    g = synth.rng(110)
+    n, m = 500, 13
+    vals = np.round(g.normal(size=n) * 3) / 3
+    vd = g.normal(size=n)
+    inds = g.integers(-2, m + 2, size=n)
+    hs, hd = oracle.hist_jvp(op, vals, vd, inds, m)
+    for b in range(m):
+        sel = np.flatnonzero(inds == b)
+        if sel.size == 0:
+            assert hd[b] == 0.0
+            continue
+        if op == "add":
+            assert abs(hd[b] - vd[sel].sum()) < 1e-12 and abs(hs[b] - vals[sel].sum()) < 1e-12
+        else:
+            v = vals[sel]
+            k = sel[int(np.argmax(v) if op == "max" else np.argmin(v))]  # first index in the bin
+            assert hs[b] == vals[k] and hd[b] == vd[k]
+    hsbar = g.normal(size=m)
+    vb, _, _ = oracle.hist_vjp(op, vals, inds, m, hsbar)
+    assert abs(np.dot(hsbar, hd) - np.dot(vb, vd)) < 1e-11
+
+
+def test_hist_prod_jvp_brute_force(oracle):
+    g = synth.rng(111)
+    n, m = 300, 7
+    vals = g.uniform(0.5, 1.5, n) * np.sign(g.normal(size=n))
+    inds = g.integers(-1, m + 1, size=n)
+    vals[np.flatnonzero(inds == 2)[:1]] = 0.0   # one zero in bin 2
+    vals[np.flatnonzero(inds == 3)[:2]] = 0.0   # two in bin 3
+    vd = g.normal(size=n)
+    r = oracle.hist_prod_jvp(vals, vd, inds, m)
+    for b in range(m):
+        sel = np.flatnonzero(inds == b)
+        v, t = vals[sel], vd[sel]
+        ref = sum(np.prod(np.delete(v, i)) * t[i] for i in range(v.size))
+        assert abs(r["hsdot"][b] - ref) <= 1e-12 * abs(ref) + 1e-300, b
+        assert r["sign"][b] == np.sign(ref)
+    assert r["hsdot"][3] == 0.0
+
+
+def test_scatter_jvp_closed_form(oracle):
+    g = synth.rng(112)
+    n, m = 50, 20
+    is_ = g.permutation(n + 10)[:m] - 5  # some out of range, no duplicates
+    vd = g.normal(size=m)
+    xd = g.normal(size=n)
+    out = oracle.scatter_jvp(n, is_, vd, xd)
+    ref = xd.copy()
+    for j, k in enumerate(is_):
+        if 0 <= k < n:
+            ref[k] = vd[j]
+    np.testing.assert_array_equal(out, ref)
+
+
+@pytest.mark.parametrize("gname,width", [("gather", 1), ("scale", 1), ("sqdist_row", 3)])
+def test_map_acc_jvp_fd_and_duality(oracle, gname, width):
+    g = synth.rng(113)
+    na, nj = 9, 40
+    as_ = g.normal(size=na * width)
+    ws = g.normal(size=nj * width)
+    is_ = g.integers(-1, na + 1, size=nj)
+    asd = g.normal(size=na * width)
+    wsd = g.normal(size=nj * width) if gname != "gather" else None
+    xd = oracle.map_acc_jvp(gname, as_, is_, asd, ws=ws, wsdot=wsd, width=width)
+
+    def F(a, w):
+        out = np.zeros(nj)
+        for j in range(nj):
+            i = is_[j]
+            if not (0 <= i < na):
+                continue
+            if gname == "gather":
+                out[j] = a[i]
+            elif gname == "scale":
+                out[j] = a[i] * w[j]
+            else:
+                out[j] = ((w[j * width:(j + 1) * width] - a[i * width:(i + 1) * width]) ** 2).sum()
+        return out
+    h = 0.5  # F is at most quadratic: central differences are exact up to rounding
+    wdir = wsd if wsd is not None else np.zeros_like(ws)
+    fd = (F(as_ + h * asd, ws + h * wdir) - F(as_ - h * asd, ws - h * wdir)) / (2 * h)
+    np.testing.assert_allclose(xd, fd, rtol=1e-12, atol=1e-12)
+    xsbar = g.normal(size=nj)
+    ab, wb = oracle.map_acc_vjp(gname, as_, is_, xsbar, ws=ws, width=width)
+    lhs = np.dot(xsbar, xd)
+    rhs = np.dot(ab, asd) + (np.dot(wb, wsd) if wsd is not None else 0.0)
+    assert abs(lhs - rhs) < 1e-11
+
+
+def test_kmeans_fwd_rev_is_the_derivative_of_the_gradient(oracle):
+    """Forward over reverse: the tangent of the oracle's own gradient along
+    Cdot equals central differences of that gradient (affine in C away from
+    argmin ties, so exact up to rounding); the loss's tangent equals central
+    differences of the loss; with Cdot = 1 it is the Hessian diagonal."""
+    g = synth.rng(114)
+    N, d, k = 300, 3, 4
+    X = g.normal(size=(N, d))
+    Cm = g.normal(size=(k, d)) * 1.5
+    Cd = g.normal(size=(k, d))
+    ybar = 0.8
+    ydot, Gd = oracle.kmeans_fwd_rev(X, Cm, Cd, ybar)
+    h = 1e-5
+    lp, ap, _, gp = oracle.kmeans(X, Cm + h * Cd, ybar)
+    lm, am, _, gm = oracle.kmeans(X, Cm - h * Cd, ybar)
+    _, a0, _, _ = oracle.kmeans(X, Cm, ybar)
+    # the steps move no point across an argmin tie
+    np.testing.assert_array_equal(ap, a0)
+    np.testing.assert_array_equal(am, a0)
+    np.testing.assert_allclose(Gd, (gp - gm) / (2 * h), rtol=1e-6, atol=1e-6)
+    assert abs(ydot - (lp - lm) / (2 * h)) <= 1e-6 * (1 + abs(ydot))
+    _, Hd = oracle.kmeans_fwd_rev(X, Cm, np.ones((k, d)), ybar)
+    np.testing.assert_allclose(Hd, oracle.kmeans_hessdiag(X, Cm, ybar=ybar), rtol=1e-13)

@@ -8,12 +8,14 @@ synthetic inputs, at the sizes the metric is quoted on:
   * max scan VJP, n = 2^28 FP32
 Inputs are resident in HBM when the timed region starts and every array is
 larger than L2 (no flush needed).  ``value`` is VJP elements/s over the
-whole job; the JSON line also carries the roofline of the dominant call,
+whole job; the JSON line also carries the HBM roofline of the dominant call,
 the VJP/primal time ratio per operator, the oracle CPU baseline, clocks
-sampled during the timed region, and an end-to-end figure through host
-buffers.
+sampled during the timed region, an end-to-end figure through host
+buffers, and (at N = 1, unless --no-rows) ``rows``: one summary measurement
+of each other configuration of the hot path (product reduce, reduce_by_index
+and scatter, the 4096-segment batch, k-means, serving).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl adpar|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl adpar|reference] [--no-rows]
 
 ``--workload NAME`` measures one other row of the hot path instead (one
 JSON line each; these are measurements, not the headline line):
@@ -345,16 +347,18 @@ def run_adpar(args, ws, rank, local):
     dom = max(per_call, key=lambda k: per_call[k]["ms"])
     dcall = [c for c in CALLS if c[0] == dom][0]
     kernel = "adpar_vjp_scan(%s): init + primal pass + adjoint pass" % dom
+    # the roofline of every scan row is HBM bandwidth on its algorithmic bytes
+    ach = dcall[4] * (1 << dcall[3]) / (per_call[dom]["ms"] / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": LINREC_F64_TRAFFIC_PER_CALL if dom == "linrec_f64" else None,
+                "kernel": kernel, "peak_source": peak_kind,
+                "algorithmic_bytes_per_element": dcall[4], "elements_per_launch": 1 << dcall[3]}
     if dom == "linrec_f64":
-        # FP64 arithmetic, not HBM, bounds this call on GB300
-        roofline = {"bound": "alu", "achieved": f64["fp64_tflops"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": f64["fp64_frac_of_derived_peak"], "traffic": LINREC_F64_TRAFFIC_PER_CALL,
-                    "kernel": kernel, "peak_source": "derived (FP64 lanes x SMs x max SM clock)",
-                    "hbm_frac_of_measured": f64["hbm_frac_of_measured"]}
-    else:
-        ach = dcall[4] * (1 << dcall[3]) / (per_call[dom]["ms"] / 1000.0) / 1e9
-        roofline = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                    "traffic": None, "kernel": kernel, "peak_source": peak_kind}
+        # GB300's FP64 rate co-bounds this call: its arithmetic against the
+        # derived FP64 peak, beside the HBM fraction
+        roofline["fp64_alu"] = {"achieved_tflops": f64["fp64_tflops"], "peak_tflops": FP64_PEAK_TFLOPS,
+                                "frac": f64["fp64_frac_of_derived_peak"],
+                                "peak_source": "derived (FP64 lanes x SMs x max SM clock)"}
 
     # primal (forward operator) times for the AD overhead ratio
     for name, op, dt, lg, vb, pb in CALLS:
@@ -436,6 +440,8 @@ def run_adpar(args, ws, rank, local):
                 "clocks": clocks, "e2e": e2e}
         if ws == 1:
             line["cpu_baseline"] = cpu_baseline()
+            if not args.no_rows:
+                line["rows"] = default_rows(args)
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
@@ -476,8 +482,7 @@ def _line(workload, **kw):
     hbm, kind = measured_peaks()
     d = {"workload": workload, "data": "synthetic", "peak_hbm_gbs": hbm, "peak_source": kind}
     d.update(kw)
-    print(json.dumps(d), flush=True)
-    return 0
+    return d
 
 
 def _dev(x):
@@ -649,7 +654,24 @@ def row_jvp(args):
                                "sample": "linear recurrence, n = 2^20 FP64"})
 
 
-def row_hist(args):
+# algorithmic bytes per element of the reduce_by_index VJPs: + reads the
+# indices and writes the adjoint (the bins' cotangents stay in L2); max also
+# reads the values in the recompute pass and the indices again in the
+# adjoint pass; * reads values and indices in both passes
+HIST_ALG_BYTES = {"add": 8, "max": 16, "mul": 20}
+HIST_CASES = [(m, dist) for m in (256, 1 << 16, 1 << 22) for dist in ("uniform", "zipf")]
+
+
+def hist_inputs(n=1 << 27, cases=HIST_CASES):
+    """Seeded reduce_by_index inputs of every (m, distribution), drawn in parallel threads."""
+    import concurrent.futures as cf
+    from paper_2202_10297_gb300 import synth
+    with cf.ThreadPoolExecutor(max_workers=len(cases)) as ex:
+        futs = {c: ex.submit(synth.hist, n, c[0], c[1], seed=synth.SEED_BASE + 2) for c in cases}
+        return {c: f.result() for c, f in futs.items()}
+
+
+def row_hist(args, inputs=None):
     """reduce_by_index VJPs (Sec. 5.1.2), n = 2^27 FP32."""
     import torch
     from oracle import oracle as O
@@ -657,23 +679,22 @@ def row_hist(args):
     from paper_2202_10297_gb300 import synth
     hbm, _ = measured_peaks()
     n = 1 << 27
-    # algorithmic bytes per element: inputs read once + adjoint written once
-    alg = {"add": 8, "max": 12, "mul": 12}
+    alg = HIST_ALG_BYTES
+    inputs = inputs or hist_inputs(n)
     cases = {}
-    for m in (256, 1 << 16, 1 << 22):
-        for dist in ("uniform", "zipf"):
-            vals, inds, hsbar = synth.hist(n, m, dist, seed=synth.SEED_BASE + 2)
-            v, ix, hb = _dev(vals), _dev(inds), _dev(hsbar)
-            vb = torch.empty_like(v)
-            for op in ("add", "max", "mul"):
-                wk = A.workspace(A.adpar_workspace_size(A.RULE_HIST, A.OPS[op], A.F32, n, m), "cuda")
-                f = lambda: A.adpar_vjp_hist(op, ix, m, hb, vals=v, valsbar=vb, work=wk)
-                fp = lambda: A.adpar_hist(op, v, ix, m, work=wk)
-                t, tp = _cuda_ms(f, 5, 2), _cuda_ms(fp, 5, 2)
-                cases["%s_m%d_%s" % (op, m, dist)] = {
-                    "ms": t, "elements_per_s": n / t * 1e3, "gbs": alg[op] * n / t / 1e6,
-                    "hbm_frac_of_measured": alg[op] * n / t / 1e6 / hbm, "primal_ms": tp, "vjp_primal_ratio": t / tp}
-            del v, ix, hb, vb
+    for (m, dist) in HIST_CASES:
+        vals, inds, hsbar = inputs[(m, dist)]
+        v, ix, hb = _dev(vals), _dev(inds), _dev(hsbar)
+        vb = torch.empty_like(v)
+        for op in ("add", "max", "mul"):
+            wk = A.workspace(A.adpar_workspace_size(A.RULE_HIST, A.OPS[op], A.F32, n, m), "cuda")
+            f = lambda: A.adpar_vjp_hist(op, ix, m, hb, vals=v, valsbar=vb, work=wk)
+            fp = lambda: A.adpar_hist(op, v, ix, m, work=wk)
+            t, tp = _cuda_ms(f, 5, 2), _cuda_ms(fp, 5, 2)
+            cases["%s_m%d_%s" % (op, m, dist)] = {
+                "ms": t, "elements_per_s": n / t * 1e3, "gbs": alg[op] * n / t / 1e6,
+                "hbm_frac_of_measured": alg[op] * n / t / 1e6 / hbm, "primal_ms": tp, "vjp_primal_ratio": t / tp}
+        del v, ix, hb, vb
     vals, inds, hsbar = synth.hist(1 << 20, 256, "zipf", seed=1)
     orate = _oracle_rate(lambda: O.hist_vjp("max", vals, inds, 256, hsbar), 1 << 20, 2.0)
     return _line("hist", metric="VJP elements/s and % of HBM", n=n, algorithmic_bytes_per_element=alg,
@@ -770,7 +791,16 @@ def row_scan_wide(args):
                                "sample": "2x2 matrix recurrence, n = 2^18"})
 
 
-def row_scatter(args):
+def scatter_inputs(n=1 << 28, m=1 << 26):
+    """The seeded random and sorted index sets of the scatter VJP, drawn in parallel threads."""
+    import concurrent.futures as cf
+    from paper_2202_10297_gb300 import synth
+    with cf.ThreadPoolExecutor(max_workers=2) as ex:
+        futs = {srt: ex.submit(synth.scatter, n, m, sort=srt, seed=synth.SEED_BASE + 2) for srt in (False, True)}
+        return {srt: f.result()[0] for srt, f in futs.items()}
+
+
+def row_scatter(args, inputs=None, map_acc=True):
     """Scatter VJP (Sec. 5.3) and map-accumulator VJPs (Sec. 5.4)."""
     import torch
     from oracle import oracle as O
@@ -778,9 +808,10 @@ def row_scatter(args):
     from paper_2202_10297_gb300 import synth
     hbm, _ = measured_peaks()
     n, m = 1 << 28, 1 << 26
+    inputs = inputs or scatter_inputs(n, m)
     cases = {}
     for sort in (False, True):
-        is_, _, _ = synth.scatter(n, m, sort=sort, seed=synth.SEED_BASE + 2)
+        is_ = inputs[sort]
         it = _dev(is_)
         ysbar = torch.randn(n, device="cuda")
         vsbar = torch.empty(m, device="cuda")
@@ -794,7 +825,7 @@ def row_scatter(args):
         del it, ysbar, vsbar
     nj = 1 << 26
     for g, na, width in (("gather", 1 << 20, 1), ("scale", 1 << 20, 1), ("gather", 4096, 1),
-                         ("sqdist_row", 256, 32)):
+                         ("sqdist_row", 256, 32)) if map_acc else ():
         as_, is_, ws, xsbar = synth.map_acc(nj // width if width > 1 else nj, na, width=width, seed=3)
         at, it, wt, xt = _dev(as_), _dev(is_), _dev(ws), _dev(xsbar)
         asb = torch.empty_like(at)
@@ -905,26 +936,91 @@ def row_batch(args):
 
 
 def row_serve(args):
-    """Poisson arrivals at 50/80/95% of the measured capacity vs one call at a time."""
-    import torch
+    """Poisson arrivals at 50/80/95% of the measured capacity vs one call at a time:
+    mixed operators, FP32 and FP64, sizes 2^U[10,24], each request on its own
+    inputs, outputs and workspace allocated from a 32 GiB device arena."""
     from paper_2202_10297_gb300 import adpar as A
     from paper_2202_10297_gb300 import serve as S
     A.lib()
     srv = S.Server(budget_bytes=32 << 30, slots=8, max_n=1 << 24)
-    warm = S.make_requests(200, rate=None, seed=1)
-    srv.serve(warm)
-    sat = S.make_requests(2000, rate=None, seed=2)
-    cap = srv.serve(sat)
-    plain_slot = S.Slot(1 << 24, torch.device("cuda"))
-    cap_plain = S.serve_plain(S.make_requests(2000, rate=None, seed=2), srv.pool, plain_slot)
+    srv.serve(S.make_requests(200, rate=None, seed=1))  # warm-up
+    cap = srv.serve(S.make_requests(2000, rate=None, seed=2))
+    cap_plain = S.serve_plain(S.make_requests(2000, rate=None, seed=2), srv.pool, srv.arena)
     out = {"capacity": cap, "capacity_plain": cap_plain, "sweep": {}}
     for frac in (0.5, 0.8, 0.95):
         rate = frac * cap["throughput_rps"]
-        reqs = S.make_requests(3000, rate=rate, seed=3)
-        res = srv.serve(reqs)
-        res_plain = S.serve_plain(S.make_requests(3000, rate=rate, seed=3), srv.pool, plain_slot)
+        res = srv.serve(S.make_requests(3000, rate=rate, seed=3))
+        res_plain = S.serve_plain(S.make_requests(3000, rate=rate, seed=3), srv.pool, srv.arena)
         out["sweep"]["%d%%" % int(frac * 100)] = {"rate_rps": rate, "served": res, "plain": res_plain}
+    out["peak_arena_bytes"] = srv.peak_resident
     return _line("serve", metric="served p50/p99 latency and throughput", budget_gib=32, slots=8, **out)
+
+
+def _sig(x, k=4):
+    """Floats rounded to k significant digits (keeps the JSON line short)."""
+    if isinstance(x, float):
+        return float("%.*g" % (k, x))
+    if isinstance(x, dict):
+        return {a: _sig(b, k) for a, b in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [_sig(v, k) for v in x]
+    return x
+
+
+def default_rows(args):
+    """The other configurations of the hot path, each measured once on this
+    GPU with CUDA events and summarised (the full per-case lines come from
+    ``--workload NAME``): the product reduce at 65536 FP64 with 0/1/2 zeros,
+    reduce_by_index at 2^27 and scatter at 2^26 -> 2^28, the 4096-segment
+    batch, the k-means loss and gradient, and the served form."""
+    t0 = time.perf_counter()
+    hin = hist_inputs()
+    sin = scatter_inputs()
+    t_gen = time.perf_counter() - t0
+    prod = row_prod(args)
+    hist = row_hist(args, hin)
+    del hin
+    sc = row_scatter(args, sin, map_acc=False)
+    del sin
+    batch = row_batch(args)
+    km = row_kmeans(args)
+    srv = row_serve(args)
+    rows = {}
+    c1 = {k: {kk: v[kk] for kk in ("vjp_value_us", "vjp_logdomain_us", "primal_us", "vjp_primal_ratio",
+                                   "launches_per_call", "oracle_elements_per_s")}
+          for k, v in prod["cases"].items() if k.startswith("n65536")}
+    big = prod["cases"]["n2^28_f64_value"]
+    c1["n2^28_f64"] = {"ms": big["ms"], "hbm_frac_of_measured": big["hbm_frac_of_measured"],
+                       "vjp_primal_ratio": big["vjp_primal_ratio"], "bytes_per_element": 16}
+    rows["config1_prod_reduce"] = c1
+    rows["config3_hist"] = {
+        "n": hist["n"], "bytes_per_element": hist["algorithmic_bytes_per_element"],
+        "fields": ["ms", "hbm_frac_of_measured", "vjp_primal_ratio"],
+        "cases": {k: [v["ms"], v["hbm_frac_of_measured"], v["vjp_primal_ratio"]] for k, v in hist["cases"].items()},
+        "oracle": hist["cpu_baseline"]}
+    rows["config3_scatter"] = {
+        "n": 1 << 28, "m": 1 << 26, "bytes_per_element": 16,
+        "cases": {k: {kk: v[kk] for kk in ("ms", "hbm_frac_of_measured", "sector_frac_of_measured")}
+                  for k, v in sc["cases"].items()},
+        "oracle": sc["cpu_baseline"]}
+    rows["config4_batch"] = {k: batch[k] for k in ("segments", "elements", "graph_ms", "plain_calls_ms",
+                                                   "speedup_vs_plain", "elements_per_s", "hbm_frac_of_measured",
+                                                   "tuned_config")}
+    rows["config5_kmeans"] = {"N": km["N"], "d": km["d"], "k": km["k"], "vjp_ms": km["vjp_ms"],
+                              "forward_ms": km["forward_ms"], "grad_and_hessdiag_ms": km["grad_and_hessdiag_ms"],
+                              "vjp_primal_ratio": km["vjp_primal_ratio"],
+                              "tensor_frac_of_tf32_peak": km["roofline"]["frac"],
+                              "hbm_frac_of_measured": km["roofline"]["hbm_frac"], "oracle": km["cpu_baseline"]}
+    sv = {"capacity_rps": srv["capacity"]["throughput_rps"],
+          "capacity_plain_rps": srv["capacity_plain"]["throughput_rps"],
+          "peak_arena_bytes": srv["peak_arena_bytes"], "budget_gib": srv["budget_gib"], "slots": srv["slots"]}
+    for load, r in srv["sweep"].items():
+        sv[load] = {"rate_rps": r["rate_rps"], "p50_ms": r["served"]["p50_ms"], "p99_ms": r["served"]["p99_ms"],
+                    "plain_p50_ms": r["plain"]["p50_ms"], "plain_p99_ms": r["plain"]["p99_ms"]}
+    rows["config5_serve"] = sv
+    rows["input_generation_s"] = t_gen
+    rows["wall_s"] = time.perf_counter() - t0
+    return _sig(rows)
 
 
 def _one_call(name, log2n):
@@ -988,7 +1084,7 @@ ROWS = {"prod": row_prod, "hist": row_hist, "hist_general": row_hist_general, "s
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="adpar", choices=["adpar", "reference"])
     ap.add_argument("--workload", default="scan",
@@ -997,12 +1093,15 @@ def main():
     ap.add_argument("--call", default="scan-linrec-f64", choices=sorted(CALLS_ONE))
     ap.add_argument("--log2n", type=int, default=24)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--no-rows", action="store_true",
+                    help="print the headline line without the other configurations' rows")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
     if args.workload != "scan":
-        return ROWS[args.workload](args)
+        print(json.dumps(ROWS[args.workload](args)), flush=True)
+        return 0
     return run_adpar(args, ws, rank, local)
 
 

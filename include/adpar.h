@@ -78,7 +78,10 @@ typedef enum {
     ADPAR_RULE_REDUCE_GENERAL = 6,
     ADPAR_RULE_SCAN_VEC = 7,  /* m = the vector length d */
     ADPAR_RULE_HIST_GENERAL = 8,
-    ADPAR_RULE_SCAN_WIDE = 9
+    ADPAR_RULE_SCAN_WIDE = 9,
+    ADPAR_RULE_JVP_REDUCE = 10,     /* adpar_jvp_reduce                       */
+    ADPAR_RULE_JVP_HIST = 11,       /* adpar_jvp_hist; m = bins               */
+    ADPAR_RULE_KMEANS_FWD_REV = 12  /* adpar_kmeans_fwd_rev; n = points, m = centroids */
 } adpar_rule;
 
 /* or'ed into the rule of adpar_workspace_size: the smallest workspace the
@@ -313,6 +316,76 @@ int adpar_jvp_scan(adpar_opdesc desc, int64_t n, const void *a, const void *b, c
                    const void *bdot, void *ys_a, void *ys_b, void *ysdot_a, void *ysdot_b, void *work,
                    size_t work_bytes, void *stream);
 
+/* Log-domain form of a tangent whose value may leave the FP64 range (the
+ * * rules below): ln|tangent| (-inf when it is 0) and its sign. */
+typedef struct {
+    double log_abs;
+    int32_t sign;      /* -1, 0 or +1 */
+    int32_t reserved;
+} adpar_jvp_aux;
+
+/* Forward mode (JVP) of reduce, the tangent of y = reduce (.) a along adot
+ * (Sec. 3's dual numbers through the operators of Sec. 5.1 and 5.1.1):
+ *   ADD      ydot = sum_i adot_i;
+ *   MIN/MAX  ydot = adot_{i_y}, i_y the recomputed argmin/argmax with the
+ *            lowest index on ties (0 for n = 0);
+ *   MUL      the product rule on the recomputed forward sweep (zero count z,
+ *            lowest zero i0, scaled product p of the nonzeros):
+ *            z = 0: ydot = p sum_i adot_i / a_i;  z = 1: ydot = p adot_i0;
+ *            z >= 2: ydot = 0.
+ * Arguments:
+ *   n           number of elements (0 allowed: ydot = 0).
+ *   a, adot     [n] inputs and their tangent (dtype); a may be NULL for ADD
+ *               when y_out is NULL.
+ *   y_out       nullable device scalar: the recomputed y.
+ *   ydot_out    device scalar (dtype): the tangent, rounded to dtype (0 or
+ *               subnormal when a long product underflows).
+ *   ydot_aux    nullable device adpar_jvp_aux: ln|ydot| and its sign,
+ *               exact where the value under- or overflows.
+ * Workspace: adpar_workspace_size(ADPAR_RULE_JVP_REDUCE, desc, n, 0).
+ * Errors: ADPAR_ERR_INVALID (bad op/dtype/width, n < 0, missing pointers),
+ * ADPAR_ERR_ALIGN, ADPAR_ERR_WORKSPACE; nothing is enqueued on error. */
+int adpar_jvp_reduce(adpar_opdesc desc, int64_t n, const void *a, const void *adot, void *y_out,
+                     void *ydot_out, adpar_jvp_aux *ydot_aux, void *work, size_t work_bytes, void *stream);
+
+/* Forward mode of reduce_by_index (Sec. 5.1.2 on dual numbers): per bin b
+ * the tangent of hs[b] = reduce (.) {vals_i : inds_i = b} along vdot, with
+ * the cases of adpar_jvp_reduce per bin (ADD is reduce_by_index + of vdot;
+ * MIN/MAX the tangent of the bin's lowest-index extremum; MUL the product
+ * rule on the bin's zero count, lowest zero and scaled product).  Indices
+ * outside [0, m) are ignored.
+ * Arguments:
+ *   n, m          elements and bins.
+ *   vals, vdot    [n] values and tangents (dtype); vals may be NULL for ADD
+ *                 when hs_out is NULL.
+ *   inds          [n] bin indices (itype).
+ *   hs_out        nullable [m]: the recomputed bins.
+ *   hsdot_out     [m] (dtype): the bins' tangents.
+ *   hsdot_aux     nullable [m] adpar_jvp_aux, MUL only (else
+ *                 ADPAR_ERR_UNSUPPORTED): ln|tangent| and sign per bin.
+ * Workspace: adpar_workspace_size(ADPAR_RULE_JVP_HIST, desc, n, m). */
+int adpar_jvp_hist(adpar_opdesc desc, int64_t n, int64_t m, const void *vals, const void *vdot,
+                   const void *inds, int itype, void *hs_out, void *hsdot_out, adpar_jvp_aux *hsdot_aux,
+                   void *work, size_t work_bytes, void *stream);
+
+/* Forward mode of scatter (Sec. 5.3): ys = scatter xs is vs is linear in
+ * (xs, vs), so ysdot = xsdot with ysdot[is_j] = vsdot_j.  ysdot_inout [n]
+ * holds xsdot on entry and ysdot on return; vsdot [m]; indices outside
+ * [0, n) are skipped; duplicate indices are a caller error.  No workspace. */
+int adpar_jvp_scatter(int dtype, int64_t n, int64_t m, const void *is, int itype, const void *vsdot,
+                      void *ysdot_inout, void *stream);
+
+/* Forward mode of map with a free array (Sec. 5.4):
+ *   xs_j = g(as[is_j, :], ws[j, :])  ->  xsdot_j = dg/da asdot[is_j, :] + dg/dw wsdot[j, :]
+ *   GATHER      xsdot_j = asdot[is_j]
+ *   SCALE       xsdot_j = asdot[is_j] ws_j + as[is_j] wsdot_j
+ *   SQDIST_ROW  xsdot_j = sum_k 2 (ws[j,k] - as[is_j,k]) (wsdot[j,k] - asdot[is_j,k])
+ * An index outside [0, na) gives xsdot_j = 0.  Arguments as for
+ * adpar_map_acc, plus asdot [na*width] (required), wsdot [nj*width]
+ * (nullable: no tangent on ws) and xsdot [nj] (output).  No workspace. */
+int adpar_jvp_map_acc(int gfun, int dtype, int64_t nj, int64_t na, int width, const void *as, const void *is,
+                      int itype, const void *ws, const void *asdot, const void *wsdot, void *xsdot, void *stream);
+
 /* The primal forward scan ys = scan (.) as (Sec. 5.2's forward sweep), on
  * its own.  It is the baseline of the AD overhead ratio (VJP time / primal
  * time, Sec. 7).  Arguments as for adpar_vjp_scan; ys_a (and ys_b for
@@ -452,7 +525,8 @@ int adpar_kmeans_vjp(int64_t N, int d, int k, const float *X, const float *C, co
                      size_t work_bytes, void *stream);
 
 /* Hessian diagonal of the same cost in C, the second-order information of
- * Sec. 7.4 (the paper nests forward mode over this VJP): with every point's
+ * Sec. 7.4, in closed form from the counts (adpar_kmeans_fwd_rev below
+ * obtains it by forward mode nested over the VJP): with every point's
  * argmin held fixed (the cost is piecewise quadratic in C),
  *   Hdiag[k][j] = d^2 loss / dc_kj^2 = 2 ybar cnt_k,
  * cnt_k the number of points whose argmin is k.  It reads the counts that
@@ -464,6 +538,23 @@ int adpar_kmeans_vjp(int64_t N, int d, int k, const float *X, const float *C, co
  * Flags: ADPAR_ACCUMULATE (Hdiag += ...). */
 int adpar_kmeans_hessdiag(int k, const float *ybar, const void *work, size_t work_bytes, float *Hdiag,
                           uint32_t flags, void *stream);
+
+/* Forward over reverse for the same cost (Sec. 7.4 nests forward mode over
+ * the VJP): the reverse sweep of adpar_kmeans_vjp run on dual numbers along
+ * a tangent Cdot of the centroids.  With k*_i the certified argmin of point
+ * i (recomputed by adpar_kmeans_vjp's forward part; it has no tangent):
+ *   ydot     = sum_i sum_j 2 (c_{k*_i j} - x_ij) cdot_{k*_i j}   (loss tangent)
+ *   Cbardot[k] = sum_{i: k*_i = k} ybar (-2)(0 - cdot_k) = 2 ybar cnt_k cdot_k,
+ * the tangent of the gradient Cbar, i.e. the Hessian-vector product H Cdot.
+ * The cost's Hessian in C is diagonal (2 ybar cnt_k on centroid k's
+ * coordinates), so Cdot = 1 gives the Hessian diagonal.
+ * Arguments: N, d, k, X, C as for adpar_kmeans_vjp; Cdot [k*32] FP32;
+ * ybar device FP32 scalar; ydot_out nullable device FP32 scalar; Cbardot
+ * [k*32] FP32 output.  Flags: ADPAR_ACCUMULATE (Cbardot += ...).
+ * Workspace: adpar_workspace_size(ADPAR_RULE_KMEANS_FWD_REV, desc, N, k). */
+int adpar_kmeans_fwd_rev(int64_t N, int d, int k, const float *X, const float *C, const float *Cdot,
+                         const float *ybar, float *ydot_out, float *Cbardot, uint32_t flags, void *work,
+                         size_t work_bytes, void *stream);
 
 /* ------------------------------------------------------------------ */
 /* batched VJPs: many instances in one persistent launch               */

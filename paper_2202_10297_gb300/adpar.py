@@ -24,7 +24,7 @@ WIDE = {OP_LINREC: 2, OP_MATREC2: 6}  # element width D of adpar_vjp_scan_wide
 G_GATHER, G_SCALE, G_SQDIST_ROW = 0, 1, 2
 GFUNS = {"gather": G_GATHER, "scale": G_SCALE, "sqdist_row": G_SQDIST_ROW}
 RULE_REDUCE, RULE_SCAN, RULE_HIST, RULE_SCATTER, RULE_MAP_ACC, RULE_KMEANS, RULE_REDUCE_GENERAL, RULE_SCAN_VEC, \
-    RULE_HIST_GENERAL, RULE_SCAN_WIDE = range(10)
+    RULE_HIST_GENERAL, RULE_SCAN_WIDE, RULE_JVP_REDUCE, RULE_JVP_HIST, RULE_KMEANS_FWD_REV = range(13)
 WS_MINIMAL = 0x100  # or'ed into a rule: the smallest accepted workspace
 ACCUMULATE, PROD_LOGDOMAIN, SCATTER_RESTORE, FULL_LIN_O = 0x1, 0x4, 0x8, 0x10
 OK, ERR_INVALID, ERR_TIMEOUT, ERR_TOO_LARGE = 0, 1, 6, 7
@@ -47,6 +47,14 @@ class ProdAux(C.Structure):
 
 
 PROD_AUX_BYTES = C.sizeof(ProdAux)
+
+
+class JvpAux(C.Structure):
+    _fields_ = [("log_abs", C.c_double), ("sign", C.c_int32), ("reserved", C.c_int32)]
+
+
+JVP_AUX_BYTES = C.sizeof(JvpAux)
+JVP_AUX_DTYPE = [("log_abs", "<f8"), ("sign", "<i4"), ("reserved", "<i4")]
 
 _lib = None
 _VP = C.c_void_p
@@ -112,6 +120,14 @@ def _bind_optional(L):
                              C.c_size_t, _VP],
         "adpar_reduce": [OpDesc, C.c_int64, _VP, _VP, _VP, _VP, _VP, C.c_size_t, _VP],
         "adpar_selftest_timeout": [_VP, C.c_size_t, _VP],
+        "adpar_jvp_reduce": [OpDesc, C.c_int64, _VP, _VP, _VP, _VP, _VP, _VP, C.c_size_t, _VP],
+        "adpar_jvp_hist": [OpDesc, C.c_int64, C.c_int64, _VP, _VP, _VP, C.c_int, _VP, _VP, _VP, _VP, C.c_size_t,
+                           _VP],
+        "adpar_jvp_scatter": [C.c_int, C.c_int64, C.c_int64, _VP, C.c_int, _VP, _VP, _VP],
+        "adpar_jvp_map_acc": [C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int, _VP, _VP, C.c_int, _VP, _VP, _VP,
+                              _VP, _VP],
+        "adpar_kmeans_fwd_rev": [C.c_int64, C.c_int, C.c_int, _VP, _VP, _VP, _VP, _VP, _VP, C.c_uint32, _VP,
+                                 C.c_size_t, _VP],
         "adpar_hist": [OpDesc, C.c_int64, C.c_int64, _VP, _VP, C.c_int, _VP, _VP, _VP, _VP, C.c_size_t, _VP],
         "adpar_scatter": [C.c_int, C.c_int64, C.c_int64, _VP, C.c_int, _VP, _VP, _VP, _VP],
         "adpar_map_acc": [C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_int, _VP, _VP, C.c_int, _VP, _VP, _VP],
@@ -672,3 +688,121 @@ def adpar_selftest_timeout(work=None, stream=None):
         work = workspace(512)
     _check("adpar_selftest_timeout", lib().adpar_selftest_timeout(_ptr(work), work.numel(), _stream(stream)))
     return work
+
+
+# ------------------------------------------------------------ forward mode
+def _aux_records(buf, count):
+    import numpy as np
+    return np.frombuffer(buf.cpu().numpy().tobytes(), dtype=np.dtype(JVP_AUX_DTYPE))[:count]
+
+
+def adpar_jvp_reduce(op, a, adot, want_y=False, want_aux=False, work=None, stream=None):
+    """Forward mode of reduce (C: adpar_jvp_reduce).  Returns a dict with
+    ``ydot`` (device scalar), ``y`` when asked for, and ``aux`` (ln|ydot|,
+    sign; read back to the host) when asked for."""
+    opc = OPS[op] if isinstance(op, str) else int(op)
+    n = adot.numel()
+    dt = _dtype_code(adot)
+    if a is not None and (a.dtype != adot.dtype or a.numel() != n):
+        raise ValueError("a and adot must share dtype and length")
+    ydot = torch.empty(1, dtype=adot.dtype, device=adot.device)
+    y = torch.empty(1, dtype=adot.dtype, device=adot.device) if want_y else None
+    aux = torch.empty(JVP_AUX_BYTES, dtype=torch.uint8, device=adot.device) if want_aux else None
+    need = adpar_workspace_size(RULE_JVP_REDUCE, opc, dt, n)
+    if work is None or work.numel() < need:
+        work = workspace(need, adot.device)
+    _check("adpar_jvp_reduce", lib().adpar_jvp_reduce(OpDesc(opc, dt, 1), n, _ptr(a), _ptr(adot), _ptr(y),
+                                                      _ptr(ydot), _ptr(aux), _ptr(work), work.numel(),
+                                                      _stream(stream)))
+    out = {"ydot": ydot}
+    if want_y:
+        out["y"] = y
+    if want_aux:
+        out["aux"] = _aux_records(aux, 1)[0]
+    return out
+
+
+def adpar_jvp_hist(op, vals, vdot, inds, m, want_hs=False, want_aux=False, work=None, stream=None):
+    """Forward mode of reduce_by_index (C: adpar_jvp_hist).  Returns a dict
+    with ``hsdot`` [m], ``hs`` [m] when asked for, and ``aux`` (structured
+    numpy array of ln|hsdot|, sign; * only) when asked for."""
+    opc = OPS[op] if isinstance(op, str) else int(op)
+    n = inds.numel()
+    dt = _dtype_code(vdot)
+    for t in (vals, vdot):
+        if t is not None and (t.dtype != vdot.dtype or t.numel() != n):
+            raise ValueError("vals, vdot and inds must share length (and vals, vdot dtype)")
+    hsdot = torch.empty(m, dtype=vdot.dtype, device=vdot.device)
+    hs = torch.empty(m, dtype=vdot.dtype, device=vdot.device) if want_hs else None
+    aux = torch.empty(max(m, 1) * JVP_AUX_BYTES, dtype=torch.uint8, device=vdot.device) if want_aux else None
+    need = adpar_workspace_size(RULE_JVP_HIST, opc, dt, n, m)
+    if work is None or work.numel() < need:
+        work = workspace(need, vdot.device)
+    _check("adpar_jvp_hist", lib().adpar_jvp_hist(OpDesc(opc, dt, 1), n, m, _ptr(vals), _ptr(vdot), _ptr(inds),
+                                                  _itype_code(inds), _ptr(hs), _ptr(hsdot), _ptr(aux), _ptr(work),
+                                                  work.numel(), _stream(stream)))
+    out = {"hsdot": hsdot}
+    if want_hs:
+        out["hs"] = hs
+    if want_aux:
+        out["aux"] = _aux_records(aux, m)
+    return out
+
+
+def adpar_jvp_scatter(is_, vsdot, ysdot_inout, stream=None):
+    """Forward mode of scatter (C: adpar_jvp_scatter): ``ysdot_inout`` holds
+    xsdot on entry and ysdot on return."""
+    if vsdot.dtype != ysdot_inout.dtype or vsdot.numel() != is_.numel():
+        raise ValueError("vsdot must match is_ in length and ysdot in dtype")
+    _check("adpar_jvp_scatter", lib().adpar_jvp_scatter(_dtype_code(vsdot), ysdot_inout.numel(), is_.numel(),
+                                                        _ptr(is_), _itype_code(is_), _ptr(vsdot), _ptr(ysdot_inout),
+                                                        _stream(stream)))
+    return ysdot_inout
+
+
+def adpar_jvp_map_acc(g, as_, is_, asdot, ws=None, wsdot=None, width=1, stream=None):
+    """Forward mode of map with a free array (C: adpar_jvp_map_acc).  Returns xsdot [nj]."""
+    gc = GFUNS[g] if isinstance(g, str) else int(g)
+    nj = is_.numel()
+    if asdot.dtype != as_.dtype or asdot.numel() != as_.numel():
+        raise ValueError("asdot must match as_")
+    for t in (ws, wsdot):
+        if t is not None and (t.dtype != as_.dtype or t.numel() != nj * width):
+            raise ValueError("ws and wsdot must hold nj * width values of as_'s dtype")
+    xsdot = torch.empty(nj, dtype=as_.dtype, device=as_.device)
+    _check("adpar_jvp_map_acc", lib().adpar_jvp_map_acc(gc, _dtype_code(as_), nj, as_.numel() // width, width,
+                                                        _ptr(as_), _ptr(is_), _itype_code(is_), _ptr(ws),
+                                                        _ptr(asdot), _ptr(wsdot), _ptr(xsdot), _stream(stream)))
+    return xsdot
+
+
+def adpar_kmeans_fwd_rev(X, C_, Cdot, ybar=1.0, Cbardot=None, accumulate=False, work=None, stream=None):
+    """Forward over reverse for the k-means cost (C: adpar_kmeans_fwd_rev):
+    the tangent along Cdot of the gradient in C (a Hessian-vector product)
+    and of the loss.  Returns (ydot device scalar, Cbardot [k, d])."""
+    N, d = X.shape
+    k = C_.shape[0]
+    for t in (X, C_, Cdot):
+        if t.dtype != torch.float32:
+            raise TypeError("k-means takes FP32 X, C and Cdot")
+    if Cdot.shape != C_.shape:
+        raise ValueError("Cdot must have C's shape")
+    yb = _scalar_dev(ybar, C_)
+    ydot = torch.empty(1, dtype=torch.float32, device=C_.device)
+    if Cbardot is None:
+        Cbardot = torch.zeros_like(C_) if accumulate else torch.empty_like(C_)
+    need = adpar_workspace_size(RULE_KMEANS_FWD_REV, 0, F32, N, k)
+    if work is None or work.numel() < need:
+        work = workspace(need, C_.device)
+    _check("adpar_kmeans_fwd_rev", lib().adpar_kmeans_fwd_rev(N, d, k, _ptr(X), _ptr(C_), _ptr(Cdot), _ptr(yb),
+                                                              _ptr(ydot), _ptr(Cbardot),
+                                                              ACCUMULATE if accumulate else 0, _ptr(work),
+                                                              work.numel(), _stream(stream)))
+    return ydot, Cbardot
+
+
+def adpar_kmeans_hessdiag_fwd_rev(X, C_, ybar=1.0, stream=None):
+    """Hessian diagonal of the k-means cost in C by forward over reverse: the
+    cost's Hessian is diagonal, so H 1 is its diagonal."""
+    _, H = adpar_kmeans_fwd_rev(X, C_, torch.ones_like(C_), ybar=ybar, stream=stream)
+    return H

@@ -7,13 +7,16 @@ intermediate) and returns the adjoints the paper's rule gives.
 
     scan(op, a, b=None)           inclusive scan; LINREC returns (A, B); reverse
                                   and forward mode (torch.autograd.forward_ad)
-    reduce(op, a)                 0-dim result
+    reduce(op, a)                 0-dim result; reverse and forward mode
     reduce_by_index(op, vals, inds, m, b=None)
-                                  LINREC (b given) by the general rule
+                                  LINREC (b given) by the general rule; the
+                                  special rules also in forward mode
     scan_wide(op, a)              scan over [n, d] elements ("linrec", "matrec2")
-    scatter(xs, is_, vs)          out of place: xs is not modified
-    map_acc(g, as_, is_, ws=None, width=1)
-    kmeans_loss(X, C)             gradient with respect to C only
+    scatter(xs, is_, vs)          out of place: xs is not modified; both modes
+    map_acc(g, as_, is_, ws=None, width=1)   both modes
+    kmeans_loss(X, C)             gradient with respect to C only; forward
+                                  mode in C
+    kmeans_hvp(X, C, Cdot)        forward over reverse: Hessian-vector product
 """
 import torch
 
@@ -68,7 +71,15 @@ class _Reduce(torch.autograd.Function):
         y, _ = A.adpar_reduce(op, a)
         ctx.op = op
         ctx.save_for_backward(a)
+        ctx.save_for_forward(a)
         return y.reshape(())
+
+    @staticmethod
+    def jvp(ctx, _, ta):
+        # forward mode: the dual-number reduce (adpar_jvp_reduce)
+        (a,) = ctx.saved_tensors
+        ta = torch.zeros_like(a) if ta is None else ta.contiguous()
+        return A.adpar_jvp_reduce(ctx.op, a, ta)["ydot"].reshape(())
 
     @staticmethod
     def backward(ctx, g):
@@ -88,7 +99,14 @@ class _Hist(torch.autograd.Function):
         hs, _ = A.adpar_hist(op, vals, inds, m)
         ctx.op, ctx.m = op, m
         ctx.save_for_backward(vals, inds)
+        ctx.save_for_forward(vals, inds)
         return hs
+
+    @staticmethod
+    def jvp(ctx, _, tv, _ti, _tm):
+        vals, inds = ctx.saved_tensors
+        tv = torch.zeros_like(vals) if tv is None else tv.contiguous()
+        return A.adpar_jvp_hist(ctx.op, vals, tv, inds, ctx.m)["hsdot"]
 
     @staticmethod
     def backward(ctx, g):
@@ -157,7 +175,17 @@ class _Scatter(torch.autograd.Function):
         ys = xs.clone()  # the functional form consumes a copy of xs
         A.adpar_scatter(is_, vs, ys)
         ctx.save_for_backward(is_)
+        ctx.save_for_forward(is_)
+        ctx.shapes = (xs, vs)
         return ys
+
+    @staticmethod
+    def jvp(ctx, txs, _ti, tvs):
+        (is_,) = ctx.saved_tensors
+        xs, vs = ctx.shapes
+        ysdot = torch.zeros_like(xs) if txs is None else txs.clone().contiguous()
+        tvs = torch.zeros_like(vs) if tvs is None else tvs.contiguous()
+        return A.adpar_jvp_scatter(is_, tvs, ysdot)
 
     @staticmethod
     def backward(ctx, g):
@@ -178,7 +206,15 @@ class _MapAcc(torch.autograd.Function):
         xs = A.adpar_map_acc(g, as_, is_, ws=ws, width=width)
         ctx.g, ctx.width = g, width
         ctx.save_for_backward(as_, is_, ws)
+        ctx.save_for_forward(as_, is_, ws)
         return xs
+
+    @staticmethod
+    def jvp(ctx, _g, tas, _ti, tws, _w):
+        as_, is_, ws = ctx.saved_tensors
+        tas = torch.zeros_like(as_) if tas is None else tas.contiguous()
+        tws = None if (tws is None or ws is None) else tws.contiguous()
+        return A.adpar_jvp_map_acc(ctx.g, as_, is_, tas, ws=ws, wsdot=tws, width=ctx.width)
 
     @staticmethod
     def backward(ctx, gx):
@@ -198,7 +234,17 @@ class _KMeans(torch.autograd.Function):
     def forward(ctx, X, C):
         out = A.adpar_kmeans_vjp(X, C, want_grad=False)
         ctx.save_for_backward(X, C)
+        ctx.save_for_forward(X, C)
         return out["loss"].reshape(())
+
+    @staticmethod
+    def jvp(ctx, tX, tC):
+        X, C = ctx.saved_tensors
+        if tX is not None and bool((tX != 0).any()):
+            raise NotImplementedError("kmeans_loss differentiates with respect to the centroids only")
+        tC = torch.zeros_like(C) if tC is None else tC.contiguous()
+        ydot, _ = A.adpar_kmeans_fwd_rev(X, C, tC)
+        return ydot.reshape(())
 
     @staticmethod
     def backward(ctx, g):
@@ -210,5 +256,12 @@ class _KMeans(torch.autograd.Function):
 
 
 def kmeans_loss(X, C):
-    """sum_i min_k ||x_i - c_k||^2 (Sec. 7.4, squared distances); gradient in C."""
+    """sum_i min_k ||x_i - c_k||^2 (Sec. 7.4, squared distances); gradient in
+    C; forward mode in C as well."""
     return _KMeans.apply(_c(X), _c(C))
+
+
+def kmeans_hvp(X, C, Cdot, ybar=1.0):
+    """Hessian-vector product of the k-means cost in C by forward mode over
+    the VJP (Sec. 7.4): the tangent of the gradient along Cdot."""
+    return A.adpar_kmeans_fwd_rev(_c(X), _c(C), _c(Cdot), ybar=ybar)[1]

@@ -10,6 +10,9 @@ size_t kmeans_workspace_size(int64_t k);
 size_t scan_vec_workspace_size(adpar_opdesc d, int64_t n, int64_t m);
 size_t hist_general_workspace_size(adpar_opdesc d, int64_t n, int64_t m);
 size_t scan_wide_workspace_size(adpar_opdesc d, int64_t n);
+size_t jvp_reduce_workspace_size(adpar_opdesc d);
+size_t jvp_hist_workspace_size(adpar_opdesc d, int64_t m);
+size_t kmeans_fwd_rev_workspace_size(int64_t N, int64_t k);
 }
 
 extern "C" const char* adpar_status_string(int status) {
@@ -40,6 +43,9 @@ extern "C" size_t adpar_workspace_size(int rule, adpar_opdesc d, int64_t n, int6
     case ADPAR_RULE_REDUCE: return n < 0 ? (size_t)-1 : adpar::reduce_workspace_size(d);
     case ADPAR_RULE_HIST: return n < 0 ? (size_t)-1 : adpar::hist_workspace_size(d, m);
     case ADPAR_RULE_KMEANS: return n < 0 ? (size_t)-1 : adpar::kmeans_workspace_size(m);
+    case ADPAR_RULE_JVP_REDUCE: return n < 0 ? (size_t)-1 : adpar::jvp_reduce_workspace_size(d);
+    case ADPAR_RULE_JVP_HIST: return n < 0 ? (size_t)-1 : adpar::jvp_hist_workspace_size(d, m);
+    case ADPAR_RULE_KMEANS_FWD_REV: return adpar::kmeans_fwd_rev_workspace_size(n, m);
     }
     return (size_t)-1;
 }

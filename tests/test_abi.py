@@ -174,3 +174,34 @@ def test_noalloc_binding_checks_every_array_without_gpu():
         A.adpar_vjp_scan_noalloc("add", None, f64(), abar=f64())
     # the status reader checks its output pointer before any CUDA call
     assert A.lib().adpar_noalloc_status(None, None) == A.ERR_INVALID
+
+
+def test_forward_mode_entry_points_validate_without_gpu():
+    """The forward-mode entry points refuse bad arguments on the host, before
+    any CUDA call, and size their workspaces."""
+    from paper_2202_10297_gb300 import adpar as A
+    L = A.lib()
+    d = A.OpDesc(A.OP_MUL, A.F64, 1)
+    assert L.adpar_jvp_reduce(d, -1, None, None, None, None, None, None, 0, None) == A.ERR_INVALID
+    assert L.adpar_jvp_reduce(A.OpDesc(A.OP_LINREC, A.F64, 2), 4, None, None, None, None, None, None, 0,
+                              None) == A.ERR_INVALID
+    assert L.adpar_jvp_reduce(d, 4, 0x1000, 0x2000, None, None, None, None, 0, None) == A.ERR_INVALID  # no ydot
+    assert L.adpar_jvp_reduce(d, 4, 0x1004, 0x2000, None, 0x3000, None, None, 0, None) == 3  # misaligned
+    assert L.adpar_jvp_reduce(d, 4, 0x1000, 0x2000, None, 0x3000, None, None, 0, None) == 4  # no workspace
+    dh = A.OpDesc(A.OP_ADD, A.F32, 1)
+    assert L.adpar_jvp_hist(dh, 10, 4, 0x1000, 0x2000, 0x3000, 0, None, 0x4000, 0x5000, None, 0,
+                            None) == 2  # log-domain tangents are for * only
+    assert L.adpar_jvp_hist(dh, 10, 4, 0x1000, 0x2000, 0x3000, 7, None, 0x4000, None, None, 0,
+                            None) == A.ERR_INVALID  # bad index type
+    assert L.adpar_jvp_map_acc(A.G_GATHER, A.F32, 10, 4, 2, None, 0x1000, 0, None, 0x2000, None, 0x3000,
+                               None) == A.ERR_INVALID  # width 2 for a scalar g
+    assert L.adpar_jvp_map_acc(A.G_SCALE, A.F32, 10, 4, 1, 0x1000, 0x2000, 0, None, 0x3000, None, 0x4000,
+                               None) == A.ERR_INVALID  # scale without ws
+    assert L.adpar_kmeans_fwd_rev(100, 16, 64, None, None, None, None, None, None, 0, None, 0,
+                                  None) == A.ERR_INVALID  # d must be 32
+    for op in (A.OP_ADD, A.OP_MUL, A.OP_MIN, A.OP_MAX):
+        assert A.adpar_workspace_size(A.RULE_JVP_REDUCE, op, A.F32, 1000) >= A.adpar_workspace_size(
+            A.RULE_REDUCE, op, A.F32, 1000)
+        assert A.adpar_workspace_size(A.RULE_JVP_HIST, op, A.F64, 1000, 300) >= A.adpar_workspace_size(
+            A.RULE_HIST, op, A.F64, 1000, 300) + 300 * 8
+    assert A.adpar_workspace_size(A.RULE_KMEANS_FWD_REV, 0, A.F32, 1 << 20, 256) >= 4 << 20

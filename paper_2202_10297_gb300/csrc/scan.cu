@@ -20,6 +20,7 @@
 #include <algorithm>
 
 #include "scan_tiles.cuh"
+#include "tc.cuh"
 
 namespace adpar {
 namespace {
@@ -512,6 +513,121 @@ __global__ void __launch_bounds__(kScanBlock) scan_forward_kernel(ScanArgs A) {
     scan_forward_tile<Op, T, Cfg::K, Cfg::E>(A, (int64_t)s_tile);
 }
 
+// --------------------------------------------- + scan, tile in shared memory
+// The return sweep of the + scan is the reverse suffix sum
+// as_bar_i = sum_{j >= i} ys_bar_j.  Every block takes one 64 KB tile,
+// brought into shared memory by one bulk copy (cp.async.bulk completing on
+// an mbarrier), so its registers hold only per-chunk sums and many blocks
+// (with their tiles' loads) stay resident per SM while look-backs run.  The
+// tile is read from shared memory twice: for the per-thread chunk sums,
+// and, once the look-back has given the sum of everything to the right,
+// for the outputs.  Chunk k of a tile holds kScanBlock 16-byte vectors, one
+// per thread (the layout of the scan engine, conflict-free in shared memory).
+template <class T>
+struct AddSmemCfg {
+    static constexpr int VEC = 16 / sizeof(T);
+    static constexpr int K = 16;
+    static constexpr int TILE = K * kScanBlock * VEC;  // 64 KB
+    static constexpr size_t kSmem = (size_t)TILE * sizeof(T);
+};
+
+template <class T>
+__global__ void __launch_bounds__(kScanBlock) scan_add_smem_kernel(ScanArgs A) {
+    using C = AddSmemCfg<T>;
+    constexpr int K = C::K, VEC = C::VEC, TILE = C::TILE, NW = kScanBlock / 32;
+    extern __shared__ __align__(128) unsigned char s_dyn[];
+    T* tile_s = reinterpret_cast<T*>(s_dyn);
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ uint32_t s_tile;
+    __shared__ T s_tot[K * NW];
+    __shared__ T s_pref;
+
+    if (threadIdx.x == 0) s_tile = atomicAdd(&A.hdr->ticket[1], 1u);
+    __syncthreads();
+    const int64_t t_log = s_tile;
+    const int64_t tile = A.tiles - 1 - t_log;  // tiles are taken right to left
+    const int64_t base = tile * TILE;
+    const bool full = base + TILE <= A.n;
+    const T* ya = static_cast<const T*>(A.ya);
+    if (full) {
+        if (threadIdx.x == 0) {
+            tc::mbar_init(&s_bar, 1);
+            tc::fence_mbar_init();
+            tc::mbar_arrive_expect_tx(&s_bar, (uint32_t)C::kSmem);
+            tc::bulk_load(tile_s, ya + base, (uint32_t)C::kSmem, &s_bar);
+        }
+        __syncthreads();
+        bool ok = false;
+        for (uint32_t w = 0; w < (1u << 20) && !ok; ++w) ok = tc::mbar_try_wait(&s_bar, 0u);
+        if (!ok) record_status(A.hdr, ADPAR_ERR_TIMEOUT);
+    } else {
+        for (int64_t i = threadIdx.x; i < TILE; i += kScanBlock) tile_s[i] = base + i < A.n ? ya[base + i] : T(0);
+        __syncthreads();
+    }
+
+    // per-thread sums of its K vectors, reverse block scan, look-back
+    auto add = [](const T& x, const T& y) { return x + y; };
+    T agg[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        T v[VEC];
+        load_chunk_smem<VEC>(tile_s, ((int64_t)k * kScanBlock + threadIdx.x) * VEC, v);
+        T sum = v[0];
+#pragma unroll
+        for (int j = 1; j < VEC; ++j) sum += v[j];
+        agg[k] = sum;
+    }
+    T wex[K];
+    const T total = block_scan_part1<T, true, K, NW>(agg, wex, s_tot, T(0), add);
+    if ((threadIdx.x >> 5) == 0) {
+        LookbackState<T> st{A.lbR_agg, A.lbR_incl};
+        const T pre = lookback(t_log, st, total, T(0), add, A.hdr);
+        if ((threadIdx.x & 31) == 0) s_pref = pre;
+    }
+    __syncthreads();
+
+    // outputs: the vector's suffix sums plus everything to its right
+    T* abar = static_cast<T*>(A.abar);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int64_t off = ((int64_t)k * kScanBlock + threadIdx.x) * VEC;
+        const int64_t e = base + off;
+        if (e >= A.n) continue;
+        T v[VEC];
+        load_chunk_smem<VEC>(tile_s, off, v);
+        T run = block_scan_excl<T, true, K, NW>(k, wex, s_tot, s_pref, add);
+#pragma unroll
+        for (int j = VEC - 1; j >= 0; --j) {
+            run += v[j];
+            v[j] = run;
+        }
+        if (A.accumulate) {
+            T old[VEC];
+            load_chunk_keep(static_cast<const T*>(A.abar), e, A.n, T(0), old);
+#pragma unroll
+            for (int j = 0; j < VEC; ++j) v[j] += old[j];
+        }
+        store_chunk(abar, e, A.n, v);
+    }
+}
+
+template <class T>
+int launch_add_smem(ScanArgs A, cudaStream_t stream) {
+    using C = AddSmemCfg<T>;
+    static bool configured[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return ADPAR_ERR_CUDA;
+    if (!configured[dev]) {
+        if (cudaFuncSetAttribute(scan_add_smem_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)C::kSmem) != cudaSuccess)
+            return ADPAR_ERR_CUDA;
+        configured[dev] = true;
+    }
+    A.tiles = (A.n + C::TILE - 1) / C::TILE;
+    scan_add_smem_kernel<T><<<(unsigned)A.tiles, kScanBlock, C::kSmem, stream>>>(A);
+    return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
+}
+
 // ------------------------------------------------------------ host side
 struct ScanLayout {
     size_t off_carry, off_slots, off_pA, off_pI, off_rA, off_rI, slot_words, total_min;
@@ -672,6 +788,12 @@ int run_scan(int64_t n, const void* a, const void* b, const void* ya, const void
         scan_minmax_runs_kernel<P><<<M.groups, kMmGroup, 0, stream>>>(M);
         scan_minmax_fixup_kernel<P, T><<<M.groups, kMmGroup, 0, stream>>>(M, static_cast<T*>(A.abar));
     } else {
+        if constexpr (std::is_same<Op, OpAdd<T>>::value) {
+            // the tile in shared memory needs fewer look-back slots than the
+            // register tile the layout is sized for (its tiles are larger)
+            static_assert(AddSmemCfg<T>::TILE >= ScanCfg<Op, T>::TILE, "no more tiles than slots");
+            if (!ys_a) return launch_add_smem<T>(A, stream);
+        }
         if (need_primal) scan_primal_kernel<Op, T><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
         if (ys_a) scan_adjoint_kernel<Op, T, true><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
         else scan_adjoint_kernel<Op, T, false><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);

@@ -90,6 +90,23 @@ __device__ __forceinline__ void store_chunk(T* p, int64_t e, int64_t n, const T 
     }
 }
 
+// E consecutive elements of a shared-memory array as 16-byte vectors
+template <int E, class T>
+__device__ __forceinline__ void load_chunk_smem(const T* p, int64_t off, T (&out)[E]) {
+    constexpr int VV = Vec16<T>::N;
+    static_assert(E % VV == 0, "whole vectors");
+#pragma unroll
+    for (int q = 0; q < E / VV; ++q) {
+        if constexpr (sizeof(T) == 4) {
+            const float4 x = *reinterpret_cast<const float4*>(p + off + q * VV);
+            out[q * VV + 0] = x.x; out[q * VV + 1] = x.y; out[q * VV + 2] = x.z; out[q * VV + 3] = x.w;
+        } else {
+            const double2 x = *reinterpret_cast<const double2*>(p + off + q * VV);
+            out[q * VV + 0] = x.x; out[q * VV + 1] = x.y;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- pass P
 template <class Op, class T, int K, int V>
 __device__ __forceinline__ void scan_primal_tile(const ScanArgs& A, int64_t tile) {

@@ -89,10 +89,11 @@ LINREC_FLOP_PER_PAIR = 10
 # FP64 peak of a GB300: 152 SMs x 2 FP64 FMA lanes per clock (one warp
 # instruction per 16 cycles per SM) x 2 flops x the maximum SM clock
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
-# DRAM bytes per call of the FP64 linear-recurrence VJP (init + primal pass +
-# adjoint pass), from the ncu capture at n = 2^24 scaled by 4 to 2^26
+# DRAM bytes per call of the FP64 linear-recurrence VJP (carry pass + reverse
+# pass of the runs path), from an ncu capture at n = 2^24 (carry: 268.5 MB
+# read + 18.8 MB written; reverse: 563.0 + 233.7 MB) scaled by 4 to 2^26
 # (traffic grows in proportion to n)
-LINREC_F64_TRAFFIC_PER_CALL = 4 * 1798297088
+LINREC_F64_TRAFFIC_PER_CALL = 4 * (268471296 + 18830336 + 563029760 + 233694208)
 
 WORKLOAD = ("scan VJPs: linear-recurrence n=2^26 pairs FP32 and FP64 (a~U[0.9,1], b,ybar~N(0,1)); "
             "+ scan and max scan n=2^28 FP32 N(0,1)")

@@ -7,21 +7,25 @@
 // which Sec. 6.1 turns into a reduction; here that reduction is a per-block
 // histogram of rows (counts and row sums per centroid) in shared memory.
 //
-// One persistent kernel, one CTA per SM, 12 warps:
+// One persistent kernel, one CTA per SM, 20 warps:
 //   warp 0     TMA producer: X tiles of 128 rows x 32 FP32 (128-byte rows,
 //              128-byte swizzle) into a 4-stage ring; C (k x 32) once.
 //   warp 1     MMA issuer: S = X_tile C^T with tcgen05.mma kind::tf32
 //              (M = 128, N = k, K = 32 in four steps of 8) into one of two
 //              TMEM accumulators (2 x 256 columns).
 //   warp 2     TMEM allocation and release.
-//   warps 4-11 epilogue, two threads per row (each half of the columns):
-//              tcgen05.ld of the distances  v_k = |c_k|^2 - 2 x.c_k, the
-//              minimum (next chunk's load in flight meanwhile), and a
-//              certified argmin: every centroid within the TF32 error
-//              bound of the minimum is recomputed exactly in FP32; if two
-//              remain within the FP32 bound, FP64 (the oracle's own
-//              arithmetic) decides, ties to the lowest k.  Then the loss
-//              term (exact distance of the argmin) and, for the gradient,
+//   warps 4-19 epilogue, four threads per row (warp w reads the TMEM lanes
+//              of quarter w % 4 and the 32-column chunks q = group (mod 4)):
+//              one tcgen05.ld pass over the distances v_k = |c_k|^2 - 2 x.c_k
+//              keeping the smallest, its column and the second smallest;
+//              the row's minimum from the four threads; every centroid
+//              within the TF32 error bound of the minimum is a candidate
+//              (a thread whose second smallest is within the bound rescans
+//              its chunks, before the accumulator is released).  The
+//              certified argmin: candidates recomputed exactly in FP32; if
+//              two remain within the FP32 bound, FP64 (the oracle's own
+//              arithmetic) decides, ties to the lowest k.  Then the loss term
+//              (exact distance of the argmin) and, for the gradient,
 //              warp-cooperative row sums into shared memory.
 // Every mbarrier wait is bounded; a timeout is recorded in the workspace
 // and the kernel drains its copies and MMAs, frees TMEM and returns.
@@ -36,7 +40,9 @@
 namespace adpar {
 namespace {
 
-constexpr int KM_THREADS = 384;  // warps 0-3 roles, 4-11 epilogue
+constexpr int KM_THREADS = 640;  // warps 0-3 roles, 4-19 epilogue
+constexpr int KM_EPI = 512;      // epilogue threads
+constexpr int KM_GROUPS = 4;     // epilogue threads per row
 constexpr int KM_STAGES = 4;
 constexpr int KM_D = 32;
 constexpr int KM_KMAX = 256;
@@ -51,10 +57,11 @@ constexpr uint32_t OFF_SUM = OFF_X + KM_STAGES * KM_X_BYTES;            // 32 KB
 constexpr uint32_t OFF_CNT = OFF_SUM + KM_KMAX * KM_D * 4;              // 1 KB
 constexpr uint32_t OFF_CN2 = OFF_CNT + KM_KMAX * 4;                     // 1 KB
 constexpr uint32_t OFF_CAND = OFF_CN2 + KM_KMAX * 4;                    // 4 KB
-constexpr uint32_t OFF_ARG = OFF_CAND + KM_TILE * KM_MAXCAND * 4;       // 512 B
-constexpr uint32_t OFF_MIN = OFF_ARG + KM_TILE * 4;                     // 1 KB: [2][128] minima
-constexpr uint32_t OFF_NC = OFF_MIN + 2 * KM_TILE * 4;                  // 512 B: candidate counts
-constexpr uint32_t OFF_BAR = OFF_NC + KM_TILE * 4;                      // barriers
+constexpr uint32_t OFF_ARG = OFF_CAND + KM_TILE * KM_MAXCAND * 4;       // 512 B: certified argmin per row
+constexpr uint32_t OFF_MIN = OFF_ARG + KM_TILE * 4;                     // 6 KB: [4][128] m1, m2, a1
+constexpr uint32_t OFF_NC = OFF_MIN + 3 * KM_GROUPS * KM_TILE * 4;      // 512 B: candidate counts
+constexpr uint32_t OFF_XN = OFF_NC + KM_TILE * 4;                       // 2 KB: [4][128] partial |x|^2
+constexpr uint32_t OFF_BAR = OFF_XN + KM_GROUPS * KM_TILE * 4;          // barriers
 constexpr uint32_t NBAR = 2 * KM_STAGES + 5;
 constexpr uint32_t OFF_MISC = OFF_BAR + NBAR * 8;
 constexpr uint32_t KM_SMEM = OFF_MISC + 64 + 1024;  // + alignment slack
@@ -82,17 +89,6 @@ __device__ __forceinline__ float sw_elem(const float* tile, int r, int j) {
     const int chunk = (j >> 2) ^ (r & 7);
     return tile[r * 32 + chunk * 4 + (j & 3)];
 }
-__device__ __forceinline__ void sw_row(const float* tile, int r, float (&x)[32]) {
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const float4 v = *reinterpret_cast<const float4*>(tile + r * 32 + ((c ^ (r & 7)) * 4));
-        x[4 * c + 0] = v.x;
-        x[4 * c + 1] = v.y;
-        x[4 * c + 2] = v.z;
-        x[4 * c + 3] = v.w;
-    }
-}
-
 // ||x_r - c_kc||^2 in FP32, sequential over the 32 coordinates (row r of
 // the X tile and row kc of the C tile, both swizzled in shared memory)
 __device__ __noinline__ float exact_f32(const float* xt, int r, const float* sC, int kc) {
@@ -123,16 +119,16 @@ __global__ void km_empty_kernel(float* loss_out, float* Cbar, int kd, int accumu
         for (int q = t; q < kd; q += gridDim.x * blockDim.x) Cbar[q] = 0.f;
 }
 
-// The 8 epilogue warps (256 threads, warps 4-11) synchronise on named
+// The 16 epilogue warps (512 threads, warps 4-19) synchronise on named
 // barrier 1.  epi_any is a barrier that also ORs a predicate over them, so
 // a decision to stop is taken by all of them together.
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
 __device__ __forceinline__ bool epi_any(bool p) {
     uint32_t r;
     asm volatile(
         "{\n\t.reg .pred q, o;\n\t"
         "setp.ne.u32 q, %1, 0;\n\t"
-        "bar.red.or.pred o, 1, 256, q;\n\t"
+        "bar.red.or.pred o, 1, 512, q;\n\t"
         "selp.u32 %0, 1, 0, o;\n\t}"
         : "=r"(r)
         : "r"((uint32_t)p)
@@ -140,15 +136,22 @@ __device__ __forceinline__ bool epi_any(bool p) {
     return r != 0;
 }
 
-// min over one 32-column chunk of v_k = |c_k|^2 - 2 S_k, two chains for ILP
-__device__ __forceinline__ void chunk_min(const uint32_t (&v)[32], const float* cn2, float& ma, float& mb) {
+// one 32-column chunk of v_k = |c_k|^2 - 2 S_k into the running smallest
+// (m1, at column a1) and second smallest (m2); ties keep the lower column
+__device__ __forceinline__ void chunk_track(const uint32_t (&v)[32], const float* cn2, int k0, float& m1, int& a1,
+                                            float& m2) {
 #pragma unroll
     for (int c4 = 0; c4 < 8; ++c4) {
         const float4 c = *reinterpret_cast<const float4*>(cn2 + 4 * c4);
-        ma = fminf(ma, fmaf(-2.f, __uint_as_float(v[4 * c4 + 0]), c.x));
-        mb = fminf(mb, fmaf(-2.f, __uint_as_float(v[4 * c4 + 1]), c.y));
-        ma = fminf(ma, fmaf(-2.f, __uint_as_float(v[4 * c4 + 2]), c.z));
-        mb = fminf(mb, fmaf(-2.f, __uint_as_float(v[4 * c4 + 3]), c.w));
+        const float cc[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float x = fmaf(-2.f, __uint_as_float(v[4 * c4 + j]), cc[j]);
+            const bool lt = x < m1;
+            m2 = lt ? m1 : fminf(m2, x);
+            a1 = lt ? k0 + 4 * c4 + j : a1;
+            m1 = lt ? x : m1;
+        }
     }
 }
 // candidates of one chunk: columns with v_k <= thr, appended to the row's list
@@ -186,9 +189,10 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
     float* s_cnt = reinterpret_cast<float*>(base + OFF_CNT);
     float* s_cn2 = reinterpret_cast<float*>(base + OFF_CN2);
     int* s_cand = reinterpret_cast<int*>(base + OFF_CAND);
-    int* s_arg = reinterpret_cast<int*>(base + OFF_ARG);
     float* s_min = reinterpret_cast<float*>(base + OFF_MIN);
+    int* s_arg = reinterpret_cast<int*>(base + OFF_ARG);
     int* s_ncand = reinterpret_cast<int*>(base + OFF_NC);
+    float* s_xn = reinterpret_cast<float*>(base + OFF_XN);
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + OFF_BAR);
     uint64_t* x_full = bars;
     uint64_t* x_empty = bars + KM_STAGES;
@@ -207,11 +211,11 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < KM_STAGES; ++s) {
             tc::mbar_init(&x_full[s], 1);
-            tc::mbar_init(&x_empty[s], 256);
+            tc::mbar_init(&x_empty[s], KM_EPI);
         }
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(&t_full[b], 1);
-            tc::mbar_init(&t_empty[b], 256);
+            tc::mbar_init(&t_empty[b], KM_EPI);
         }
         tc::mbar_init(c_bar, 1);
         *s_abort = 0;
@@ -283,13 +287,16 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
             }
         }
     } else if (warp >= 4) {
-        // 8 epilogue warps: warp (quarter, half) reads TMEM lanes of its
-        // quarter and the 32-column chunks q with q % 2 == half
+        // 16 epilogue warps: warp w reads the TMEM lanes of quarter w % 4 and
+        // the 32-column chunks q with q % 4 == its group
         const int ew = warp - 4;
-        const int quarter = warp & 3, half = ew >> 2;
+        const int quarter = warp & 3, grp = ew >> 2;
         const int r = quarter * 32 + lane;  // row of the tile == TMEM lane
         const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
         const int nq = k / 32;
+        float* s_m1 = s_min;
+        float* s_m2 = s_min + KM_GROUPS * KM_TILE;
+        int* s_a1 = reinterpret_cast<int*>(s_min + 2 * KM_GROUPS * KM_TILE);
         double loss_local = 0.0;
         if (!tc::mbar_wait(c_bar, 0, s_abort)) *s_abort = 1;
         int i = 0;
@@ -303,63 +310,71 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
             }
             tc::fence_after_sync();
             const float* xt = sX + s * (KM_X_BYTES / 4);
-            const int64_t row = t * KM_TILE + r;
-            const bool valid = row < A.N;
-            float xn2 = 0.f;
             {
-                float x[32];
-                sw_row(xt, r, x);
+                // this thread's quarter of |x|^2 (coordinates 8 grp .. 8 grp + 7)
+                float xp = 0.f;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) xn2 = fmaf(x[j], x[j], xn2);
+                for (int c = 2 * grp; c < 2 * grp + 2; ++c) {
+                    const float4 v = *reinterpret_cast<const float4*>(xt + r * 32 + ((c ^ (r & 7)) * 4));
+                    xp = fmaf(v.x, v.x, xp);
+                    xp = fmaf(v.y, v.y, xp);
+                    xp = fmaf(v.z, v.z, xp);
+                    xp = fmaf(v.w, v.w, xp);
+                }
+                s_xn[grp * KM_TILE + r] = xp;
+            }
+            const uint32_t tb = tmem + lane_base + (uint32_t)(b * 256);
+
+            // one pass: smallest, its column and second smallest of this
+            // thread's chunks (sixteen warps hide the load latency)
+            float m1 = CUDART_INF_F, m2 = CUDART_INF_F;
+            int a1 = 0;
+            for (int q = grp; q < nq; q += KM_GROUPS) {
+                uint32_t va[32];
+                __syncwarp();
+                tc::tmem_ld32(tb + (uint32_t)(q * 32), va);
+                tc::tmem_ld_wait();
+                chunk_track(va, s_cn2 + q * 32, q * 32, m1, a1, m2);
+            }
+            s_m1[grp * KM_TILE + r] = m1;
+            s_m2[grp * KM_TILE + r] = m2;
+            s_a1[grp * KM_TILE + r] = a1;
+            if (grp == 0) s_ncand[r] = 0;
+            epi_sync();
+            float mrow = s_m1[r], xn2 = s_xn[r];
+#pragma unroll
+            for (int g = 1; g < KM_GROUPS; ++g) {
+                mrow = fminf(mrow, s_m1[g * KM_TILE + r]);
+                xn2 += s_xn[g * KM_TILE + r];
             }
             const float xn = sqrtf(xn2);
             // |v~_k - v_k| <= 2 |S~ - S| + rounding <= 2^-8 |x| |c_k| (TF32 keeps 10
             // mantissa bits of each operand) plus FP32 terms; 2x margin
             const float tol = 8.0e-3f * xn * cmax + 1.0e-5f * (cmax * cmax + xn * cmax) + 1e-20f;
-            const uint32_t tb = tmem + lane_base + (uint32_t)(b * 256);
-
-            // pass 1: the minimum of v_k over this thread's chunks; the load
-            // of the next chunk is in flight while the current one is scanned
-            float m1a = CUDART_INF_F, m1b = CUDART_INF_F;
-            {
-                uint32_t va[32], vb[32];
-                int q = half;
-                if (q < nq) { __syncwarp(); tc::tmem_ld32(tb + (uint32_t)(q * 32), va); }
-                for (; q < nq; q += 4) {
+            const float thr = mrow + 2.f * tol;
+            // candidates: every column within 2 tol of the row's minimum; a
+            // thread with two or more of them rescans its chunks (the whole
+            // warp loads together), the others add at most their smallest
+            const bool multi = m2 <= thr;
+            if (__any_sync(0xffffffffu, multi)) {
+                for (int q = grp; q < nq; q += KM_GROUPS) {
+                    uint32_t va[32];
+                    __syncwarp();
+                    tc::tmem_ld32(tb + (uint32_t)(q * 32), va);
                     tc::tmem_ld_wait();
-                    if (q + 2 < nq) { __syncwarp(); tc::tmem_ld32(tb + (uint32_t)((q + 2) * 32), vb); }
-                    chunk_min(va, s_cn2 + q * 32, m1a, m1b);
-                    if (q + 2 >= nq) break;
-                    tc::tmem_ld_wait();
-                    if (q + 4 < nq) { __syncwarp(); tc::tmem_ld32(tb + (uint32_t)((q + 4) * 32), va); }
-                    chunk_min(vb, s_cn2 + (q + 2) * 32, m1a, m1b);
+                    if (multi) chunk_cand(va, s_cn2 + q * 32, q * 32, thr, s_ncand + r, s_cand + r * KM_MAXCAND);
                 }
             }
-            s_min[half * KM_TILE + r] = fminf(m1a, m1b);
-            if (half == 0) s_ncand[r] = 0;
-            epi_sync();
-            const float thr = fminf(s_min[r], s_min[KM_TILE + r]) + 2.f * tol;
-            // pass 2: every k with v_k <= min + 2 tol is a candidate argmin
-            {
-                uint32_t va[32], vb[32];
-                int q = half;
-                if (q < nq) { __syncwarp(); tc::tmem_ld32(tb + (uint32_t)(q * 32), va); }
-                for (; q < nq; q += 4) {
-                    tc::tmem_ld_wait();
-                    if (q + 2 < nq) { __syncwarp(); tc::tmem_ld32(tb + (uint32_t)((q + 2) * 32), vb); }
-                    chunk_cand(va, s_cn2 + q * 32, q * 32, thr, s_ncand + r, s_cand + r * KM_MAXCAND);
-                    if (q + 2 >= nq) break;
-                    tc::tmem_ld_wait();
-                    if (q + 4 < nq) { __syncwarp(); tc::tmem_ld32(tb + (uint32_t)((q + 4) * 32), va); }
-                    chunk_cand(vb, s_cn2 + (q + 2) * 32, (q + 2) * 32, thr, s_ncand + r, s_cand + r * KM_MAXCAND);
-                }
+            if (!multi && m1 <= thr) {
+                const int slot = atomicAdd(s_ncand + r, 1);
+                if (slot < KM_MAXCAND) s_cand[r * KM_MAXCAND + slot] = a1;
             }
             tc::fence_before_sync();
             tc::mbar_arrive(&t_empty[b]);  // the accumulator may be overwritten now
             epi_sync();
 
-            // certify the argmin among the candidates (half 0 of each row)
-            if (half == 0) {
+            // certify the argmin among the candidates (group 0 of each row)
+            if (grp == 0) {
                 const int nc = s_ncand[r];
                 int best = 0;
                 double dist = 0.0;
@@ -368,20 +383,19 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
                     dist = (double)exact_f32(xt, r, sC, best);
                 } else {
                     const int ncc = nc <= KM_MAXCAND ? nc : 0;  // 0: fall back to all k
+                    float e32[KM_MAXCAND];
                     float u32 = CUDART_INF_F;
                     for (int c = 0; c < ncc; ++c) {
-                        const float e = exact_f32(xt, r, sC, s_cand[r * KM_MAXCAND + c]);
-                        u32 = fminf(u32, e + 4.0e-6f * e + 1e-30f);
+                        e32[c] = exact_f32(xt, r, sC, s_cand[r * KM_MAXCAND + c]);
+                        u32 = fminf(u32, e32[c] + 4.0e-6f * e32[c] + 1e-30f);
                     }
                     int n2 = 0, only = -1;
                     float only_e = 0.f;
                     for (int c = 0; c < ncc; ++c) {
-                        const int kc = s_cand[r * KM_MAXCAND + c];
-                        const float e = exact_f32(xt, r, sC, kc);
-                        if (e - 4.0e-6f * e <= u32) {
+                        if (e32[c] - 4.0e-6f * e32[c] <= u32) {
                             ++n2;
-                            only = kc;
-                            only_e = e;
+                            only = s_cand[r * KM_MAXCAND + c];
+                            only_e = e32[c];
                         }
                     }
                     if (ncc > 0 && n2 == 1) {
@@ -394,16 +408,15 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
                         const int lim = ncc > 0 ? ncc : k;
                         for (int c = 0; c < lim; ++c) {
                             const int kc = ncc > 0 ? s_cand[r * KM_MAXCAND + c] : c;
-                            if (ncc > 0) {
-                                const float e = exact_f32(xt, r, sC, kc);
-                                if (!(e - 4.0e-6f * e <= u32)) continue;
-                            }
+                            if (ncc > 0 && !(e32[c] - 4.0e-6f * e32[c] <= u32)) continue;
                             const double d = exact_f64(xt, r, sC, kc);
                             if (d < bd || (d == bd && kc < best)) { bd = d; best = kc; }
                         }
                         dist = bd;
                     }
                 }
+                const int64_t row = t * KM_TILE + r;
+                const bool valid = row < A.N;
                 if (valid) {
                     loss_local += dist;
                     if (A.argmin_out) A.argmin_out[row] = best;
@@ -412,9 +425,9 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
             }
             if (want_grad) {
                 epi_sync();
-                // row sums: warp ew takes rows [16 ew, 16 ew + 16), one row per step,
+                // row sums: warp ew takes rows [8 ew, 8 ew + 8), one row per step,
                 // lanes = coordinates (32 consecutive floats: no bank conflicts)
-                for (int rr = ew * 16; rr < ew * 16 + 16; ++rr) {
+                for (int rr = ew * 8; rr < ew * 8 + 8; ++rr) {
                     const int kc = s_arg[rr];
                     if (kc >= 0) {
                         atomicAdd(&s_sum[kc * KM_D + lane], sw_elem(xt, rr, lane));

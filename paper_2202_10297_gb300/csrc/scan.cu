@@ -18,7 +18,9 @@
 //         the tile from its carry, build the lin_o elements, reverse-scan
 //         them with look-back, and write as_bar (and optionally ys).
 #include <algorithm>
+#include <cstring>
 
+#include "scan_runs.cuh"
 #include "scan_tiles.cuh"
 #include "tc.cuh"
 
@@ -52,6 +54,83 @@ __global__ void __launch_bounds__(kScanBlock) scan_primal_kernel(ScanArgs A) {
     if (threadIdx.x == 0) s_tile = atomicAdd(&A.hdr->ticket[0], 1u);
     __syncthreads();
     scan_primal_tile<Op, T, Cfg::K, Cfg::E>(A, (int64_t)s_tile);
+}
+
+// Pass P as reduce-then-scan, for the return sweeps that read only each
+// tile's exclusive carry: every block reduces its tile to the tile's primal
+// aggregate (a streaming read of the inputs in which no block waits on
+// another), then one block scans the aggregates, in order, into the carries.
+// The single-pass form spent most of its time in look-backs: a pass that
+// writes nothing per element has little work to hide them behind.
+template <class Op, class T>
+__global__ void __launch_bounds__(kScanBlock) scan_tile_agg_kernel(ScanArgs A, typename Op::P* agg) {
+    using Cfg = ScanCfg<Op, T>;
+    using P = typename Op::P;
+    constexpr int K = Cfg::K, V = Cfg::E, NW = kScanBlock / 32, TILE = Cfg::TILE;
+    __shared__ P s_tot[K * NW];
+    const int64_t tile = blockIdx.x;
+    const int64_t base = tile * TILE;
+    const T* a = static_cast<const T*>(A.a);
+    const T* b = static_cast<const T*>(A.b);
+    P part[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int64_t e = base + (int64_t)k * kScanBlock * V + threadIdx.x * V;
+        T av[V], bv[V];
+        load_chunk(a, e, A.n, Op::pad_a(), av);
+        if constexpr (Op::kWidth == 2) load_chunk(b, e, A.n, T(0), bv);
+        else {
+#pragma unroll
+            for (int j = 0; j < V; ++j) bv[j] = T(0);
+        }
+        P acc = Op::pelem(av[0], bv[0]);
+#pragma unroll
+        for (int j = 1; j < V; ++j) acc = Op::pcomb(acc, Op::pelem(av[j], bv[j]));
+        part[k] = acc;
+    }
+    auto comb = [](const P& l, const P& r) { return Op::pcomb(l, r); };
+    P wex[K];
+    const P total = block_scan_part1<P, false, K, NW>(part, wex, s_tot, Op::pid(), comb);
+    if (threadIdx.x == 0) agg[tile] = total;
+}
+
+// One block: carry[i] = agg[0] (.) ... (.) agg[i-1], in order.
+constexpr int kCarryBlock = 1024;
+template <class Op>
+__global__ void __launch_bounds__(kCarryBlock) scan_carry_kernel(const typename Op::P* agg, typename Op::P* carry,
+                                                                 int64_t tiles) {
+    using P = typename Op::P;
+    __shared__ P s_w[kCarryBlock / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t per = (tiles + kCarryBlock - 1) / kCarryBlock;
+    const int64_t lo = threadIdx.x * per, hi = lo + per < tiles ? lo + per : tiles;
+    P run = Op::pid();
+    for (int64_t i = lo; i < hi; ++i) run = Op::pcomb(run, agg[i]);
+    P inc = run;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const P o = shfl_up_s(inc, off);
+        if (lane >= off) inc = Op::pcomb(o, inc);
+    }
+    if (lane == 31) s_w[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        P v = s_w[lane];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const P o = shfl_up_s(v, off);
+            if (lane >= off) v = Op::pcomb(o, v);
+        }
+        s_w[lane] = v;
+    }
+    __syncthreads();
+    P ex = shfl_up_s(inc, 1);
+    if (lane == 0) ex = Op::pid();
+    if (warp > 0) ex = Op::pcomb(s_w[warp - 1], ex);
+    for (int64_t i = lo; i < hi; ++i) {
+        carry[i] = ex;
+        ex = Op::pcomb(ex, agg[i]);
+    }
 }
 
 // MIN/MAX scans: the return sweep fused into the forward pass.  For these
@@ -628,6 +707,122 @@ int launch_add_smem(ScanArgs A, cudaStream_t stream) {
     return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
 }
 
+// ------------------------------------- FP64 linear recurrence, per-thread runs
+// Host side of scan_runs.cuh: workspace layout, tensor maps, launches.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// An FP64 array of n elements seen as [n / kRunV runs][kRunRows][16]: box
+// of kRunNT runs, 128-byte swizzle (one array tile per copy).
+bool make_run_map(CUtensorMap* m, const double* ptr, int64_t n) {
+    EncodeTiledFn f = encode_tiled();
+    if (!f) return false;
+    cuuint64_t dims[3] = {16, (cuuint64_t)kRunRows, (cuuint64_t)(n / kRunV)};
+    cuuint64_t strides[2] = {128, (cuuint64_t)(128 * kRunRows)};
+    cuuint32_t box[3] = {16, (cuuint32_t)kRunRows, (cuuint32_t)kRunNT};
+    cuuint32_t es[3] = {1, 1, 1};
+    return f(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<double*>(ptr), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct RunLayout {
+    size_t off_slots, slot_words, off_pA, off_pI, off_rA, off_rI, off_carA, off_carB, off_prod, total;
+    int64_t tiles;
+};
+
+RunLayout run_layout(int64_t n) {
+    RunLayout L;
+    L.tiles = (n + kRunTile - 1) / kRunTile;
+    const size_t t = (size_t)L.tiles;
+    const size_t wp = t * (size_t)lb_words<RunP>(), wr = t * (size_t)lb_words<RunL>();
+    size_t o = sizeof(WsHeader);
+    L.off_slots = o;
+    L.off_pA = o; o += wp * 8;
+    L.off_pI = o; o += wp * 8;
+    L.off_rA = o; o += wr * 8;
+    L.off_rI = o; o += wr * 8;
+    L.slot_words = (o - L.off_slots) / 8;
+    const size_t runs = t * (size_t)kRunNT;
+    o = round_up(o, 256);
+    L.off_carA = o; o = round_up(o + runs * 8, 256);
+    L.off_carB = o; o = round_up(o + runs * 8, 256);
+    L.off_prod = o; o = round_up(o + runs * 8, 256);
+    L.total = o;
+    return L;
+}
+
+int run_linrec_runs(int64_t n, const void* a, const void* b, const void* ya, const void* yb, void* abar,
+                    void* bbar, uint32_t flags, void* work, cudaStream_t stream) {
+    const RunLayout L = run_layout(n);
+    char* w = static_cast<char*>(work);
+    RunArgs R{};
+    R.n = n;
+    R.tiles = L.tiles;
+    R.a = static_cast<const double*>(a);
+    R.b = static_cast<const double*>(b);
+    R.ya = static_cast<const double*>(ya);
+    R.yb = static_cast<const double*>(yb);
+    R.abar = static_cast<double*>(abar);
+    R.bbar = static_cast<double*>(bbar);
+    R.accumulate = (flags & ADPAR_ACCUMULATE) ? 1 : 0;
+    R.hdr = reinterpret_cast<WsHeader*>(w);
+    R.lbP_agg = reinterpret_cast<unsigned long long*>(w + L.off_pA);
+    R.lbP_incl = reinterpret_cast<unsigned long long*>(w + L.off_pI);
+    R.lbR_agg = reinterpret_cast<unsigned long long*>(w + L.off_rA);
+    R.lbR_incl = reinterpret_cast<unsigned long long*>(w + L.off_rI);
+    R.carA = reinterpret_cast<double*>(w + L.off_carA);
+    R.carB = reinterpret_cast<double*>(w + L.off_carB);
+    R.prod = reinterpret_cast<double*>(w + L.off_prod);
+    // the tile aggregates and carries take the primal look-back slots
+    static_assert(lb_words<RunP>() * 8 >= sizeof(RunP), "a state fits a slot");
+    R.tagg = reinterpret_cast<RunP*>(w + L.off_pA);
+    R.tcar = reinterpret_cast<RunP*>(w + L.off_pI);
+    CUtensorMap tm[6];
+    memset(tm, 0, sizeof(tm));
+    if (n >= kRunTile) {
+        // whole tiles exist: their copies go through TMA (the partial last
+        // tile, and every tile when n < kRunTile, is copied element-wise)
+        const double* ptr[6] = {R.a, R.b, R.ya, R.yb, R.abar, R.bbar};
+        for (int i = 0; i < 6; ++i)
+            if (!make_run_map(&tm[i], ptr[i], n)) return ADPAR_ERR_CUDA;
+    }
+    static bool configured[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return ADPAR_ERR_CUDA;
+    if (!configured[dev]) {
+        if (cudaFuncSetAttribute(linrec_runs_carry_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 2 * kRunArrBytes) != cudaSuccess ||
+            cudaFuncSetAttribute(linrec_runs_vjp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 4 * kRunArrBytes) != cudaSuccess)
+            return ADPAR_ERR_CUDA;
+        configured[dev] = true;
+    }
+    const int64_t words = (int64_t)L.slot_words;
+    const int iblocks = (int)std::min<int64_t>((words + 255) / 256 + 1, 2048);
+    scan_init_kernel<<<iblocks, 256, 0, stream>>>(R.hdr, reinterpret_cast<unsigned long long*>(w + L.off_slots),
+                                                  words);
+    linrec_runs_carry_kernel<<<(unsigned)L.tiles, kRunNT, 2 * kRunArrBytes, stream>>>(tm[0], tm[1], R);
+    scan_carry_kernel<RunPOp><<<1, kCarryBlock, 0, stream>>>(R.tagg, R.tcar, L.tiles);
+    linrec_runs_vjp_kernel<<<(unsigned)L.tiles, kRunNT, 4 * kRunArrBytes, stream>>>(tm[0], tm[1], tm[2], tm[3],
+                                                                                    tm[4], tm[5], R);
+    return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
+}
+
 // ------------------------------------------------------------ host side
 struct ScanLayout {
     size_t off_carry, off_slots, off_pA, off_pI, off_rA, off_rI, slot_words, total_min;
@@ -635,10 +830,11 @@ struct ScanLayout {
     size_t off_xloc, off_floc, off_gagg, off_fx, off_ff;  // min/max rule only
 };
 
-// The FP64 operators with J_left = a_i take the factored forward result
-// (scan_primal_fac_tile) when the workspace holds it.
+// The FP64 * scan takes the factored forward result (scan_primal_fac_tile)
+// when the workspace holds it; the FP64 linear recurrence takes per-thread
+// runs (scan_runs.cuh) instead.
 template <class Op, class T>
-constexpr bool kFactored = Op::kCoefIsA && sizeof(T) == 8;
+constexpr bool kFactored = Op::kCoefIsA && sizeof(T) == 8 && Op::kWidth == 1;
 
 // MIN/MAX take the fused single-pass rule (scan_minmax_fused_kernel).
 template <class Op, class T>
@@ -688,6 +884,8 @@ ScanLayout scan_layout(int64_t n) {
         s.off_thc = o; o = round_up(o + ptiles * (size_t)kScanBlock * sizeof(P), 256);
     }
     s.total = o;
+    if constexpr (std::is_same<Op, OpLinrec<T>>::value && sizeof(T) == 8)
+        s.total = std::max(s.total, run_layout(n).total);
     return s;
 }
 
@@ -737,6 +935,11 @@ int run_scan(int64_t n, const void* a, const void* b, const void* ya, const void
     A.hdr = reinterpret_cast<WsHeader*>(w);
     set_slots(A, w, L);
     const bool need_primal = Op::kNeedPrimal || Op::kCoefNeedsPrimal || ys_a != nullptr;
+    if constexpr (std::is_same<Op, OpLinrec<T>>::value && sizeof(T) == 8) {
+        // per-thread runs, when the workspace holds the runs' carries
+        if (!ys_a && work_bytes >= run_layout(n).total)
+            return run_linrec_runs(n, a, b, ya, yb, abar, bbar, flags, work, stream);
+    }
     launch_init(A, w, L, stream);
     if constexpr (kFactored<Op, T>) {
         if (work_bytes >= L.total) {
@@ -794,7 +997,14 @@ int run_scan(int64_t n, const void* a, const void* b, const void* ya, const void
             static_assert(AddSmemCfg<T>::TILE >= ScanCfg<Op, T>::TILE, "no more tiles than slots");
             if (!ys_a) return launch_add_smem<T>(A, stream);
         }
-        if (need_primal) scan_primal_kernel<Op, T><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
+        if (need_primal) {
+            // the tile aggregates take the primal aggregate slots, unused here
+            using P = typename Op::P;
+            static_assert(lb_words<P>() * 8 >= sizeof(P), "an aggregate fits a slot");
+            P* agg = reinterpret_cast<P*>(A.lbP_agg);
+            scan_tile_agg_kernel<Op, T><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A, agg);
+            scan_carry_kernel<Op><<<1, kCarryBlock, 0, stream>>>(agg, static_cast<P*>(A.carry), A.tiles);
+        }
         if (ys_a) scan_adjoint_kernel<Op, T, true><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
         else scan_adjoint_kernel<Op, T, false><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
     }

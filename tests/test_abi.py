@@ -63,13 +63,16 @@ def test_host_side_validation_without_gpu():
     assert ws >= 256
     assert A.adpar_workspace_size(A.RULE_SCAN, A.OP_LINREC, A.F64, 1 << 26) > A.adpar_workspace_size(
         A.RULE_SCAN, A.OP_LINREC, A.F64, 1 << 20)
-    # the full scan workspace of FP64 MUL/LINREC holds the factored forward
-    # result (8 bytes per element and component); elsewhere both sizes agree
+    # the full scan workspace of FP64 MUL holds the factored forward result
+    # (8 bytes per element), that of the FP64 linear recurrence the carries
+    # of its 16-element runs (24 bytes per run); elsewhere both sizes agree
     n = 100001
-    for op, w in ((A.OP_MUL, 1), (A.OP_LINREC, 2)):
-        full = A.adpar_workspace_size(A.RULE_SCAN, op, A.F64, n)
-        mini = A.adpar_workspace_size(A.RULE_SCAN | A.WS_MINIMAL, op, A.F64, n)
-        assert full >= mini + 8 * w * n
+    full = A.adpar_workspace_size(A.RULE_SCAN, A.OP_MUL, A.F64, n)
+    mini = A.adpar_workspace_size(A.RULE_SCAN | A.WS_MINIMAL, A.OP_MUL, A.F64, n)
+    assert full >= mini + 8 * n
+    full = A.adpar_workspace_size(A.RULE_SCAN, A.OP_LINREC, A.F64, n)
+    mini = A.adpar_workspace_size(A.RULE_SCAN | A.WS_MINIMAL, A.OP_LINREC, A.F64, n)
+    assert full >= 24 * (n // 16) and full < mini + 8 * n
     for op in (A.OP_ADD, A.OP_MUL, A.OP_MIN, A.OP_MAX, A.OP_LINREC):
         assert A.adpar_workspace_size(A.RULE_SCAN, op, A.F32, n) == A.adpar_workspace_size(
             A.RULE_SCAN | A.WS_MINIMAL, op, A.F32, n)

@@ -127,10 +127,11 @@ def test_primal_scan(A, oracle, op, dt):
 @pytest.mark.parametrize("op", ["mul", "linrec"])
 @pytest.mark.parametrize("n", [1, 2047, 2049, 3 * 2048 + 5, 4 * 4096 + 3, 100001])
 def test_fp64_factored_and_minimal_workspace_paths(A, oracle, op, n):
-    """FP64 MUL and LINREC read the factored forward result when the
-    workspace has room for it and re-form the primal prefixes in the return
-    sweep when it has only the minimal size: both match the oracle, with the
-    recomputed ys and with accumulation into existing adjoints."""
+    """With the recomputed ys requested, FP64 MUL reads the factored forward
+    result when the workspace has room for it and both operators re-form the
+    primal prefixes in the return sweep when it has only the minimal size:
+    every path matches the oracle, with the recomputed ys and with
+    accumulation into existing adjoints."""
     dt = np.float64
     code = A.OPS[op]
     if op == "linrec":
@@ -143,7 +144,7 @@ def test_fp64_factored_and_minimal_workspace_paths(A, oracle, op, n):
     rab, rbb, rya, ryb = oracle.scan_vjp(op, a, ya, b, yb, abar=base, bbar=base_b)
     full = A.adpar_workspace_size(A.RULE_SCAN, code, A.F64, n)
     minimal = A.adpar_workspace_size(A.RULE_SCAN | A.WS_MINIMAL, code, A.F64, n)
-    assert full >= minimal + 8 * n
+    assert full >= minimal + (8 * n if op == "mul" else 0)
     for nbytes in (full, minimal):
         work = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
         ab0 = dev(base)
@@ -237,3 +238,41 @@ def test_add_max_scan_full_size(A, oracle, op):
     assert rel_l2(got, ref) < 1e-3
     if op == "max":
         np.testing.assert_array_equal(np.flatnonzero(got), np.flatnonzero(ref))
+
+
+@pytest.mark.parametrize("n", [1, 15, 16, 17, 2047, 2048, 2049, 3 * 2048 + 5, 100001, (1 << 20) + 3])
+@pytest.mark.parametrize("accumulate", [False, True])
+def test_fp64_linrec_runs_path(A, oracle, n, accumulate):
+    """The FP64 linear recurrence with the full workspace runs on 16-element
+    runs and 2048-element tiles (whole tiles through TMA, the last one
+    element by element): ragged sizes around run and tile edges, overwrite
+    and accumulation, against the oracle."""
+    a, b, ya, yb = synth.linrec(n, np.float64, seed=n + 21)
+    base = synth.normal(n, np.float64, seed=22) if accumulate else np.zeros(n)
+    base_b = base[::-1].copy()
+    rab, rbb, _, _ = oracle.scan_vjp("linrec", a, ya, b, yb, abar=base, bbar=base_b)
+    ab0, bb0 = dev(base), dev(base_b)
+    work = A.workspace(A.adpar_workspace_size(A.RULE_SCAN, A.OP_LINREC, A.F64, n))
+    A.adpar_vjp_scan("linrec", dev(a), dev(ya), b=dev(b), ybar_b=dev(yb), abar=ab0, bbar=bb0,
+                     accumulate=accumulate, work=work)
+    assert A.adpar_workspace_status(work) == A.OK
+    assert rel_l2(ab0.cpu().numpy(), rab) < 1e-12
+    assert rel_l2(bb0.cpu().numpy(), rbb) < 1e-12
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+@pytest.mark.parametrize("n", [1, 3, 4, 5, 8191, 8192, 8193, 16383, 16384, 16385, 3 * 16384 + 7, 1000003])
+@pytest.mark.parametrize("accumulate", [False, True])
+def test_add_scan_shared_tile_path(A, oracle, dt, n, accumulate):
+    """The + scan VJP without the recomputed ys takes whole 64 KB tiles
+    through one bulk copy into shared memory (the last tile element by
+    element): sizes around its tile edges (16384 FP32 / 8192 FP64 elements),
+    overwrite and accumulation, against the oracle."""
+    y = synth.normal(n, dt, seed=n + 31)
+    base = synth.normal(n, dt, seed=32) if accumulate else np.zeros(n, dt)
+    ref, _, _, _ = oracle.scan_vjp("add", np.zeros(n), y, abar=base)
+    ab0 = dev(base)
+    work = A.workspace(A.adpar_workspace_size(A.RULE_SCAN, A.OP_ADD, A.F64 if dt == np.float64 else A.F32, n))
+    A.adpar_vjp_scan("add", None, dev(y), abar=ab0, accumulate=accumulate, work=work)
+    assert A.adpar_workspace_status(work) == A.OK
+    assert rel_l2(ab0.cpu().numpy(), ref) < tol(dt, n)

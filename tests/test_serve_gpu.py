@@ -79,7 +79,7 @@ def test_same_alone_and_in_the_mix(S):
 def test_budget_admission_and_rejection(S):
     serve, pool = S
     reqs = serve.make_requests(60, rate=None, lo=10, hi=16, seed=6, window=pool.window)
-    big = serve.Request(999, "linrec", 1 << 17, dtype="f64")  # larger than the arena below
+    big = serve.Request(999, "linrec", 1 << 18, dtype="f64")  # larger than the arena below
     budget = 3 * (1 << 20)
     assert big.bytes() > budget
     srv = serve.Server(budget_bytes=budget, slots=8, max_n=pool.max_n, pool=pool)

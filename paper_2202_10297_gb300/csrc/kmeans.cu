@@ -21,12 +21,13 @@
 //              the row's minimum from the four threads; every centroid
 //              within the TF32 error bound of the minimum is a candidate
 //              (a thread whose second smallest is within the bound rescans
-//              its chunks, before the accumulator is released).  The
-//              certified argmin: candidates recomputed exactly in FP32; if
-//              two remain within the FP32 bound, FP64 (the oracle's own
-//              arithmetic) decides, ties to the lowest k.  Then the loss term
-//              (exact distance of the argmin) and, for the gradient,
-//              warp-cooperative row sums into shared memory.
+//              its chunks, before the accumulator is released).  Then,
+//              with warp w taking 8 rows and four adjacent lanes per row
+//              (8 coordinates each): the candidates' distances recomputed
+//              in FP32; if two remain within the FP32 bound, FP64 (the
+//              oracle's own arithmetic) decides, ties to the lowest k; the
+//              loss term (the argmin's distance) and, for the gradient,
+//              the row added into shared-memory row sums.
 // Every mbarrier wait is bounded; a timeout is recorded in the workspace
 // and the kernel drains its copies and MMAs, frees TMEM and returns.
 #include <cuda.h>
@@ -53,14 +54,14 @@ constexpr int KM_MAXCAND = 8;
 // shared memory layout (offsets from a 1024-aligned base)
 constexpr uint32_t OFF_C = 0;                                           // 32 KB
 constexpr uint32_t OFF_X = OFF_C + KM_KMAX * KM_D * 4;                  // 4 x 16 KB
-constexpr uint32_t OFF_SUM = OFF_X + KM_STAGES * KM_X_BYTES;            // 32 KB
-constexpr uint32_t OFF_CNT = OFF_SUM + KM_KMAX * KM_D * 4;              // 1 KB
+constexpr int KM_SUM_LD = KM_D + 1;  // row-sum stride: rows of other centroids on other banks
+constexpr uint32_t OFF_SUM = OFF_X + KM_STAGES * KM_X_BYTES;            // 33 KB
+constexpr uint32_t OFF_CNT = OFF_SUM + KM_KMAX * KM_SUM_LD * 4;         // 1 KB
 constexpr uint32_t OFF_CN2 = OFF_CNT + KM_KMAX * 4;                     // 1 KB
 constexpr uint32_t OFF_CAND = OFF_CN2 + KM_KMAX * 4;                    // 4 KB
-constexpr uint32_t OFF_ARG = OFF_CAND + KM_TILE * KM_MAXCAND * 4;       // 512 B: certified argmin per row
-constexpr uint32_t OFF_MIN = OFF_ARG + KM_TILE * 4;                     // 6 KB: [4][128] m1, m2, a1
-constexpr uint32_t OFF_NC = OFF_MIN + 3 * KM_GROUPS * KM_TILE * 4;      // 512 B: candidate counts
-constexpr uint32_t OFF_XN = OFF_NC + KM_TILE * 4;                       // 2 KB: [4][128] partial |x|^2
+constexpr uint32_t OFF_MIN = OFF_CAND + KM_TILE * KM_MAXCAND * 4;       // 6 KB: [4][128] m1, m2, a1
+constexpr uint32_t OFF_NC = OFF_MIN + 3 * KM_GROUPS * KM_TILE * 4;      // 1 KB: candidate counts, by tile parity
+constexpr uint32_t OFF_XN = OFF_NC + 2 * KM_TILE * 4;                   // 2 KB: [4][128] partial |x|^2
 constexpr uint32_t OFF_BAR = OFF_XN + KM_GROUPS * KM_TILE * 4;          // barriers
 constexpr uint32_t NBAR = 2 * KM_STAGES + 5;
 constexpr uint32_t OFF_MISC = OFF_BAR + NBAR * 8;
@@ -89,17 +90,28 @@ __device__ __forceinline__ float sw_elem(const float* tile, int r, int j) {
     const int chunk = (j >> 2) ^ (r & 7);
     return tile[r * 32 + chunk * 4 + (j & 3)];
 }
-// ||x_r - c_kc||^2 in FP32, sequential over the 32 coordinates (row r of
-// the X tile and row kc of the C tile, both swizzled in shared memory)
-__device__ __noinline__ float exact_f32(const float* xt, int r, const float* sC, int kc) {
-    float s = 0.f;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        const float d = sw_elem(xt, r, j) - sw_elem(sC, kc, j);
-        s = fmaf(d, d, s);
-    }
+// ||x - c_kc||^2 in FP32 for one row: each of four adjacent lanes sums the
+// squares of its 8 coordinates (x0, x1: the row's chunks 2 g, 2 g + 1), then
+// two butterfly steps add the partial sums, so that the four lanes hold the
+// same value.  All lanes of the warp call it.
+__device__ __forceinline__ float cand_dist_f32(const float4& x0, const float4& x1, const float* sC, int kc, int g) {
+    const float* crow = sC + kc * KM_D;
+    const float4 c0 = *reinterpret_cast<const float4*>(crow + (((2 * g) ^ (kc & 7)) * 4));
+    const float4 c1 = *reinterpret_cast<const float4*>(crow + (((2 * g + 1) ^ (kc & 7)) * 4));
+    float d, s = 0.f;
+    d = x0.x - c0.x; s = fmaf(d, d, s);
+    d = x0.y - c0.y; s = fmaf(d, d, s);
+    d = x0.z - c0.z; s = fmaf(d, d, s);
+    d = x0.w - c0.w; s = fmaf(d, d, s);
+    d = x1.x - c1.x; s = fmaf(d, d, s);
+    d = x1.y - c1.y; s = fmaf(d, d, s);
+    d = x1.z - c1.z; s = fmaf(d, d, s);
+    d = x1.w - c1.w; s = fmaf(d, d, s);
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
     return s;
 }
+
 // the oracle's FP64 arithmetic: s += (x - c)^2 with no fused multiply-add
 __device__ __noinline__ double exact_f64(const float* xt, int r, const float* sC, int kc) {
     double s = 0.0;
@@ -190,8 +202,7 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
     float* s_cn2 = reinterpret_cast<float*>(base + OFF_CN2);
     int* s_cand = reinterpret_cast<int*>(base + OFF_CAND);
     float* s_min = reinterpret_cast<float*>(base + OFF_MIN);
-    int* s_arg = reinterpret_cast<int*>(base + OFF_ARG);
-    int* s_ncand = reinterpret_cast<int*>(base + OFF_NC);
+    int* s_ncand_buf = reinterpret_cast<int*>(base + OFF_NC);
     float* s_xn = reinterpret_cast<float*>(base + OFF_XN);
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + OFF_BAR);
     uint64_t* x_full = bars;
@@ -224,7 +235,7 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
         tc::tma_prefetch_desc(&tmX);
         tc::tma_prefetch_desc(&tmC);
     }
-    for (int q = threadIdx.x; q < k * KM_D; q += KM_THREADS) s_sum[q] = 0.f;
+    for (int q = threadIdx.x; q < k * KM_SUM_LD; q += KM_THREADS) s_sum[q] = 0.f;
     float cm = 0.f;
     for (int c = threadIdx.x; c < k; c += KM_THREADS) {
         float s = 0.f;
@@ -302,6 +313,9 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
         int i = 0;
         for (int64_t t = blockIdx.x; t < A.ntiles; t += gridDim.x, ++i) {
             const int s = i % KM_STAGES, b = i & 1;
+            // the counts alternate between two buffers: a warp may reset the
+            // next tile's while others still read this tile's
+            int* s_ncand = s_ncand_buf + b * KM_TILE;
             const bool ok = tc::mbar_wait(&t_full[b], (i >> 1) & 1, s_abort) &&
                             tc::mbar_wait(&x_full[s], (i / KM_STAGES) & 1, s_abort);
             if (epi_any(!ok)) {  // every epilogue thread leaves together
@@ -373,65 +387,78 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
             tc::mbar_arrive(&t_empty[b]);  // the accumulator may be overwritten now
             epi_sync();
 
-            // certify the argmin among the candidates (group 0 of each row)
-            if (grp == 0) {
-                const int nc = s_ncand[r];
-                int best = 0;
-                double dist = 0.0;
-                if (nc == 1) {
-                    best = s_cand[r * KM_MAXCAND];
-                    dist = (double)exact_f32(xt, r, sC, best);
-                } else {
-                    const int ncc = nc <= KM_MAXCAND ? nc : 0;  // 0: fall back to all k
-                    float e32[KM_MAXCAND];
-                    float u32 = CUDART_INF_F;
-                    for (int c = 0; c < ncc; ++c) {
-                        e32[c] = exact_f32(xt, r, sC, s_cand[r * KM_MAXCAND + c]);
-                        u32 = fminf(u32, e32[c] + 4.0e-6f * e32[c] + 1e-30f);
-                    }
-                    int n2 = 0, only = -1;
-                    float only_e = 0.f;
-                    for (int c = 0; c < ncc; ++c) {
-                        if (e32[c] - 4.0e-6f * e32[c] <= u32) {
-                            ++n2;
-                            only = s_cand[r * KM_MAXCAND + c];
-                            only_e = e32[c];
+            // certification, loss and row sums: warp ew takes rows 8 ew ..
+            // 8 ew + 7, four adjacent lanes per row, lane g of a row the
+            // coordinates 8 g .. 8 g + 7
+            {
+                const int rc = ew * 8 + (lane >> 2), g = lane & 3;
+                const float* xrow = xt + rc * KM_D;
+                const float4 x0 = *reinterpret_cast<const float4*>(xrow + (((2 * g) ^ (rc & 7)) * 4));
+                const float4 x1 = *reinterpret_cast<const float4*>(xrow + (((2 * g + 1) ^ (rc & 7)) * 4));
+                const int nc = s_ncand[rc];
+                // more than KM_MAXCAND candidates: every centroid is one
+                const int cnt = nc <= KM_MAXCAND ? nc : k;
+                int cmax_w = cnt;
+#pragma unroll
+                for (int off = 4; off < 32; off <<= 1) cmax_w = max(cmax_w, __shfl_xor_sync(0xffffffffu, cmax_w, off));
+                // FP32 distances of the candidates (a sum of four 8-term
+                // partial sums); the smallest, its centroid, the second smallest
+                float emin = CUDART_INF_F, e2 = CUDART_INF_F;
+                int kmin = 0;
+                for (int c = 0; c < cmax_w; ++c) {
+                    const bool has = c < cnt;
+                    const int kc = has ? (nc <= KM_MAXCAND ? s_cand[rc * KM_MAXCAND + c] : c) : 0;
+                    const float e = cand_dist_f32(x0, x1, sC, kc, g);
+                    if (has) {
+                        if (e < emin) {
+                            e2 = emin;
+                            emin = e;
+                            kmin = kc;
+                        } else if (e < e2) {
+                            e2 = e;
                         }
                     }
-                    if (ncc > 0 && n2 == 1) {
-                        best = only;
-                        dist = (double)only_e;
-                    } else {
-                        // FP64 over what FP32 cannot separate; ties to the lowest k
-                        double bd = CUDART_INF;
-                        best = k;
-                        const int lim = ncc > 0 ? ncc : k;
-                        for (int c = 0; c < lim; ++c) {
-                            const int kc = ncc > 0 ? s_cand[r * KM_MAXCAND + c] : c;
-                            if (ncc > 0 && !(e32[c] - 4.0e-6f * e32[c] <= u32)) continue;
-                            const double d = exact_f64(xt, r, sC, kc);
-                            if (d < bd || (d == bd && kc < best)) { bd = d; best = kc; }
+                }
+                // FP32 separates the smallest when no other candidate is
+                // within the FP32 bound of it; else FP64 (the oracle's own
+                // arithmetic) decides among those within it, ties to the lowest k
+                const float u32 = emin + 4.0e-6f * emin + 1e-30f;
+                const bool need64 = e2 - 4.0e-6f * e2 <= u32;
+                int best = kmin;
+                double dist = (double)emin;
+                if (__any_sync(0xffffffffu, need64)) {
+                    double bd = CUDART_INF;
+                    int bk = k;
+                    for (int c = 0; c < cmax_w; ++c) {
+                        const bool has = c < cnt;
+                        const int kc = has ? (nc <= KM_MAXCAND ? s_cand[rc * KM_MAXCAND + c] : c) : 0;
+                        const float e = cand_dist_f32(x0, x1, sC, kc, g);
+                        if (need64 && has && g == 0 && e - 4.0e-6f * e <= u32) {
+                            const double d = exact_f64(xt, rc, sC, kc);
+                            if (d < bd || (d == bd && kc < bk)) { bd = d; bk = kc; }
                         }
-                        dist = bd;
                     }
+                    bk = __shfl_sync(0xffffffffu, bk, lane & ~3);
+                    bd = __shfl_sync(0xffffffffu, bd, lane & ~3);
+                    if (need64) { best = bk; dist = bd; }
                 }
-                const int64_t row = t * KM_TILE + r;
-                const bool valid = row < A.N;
-                if (valid) {
-                    loss_local += dist;
-                    if (A.argmin_out) A.argmin_out[row] = best;
-                }
-                s_arg[r] = valid ? best : -1;
-            }
-            if (want_grad) {
-                epi_sync();
-                // row sums: warp ew takes rows [8 ew, 8 ew + 8), one row per step,
-                // lanes = coordinates (32 consecutive floats: no bank conflicts)
-                for (int rr = ew * 8; rr < ew * 8 + 8; ++rr) {
-                    const int kc = s_arg[rr];
-                    if (kc >= 0) {
-                        atomicAdd(&s_sum[kc * KM_D + lane], sw_elem(xt, rr, lane));
-                        if (lane == 0) atomicAdd(&s_cnt[kc], 1.f);
+                const int64_t row = t * KM_TILE + rc;
+                if (row < A.N) {
+                    if (g == 0) {
+                        loss_local += dist;
+                        if (A.argmin_out) A.argmin_out[row] = best;
+                    }
+                    if (want_grad) {
+                        float* srow = s_sum + best * KM_SUM_LD + 8 * g;
+                        atomicAdd(srow + 0, x0.x);
+                        atomicAdd(srow + 1, x0.y);
+                        atomicAdd(srow + 2, x0.z);
+                        atomicAdd(srow + 3, x0.w);
+                        atomicAdd(srow + 4, x1.x);
+                        atomicAdd(srow + 5, x1.y);
+                        atomicAdd(srow + 6, x1.z);
+                        atomicAdd(srow + 7, x1.w);
+                        if (g == 0) atomicAdd(&s_cnt[best], 1.f);
                     }
                 }
             }
@@ -458,7 +485,8 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
 
     if (want_grad) {
         for (int q = threadIdx.x; q < k * KM_D; q += KM_THREADS)
-            if (s_sum[q] != 0.f) atomicAdd(&A.gsum[q], s_sum[q]);
+            if (s_sum[(q / KM_D) * KM_SUM_LD + q % KM_D] != 0.f)
+                atomicAdd(&A.gsum[q], s_sum[(q / KM_D) * KM_SUM_LD + q % KM_D]);
         for (int q = threadIdx.x; q < k; q += KM_THREADS)
             if (s_cnt[q] != 0.f) atomicAdd(&A.gcnt[q], s_cnt[q]);
     }

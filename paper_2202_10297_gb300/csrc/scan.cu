@@ -707,7 +707,7 @@ int launch_add_smem(ScanArgs A, cudaStream_t stream) {
     return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
 }
 
-// ------------------------------------- FP64 linear recurrence, per-thread runs
+// ------------------------------------------ linear recurrence, per-thread runs
 // Host side of scan_runs.cuh: workspace layout, tensor maps, launches.
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -726,17 +726,20 @@ EncodeTiledFn encode_tiled() {
     return fn;
 }
 
-// An FP64 array of n elements seen as [n / kRunV runs][kRunRows][16]: box
-// of kRunNT runs, 128-byte swizzle (one array tile per copy).
-bool make_run_map(CUtensorMap* m, const double* ptr, int64_t n) {
+// An array of n elements seen as [n / V runs][1][V] (one 128-byte row per
+// run): box of kRunNT runs, 128-byte swizzle (one array tile per copy).
+template <class T>
+bool make_run_map(CUtensorMap* m, const T* ptr, int64_t n) {
     EncodeTiledFn f = encode_tiled();
     if (!f) return false;
-    cuuint64_t dims[3] = {16, (cuuint64_t)kRunRows, (cuuint64_t)(n / kRunV)};
-    cuuint64_t strides[2] = {128, (cuuint64_t)(128 * kRunRows)};
-    cuuint32_t box[3] = {16, (cuuint32_t)kRunRows, (cuuint32_t)kRunNT};
+    constexpr int V = RunCfg<T>::V;
+    cuuint64_t dims[3] = {(cuuint64_t)V, 1, (cuuint64_t)(n / V)};
+    cuuint64_t strides[2] = {128, 128};
+    cuuint32_t box[3] = {(cuuint32_t)V, 1, (cuuint32_t)kRunNT};
     cuuint32_t es[3] = {1, 1, 1};
-    return f(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, const_cast<double*>(ptr), dims, strides, box, es,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+    const CUtensorMapDataType dt = sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    return f(m, dt, 3, const_cast<T*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -745,11 +748,12 @@ struct RunLayout {
     int64_t tiles;
 };
 
+template <class T>
 RunLayout run_layout(int64_t n) {
     RunLayout L;
-    L.tiles = (n + kRunTile - 1) / kRunTile;
+    L.tiles = (n + RunCfg<T>::TILE - 1) / RunCfg<T>::TILE;
     const size_t t = (size_t)L.tiles;
-    const size_t wp = t * (size_t)lb_words<RunP>(), wr = t * (size_t)lb_words<RunL>();
+    const size_t wp = t * (size_t)lb_words<RunP<T>>(), wr = t * (size_t)lb_words<RunL<T>>();
     size_t o = sizeof(WsHeader);
     L.off_slots = o;
     L.off_pA = o; o += wp * 8;
@@ -759,55 +763,55 @@ RunLayout run_layout(int64_t n) {
     L.slot_words = (o - L.off_slots) / 8;
     const size_t runs = t * (size_t)kRunNT;
     o = round_up(o, 256);
-    L.off_carA = o; o = round_up(o + runs * 8, 256);
-    L.off_carB = o; o = round_up(o + runs * 8, 256);
-    L.off_prod = o; o = round_up(o + runs * 8, 256);
+    L.off_carA = o; o = round_up(o + runs * sizeof(T), 256);
+    L.off_carB = o; o = round_up(o + runs * sizeof(T), 256);
+    L.off_prod = o; o = round_up(o + runs * sizeof(T), 256);
     L.total = o;
     return L;
 }
 
+template <class T>
 int run_linrec_runs(int64_t n, const void* a, const void* b, const void* ya, const void* yb, void* abar,
                     void* bbar, uint32_t flags, void* work, cudaStream_t stream) {
-    const RunLayout L = run_layout(n);
+    using Cf = RunCfg<T>;
+    const RunLayout L = run_layout<T>(n);
     char* w = static_cast<char*>(work);
-    RunArgs R{};
+    RunArgs<T> R{};
     R.n = n;
     R.tiles = L.tiles;
-    R.a = static_cast<const double*>(a);
-    R.b = static_cast<const double*>(b);
-    R.ya = static_cast<const double*>(ya);
-    R.yb = static_cast<const double*>(yb);
-    R.abar = static_cast<double*>(abar);
-    R.bbar = static_cast<double*>(bbar);
+    R.a = static_cast<const T*>(a);
+    R.b = static_cast<const T*>(b);
+    R.ya = static_cast<const T*>(ya);
+    R.yb = static_cast<const T*>(yb);
+    R.abar = static_cast<T*>(abar);
+    R.bbar = static_cast<T*>(bbar);
     R.accumulate = (flags & ADPAR_ACCUMULATE) ? 1 : 0;
     R.hdr = reinterpret_cast<WsHeader*>(w);
-    R.lbP_agg = reinterpret_cast<unsigned long long*>(w + L.off_pA);
-    R.lbP_incl = reinterpret_cast<unsigned long long*>(w + L.off_pI);
     R.lbR_agg = reinterpret_cast<unsigned long long*>(w + L.off_rA);
     R.lbR_incl = reinterpret_cast<unsigned long long*>(w + L.off_rI);
-    R.carA = reinterpret_cast<double*>(w + L.off_carA);
-    R.carB = reinterpret_cast<double*>(w + L.off_carB);
-    R.prod = reinterpret_cast<double*>(w + L.off_prod);
+    R.carA = reinterpret_cast<T*>(w + L.off_carA);
+    R.carB = reinterpret_cast<T*>(w + L.off_carB);
+    R.prod = reinterpret_cast<T*>(w + L.off_prod);
     // the tile aggregates and carries take the primal look-back slots
-    static_assert(lb_words<RunP>() * 8 >= sizeof(RunP), "a state fits a slot");
-    R.tagg = reinterpret_cast<RunP*>(w + L.off_pA);
-    R.tcar = reinterpret_cast<RunP*>(w + L.off_pI);
+    static_assert(lb_words<RunP<T>>() * 8 >= sizeof(RunP<T>), "a state fits a slot");
+    R.tagg = reinterpret_cast<RunP<T>*>(w + L.off_pA);
+    R.tcar = reinterpret_cast<RunP<T>*>(w + L.off_pI);
     CUtensorMap tm[6];
     memset(tm, 0, sizeof(tm));
-    if (n >= kRunTile) {
+    if (n >= Cf::TILE) {
         // whole tiles exist: their copies go through TMA (the partial last
-        // tile, and every tile when n < kRunTile, is copied element-wise)
-        const double* ptr[6] = {R.a, R.b, R.ya, R.yb, R.abar, R.bbar};
+        // tile, and every tile when n < one tile, is copied element-wise)
+        const T* ptr[6] = {R.a, R.b, R.ya, R.yb, R.abar, R.bbar};
         for (int i = 0; i < 6; ++i)
-            if (!make_run_map(&tm[i], ptr[i], n)) return ADPAR_ERR_CUDA;
+            if (!make_run_map<T>(&tm[i], ptr[i], n)) return ADPAR_ERR_CUDA;
     }
     static bool configured[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return ADPAR_ERR_CUDA;
     if (!configured[dev]) {
-        if (cudaFuncSetAttribute(linrec_runs_carry_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(linrec_runs_carry_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  2 * kRunArrBytes) != cudaSuccess ||
-            cudaFuncSetAttribute(linrec_runs_vjp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaFuncSetAttribute(linrec_runs_vjp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  4 * kRunArrBytes) != cudaSuccess)
             return ADPAR_ERR_CUDA;
         configured[dev] = true;
@@ -816,10 +820,10 @@ int run_linrec_runs(int64_t n, const void* a, const void* b, const void* ya, con
     const int iblocks = (int)std::min<int64_t>((words + 255) / 256 + 1, 2048);
     scan_init_kernel<<<iblocks, 256, 0, stream>>>(R.hdr, reinterpret_cast<unsigned long long*>(w + L.off_slots),
                                                   words);
-    linrec_runs_carry_kernel<<<(unsigned)L.tiles, kRunNT, 2 * kRunArrBytes, stream>>>(tm[0], tm[1], R);
-    scan_carry_kernel<RunPOp><<<1, kCarryBlock, 0, stream>>>(R.tagg, R.tcar, L.tiles);
-    linrec_runs_vjp_kernel<<<(unsigned)L.tiles, kRunNT, 4 * kRunArrBytes, stream>>>(tm[0], tm[1], tm[2], tm[3],
-                                                                                    tm[4], tm[5], R);
+    linrec_runs_carry_kernel<T><<<(unsigned)L.tiles, kRunNT, 2 * kRunArrBytes, stream>>>(tm[0], tm[1], R);
+    scan_carry_kernel<RunPOp<T>><<<1, kCarryBlock, 0, stream>>>(R.tagg, R.tcar, L.tiles);
+    linrec_runs_vjp_kernel<T><<<(unsigned)L.tiles, kRunNT, 4 * kRunArrBytes, stream>>>(tm[0], tm[1], tm[2], tm[3],
+                                                                                       tm[4], tm[5], R);
     return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
 }
 
@@ -884,8 +888,8 @@ ScanLayout scan_layout(int64_t n) {
         s.off_thc = o; o = round_up(o + ptiles * (size_t)kScanBlock * sizeof(P), 256);
     }
     s.total = o;
-    if constexpr (std::is_same<Op, OpLinrec<T>>::value && sizeof(T) == 8)
-        s.total = std::max(s.total, run_layout(n).total);
+    if constexpr (std::is_same<Op, OpLinrec<T>>::value)
+        s.total = std::max(s.total, run_layout<T>(n).total);
     return s;
 }
 
@@ -935,10 +939,10 @@ int run_scan(int64_t n, const void* a, const void* b, const void* ya, const void
     A.hdr = reinterpret_cast<WsHeader*>(w);
     set_slots(A, w, L);
     const bool need_primal = Op::kNeedPrimal || Op::kCoefNeedsPrimal || ys_a != nullptr;
-    if constexpr (std::is_same<Op, OpLinrec<T>>::value && sizeof(T) == 8) {
+    if constexpr (std::is_same<Op, OpLinrec<T>>::value) {
         // per-thread runs, when the workspace holds the runs' carries
-        if (!ys_a && work_bytes >= run_layout(n).total)
-            return run_linrec_runs(n, a, b, ya, yb, abar, bbar, flags, work, stream);
+        if (!ys_a && work_bytes >= run_layout<T>(n).total)
+            return run_linrec_runs<T>(n, a, b, ya, yb, abar, bbar, flags, work, stream);
     }
     launch_init(A, w, L, stream);
     if constexpr (kFactored<Op, T>) {

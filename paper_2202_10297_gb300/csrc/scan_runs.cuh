@@ -1,17 +1,19 @@
-// The linear-recurrence scan VJP in FP64 with per-thread runs (Sec. 5.2's
-// rule for (a1,b1) (.) (a2,b2) = (a2 a1, a2 b1 + b2)), for GB300, whose FP64
-// rate (2 lanes per SM per clock) rather than HBM bounds this operator.
+// The linear-recurrence scan VJP with per-thread runs (Sec. 5.2's rule for
+// (a1,b1) (.) (a2,b2) = (a2 a1, a2 b1 + b2)), in FP64 and FP32.  In FP64 the
+// GB300's FP64 rate (2 lanes per SM per clock) rather than HBM bounds this
+// operator; in FP32 HBM does.
 //
-// Every thread owns a run of kRunV consecutive elements, so the per-element
-// work is plain sequential recurrences and the block-level scans (a few FP64
-// operations per combine) run once per run instead of once per element:
+// Every thread owns a run of V consecutive elements (one 128-byte row: 16
+// doubles or 32 floats), so the per-element work is plain sequential
+// recurrences and the block-level scans (a few operations per combine) run
+// once per run instead of once per element:
 //
 //  pass C (forward): fold each run into its primal aggregate (prod of a, B
-//     over the run: 2 FP64 operations per element), scan the runs of a tile,
-//     and store per run the exclusive carry from the tile's start and the
-//     run's product of a, and per tile its aggregate; one block then scans
-//     the tile aggregates into the state before each tile (no look-back:
-//     a pass that writes little per element has nothing to hide one behind).
+//     over the run: 2 operations per element), scan the runs of a tile, and
+//     store per run the exclusive carry from the tile's start and the run's
+//     product of a, and per tile its aggregate; one block then scans the
+//     tile aggregates into the state before each tile (no look-back: a pass
+//     that writes little per element has nothing to hide one behind).
 //  pass R (reverse, tiles right to left), per run, with U_j = a_j rs_bar_j
 //     (the adjoint flowing left out of element j):
 //     1. the primal from the run's carry: A_{j-1}, B_{j-1} (2 per element);
@@ -23,11 +25,11 @@
 //     4. rs_bar_j = ybar_j + a_{j+1} rs_bar_{j+1} (rs_bar_e = ybar_e + U_{e+1})
 //        and the outputs abar_j = A_{j-1} rsA_j + B_{j-1} rsB_j,
 //        bbar_j = rsB_j (4 per element).
-//  That is 10 FP64 operations per element plus a share of the run scans,
-//  and 16 + 32 + 16 bytes of HBM traffic per element plus 48 bytes per run.
+//  That is 10 operations per element plus a share of the run scans, and
+//  (2 + 4 + 2) element sizes of HBM traffic per element plus 3 per run.
 //
-// A tile is kRunNT runs; each input array's tile (kRunNT runs of kRunV
-// doubles) comes into shared memory by one 3-D TMA copy with the 128-byte swizzle
+// A tile is kRunNT runs; each input array's tile (kRunNT runs of 128 bytes)
+// comes into shared memory by one 3-D TMA copy with the 128-byte swizzle
 // (16-byte chunk c of 128-byte row r stored at chunk c ^ (r & 7)), so that a
 // thread reading its own run with 16-byte loads meets few bank conflicts.
 // The outputs are written back into the cotangents' tiles and stored by TMA.
@@ -42,60 +44,74 @@
 
 namespace adpar {
 
-constexpr int kRunV = 16;                   // elements per run (a multiple of 16)
-constexpr int kRunRows = kRunV / 16;        // 128-byte rows per run
 constexpr int kRunNT = 128;                 // runs (threads) per tile
 constexpr int kRunNW = kRunNT / 32;         // warps per tile
-constexpr int kRunTile = kRunV * kRunNT;    // elements per tile
-constexpr int kRunArrBytes = kRunTile * 8;  // one array's tile
+constexpr int kRunChunks = 8;               // 16-byte chunks per run
+constexpr int kRunArrBytes = kRunNT * 128;  // one array's tile (16 KB)
 
+template <class T>
+struct RunCfg {
+    static constexpr int V = 128 / (int)sizeof(T);   // elements per run
+    static constexpr int EPC = 16 / (int)sizeof(T);  // elements per 16-byte chunk
+    static constexpr int TILE = V * kRunNT;          // elements per tile
+};
+
+template <class T>
+struct alignas(16) RunVec {
+    T v[16 / sizeof(T)];
+};
+
+template <class T>
 struct RunP {  // primal state (A, B)
-    double A, B;
+    T A, B;
 };
+template <class T>
 struct RunL {  // reverse transfer U -> d + c U, for both components
-    double c, dA, dB;
-};
-// the primal operator on RunP, in the shape the carry scan takes
-struct RunPOp {
-    using P = RunP;
-    __device__ static P pid() { return P{1.0, 0.0}; }
-    __device__ static P pcomb(const P& l, const P& r) { return P{l.A * r.A, fma(r.A, l.B, r.B)}; }
+    T c, dA, dB;
 };
 
+__device__ __forceinline__ double run_fma(double x, double y, double z) { return fma(x, y, z); }
+__device__ __forceinline__ float run_fma(float x, float y, float z) { return fmaf(x, y, z); }
+
+// the primal operator on RunP, in the shape the carry scan takes
+template <class T>
+struct RunPOp {
+    using P = RunP<T>;
+    __device__ static P pid() { return P{T(1), T(0)}; }
+    __device__ static P pcomb(const P& l, const P& r) { return P{l.A * r.A, run_fma(r.A, l.B, r.B)}; }
+};
+
+template <class T>
 struct RunArgs {
     int64_t n;
     int64_t tiles;
-    const double* a;
-    const double* b;
-    const double* ya;
-    const double* yb;
-    double* abar;
-    double* bbar;
+    const T* a;
+    const T* b;
+    const T* ya;
+    const T* yb;
+    T* abar;
+    T* bbar;
     int accumulate;
     WsHeader* hdr;
-    unsigned long long* lbP_agg;
-    unsigned long long* lbP_incl;
     unsigned long long* lbR_agg;
     unsigned long long* lbR_incl;
-    double* carA;  // [tiles * kRunNT] A before the run, from the tile's start
-    double* carB;  // [tiles * kRunNT] B before the run, from the tile's start
-    double* prod;  // [tiles * kRunNT] product of a over the run
-    RunP* tagg;    // [tiles] the tile's primal aggregate
-    RunP* tcar;    // [tiles] the primal state before the tile
+    T* carA;        // [tiles * kRunNT] A before the run, from the tile's start
+    T* carB;        // [tiles * kRunNT] B before the run, from the tile's start
+    T* prod;        // [tiles * kRunNT] product of a over the run
+    RunP<T>* tagg;  // [tiles] the tile's primal aggregate
+    RunP<T>* tcar;  // [tiles] the primal state before the tile
 };
 
-// byte offset of the 16-byte pair p (elements 2p, 2p+1) of run t in a
-// swizzled array tile
-__device__ __forceinline__ int run_pair_off(int t, int p) {
-    const int r = kRunRows * t + (p >> 3);
-    return r * 128 + (((p & 7) ^ (r & 7)) << 4);
-}
+// byte offset of 16-byte chunk p of run t in a swizzled array tile
+__device__ __forceinline__ int run_chunk_off(int t, int p) { return t * 128 + (((p & 7) ^ (t & 7)) << 4); }
 
-__device__ __forceinline__ double2 lds2(const unsigned char* base, int off) {
-    return *reinterpret_cast<const double2*>(base + off);
+template <class T>
+__device__ __forceinline__ RunVec<T> run_ld(const unsigned char* base, int off) {
+    return *reinterpret_cast<const RunVec<T>*>(base + off);
 }
-__device__ __forceinline__ void sts2(unsigned char* base, int off, double x, double y) {
-    *reinterpret_cast<double2*>(base + off) = make_double2(x, y);
+template <class T>
+__device__ __forceinline__ void run_st(unsigned char* base, int off, const RunVec<T>& v) {
+    *reinterpret_cast<RunVec<T>*>(base + off) = v;
 }
 
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int z, uint64_t* bar) {
@@ -118,10 +134,11 @@ __device__ __forceinline__ void bulk_commit_and_wait_read() {
 // One tile's arrays into shared memory: TMA when the tile is whole, else
 // element by element (pad past the end of the data).  All threads call it;
 // on return the data is visible to the block.
-template <int NA>
+template <class T, int NA>
 __device__ __forceinline__ void run_tile_load(unsigned char* const (&dst)[NA], const CUtensorMap* const (&tm)[NA],
-                                              const double* const (&src)[NA], const double (&pad)[NA], bool whole,
+                                              const T* const (&src)[NA], const T (&pad)[NA], bool whole,
                                               int64_t tile, int64_t n, uint64_t* bar, WsHeader* hdr) {
+    using Cf = RunCfg<T>;
     if (whole) {
         if (threadIdx.x == 0) {
             tc::mbar_init(bar, 1);
@@ -135,16 +152,17 @@ __device__ __forceinline__ void run_tile_load(unsigned char* const (&dst)[NA], c
         for (uint32_t w = 0; w < (1u << 20) && !ok; ++w) ok = tc::mbar_try_wait(bar, 0u);
         if (!ok) record_status(hdr, ADPAR_ERR_TIMEOUT);
     } else {
-        const int64_t e0 = tile * kRunTile;
-        for (int i = threadIdx.x; i < kRunTile / 2; i += kRunNT) {
-            const int t = i / (kRunV / 2), p = i % (kRunV / 2);
-            const int64_t e = e0 + (int64_t)t * kRunV + 2 * p;
-            const int off = run_pair_off(t, p);
+        const int64_t e0 = tile * Cf::TILE;
+        for (int i = threadIdx.x; i < kRunNT * kRunChunks; i += kRunNT) {
+            const int t = i / kRunChunks, p = i % kRunChunks;
+            const int64_t e = e0 + (int64_t)t * Cf::V + Cf::EPC * p;
+            const int off = run_chunk_off(t, p);
 #pragma unroll
             for (int q = 0; q < NA; ++q) {
-                const double x = e < n ? src[q][e] : pad[q];
-                const double y = e + 1 < n ? src[q][e + 1] : pad[q];
-                sts2(dst[q], off, x, y);
+                RunVec<T> v;
+#pragma unroll
+                for (int j = 0; j < Cf::EPC; ++j) v.v[j] = e + j < n ? src[q][e + j] : pad[q];
+                run_st<T>(dst[q], off, v);
             }
         }
         __syncthreads();
@@ -152,42 +170,46 @@ __device__ __forceinline__ void run_tile_load(unsigned char* const (&dst)[NA], c
 }
 
 // ---------------------------------------------------------------- pass C
+template <class T>
 __global__ void __launch_bounds__(kRunNT) linrec_runs_carry_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                    const __grid_constant__ CUtensorMap tmB,
-                                                                   RunArgs R) {
+                                                                   RunArgs<T> R) {
+    using Cf = RunCfg<T>;
+    using P = RunP<T>;
     extern __shared__ __align__(1024) unsigned char s_dyn[];
     unsigned char* sA = s_dyn;
     unsigned char* sB = s_dyn + kRunArrBytes;
     __shared__ __align__(8) uint64_t s_bar;
-    __shared__ RunP s_tot[kRunNW];
+    __shared__ P s_tot[kRunNW];
     const int64_t tile = blockIdx.x;
-    const bool whole = (tile + 1) * kRunTile <= R.n;
+    const bool whole = (tile + 1) * Cf::TILE <= R.n;
     {
         unsigned char* const dst[2] = {sA, sB};
         const CUtensorMap* const tm[2] = {&tmA, &tmB};
-        const double* const src[2] = {R.a, R.b};
-        const double pad[2] = {1.0, 0.0};  // (1, 0) is the neutral element
-        run_tile_load<2>(dst, tm, src, pad, whole, tile, R.n, &s_bar, R.hdr);
+        const T* const src[2] = {R.a, R.b};
+        const T pad[2] = {T(1), T(0)};  // (1, 0) is the neutral element
+        run_tile_load<T, 2>(dst, tm, src, pad, whole, tile, R.n, &s_bar, R.hdr);
     }
     const int t = threadIdx.x;
-    double A = 1.0, B = 0.0;
+    T A = T(1), B = T(0);
 #pragma unroll
-    for (int p = 0; p < kRunV / 2; ++p) {
-        const double2 x = lds2(sA, run_pair_off(t, p));
-        const double2 y = lds2(sB, run_pair_off(t, p));
-        B = fma(x.x, B, y.x);
-        A *= x.x;
-        B = fma(x.y, B, y.y);
-        A *= x.y;
+    for (int p = 0; p < kRunChunks; ++p) {
+        const RunVec<T> x = run_ld<T>(sA, run_chunk_off(t, p));
+        const RunVec<T> y = run_ld<T>(sB, run_chunk_off(t, p));
+#pragma unroll
+        for (int j = 0; j < Cf::EPC; ++j) {
+            B = run_fma(x.v[j], B, y.v[j]);
+            A *= x.v[j];
+        }
     }
-    const RunP agg[1] = {RunP{A, B}};
-    auto comb = [](const RunP& l, const RunP& r) { return RunP{l.A * r.A, fma(r.A, l.B, r.B)}; };
-    RunP wex[1];
-    const RunP ident{1.0, 0.0};
-    const RunP total = block_scan_part1<RunP, false, 1, kRunNW>(agg, wex, s_tot, ident, comb);
+    const P agg[1] = {P{A, B}};
+    auto comb = [](const P& l, const P& r) { return P{l.A * r.A, run_fma(r.A, l.B, r.B)}; };
+    P wex[1];
+    const P ident{T(1), T(0)};
+    const P total = block_scan_part1<P, false, 1, kRunNW>(agg, wex, s_tot, ident, comb);
     if (threadIdx.x == 0) R.tagg[tile] = total;
     __syncthreads();
-    const RunP ex = block_scan_excl<RunP, false, 1, kRunNW>(0, wex, s_tot, ident, comb);
+    const P ex = block_scan_excl<P, false, 1, kRunNW>(0, wex, s_tot, ident, comb);
     const int64_t run = tile * kRunNT + t;
     R.carA[run] = ex.A;
     R.carB[run] = ex.B;
@@ -195,10 +217,14 @@ __global__ void __launch_bounds__(kRunNT) linrec_runs_carry_kernel(const __grid_
 }
 
 // ---------------------------------------------------------------- pass R
+template <class T>
 __global__ void __launch_bounds__(kRunNT) linrec_runs_vjp_kernel(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
     const __grid_constant__ CUtensorMap tmYA, const __grid_constant__ CUtensorMap tmYB,
-    const __grid_constant__ CUtensorMap tmOA, const __grid_constant__ CUtensorMap tmOB, RunArgs R) {
+    const __grid_constant__ CUtensorMap tmOA, const __grid_constant__ CUtensorMap tmOB, RunArgs<T> R) {
+    using Cf = RunCfg<T>;
+    using L = RunL<T>;
+    constexpr int V = Cf::V, EPC = Cf::EPC;
     extern __shared__ __align__(1024) unsigned char s_dyn[];
     unsigned char* sA = s_dyn;
     unsigned char* sB = s_dyn + kRunArrBytes;      // b, then B_{j-1}
@@ -206,115 +232,106 @@ __global__ void __launch_bounds__(kRunNT) linrec_runs_vjp_kernel(
     unsigned char* sYB = s_dyn + 3 * kRunArrBytes;  // ybar_B, then bbar
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ uint32_t s_tile;
-    __shared__ RunL s_tot[kRunNW];
-    __shared__ RunL s_pre;
+    __shared__ L s_tot[kRunNW];
+    __shared__ L s_pre;
     if (threadIdx.x == 0) s_tile = atomicAdd(&R.hdr->ticket[1], 1u);
     __syncthreads();
     const int64_t t_log = s_tile;
     const int64_t tile = R.tiles - 1 - t_log;  // tiles are taken right to left
-    const bool whole = (tile + 1) * kRunTile <= R.n;
+    const bool whole = (tile + 1) * Cf::TILE <= R.n;
     const int t = threadIdx.x;
     const int64_t run = tile * kRunNT + t;
     // the run's carry (the state before the tile, then the run's local
     // carry within it) and product (pass C) load while the tile arrives
-    const RunP tc0 = R.tcar[tile];
-    const double lA = R.carA[run], lB = R.carB[run], cprod = R.prod[run];
-    const double PA = tc0.A * lA, PB = fma(lA, tc0.B, lB);
+    const RunP<T> tc0 = R.tcar[tile];
+    const T lA = R.carA[run], lB = R.carB[run], cprod = R.prod[run];
+    const T PA = tc0.A * lA, PB = run_fma(lA, tc0.B, lB);
     {
         unsigned char* const dst[4] = {sA, sB, sYA, sYB};
         const CUtensorMap* const tm[4] = {&tmA, &tmB, &tmYA, &tmYB};
-        const double* const src[4] = {R.a, R.b, R.ya, R.yb};
-        const double pad[4] = {1.0, 0.0, 0.0, 0.0};
-        run_tile_load<4>(dst, tm, src, pad, whole, tile, R.n, &s_bar, R.hdr);
+        const T* const src[4] = {R.a, R.b, R.ya, R.yb};
+        const T pad[4] = {T(1), T(0), T(0), T(0)};
+        run_tile_load<T, 4>(dst, tm, src, pad, whole, tile, R.n, &s_bar, R.hdr);
     }
 
     // 1. the primal from the carry: A_{j-1} in registers, B_{j-1} over b
-    double Aprev[kRunV];
+    T Aprev[V];
     {
-        double A = PA, B = PB;
+        T A = PA, B = PB;
 #pragma unroll
-        for (int p = 0; p < kRunV / 2; ++p) {
-            const int off = run_pair_off(t, p);
-            const double2 x = lds2(sA, off);
-            const double2 y = lds2(sB, off);
-            const double B0 = B;
-            Aprev[2 * p] = A;
-            B = fma(x.x, B, y.x);
-            A *= x.x;
-            Aprev[2 * p + 1] = A;
-            sts2(sB, off, B0, B);
-            B = fma(x.y, B, y.y);
-            A *= x.y;
+        for (int p = 0; p < kRunChunks; ++p) {
+            const int off = run_chunk_off(t, p);
+            const RunVec<T> x = run_ld<T>(sA, off);
+            const RunVec<T> y = run_ld<T>(sB, off);
+            RunVec<T> bp;
+#pragma unroll
+            for (int j = 0; j < EPC; ++j) {
+                Aprev[EPC * p + j] = A;
+                bp.v[j] = B;
+                B = run_fma(x.v[j], B, y.v[j]);
+                A *= x.v[j];
+            }
+            run_st<T>(sB, off, bp);
         }
     }
-    // 2. the run's reverse transfer: R_j = ybar_j + a_{j+1} R_{j+1}
-    double RA, RB, a_next;
-    {
-        const double2 y1 = lds2(sYA, run_pair_off(t, kRunV / 2 - 1));
-        const double2 y2 = lds2(sYB, run_pair_off(t, kRunV / 2 - 1));
-        const double2 x = lds2(sA, run_pair_off(t, kRunV / 2 - 1));
-        RA = fma(x.y, y1.y, y1.x);
-        RB = fma(x.y, y2.y, y2.x);
-        a_next = x.x;
+    // 2. the run's reverse transfer: R_j = ybar_j + a_{j+1} R_{j+1}, from
+    //    R_e = ybar_e; a_next ends as a_s, the run's first a
+    T RA = T(0), RB = T(0), a_next = T(0);
 #pragma unroll
-        for (int p = kRunV / 2 - 2; p >= 0; --p) {
-            const int off = run_pair_off(t, p);
-            const double2 ya = lds2(sYA, off);
-            const double2 yb = lds2(sYB, off);
-            const double2 aa = lds2(sA, off);
-            RA = fma(a_next, RA, ya.y);
-            RB = fma(a_next, RB, yb.y);
-            RA = fma(aa.y, RA, ya.x);
-            RB = fma(aa.y, RB, yb.x);
-            a_next = aa.x;
+    for (int p = kRunChunks - 1; p >= 0; --p) {
+        const int off = run_chunk_off(t, p);
+        const RunVec<T> ya = run_ld<T>(sYA, off);
+        const RunVec<T> yb = run_ld<T>(sYB, off);
+        const RunVec<T> aa = run_ld<T>(sA, off);
+#pragma unroll
+        for (int j = EPC - 1; j >= 0; --j) {
+            RA = run_fma(a_next, RA, ya.v[j]);
+            RB = run_fma(a_next, RB, yb.v[j]);
+            a_next = aa.v[j];
         }
     }
-    // a_next is now a_s, the run's first a
-    const RunL agg[1] = {RunL{cprod, a_next * RA, a_next * RB}};
+    const L agg[1] = {L{cprod, a_next * RA, a_next * RB}};
     // 3. scan of the transfers, right to left: comb(x, y) with x to the
     //    right of y is "x, then y"
-    auto comb = [](const RunL& x, const RunL& y) {
-        return RunL{y.c * x.c, fma(y.c, x.dA, y.dA), fma(y.c, x.dB, y.dB)};
+    auto comb = [](const L& x, const L& y) {
+        return L{y.c * x.c, run_fma(y.c, x.dA, y.dA), run_fma(y.c, x.dB, y.dB)};
     };
-    const RunL ident{1.0, 0.0, 0.0};
-    RunL wex[1];
-    const RunL total = block_scan_part1<RunL, true, 1, kRunNW>(agg, wex, s_tot, ident, comb);
+    const L ident{T(1), T(0), T(0)};
+    L wex[1];
+    const L total = block_scan_part1<L, true, 1, kRunNW>(agg, wex, s_tot, ident, comb);
     if ((threadIdx.x >> 5) == 0) {
-        LookbackState<RunL> st{R.lbR_agg, R.lbR_incl};
-        const RunL pre = lookback(t_log, st, total, ident, comb, R.hdr);
+        LookbackState<L> st{R.lbR_agg, R.lbR_incl};
+        const L pre = lookback(t_log, st, total, ident, comb, R.hdr);
         if ((threadIdx.x & 31) == 0) s_pre = pre;
     }
     __syncthreads();
-    const RunL ex = block_scan_excl<RunL, true, 1, kRunNW>(0, wex, s_tot, s_pre, comb);
+    const L ex = block_scan_excl<L, true, 1, kRunNW>(0, wex, s_tot, s_pre, comb);
 
-    // 4. rs_bar right to left and the outputs, written over the cotangents
+    // 4. rs_bar right to left and the outputs, written over the cotangents;
+    //    rs_bar_e = ybar_e + U_{e+1} with U_{e+1} = ex.d (a_up starts at 1)
     {
-        double rA = ex.dA, rB = ex.dB;  // U entering the run's last element
-        double a_up = 1.0;              // a_{j+1} (the factor carried into U)
+        T rA = ex.dA, rB = ex.dB;  // U entering the run's last element
+        T a_up = T(1);             // a_{j+1} (the factor carried into U)
 #pragma unroll
-        for (int p = kRunV / 2 - 1; p >= 0; --p) {
-            const int off = run_pair_off(t, p);
-            const double2 ya = lds2(sYA, off);
-            const double2 yb = lds2(sYB, off);
-            const double2 aa = lds2(sA, off);
-            const double2 bp = lds2(sB, off);  // B_{j-1}
-            // element 2p+1
-            const double rA1 = fma(a_up, rA, ya.y);
-            const double rB1 = fma(a_up, rB, yb.y);
-            const double o1 = fma(Aprev[2 * p + 1], rA1, bp.y * rB1);
-            // element 2p
-            const double rA0 = fma(aa.y, rA1, ya.x);
-            const double rB0 = fma(aa.y, rB1, yb.x);
-            const double o0 = fma(Aprev[2 * p], rA0, bp.x * rB0);
-            sts2(sYA, off, o0, o1);
-            sts2(sYB, off, rB0, rB1);
-            rA = rA0;
-            rB = rB0;
-            a_up = aa.x;
+        for (int p = kRunChunks - 1; p >= 0; --p) {
+            const int off = run_chunk_off(t, p);
+            const RunVec<T> ya = run_ld<T>(sYA, off);
+            const RunVec<T> yb = run_ld<T>(sYB, off);
+            const RunVec<T> aa = run_ld<T>(sA, off);
+            const RunVec<T> bp = run_ld<T>(sB, off);  // B_{j-1}
+            RunVec<T> oa, ob;
+#pragma unroll
+            for (int j = EPC - 1; j >= 0; --j) {
+                rA = run_fma(a_up, rA, ya.v[j]);
+                rB = run_fma(a_up, rB, yb.v[j]);
+                oa.v[j] = run_fma(Aprev[EPC * p + j], rA, bp.v[j] * rB);
+                ob.v[j] = rB;
+                a_up = aa.v[j];
+            }
+            run_st<T>(sYA, off, oa);
+            run_st<T>(sYB, off, ob);
         }
     }
-    // the first element's factor a_{j+1} for j = e is applied through U:
-    // rs_bar_e = ybar_e + U_{e+1} with U_{e+1} = ex.d (a_up starts at 1)
 
     if (whole && !R.accumulate) {
         tc::fence_proxy_async();
@@ -326,20 +343,19 @@ __global__ void __launch_bounds__(kRunNT) linrec_runs_vjp_kernel(
         }
         __syncthreads();
     } else {
-        const int64_t e0 = tile * kRunTile + (int64_t)t * kRunV;
-#pragma unroll 4
-        for (int p = 0; p < kRunV / 2; ++p) {
-            const int off = run_pair_off(t, p);
-            const double2 oa = lds2(sYA, off);
-            const double2 ob = lds2(sYB, off);
-            const int64_t e = e0 + 2 * p;
-            if (e < R.n) {
-                R.abar[e] = R.accumulate ? R.abar[e] + oa.x : oa.x;
-                R.bbar[e] = R.accumulate ? R.bbar[e] + ob.x : ob.x;
-            }
-            if (e + 1 < R.n) {
-                R.abar[e + 1] = R.accumulate ? R.abar[e + 1] + oa.y : oa.y;
-                R.bbar[e + 1] = R.accumulate ? R.bbar[e + 1] + ob.y : ob.y;
+        const int64_t e0 = tile * Cf::TILE + (int64_t)t * V;
+#pragma unroll 2
+        for (int p = 0; p < kRunChunks; ++p) {
+            const int off = run_chunk_off(t, p);
+            const RunVec<T> oa = run_ld<T>(sYA, off);
+            const RunVec<T> ob = run_ld<T>(sYB, off);
+#pragma unroll
+            for (int j = 0; j < EPC; ++j) {
+                const int64_t e = e0 + EPC * p + j;
+                if (e < R.n) {
+                    R.abar[e] = R.accumulate ? R.abar[e] + oa.v[j] : oa.v[j];
+                    R.bbar[e] = R.accumulate ? R.bbar[e] + ob.v[j] : ob.v[j];
+                }
             }
         }
     }

@@ -64,16 +64,18 @@ def test_host_side_validation_without_gpu():
     assert A.adpar_workspace_size(A.RULE_SCAN, A.OP_LINREC, A.F64, 1 << 26) > A.adpar_workspace_size(
         A.RULE_SCAN, A.OP_LINREC, A.F64, 1 << 20)
     # the full scan workspace of FP64 MUL holds the factored forward result
-    # (8 bytes per element), that of the FP64 linear recurrence the carries
-    # of its 16-element runs (24 bytes per run); elsewhere both sizes agree
+    # (8 bytes per element), that of the linear recurrence the carries of
+    # its runs (3 elements per run of 16 FP64 / 32 FP32 elements); elsewhere
+    # both sizes agree
     n = 100001
     full = A.adpar_workspace_size(A.RULE_SCAN, A.OP_MUL, A.F64, n)
     mini = A.adpar_workspace_size(A.RULE_SCAN | A.WS_MINIMAL, A.OP_MUL, A.F64, n)
     assert full >= mini + 8 * n
-    full = A.adpar_workspace_size(A.RULE_SCAN, A.OP_LINREC, A.F64, n)
-    mini = A.adpar_workspace_size(A.RULE_SCAN | A.WS_MINIMAL, A.OP_LINREC, A.F64, n)
-    assert full >= 24 * (n // 16) and full < mini + 8 * n
-    for op in (A.OP_ADD, A.OP_MUL, A.OP_MIN, A.OP_MAX, A.OP_LINREC):
+    for dt, run, es in ((A.F64, 16, 8), (A.F32, 32, 4)):
+        full = A.adpar_workspace_size(A.RULE_SCAN, A.OP_LINREC, dt, n)
+        mini = A.adpar_workspace_size(A.RULE_SCAN | A.WS_MINIMAL, A.OP_LINREC, dt, n)
+        assert full >= 3 * es * (n // run) and full < mini + es * n
+    for op in (A.OP_ADD, A.OP_MUL, A.OP_MIN, A.OP_MAX):
         assert A.adpar_workspace_size(A.RULE_SCAN, op, A.F32, n) == A.adpar_workspace_size(
             A.RULE_SCAN | A.WS_MINIMAL, op, A.F32, n)
     for op in (A.OP_ADD, A.OP_MIN, A.OP_MAX):

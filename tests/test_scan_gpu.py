@@ -240,24 +240,31 @@ def test_add_max_scan_full_size(A, oracle, op):
         np.testing.assert_array_equal(np.flatnonzero(got), np.flatnonzero(ref))
 
 
-@pytest.mark.parametrize("n", [1, 15, 16, 17, 2047, 2048, 2049, 3 * 2048 + 5, 100001, (1 << 20) + 3])
+RUN_SIZES = {np.float64: [1, 15, 16, 17, 2047, 2048, 2049, 3 * 2048 + 5, 100001, (1 << 20) + 3],
+             np.float32: [1, 31, 32, 33, 4095, 4096, 4097, 3 * 4096 + 5, 100001, (1 << 20) + 3]}
+
+
+@pytest.mark.parametrize("dt,n", [(dt, n) for dt in (np.float64, np.float32) for n in RUN_SIZES[dt]])
 @pytest.mark.parametrize("accumulate", [False, True])
-def test_fp64_linrec_runs_path(A, oracle, n, accumulate):
-    """The FP64 linear recurrence with the full workspace runs on 16-element
-    runs and 2048-element tiles (whole tiles through TMA, the last one
-    element by element): ragged sizes around run and tile edges, overwrite
-    and accumulation, against the oracle."""
-    a, b, ya, yb = synth.linrec(n, np.float64, seed=n + 21)
-    base = synth.normal(n, np.float64, seed=22) if accumulate else np.zeros(n)
+def test_linrec_runs_path(A, oracle, dt, n, accumulate):
+    """The linear recurrence with the full workspace runs on per-thread runs
+    of one 128-byte row (16 FP64 / 32 FP32 elements) and tiles of 128 runs
+    (whole tiles through TMA, the last one element by element): ragged sizes
+    around run and tile edges, overwrite and accumulation, against the
+    oracle."""
+    f64 = dt == np.float64
+    a, b, ya, yb = synth.linrec(n, dt, seed=n + 21)
+    base = synth.normal(n, dt, seed=22) if accumulate else np.zeros(n, dt)
     base_b = base[::-1].copy()
     rab, rbb, _, _ = oracle.scan_vjp("linrec", a, ya, b, yb, abar=base, bbar=base_b)
     ab0, bb0 = dev(base), dev(base_b)
-    work = A.workspace(A.adpar_workspace_size(A.RULE_SCAN, A.OP_LINREC, A.F64, n))
+    work = A.workspace(A.adpar_workspace_size(A.RULE_SCAN, A.OP_LINREC, A.F64 if f64 else A.F32, n))
     A.adpar_vjp_scan("linrec", dev(a), dev(ya), b=dev(b), ybar_b=dev(yb), abar=ab0, bbar=bb0,
                      accumulate=accumulate, work=work)
     assert A.adpar_workspace_status(work) == A.OK
-    assert rel_l2(ab0.cpu().numpy(), rab) < 1e-12
-    assert rel_l2(bb0.cpu().numpy(), rbb) < 1e-12
+    tol = 1e-12 if f64 else 1e-4
+    assert rel_l2(ab0.cpu().numpy(), rab) < tol
+    assert rel_l2(bb0.cpu().numpy(), rbb) < tol
 
 
 @pytest.mark.parametrize("dt", [np.float32, np.float64])

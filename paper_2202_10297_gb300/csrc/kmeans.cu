@@ -10,18 +10,20 @@
 // One persistent kernel, one CTA per SM, 20 warps:
 //   warp 0     TMA producer: X tiles of 128 rows x 32 FP32 (128-byte rows,
 //              128-byte swizzle) into a 4-stage ring; C (k x 32) once.
-//   warp 1     MMA issuer: S = X_tile C^T with tcgen05.mma kind::tf32
-//              (M = 128, N = k, K = 32 in four steps of 8) into one of two
-//              TMEM accumulators (2 x 256 columns).
+//   warp 1     MMA issuer: acc = X_tile C^T - |c|^2 / 2 with tcgen05.mma
+//              kind::tf32 (M = 128, N = k, K = 32 in four steps of 8, then
+//              one more K step with A rows (1, 1, 0, ..) and B rows holding
+//              -|c_k|^2 / 2 split into two TF32 parts) into one of two TMEM
+//              accumulators (2 x 256 columns).  The distance is
+//              |x|^2 - 2 acc_k, so the argmin is the argmax of acc.
 //   warp 2     TMEM allocation and release.
 //   warps 4-19 epilogue, four threads per row (warp w reads the TMEM lanes
 //              of quarter w % 4 and the 32-column chunks q = group (mod 4)):
-//              one tcgen05.ld pass over the distances v_k = |c_k|^2 - 2 x.c_k
-//              keeping the smallest, its column and the second smallest;
-//              the row's minimum from the four threads; every centroid
-//              within the TF32 error bound of the minimum is a candidate
-//              (a thread whose second smallest is within the bound rescans
-//              its chunks, before the accumulator is released).  Then,
+//              a tcgen05.ld pass keeping the largest acc_k (one max per
+//              value); the row's maximum from the four threads; a second
+//              pass listing every centroid within the TF32 error bound of
+//              it (one compare per value), before the accumulator is
+//              released.  Then,
 //              with warp w taking 8 rows and four adjacent lanes per row
 //              (8 coordinates each): the candidates' distances recomputed
 //              in FP32; if two remain within the FP32 bound, FP64 (the
@@ -55,18 +57,24 @@ constexpr int KM_MAXCAND = 8;
 constexpr uint32_t OFF_C = 0;                                           // 32 KB
 constexpr uint32_t OFF_X = OFF_C + KM_KMAX * KM_D * 4;                  // 4 x 16 KB
 constexpr int KM_SUM_LD = KM_D + 1;  // row-sum stride: rows of other centroids on other banks
-constexpr uint32_t OFF_SUM = OFF_X + KM_STAGES * KM_X_BYTES;            // 33 KB
+// the |c|^2 term as one more K step of 8: A rows (1, 1, 0, ..), B rows
+// (h_k, l_k, 0, ..) with h_k + l_k = -|c_k|^2 / 2, in the same swizzled layout
+constexpr uint32_t OFF_AX = OFF_X + KM_STAGES * KM_X_BYTES;             // 16 KB
+constexpr uint32_t OFF_BX = OFF_AX + KM_TILE * 128;                     // 32 KB
+constexpr uint32_t OFF_SUM = OFF_BX + KM_KMAX * 128;                    // 33 KB
 constexpr uint32_t OFF_CNT = OFF_SUM + KM_KMAX * KM_SUM_LD * 4;         // 1 KB
 constexpr uint32_t OFF_CN2 = OFF_CNT + KM_KMAX * 4;                     // 1 KB
 constexpr uint32_t OFF_CAND = OFF_CN2 + KM_KMAX * 4;                    // 4 KB
-constexpr uint32_t OFF_MIN = OFF_CAND + KM_TILE * KM_MAXCAND * 4;       // 6 KB: [4][128] m1, m2, a1
-constexpr uint32_t OFF_NC = OFF_MIN + 3 * KM_GROUPS * KM_TILE * 4;      // 1 KB: candidate counts, by tile parity
+constexpr uint32_t OFF_MAX = OFF_CAND + KM_TILE * KM_MAXCAND * 4;       // 2 KB: [4][128] partial row maxima
+constexpr uint32_t OFF_NC = OFF_MAX + KM_GROUPS * KM_TILE * 4;          // 1 KB: candidate counts, by tile parity
 constexpr uint32_t OFF_XN = OFF_NC + 2 * KM_TILE * 4;                   // 2 KB: [4][128] partial |x|^2
 constexpr uint32_t OFF_BAR = OFF_XN + KM_GROUPS * KM_TILE * 4;          // barriers
 constexpr uint32_t NBAR = 2 * KM_STAGES + 5;
 constexpr uint32_t OFF_MISC = OFF_BAR + NBAR * 8;
 constexpr uint32_t KM_SMEM = OFF_MISC + 64 + 1024;  // + alignment slack
-static_assert(OFF_X % 1024 == 0 && KM_X_BYTES % 1024 == 0, "swizzled tiles need 1024-byte alignment");
+static_assert(OFF_X % 1024 == 0 && KM_X_BYTES % 1024 == 0 && OFF_AX % 1024 == 0 && OFF_BX % 1024 == 0,
+              "swizzled tiles need 1024-byte alignment");
+static_assert(KM_SMEM <= 227 * 1024, "shared memory of one CTA");
 
 struct KmArgs {
     int64_t N;
@@ -148,38 +156,18 @@ __device__ __forceinline__ bool epi_any(bool p) {
     return r != 0;
 }
 
-// one 32-column chunk of v_k = |c_k|^2 - 2 S_k into the running smallest
-// (m1, at column a1) and second smallest (m2); ties keep the lower column
-__device__ __forceinline__ void chunk_track(const uint32_t (&v)[32], const float* cn2, int k0, float& m1, int& a1,
-                                            float& m2) {
+// candidates of one chunk: columns whose accumulator is at least thr,
+// appended to the row's list (a bit mask first, so that the 32 values are
+// dead before the rare appends)
+__device__ __forceinline__ void chunk_cand(const uint32_t (&v)[32], int k0, float thr, int* ncand, int* list) {
+    uint32_t mask = 0;
 #pragma unroll
-    for (int c4 = 0; c4 < 8; ++c4) {
-        const float4 c = *reinterpret_cast<const float4*>(cn2 + 4 * c4);
-        const float cc[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float x = fmaf(-2.f, __uint_as_float(v[4 * c4 + j]), cc[j]);
-            const bool lt = x < m1;
-            m2 = lt ? m1 : fminf(m2, x);
-            a1 = lt ? k0 + 4 * c4 + j : a1;
-            m1 = lt ? x : m1;
-        }
-    }
-}
-// candidates of one chunk: columns with v_k <= thr, appended to the row's list
-__device__ __forceinline__ void chunk_cand(const uint32_t (&v)[32], const float* cn2, int k0, float thr,
-                                           int* ncand, int* list) {
-#pragma unroll
-    for (int c4 = 0; c4 < 8; ++c4) {
-        const float4 c = *reinterpret_cast<const float4*>(cn2 + 4 * c4);
-        const float cc[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (fmaf(-2.f, __uint_as_float(v[4 * c4 + j]), cc[j]) <= thr) {
-                const int slot = atomicAdd(ncand, 1);
-                if (slot < KM_MAXCAND) list[slot] = k0 + 4 * c4 + j;
-            }
-        }
+    for (int j = 0; j < 32; ++j) mask |= (__uint_as_float(v[j]) >= thr ? 1u : 0u) << j;
+    while (mask) {
+        const int j = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int slot = atomicAdd(ncand, 1);
+        if (slot < KM_MAXCAND) list[slot] = k0 + j;
     }
 }
 
@@ -194,14 +182,19 @@ __global__ void km_init_kernel(KmArgs A) {
 __global__ void __launch_bounds__(KM_THREADS, 1)
     kmeans_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmC, KmArgs A) {
     extern __shared__ unsigned char smem_raw[];
-    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    // 1024-byte alignment by an offset into the shared array, so that every
+    // access below stays a shared-memory access (a round trip through an
+    // integer would leave the compiler generic loads, stores and atomics)
+    unsigned char* base = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
     float* sC = reinterpret_cast<float*>(base + OFF_C);
     float* sX = reinterpret_cast<float*>(base + OFF_X);
     float* s_sum = reinterpret_cast<float*>(base + OFF_SUM);
     float* s_cnt = reinterpret_cast<float*>(base + OFF_CNT);
     float* s_cn2 = reinterpret_cast<float*>(base + OFF_CN2);
     int* s_cand = reinterpret_cast<int*>(base + OFF_CAND);
-    float* s_min = reinterpret_cast<float*>(base + OFF_MIN);
+    float* s_max = reinterpret_cast<float*>(base + OFF_MAX);
+    float* sAX = reinterpret_cast<float*>(base + OFF_AX);
+    float* sBX = reinterpret_cast<float*>(base + OFF_BX);
     int* s_ncand_buf = reinterpret_cast<int*>(base + OFF_NC);
     float* s_xn = reinterpret_cast<float*>(base + OFF_XN);
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + OFF_BAR);
@@ -222,11 +215,11 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < KM_STAGES; ++s) {
             tc::mbar_init(&x_full[s], 1);
-            tc::mbar_init(&x_empty[s], KM_EPI);
+            tc::mbar_init(&x_empty[s], KM_EPI / 32);  // one arrival per epilogue warp
         }
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(&t_full[b], 1);
-            tc::mbar_init(&t_empty[b], KM_EPI);
+            tc::mbar_init(&t_empty[b], 1);  // one arrival after the epilogue barrier
         }
         tc::mbar_init(c_bar, 1);
         *s_abort = 0;
@@ -246,7 +239,24 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
         s_cn2[c] = s;
         s_cnt[c] = 0.f;
         cm = fmaxf(cm, s);
+        // -|c|^2 / 2 = h + l: h keeps the 10 mantissa bits TF32 reads, l
+        // (exact in FP32) the rest, of which TF32 keeps 10 more
+        const float hv = -0.5f * s;
+        const float h = __uint_as_float(__float_as_uint(hv) & 0xFFFFE000u);
+        sBX[c * KM_D + ((0 ^ (c & 7)) << 2) + 0] = h;
+        sBX[c * KM_D + ((0 ^ (c & 7)) << 2) + 1] = hv - h;
     }
+    // the rest of the two extra operands: A rows (1, 1, 0, ..), B rows of
+    // zeros past the first two elements (and past k)
+    for (int q = threadIdx.x; q < KM_TILE * KM_D; q += KM_THREADS) {
+        const int r = q / KM_D, j = q % KM_D;  // logical element j of row r
+        sAX[r * KM_D + (((j >> 2) ^ (r & 7)) << 2) + (j & 3)] = j < 2 ? 1.f : 0.f;
+    }
+    for (int q = threadIdx.x; q < KM_KMAX * KM_D; q += KM_THREADS) {
+        const int r = q / KM_D, j = q % KM_D;
+        if (j >= 2 || r >= k) sBX[r * KM_D + (((j >> 2) ^ (r & 7)) << 2) + (j & 3)] = 0.f;
+    }
+    tc::fence_proxy_async();  // generic-proxy writes, read by the tensor core
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) cm = fmaxf(cm, __shfl_xor_sync(0xffffffffu, cm, off));
     if (threadIdx.x == 0) *s_cmax = 0.f;
@@ -282,6 +292,8 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
         if (lane == 0) {
             const uint32_t idesc = tc::idesc_tf32_m128((uint32_t)k);
             const uint64_t bdesc = tc::desc_sw128_kmajor(tc::smem_u32(sC));
+            const uint64_t axdesc = tc::desc_sw128_kmajor(tc::smem_u32(sAX));
+            const uint64_t bxdesc = tc::desc_sw128_kmajor(tc::smem_u32(sBX));
             if (!tc::mbar_wait(c_bar, 0, s_abort)) *s_abort = 1;
             int i = 0;
             for (int64_t t = blockIdx.x; t < A.ntiles && !*s_abort; t += gridDim.x, ++i) {
@@ -293,6 +305,8 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
 #pragma unroll
                 for (int kk = 0; kk < KM_D / 8; ++kk)  // K step of 8 TF32 = 32 bytes = +2 in the address field
                     tc::mma_tf32(tmem + (uint32_t)(b * 256), adesc + 2 * kk, bdesc + 2 * kk, idesc, kk > 0);
+                // + (-|c_k|^2 / 2): the accumulator holds x.c_k - |c_k|^2 / 2
+                tc::mma_tf32(tmem + (uint32_t)(b * 256), axdesc, bxdesc, idesc, 1u);
                 tc::mma_commit(&t_full[b]);
                 committed = i + 1;
             }
@@ -305,9 +319,6 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
         const int r = quarter * 32 + lane;  // row of the tile == TMEM lane
         const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
         const int nq = k / 32;
-        float* s_m1 = s_min;
-        float* s_m2 = s_min + KM_GROUPS * KM_TILE;
-        int* s_a1 = reinterpret_cast<int*>(s_min + 2 * KM_GROUPS * KM_TILE);
         double loss_local = 0.0;
         if (!tc::mbar_wait(c_bar, 0, s_abort)) *s_abort = 1;
         int i = 0;
@@ -339,53 +350,46 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
             }
             const uint32_t tb = tmem + lane_base + (uint32_t)(b * 256);
 
-            // one pass: smallest, its column and second smallest of this
-            // thread's chunks (sixteen warps hide the load latency)
-            float m1 = CUDART_INF_F, m2 = CUDART_INF_F;
-            int a1 = 0;
+            // pass 1: the largest x.c_k - |c_k|^2 / 2 (the smallest distance)
+            // of this thread's chunks (sixteen warps hide the load latency)
+            float m1 = -CUDART_INF_F;
             for (int q = grp; q < nq; q += KM_GROUPS) {
                 uint32_t va[32];
                 __syncwarp();
                 tc::tmem_ld32(tb + (uint32_t)(q * 32), va);
                 tc::tmem_ld_wait();
-                chunk_track(va, s_cn2 + q * 32, q * 32, m1, a1, m2);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) m1 = fmaxf(m1, __uint_as_float(va[j]));
             }
-            s_m1[grp * KM_TILE + r] = m1;
-            s_m2[grp * KM_TILE + r] = m2;
-            s_a1[grp * KM_TILE + r] = a1;
+            s_max[grp * KM_TILE + r] = m1;
             if (grp == 0) s_ncand[r] = 0;
             epi_sync();
-            float mrow = s_m1[r], xn2 = s_xn[r];
+            float amax = s_max[r], xn2 = s_xn[r];
 #pragma unroll
             for (int g = 1; g < KM_GROUPS; ++g) {
-                mrow = fminf(mrow, s_m1[g * KM_TILE + r]);
+                amax = fmaxf(amax, s_max[g * KM_TILE + r]);
                 xn2 += s_xn[g * KM_TILE + r];
             }
             const float xn = sqrtf(xn2);
-            // |v~_k - v_k| <= 2 |S~ - S| + rounding <= 2^-8 |x| |c_k| (TF32 keeps 10
-            // mantissa bits of each operand) plus FP32 terms; 2x margin
+            // the distance is |x|^2 - 2 acc_k.  |acc~_k - acc_k| <= |S~ - S| +
+            // rounding <= 2^-9 |x| |c_k| (TF32 keeps 10 mantissa bits of each
+            // operand of S = x.c_k) plus FP32 terms, the norm term within
+            // 2^-21 |c_k|^2; the true argmin is within twice that of the
+            // computed maximum, and tol is 4x that bound
             const float tol = 8.0e-3f * xn * cmax + 1.0e-5f * (cmax * cmax + xn * cmax) + 1e-20f;
-            const float thr = mrow + 2.f * tol;
-            // candidates: every column within 2 tol of the row's minimum; a
-            // thread with two or more of them rescans its chunks (the whole
-            // warp loads together), the others add at most their smallest
-            const bool multi = m2 <= thr;
-            if (__any_sync(0xffffffffu, multi)) {
-                for (int q = grp; q < nq; q += KM_GROUPS) {
-                    uint32_t va[32];
-                    __syncwarp();
-                    tc::tmem_ld32(tb + (uint32_t)(q * 32), va);
-                    tc::tmem_ld_wait();
-                    if (multi) chunk_cand(va, s_cn2 + q * 32, q * 32, thr, s_ncand + r, s_cand + r * KM_MAXCAND);
-                }
+            const float thr = amax - tol;
+            // pass 2: candidates, every column within tol of the row's maximum
+            for (int q = grp; q < nq; q += KM_GROUPS) {
+                uint32_t va[32];
+                __syncwarp();
+                tc::tmem_ld32(tb + (uint32_t)(q * 32), va);
+                tc::tmem_ld_wait();
+                chunk_cand(va, q * 32, thr, s_ncand + r, s_cand + r * KM_MAXCAND);
             }
-            if (!multi && m1 <= thr) {
-                const int slot = atomicAdd(s_ncand + r, 1);
-                if (slot < KM_MAXCAND) s_cand[r * KM_MAXCAND + slot] = a1;
-            }
+            // every epilogue thread has read the accumulator past this barrier
             tc::fence_before_sync();
-            tc::mbar_arrive(&t_empty[b]);  // the accumulator may be overwritten now
             epi_sync();
+            if (ew == 0 && lane == 0) tc::mbar_arrive(&t_empty[b]);
 
             // certification, loss and row sums: warp ew takes rows 8 ew ..
             // 8 ew + 7, four adjacent lanes per row, lane g of a row the
@@ -462,7 +466,8 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
                     }
                 }
             }
-            tc::mbar_arrive(&x_empty[s]);  // the X stage may be refilled now
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&x_empty[s]);  // the X stage may be refilled now
         }
         // loss: warp reduce, then one double atomic per warp
 #pragma unroll

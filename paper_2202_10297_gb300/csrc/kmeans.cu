@@ -7,17 +7,17 @@
 // which Sec. 6.1 turns into a reduction; here that reduction is a per-block
 // histogram of rows (counts and row sums per centroid) in shared memory.
 //
-// One persistent kernel, one CTA per SM, 20 warps:
-//   warp 0     TMA producer: X tiles of 128 rows x 32 FP32 (128-byte rows,
-//              128-byte swizzle) into a 4-stage ring; C (k x 32) once.
+// One persistent kernel, one CTA per SM, 18 warps:
+//   warp 0     TMEM allocation and release; TMA producer: X tiles of 128
+//              rows x 32 FP32 (128-byte rows, 128-byte swizzle) into a
+//              4-stage ring; C (k x 32) once.
 //   warp 1     MMA issuer: acc = X_tile C^T - |c|^2 / 2 with tcgen05.mma
 //              kind::tf32 (M = 128, N = k, K = 32 in four steps of 8, then
 //              one more K step with A rows (1, 1, 0, ..) and B rows holding
 //              -|c_k|^2 / 2 split into two TF32 parts) into one of two TMEM
 //              accumulators (2 x 256 columns).  The distance is
 //              |x|^2 - 2 acc_k, so the argmin is the argmax of acc.
-//   warp 2     TMEM allocation and release.
-//   warps 4-19 epilogue, four threads per row (warp w reads the TMEM lanes
+//   warps 2-17 epilogue, four threads per row (warp w reads the TMEM lanes
 //              of quarter w % 4 and the 32-column chunks q = group (mod 4)):
 //              a tcgen05.ld pass keeping the largest acc_k (one max per
 //              value); the row's maximum from the four threads; a second
@@ -43,7 +43,7 @@
 namespace adpar {
 namespace {
 
-constexpr int KM_THREADS = 640;  // warps 0-3 roles, 4-19 epilogue
+constexpr int KM_THREADS = 576;  // warps 0-1 roles, 2-17 epilogue
 constexpr int KM_EPI = 512;      // epilogue threads
 constexpr int KM_GROUPS = 4;     // epilogue threads per row
 constexpr int KM_STAGES = 4;
@@ -51,7 +51,8 @@ constexpr int KM_D = 32;
 constexpr int KM_KMAX = 256;
 constexpr int KM_TILE = 128;
 constexpr uint32_t KM_X_BYTES = KM_TILE * KM_D * 4;  // 16 KB
-constexpr int KM_MAXCAND = 8;
+constexpr int KM_SLOTS = 4;                       // candidate slots per thread (row, group)
+constexpr int KM_MAXCAND = KM_GROUPS * KM_SLOTS;  // per row
 
 // shared memory layout (offsets from a 1024-aligned base)
 constexpr uint32_t OFF_C = 0;                                           // 32 KB
@@ -66,8 +67,8 @@ constexpr uint32_t OFF_CNT = OFF_SUM + KM_KMAX * KM_SUM_LD * 4;         // 1 KB
 constexpr uint32_t OFF_CN2 = OFF_CNT + KM_KMAX * 4;                     // 1 KB
 constexpr uint32_t OFF_CAND = OFF_CN2 + KM_KMAX * 4;                    // 4 KB
 constexpr uint32_t OFF_MAX = OFF_CAND + KM_TILE * KM_MAXCAND * 4;       // 2 KB: [4][128] partial row maxima
-constexpr uint32_t OFF_NC = OFF_MAX + KM_GROUPS * KM_TILE * 4;          // 1 KB: candidate counts, by tile parity
-constexpr uint32_t OFF_XN = OFF_NC + 2 * KM_TILE * 4;                   // 2 KB: [4][128] partial |x|^2
+constexpr uint32_t OFF_NC = OFF_MAX + KM_GROUPS * KM_TILE * 4;          // 2 KB: [128][4] candidate counts
+constexpr uint32_t OFF_XN = OFF_NC + KM_TILE * KM_GROUPS * 4;           // 2 KB: [4][128] partial |x|^2
 constexpr uint32_t OFF_BAR = OFF_XN + KM_GROUPS * KM_TILE * 4;          // barriers
 constexpr uint32_t NBAR = 2 * KM_STAGES + 5;
 constexpr uint32_t OFF_MISC = OFF_BAR + NBAR * 8;
@@ -139,7 +140,7 @@ __global__ void km_empty_kernel(float* loss_out, float* Cbar, int kd, int accumu
         for (int q = t; q < kd; q += gridDim.x * blockDim.x) Cbar[q] = 0.f;
 }
 
-// The 16 epilogue warps (512 threads, warps 4-19) synchronise on named
+// The 16 epilogue warps (512 threads, warps 2-17) synchronise on named
 // barrier 1.  epi_any is a barrier that also ORs a predicate over them, so
 // a decision to stop is taken by all of them together.
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
@@ -154,21 +155,6 @@ __device__ __forceinline__ bool epi_any(bool p) {
         : "r"((uint32_t)p)
         : "memory");
     return r != 0;
-}
-
-// candidates of one chunk: columns whose accumulator is at least thr,
-// appended to the row's list (a bit mask first, so that the 32 values are
-// dead before the rare appends)
-__device__ __forceinline__ void chunk_cand(const uint32_t (&v)[32], int k0, float thr, int* ncand, int* list) {
-    uint32_t mask = 0;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) mask |= (__uint_as_float(v[j]) >= thr ? 1u : 0u) << j;
-    while (mask) {
-        const int j = __ffs(mask) - 1;
-        mask &= mask - 1;
-        const int slot = atomicAdd(ncand, 1);
-        if (slot < KM_MAXCAND) list[slot] = k0 + j;
-    }
 }
 
 __global__ void km_init_kernel(KmArgs A) {
@@ -195,7 +181,7 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
     float* s_max = reinterpret_cast<float*>(base + OFF_MAX);
     float* sAX = reinterpret_cast<float*>(base + OFF_AX);
     float* sBX = reinterpret_cast<float*>(base + OFF_BX);
-    int* s_ncand_buf = reinterpret_cast<int*>(base + OFF_NC);
+    int* s_ncnt = reinterpret_cast<int*>(base + OFF_NC);
     float* s_xn = reinterpret_cast<float*>(base + OFF_XN);
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + OFF_BAR);
     uint64_t* x_full = bars;
@@ -260,7 +246,7 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) cm = fmaxf(cm, __shfl_xor_sync(0xffffffffu, cm, off));
     if (threadIdx.x == 0) *s_cmax = 0.f;
-    if (warp == 2) {
+    if (warp == 0) {
         tc::tmem_alloc(s_tmem, 512);
         tc::fence_before_sync();
     }
@@ -311,28 +297,29 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
                 committed = i + 1;
             }
         }
-    } else if (warp >= 4) {
+    } else if (warp >= 2) {
         // 16 epilogue warps: warp w reads the TMEM lanes of quarter w % 4 and
         // the 32-column chunks q with q % 4 == its group
-        const int ew = warp - 4;
+        const int ew = warp - 2;
         const int quarter = warp & 3, grp = ew >> 2;
         const int r = quarter * 32 + lane;  // row of the tile == TMEM lane
         const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
         const int nq = k / 32;
-        double loss_local = 0.0;
+        // loss: FP32 sum with Neumaier's compensation of the FP32-certified
+        // distances, FP64 sum of those FP64 decided (FP64 instructions, on a
+        // GB300 one warp instruction per 16 cycles per SM, stay off the
+        // per-row path)
+        float lsum = 0.f, lcomp = 0.f;
+        double loss64 = 0.0;
         if (!tc::mbar_wait(c_bar, 0, s_abort)) *s_abort = 1;
         int i = 0;
         for (int64_t t = blockIdx.x; t < A.ntiles; t += gridDim.x, ++i) {
             const int s = i % KM_STAGES, b = i & 1;
-            // the counts alternate between two buffers: a warp may reset the
-            // next tile's while others still read this tile's
-            int* s_ncand = s_ncand_buf + b * KM_TILE;
-            const bool ok = tc::mbar_wait(&t_full[b], (i >> 1) & 1, s_abort) &&
-                            tc::mbar_wait(&x_full[s], (i / KM_STAGES) & 1, s_abort);
-            if (epi_any(!ok)) {  // every epilogue thread leaves together
-                *s_abort = 1;
-                break;
-            }
+            // a wait that gives up makes the warp skip its reads of the
+            // accumulator; the first barrier of the tile then takes every
+            // epilogue thread out together
+            const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&t_full[b], (i >> 1) & 1, s_abort) &&
+                                                        tc::mbar_wait(&x_full[s], (i / KM_STAGES) & 1, s_abort));
             tc::fence_after_sync();
             const float* xt = sX + s * (KM_X_BYTES / 4);
             {
@@ -353,7 +340,7 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
             // pass 1: the largest x.c_k - |c_k|^2 / 2 (the smallest distance)
             // of this thread's chunks (sixteen warps hide the load latency)
             float m1 = -CUDART_INF_F;
-            for (int q = grp; q < nq; q += KM_GROUPS) {
+            for (int q = grp; ok && q < nq; q += KM_GROUPS) {
                 uint32_t va[32];
                 __syncwarp();
                 tc::tmem_ld32(tb + (uint32_t)(q * 32), va);
@@ -362,8 +349,10 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
                 for (int j = 0; j < 32; ++j) m1 = fmaxf(m1, __uint_as_float(va[j]));
             }
             s_max[grp * KM_TILE + r] = m1;
-            if (grp == 0) s_ncand[r] = 0;
-            epi_sync();
+            if (epi_any(!ok)) {  // every epilogue thread leaves together
+                *s_abort = 1;
+                break;
+            }
             float amax = s_max[r], xn2 = s_xn[r];
 #pragma unroll
             for (int g = 1; g < KM_GROUPS; ++g) {
@@ -379,13 +368,26 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
             const float tol = 8.0e-3f * xn * cmax + 1.0e-5f * (cmax * cmax + xn * cmax) + 1e-20f;
             const float thr = amax - tol;
             // pass 2: candidates, every column within tol of the row's maximum
+            // (this thread's first KM_SLOTS in its own slots; a count above
+            // KM_SLOTS sends the row to the all-centroids path)
+            int ncnt = 0;
+            int* slots = s_cand + r * KM_MAXCAND + grp * KM_SLOTS;
             for (int q = grp; q < nq; q += KM_GROUPS) {
                 uint32_t va[32];
                 __syncwarp();
                 tc::tmem_ld32(tb + (uint32_t)(q * 32), va);
                 tc::tmem_ld_wait();
-                chunk_cand(va, q * 32, thr, s_ncand + r, s_cand + r * KM_MAXCAND);
+                uint32_t mask = 0;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) mask |= (__uint_as_float(va[j]) >= thr ? 1u : 0u) << j;
+                while (mask) {
+                    const int j = __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    if (ncnt < KM_SLOTS) slots[ncnt] = q * 32 + j;
+                    ++ncnt;
+                }
             }
+            s_ncnt[r * KM_GROUPS + grp] = ncnt;
             // every epilogue thread has read the accumulator past this barrier
             tc::fence_before_sync();
             epi_sync();
@@ -399,29 +401,45 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
                 const float* xrow = xt + rc * KM_D;
                 const float4 x0 = *reinterpret_cast<const float4*>(xrow + (((2 * g) ^ (rc & 7)) * 4));
                 const float4 x1 = *reinterpret_cast<const float4*>(xrow + (((2 * g + 1) ^ (rc & 7)) * 4));
-                const int nc = s_ncand[rc];
-                // more than KM_MAXCAND candidates: every centroid is one
-                const int cnt = nc <= KM_MAXCAND ? nc : k;
+                // the row's candidates: group g's first min(count, KM_SLOTS)
+                // slots, in group order; a count above KM_SLOTS in any group
+                // makes every centroid a candidate
+                const int4 cn = *reinterpret_cast<const int4*>(s_ncnt + rc * KM_GROUPS);
+                const bool ovf = max(max(cn.x, cn.y), max(cn.z, cn.w)) > KM_SLOTS;
+                const int p1 = min(cn.x, KM_SLOTS), p2 = p1 + min(cn.y, KM_SLOTS), p3 = p2 + min(cn.z, KM_SLOTS);
+                const int cnt = ovf ? k : p3 + min(cn.w, KM_SLOTS);
+                const int* rslots = s_cand + rc * KM_MAXCAND;
+                auto cand_at = [&](int c) -> int {
+                    if (ovf) return c;
+                    const int gg = (c >= p1) + (c >= p2) + (c >= p3);
+                    const int pre = gg == 0 ? 0 : gg == 1 ? p1 : gg == 2 ? p2 : p3;
+                    return rslots[gg * KM_SLOTS + (c - pre)];
+                };
                 int cmax_w = cnt;
 #pragma unroll
                 for (int off = 4; off < 32; off <<= 1) cmax_w = max(cmax_w, __shfl_xor_sync(0xffffffffu, cmax_w, off));
                 // FP32 distances of the candidates (a sum of four 8-term
-                // partial sums); the smallest, its centroid, the second smallest
+                // partial sums), two at a time; the smallest, its centroid,
+                // the second smallest
                 float emin = CUDART_INF_F, e2 = CUDART_INF_F;
                 int kmin = 0;
-                for (int c = 0; c < cmax_w; ++c) {
-                    const bool has = c < cnt;
-                    const int kc = has ? (nc <= KM_MAXCAND ? s_cand[rc * KM_MAXCAND + c] : c) : 0;
-                    const float e = cand_dist_f32(x0, x1, sC, kc, g);
-                    if (has) {
-                        if (e < emin) {
-                            e2 = emin;
-                            emin = e;
-                            kmin = kc;
-                        } else if (e < e2) {
-                            e2 = e;
-                        }
+                auto take = [&](float e, int kc) {
+                    if (e < emin) {
+                        e2 = emin;
+                        emin = e;
+                        kmin = kc;
+                    } else if (e < e2) {
+                        e2 = e;
                     }
+                };
+                for (int c = 0; c < cmax_w; c += 2) {
+                    const bool h0 = c < cnt, h1 = c + 1 < cnt;
+                    const int k0 = h0 ? cand_at(c) : 0;
+                    const int k1 = h1 ? cand_at(c + 1) : 0;
+                    const float e0 = cand_dist_f32(x0, x1, sC, k0, g);
+                    const float e1 = cand_dist_f32(x0, x1, sC, k1, g);
+                    if (h0) take(e0, k0);
+                    if (h1) take(e1, k1);
                 }
                 // FP32 separates the smallest when no other candidate is
                 // within the FP32 bound of it; else FP64 (the oracle's own
@@ -429,13 +447,13 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
                 const float u32 = emin + 4.0e-6f * emin + 1e-30f;
                 const bool need64 = e2 - 4.0e-6f * e2 <= u32;
                 int best = kmin;
-                double dist = (double)emin;
+                double dist64 = 0.0;
                 if (__any_sync(0xffffffffu, need64)) {
                     double bd = CUDART_INF;
                     int bk = k;
                     for (int c = 0; c < cmax_w; ++c) {
                         const bool has = c < cnt;
-                        const int kc = has ? (nc <= KM_MAXCAND ? s_cand[rc * KM_MAXCAND + c] : c) : 0;
+                        const int kc = has ? cand_at(c) : 0;
                         const float e = cand_dist_f32(x0, x1, sC, kc, g);
                         if (need64 && has && g == 0 && e - 4.0e-6f * e <= u32) {
                             const double d = exact_f64(xt, rc, sC, kc);
@@ -444,12 +462,18 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
                     }
                     bk = __shfl_sync(0xffffffffu, bk, lane & ~3);
                     bd = __shfl_sync(0xffffffffu, bd, lane & ~3);
-                    if (need64) { best = bk; dist = bd; }
+                    if (need64) { best = bk; dist64 = bd; }
                 }
                 const int64_t row = t * KM_TILE + rc;
                 if (row < A.N) {
                     if (g == 0) {
-                        loss_local += dist;
+                        if (need64) {
+                            loss64 += dist64;
+                        } else {
+                            const float ts = lsum + emin;  // emin >= 0
+                            lcomp += lsum >= emin ? (lsum - ts) + emin : (emin - ts) + lsum;
+                            lsum = ts;
+                        }
                         if (A.argmin_out) A.argmin_out[row] = best;
                     }
                     if (want_grad) {
@@ -470,6 +494,7 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
             if (lane == 0) tc::mbar_arrive(&x_empty[s]);  // the X stage may be refilled now
         }
         // loss: warp reduce, then one double atomic per warp
+        double loss_local = (double)lsum + (double)lcomp + loss64;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) loss_local += __shfl_xor_sync(0xffffffffu, loss_local, off);
         if (lane == 0 && loss_local != 0.0) atomicAdd(A.loss_acc, loss_local);
@@ -516,7 +541,7 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
         }
     }
     __syncthreads();
-    if (warp == 2) {
+    if (warp == 0) {
         tc::fence_after_sync();
         tc::tmem_dealloc(tmem, 512);
     }

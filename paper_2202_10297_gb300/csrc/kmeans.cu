@@ -45,14 +45,16 @@ namespace {
 
 constexpr int KM_THREADS = 576;  // warps 0-1 roles, 2-17 epilogue
 constexpr int KM_EPI = 512;      // epilogue threads
-constexpr int KM_GROUPS = 4;     // epilogue threads per row
+constexpr int KM_PG = 2;         // epilogue groups, taking alternate tiles
+constexpr int KM_PG_THREADS = KM_EPI / KM_PG;
+constexpr int KM_TPR = 2;        // threads per row in a group's scan passes
 constexpr int KM_STAGES = 4;
 constexpr int KM_D = 32;
 constexpr int KM_KMAX = 256;
 constexpr int KM_TILE = 128;
 constexpr uint32_t KM_X_BYTES = KM_TILE * KM_D * 4;  // 16 KB
-constexpr int KM_SLOTS = 4;                       // candidate slots per thread (row, group)
-constexpr int KM_MAXCAND = KM_GROUPS * KM_SLOTS;  // per row
+constexpr int KM_SLOTS = 4;                    // candidate slots per scanning thread
+constexpr int KM_MAXCAND = KM_TPR * KM_SLOTS;  // per row
 
 // shared memory layout (offsets from a 1024-aligned base)
 constexpr uint32_t OFF_C = 0;                                           // 32 KB
@@ -65,11 +67,12 @@ constexpr uint32_t OFF_BX = OFF_AX + KM_TILE * 128;                     // 32 KB
 constexpr uint32_t OFF_SUM = OFF_BX + KM_KMAX * 128;                    // 33 KB
 constexpr uint32_t OFF_CNT = OFF_SUM + KM_KMAX * KM_SUM_LD * 4;         // 1 KB
 constexpr uint32_t OFF_CN2 = OFF_CNT + KM_KMAX * 4;                     // 1 KB
-constexpr uint32_t OFF_CAND = OFF_CN2 + KM_KMAX * 4;                    // 4 KB
-constexpr uint32_t OFF_MAX = OFF_CAND + KM_TILE * KM_MAXCAND * 4;       // 2 KB: [4][128] partial row maxima
-constexpr uint32_t OFF_NC = OFF_MAX + KM_GROUPS * KM_TILE * 4;          // 2 KB: [128][4] candidate counts
-constexpr uint32_t OFF_XN = OFF_NC + KM_TILE * KM_GROUPS * 4;           // 2 KB: [4][128] partial |x|^2
-constexpr uint32_t OFF_BAR = OFF_XN + KM_GROUPS * KM_TILE * 4;          // barriers
+// per epilogue group:
+constexpr uint32_t OFF_CAND = OFF_CN2 + KM_KMAX * 4;                    // 8 KB: [2][128][8] candidate slots
+constexpr uint32_t OFF_MAX = OFF_CAND + KM_PG * KM_TILE * KM_MAXCAND * 4;  // 2 KB: [2][2][128] partial row maxima
+constexpr uint32_t OFF_NC = OFF_MAX + KM_PG * KM_TPR * KM_TILE * 4;     // 2 KB: [2][128][2] candidate counts
+constexpr uint32_t OFF_XN = OFF_NC + KM_PG * KM_TILE * KM_TPR * 4;      // 2 KB: [2][2][128] partial |x|^2
+constexpr uint32_t OFF_BAR = OFF_XN + KM_PG * KM_TPR * KM_TILE * 4;     // barriers
 constexpr uint32_t NBAR = 2 * KM_STAGES + 5;
 constexpr uint32_t OFF_MISC = OFF_BAR + NBAR * 8;
 constexpr uint32_t KM_SMEM = OFF_MISC + 64 + 1024;  // + alignment slack
@@ -140,19 +143,22 @@ __global__ void km_empty_kernel(float* loss_out, float* Cbar, int kd, int accumu
         for (int q = t; q < kd; q += gridDim.x * blockDim.x) Cbar[q] = 0.f;
 }
 
-// The 16 epilogue warps (512 threads, warps 2-17) synchronise on named
-// barrier 1.  epi_any is a barrier that also ORs a predicate over them, so
-// a decision to stop is taken by all of them together.
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
-__device__ __forceinline__ bool epi_any(bool p) {
+// The 16 epilogue warps (warps 2-17) form two groups of 8 (256 threads)
+// that take alternate tiles, group p synchronising on named barrier 1 + p.
+// epi_any is a barrier that also ORs a predicate over the group, so a
+// decision to stop is taken by all of its threads together.
+__device__ __forceinline__ void epi_sync(int pg) {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + pg), "r"(KM_PG_THREADS) : "memory");
+}
+__device__ __forceinline__ bool epi_any(int pg, bool p) {
     uint32_t r;
     asm volatile(
         "{\n\t.reg .pred q, o;\n\t"
         "setp.ne.u32 q, %1, 0;\n\t"
-        "bar.red.or.pred o, 1, 512, q;\n\t"
+        "bar.red.or.pred o, %2, %3, q;\n\t"
         "selp.u32 %0, 1, 0, o;\n\t}"
         : "=r"(r)
-        : "r"((uint32_t)p)
+        : "r"((uint32_t)p), "r"(1 + pg), "r"(KM_PG_THREADS)
         : "memory");
     return r != 0;
 }
@@ -193,6 +199,9 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
     volatile int* s_abort = reinterpret_cast<volatile int*>(base + OFF_MISC + 4);
     volatile int* s_never = reinterpret_cast<volatile int*>(base + OFF_MISC + 12);  // stays 0
     float* s_cmax = reinterpret_cast<float*>(base + OFF_MISC + 8);
+    // the tile in each X stage (-1: no more tiles), written by the producer
+    // before the stage's x_full phase completes
+    volatile int* s_tile = reinterpret_cast<volatile int*>(base + OFF_MISC + 16);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k = A.k;
@@ -201,7 +210,7 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < KM_STAGES; ++s) {
             tc::mbar_init(&x_full[s], 1);
-            tc::mbar_init(&x_empty[s], KM_EPI / 32);  // one arrival per epilogue warp
+            tc::mbar_init(&x_empty[s], KM_PG_THREADS / 32);  // one arrival per warp of a group
         }
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(&t_full[b], 1);
@@ -262,15 +271,26 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
         if (lane == 0) {
             tc::mbar_arrive_expect_tx(c_bar, (uint32_t)(k * KM_D * 4));
             tc::tma_load_2d(sC, &tmC, 0, 0, c_bar);
-            int i = 0;
-            for (int64_t t = blockIdx.x; t < A.ntiles; t += gridDim.x, ++i) {
+            // tiles by a global ticket (CTAs ran at different speeds: static
+            // shares left the slowest SMs 40% behind the median); once the
+            // tickets run out, one end marker for each epilogue group
+            int ended = 0;
+            for (int i = 0; ended < KM_PG; ++i) {
                 const int s = i % KM_STAGES;
                 if (i >= KM_STAGES && !tc::mbar_wait(&x_empty[s], ((i / KM_STAGES) - 1) & 1, s_abort)) {
                     *s_abort = 1;
                     break;
                 }
-                tc::mbar_arrive_expect_tx(&x_full[s], KM_X_BYTES);
-                tc::tma_load_2d(sX + s * (KM_X_BYTES / 4), &tmX, 0, (int)(t * KM_TILE), &x_full[s]);
+                int64_t t = ended ? A.ntiles : (int64_t)atomicAdd(&A.hdr->ticket[0], 1u);
+                if (t >= A.ntiles) {
+                    s_tile[s] = -1;
+                    tc::mbar_arrive(&x_full[s]);  // no copy: the phase completes at once
+                    ++ended;
+                } else {
+                    s_tile[s] = (int)t;
+                    tc::mbar_arrive_expect_tx(&x_full[s], KM_X_BYTES);
+                    tc::tma_load_2d(sX + s * (KM_X_BYTES / 4), &tmX, 0, (int)(t * KM_TILE), &x_full[s]);
+                }
                 issued = i + 1;
             }
         }
@@ -281,10 +301,10 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
             const uint64_t axdesc = tc::desc_sw128_kmajor(tc::smem_u32(sAX));
             const uint64_t bxdesc = tc::desc_sw128_kmajor(tc::smem_u32(sBX));
             if (!tc::mbar_wait(c_bar, 0, s_abort)) *s_abort = 1;
-            int i = 0;
-            for (int64_t t = blockIdx.x; t < A.ntiles && !*s_abort; t += gridDim.x, ++i) {
+            for (int i = 0; !*s_abort; ++i) {
                 const int s = i % KM_STAGES, b = i & 1;
                 if (!tc::mbar_wait(&x_full[s], (i / KM_STAGES) & 1, s_abort)) { *s_abort = 1; break; }
+                if (s_tile[s] < 0) break;  // no more tiles
                 if (i >= 2 && !tc::mbar_wait(&t_empty[b], ((i >> 1) - 1) & 1, s_abort)) { *s_abort = 1; break; }
                 tc::fence_after_sync();
                 const uint64_t adesc = tc::desc_sw128_kmajor(tc::smem_u32(sX + s * (KM_X_BYTES / 4)));
@@ -298,13 +318,20 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
             }
         }
     } else if (warp >= 2) {
-        // 16 epilogue warps: warp w reads the TMEM lanes of quarter w % 4 and
-        // the 32-column chunks q with q % 4 == its group
+        // 16 epilogue warps in two groups; group pg takes the tiles i with
+        // i % 2 == pg, in accumulator pg.  Warp w reads the TMEM lanes of
+        // quarter w % 4; the two warps of a group on a quarter split the
+        // 32-column chunks (q % 2 == grp)
         const int ew = warp - 2;
-        const int quarter = warp & 3, grp = ew >> 2;
+        const int pg = ew >> 3, gw = ew & 7;
+        const int quarter = warp & 3, grp = gw >> 2;
         const int r = quarter * 32 + lane;  // row of the tile == TMEM lane
         const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
         const int nq = k / 32;
+        float* g_max = s_max + pg * KM_TPR * KM_TILE;
+        float* g_xn = s_xn + pg * KM_TPR * KM_TILE;
+        int* g_ncnt = s_ncnt + pg * KM_TILE * KM_TPR;
+        int* g_cand = s_cand + pg * KM_TILE * KM_MAXCAND;
         // loss: FP32 sum with Neumaier's compensation of the FP32-certified
         // distances, FP64 sum of those FP64 decided (FP64 instructions, on a
         // GB300 one warp instruction per 16 cycles per SM, stay off the
@@ -312,35 +339,38 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
         float lsum = 0.f, lcomp = 0.f;
         double loss64 = 0.0;
         if (!tc::mbar_wait(c_bar, 0, s_abort)) *s_abort = 1;
-        int i = 0;
-        for (int64_t t = blockIdx.x; t < A.ntiles; t += gridDim.x, ++i) {
-            const int s = i % KM_STAGES, b = i & 1;
-            // a wait that gives up makes the warp skip its reads of the
-            // accumulator; the first barrier of the tile then takes every
-            // epilogue thread out together
-            const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&t_full[b], (i >> 1) & 1, s_abort) &&
-                                                        tc::mbar_wait(&x_full[s], (i / KM_STAGES) & 1, s_abort));
+        for (int i = pg;; i += KM_PG) {
+            const int s = i % KM_STAGES, b = pg;
+            // the stage's tile (or the end marker), then the accumulator.  A
+            // wait that gives up, or the end marker, makes the warp skip its
+            // reads of the accumulator; the first barrier of the tile then
+            // takes every thread of the group out together
+            const bool okx = __all_sync(0xffffffffu, tc::mbar_wait(&x_full[s], (i / KM_STAGES) & 1, s_abort));
+            const int64_t t = s_tile[s];
+            const bool more = okx && t >= 0;
+            const bool ok = more && __all_sync(0xffffffffu, tc::mbar_wait(&t_full[b], (i >> 1) & 1, s_abort));
+            if (!okx || (more && !ok)) *s_abort = 1;
             tc::fence_after_sync();
             const float* xt = sX + s * (KM_X_BYTES / 4);
             {
-                // this thread's quarter of |x|^2 (coordinates 8 grp .. 8 grp + 7)
+                // this thread's half of |x|^2 (coordinates 16 grp .. 16 grp + 15)
                 float xp = 0.f;
 #pragma unroll
-                for (int c = 2 * grp; c < 2 * grp + 2; ++c) {
+                for (int c = 4 * grp; c < 4 * grp + 4; ++c) {
                     const float4 v = *reinterpret_cast<const float4*>(xt + r * 32 + ((c ^ (r & 7)) * 4));
                     xp = fmaf(v.x, v.x, xp);
                     xp = fmaf(v.y, v.y, xp);
                     xp = fmaf(v.z, v.z, xp);
                     xp = fmaf(v.w, v.w, xp);
                 }
-                s_xn[grp * KM_TILE + r] = xp;
+                g_xn[grp * KM_TILE + r] = xp;
             }
             const uint32_t tb = tmem + lane_base + (uint32_t)(b * 256);
 
             // pass 1: the largest x.c_k - |c_k|^2 / 2 (the smallest distance)
-            // of this thread's chunks (sixteen warps hide the load latency)
+            // of this thread's chunks
             float m1 = -CUDART_INF_F;
-            for (int q = grp; ok && q < nq; q += KM_GROUPS) {
+            for (int q = grp; ok && q < nq; q += KM_TPR) {
                 uint32_t va[32];
                 __syncwarp();
                 tc::tmem_ld32(tb + (uint32_t)(q * 32), va);
@@ -348,16 +378,13 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
 #pragma unroll
                 for (int j = 0; j < 32; ++j) m1 = fmaxf(m1, __uint_as_float(va[j]));
             }
-            s_max[grp * KM_TILE + r] = m1;
-            if (epi_any(!ok)) {  // every epilogue thread leaves together
-                *s_abort = 1;
-                break;
-            }
-            float amax = s_max[r], xn2 = s_xn[r];
+            g_max[grp * KM_TILE + r] = m1;
+            if (epi_any(pg, !ok)) break;  // every thread of the group leaves together
+            float amax = g_max[r], xn2 = g_xn[r];
 #pragma unroll
-            for (int g = 1; g < KM_GROUPS; ++g) {
-                amax = fmaxf(amax, s_max[g * KM_TILE + r]);
-                xn2 += s_xn[g * KM_TILE + r];
+            for (int g = 1; g < KM_TPR; ++g) {
+                amax = fmaxf(amax, g_max[g * KM_TILE + r]);
+                xn2 += g_xn[g * KM_TILE + r];
             }
             const float xn = sqrtf(xn2);
             // the distance is |x|^2 - 2 acc_k.  |acc~_k - acc_k| <= |S~ - S| +
@@ -371,8 +398,8 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
             // (this thread's first KM_SLOTS in its own slots; a count above
             // KM_SLOTS sends the row to the all-centroids path)
             int ncnt = 0;
-            int* slots = s_cand + r * KM_MAXCAND + grp * KM_SLOTS;
-            for (int q = grp; q < nq; q += KM_GROUPS) {
+            int* slots = g_cand + r * KM_MAXCAND + grp * KM_SLOTS;
+            for (int q = grp; q < nq; q += KM_TPR) {
                 uint32_t va[32];
                 __syncwarp();
                 tc::tmem_ld32(tb + (uint32_t)(q * 32), va);
@@ -387,33 +414,32 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
                     ++ncnt;
                 }
             }
-            s_ncnt[r * KM_GROUPS + grp] = ncnt;
-            // every epilogue thread has read the accumulator past this barrier
+            g_ncnt[r * KM_TPR + grp] = ncnt;
+            // every thread of the group has read the accumulator past this barrier
             tc::fence_before_sync();
-            epi_sync();
-            if (ew == 0 && lane == 0) tc::mbar_arrive(&t_empty[b]);
+            epi_sync(pg);
+            if (gw == 0 && lane == 0) tc::mbar_arrive(&t_empty[b]);
 
-            // certification, loss and row sums: warp ew takes rows 8 ew ..
-            // 8 ew + 7, four adjacent lanes per row, lane g of a row the
-            // coordinates 8 g .. 8 g + 7
-            {
-                const int rc = ew * 8 + (lane >> 2), g = lane & 3;
+            // certification, loss and row sums: warp gw takes rows 16 gw ..
+            // 16 gw + 15, 8 at a time, four adjacent lanes per row, lane g of
+            // a row the coordinates 8 g .. 8 g + 7
+#pragma unroll 1
+            for (int rd = 0; rd < 2; ++rd) {
+                const int rc = gw * 16 + rd * 8 + (lane >> 2), g = lane & 3;
                 const float* xrow = xt + rc * KM_D;
                 const float4 x0 = *reinterpret_cast<const float4*>(xrow + (((2 * g) ^ (rc & 7)) * 4));
                 const float4 x1 = *reinterpret_cast<const float4*>(xrow + (((2 * g + 1) ^ (rc & 7)) * 4));
-                // the row's candidates: group g's first min(count, KM_SLOTS)
-                // slots, in group order; a count above KM_SLOTS in any group
+                // the row's candidates: scanning thread 0's first min(count,
+                // KM_SLOTS) slots, then thread 1's; a count above KM_SLOTS
                 // makes every centroid a candidate
-                const int4 cn = *reinterpret_cast<const int4*>(s_ncnt + rc * KM_GROUPS);
-                const bool ovf = max(max(cn.x, cn.y), max(cn.z, cn.w)) > KM_SLOTS;
-                const int p1 = min(cn.x, KM_SLOTS), p2 = p1 + min(cn.y, KM_SLOTS), p3 = p2 + min(cn.z, KM_SLOTS);
-                const int cnt = ovf ? k : p3 + min(cn.w, KM_SLOTS);
-                const int* rslots = s_cand + rc * KM_MAXCAND;
+                const int2 cn = *reinterpret_cast<const int2*>(g_ncnt + rc * KM_TPR);
+                const bool ovf = max(cn.x, cn.y) > KM_SLOTS;
+                const int p1 = min(cn.x, KM_SLOTS);
+                const int cnt = ovf ? k : p1 + min(cn.y, KM_SLOTS);
+                const int* rslots = g_cand + rc * KM_MAXCAND;
                 auto cand_at = [&](int c) -> int {
                     if (ovf) return c;
-                    const int gg = (c >= p1) + (c >= p2) + (c >= p3);
-                    const int pre = gg == 0 ? 0 : gg == 1 ? p1 : gg == 2 ? p2 : p3;
-                    return rslots[gg * KM_SLOTS + (c - pre)];
+                    return c < p1 ? rslots[c] : rslots[KM_SLOTS + c - p1];
                 };
                 int cmax_w = cnt;
 #pragma unroll
@@ -447,7 +473,7 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
                 const float u32 = emin + 4.0e-6f * emin + 1e-30f;
                 const bool need64 = e2 - 4.0e-6f * e2 <= u32;
                 int best = kmin;
-                double dist64 = 0.0;
+                const int64_t row = t * KM_TILE + rc;
                 if (__any_sync(0xffffffffu, need64)) {
                     double bd = CUDART_INF;
                     int bk = k;
@@ -462,14 +488,14 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
                     }
                     bk = __shfl_sync(0xffffffffu, bk, lane & ~3);
                     bd = __shfl_sync(0xffffffffu, bd, lane & ~3);
-                    if (need64) { best = bk; dist64 = bd; }
+                    if (need64) {
+                        best = bk;
+                        if (g == 0 && row < A.N) loss64 += bd;  // FP64 only on this rare path
+                    }
                 }
-                const int64_t row = t * KM_TILE + rc;
                 if (row < A.N) {
                     if (g == 0) {
-                        if (need64) {
-                            loss64 += dist64;
-                        } else {
+                        if (!need64) {
                             const float ts = lsum + emin;  // emin >= 0
                             lcomp += lsum >= emin ? (lsum - ts) + emin : (emin - ts) + lsum;
                             lsum = ts;

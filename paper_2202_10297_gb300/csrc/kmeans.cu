@@ -17,19 +17,22 @@
 //              -|c_k|^2 / 2 split into two TF32 parts) into one of two TMEM
 //              accumulators (2 x 256 columns).  The distance is
 //              |x|^2 - 2 acc_k, so the argmin is the argmax of acc.
-//   warps 2-17 epilogue, four threads per row (warp w reads the TMEM lanes
-//              of quarter w % 4 and the 32-column chunks q = group (mod 4)):
-//              a tcgen05.ld pass keeping the largest acc_k (one max per
-//              value); the row's maximum from the four threads; a second
-//              pass listing every centroid within the TF32 error bound of
-//              it (one compare per value), before the accumulator is
-//              released.  Then,
-//              with warp w taking 8 rows and four adjacent lanes per row
-//              (8 coordinates each): the candidates' distances recomputed
-//              in FP32; if two remain within the FP32 bound, FP64 (the
-//              oracle's own arithmetic) decides, ties to the lowest k; the
-//              loss term (the argmin's distance) and, for the gradient,
-//              the row added into shared-memory row sums.
+//   warps 2-17 epilogue, two groups of 8 warps taking alternate tiles (group
+//              p reads accumulator p and synchronises on its own named
+//              barrier), tiles handed out by a global ticket through the
+//              producer.  In a group, two threads per row (warp w reads the
+//              TMEM lanes of quarter w % 4, and every other 32-column chunk):
+//              a tcgen05.ld.red pass (the load's own max reduction, sm_103a)
+//              for the largest acc_k; the row's maximum from its two
+//              threads; a second pass listing every centroid within the
+//              TF32 error bound of it (one compare per value), before the
+//              accumulator is released.  Then, with warp w of the group
+//              taking 16 rows, 8 at a time, four adjacent lanes per row (8
+//              coordinates each): the candidates' distances recomputed in
+//              FP32; if two remain within the FP32 bound, FP64 (the oracle's
+//              own arithmetic) decides, ties to the lowest k; the loss term
+//              (the argmin's distance) and, for the gradient, the row added
+//              into shared-memory row sums.
 // Every mbarrier wait is bounded; a timeout is recorded in the workspace
 // and the kernel drains its copies and MMAs, frees TMEM and returns.
 #include <cuda.h>
@@ -110,15 +113,17 @@ __device__ __forceinline__ float cand_dist_f32(const float4& x0, const float4& x
     const float* crow = sC + kc * KM_D;
     const float4 c0 = *reinterpret_cast<const float4*>(crow + (((2 * g) ^ (kc & 7)) * 4));
     const float4 c1 = *reinterpret_cast<const float4*>(crow + (((2 * g + 1) ^ (kc & 7)) * 4));
-    float d, s = 0.f;
+    // two chains of four (chunk 2 g, chunk 2 g + 1), then their sum
+    float d, s = 0.f, u = 0.f;
     d = x0.x - c0.x; s = fmaf(d, d, s);
+    d = x1.x - c1.x; u = fmaf(d, d, u);
     d = x0.y - c0.y; s = fmaf(d, d, s);
+    d = x1.y - c1.y; u = fmaf(d, d, u);
     d = x0.z - c0.z; s = fmaf(d, d, s);
+    d = x1.z - c1.z; u = fmaf(d, d, u);
     d = x0.w - c0.w; s = fmaf(d, d, s);
-    d = x1.x - c1.x; s = fmaf(d, d, s);
-    d = x1.y - c1.y; s = fmaf(d, d, s);
-    d = x1.z - c1.z; s = fmaf(d, d, s);
-    d = x1.w - c1.w; s = fmaf(d, d, s);
+    d = x1.w - c1.w; u = fmaf(d, d, u);
+    s += u;
     s += __shfl_xor_sync(0xffffffffu, s, 1);
     s += __shfl_xor_sync(0xffffffffu, s, 2);
     return s;
@@ -368,15 +373,15 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
             const uint32_t tb = tmem + lane_base + (uint32_t)(b * 256);
 
             // pass 1: the largest x.c_k - |c_k|^2 / 2 (the smallest distance)
-            // of this thread's chunks
+            // of this thread's chunks, from the TMEM load's own max reduction
             float m1 = -CUDART_INF_F;
             for (int q = grp; ok && q < nq; q += KM_TPR) {
                 uint32_t va[32];
+                float cm;
                 __syncwarp();
-                tc::tmem_ld32(tb + (uint32_t)(q * 32), va);
+                tc::tmem_ld32_max(tb + (uint32_t)(q * 32), va, &cm);
                 tc::tmem_ld_wait();
-#pragma unroll
-                for (int j = 0; j < 32; ++j) m1 = fmaxf(m1, __uint_as_float(va[j]));
+                m1 = fmaxf(m1, cm);
             }
             g_max[grp * KM_TILE + r] = m1;
             if (epi_any(pg, !ok)) break;  // every thread of the group leaves together
@@ -404,9 +409,11 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
                 __syncwarp();
                 tc::tmem_ld32(tb + (uint32_t)(q * 32), va);
                 tc::tmem_ld_wait();
-                uint32_t mask = 0;
+                // four independent OR chains (one long chain waits on itself)
+                uint32_t mk[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-                for (int j = 0; j < 32; ++j) mask |= (__uint_as_float(va[j]) >= thr ? 1u : 0u) << j;
+                for (int j = 0; j < 32; ++j) mk[j & 3] |= (__uint_as_float(va[j]) >= thr ? 1u : 0u) << j;
+                uint32_t mask = (mk[0] | mk[1]) | (mk[2] | mk[3]);
                 while (mask) {
                     const int j = __ffs(mask) - 1;
                     mask &= mask - 1;

@@ -727,7 +727,7 @@ EncodeTiledFn encode_tiled() {
 }
 
 // An array of n elements seen as [n / V runs][1][V] (one 128-byte row per
-// run): box of kRunNT runs, 128-byte swizzle (one array tile per copy).
+// run): box of NT runs, 128-byte swizzle (one array tile per copy).
 template <class T>
 bool make_run_map(CUtensorMap* m, const T* ptr, int64_t n) {
     EncodeTiledFn f = encode_tiled();
@@ -735,7 +735,7 @@ bool make_run_map(CUtensorMap* m, const T* ptr, int64_t n) {
     constexpr int V = RunCfg<T>::V;
     cuuint64_t dims[3] = {(cuuint64_t)V, 1, (cuuint64_t)(n / V)};
     cuuint64_t strides[2] = {128, 128};
-    cuuint32_t box[3] = {(cuuint32_t)V, 1, (cuuint32_t)kRunNT};
+    cuuint32_t box[3] = {(cuuint32_t)V, 1, (cuuint32_t)RunCfg<T>::NT};
     cuuint32_t es[3] = {1, 1, 1};
     const CUtensorMapDataType dt = sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     return f(m, dt, 3, const_cast<T*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -761,7 +761,7 @@ RunLayout run_layout(int64_t n) {
     L.off_rA = o; o += wr * 8;
     L.off_rI = o; o += wr * 8;
     L.slot_words = (o - L.off_slots) / 8;
-    const size_t runs = t * (size_t)kRunNT;
+    const size_t runs = t * (size_t)RunCfg<T>::NT;
     o = round_up(o, 256);
     L.off_carA = o; o = round_up(o + runs * sizeof(T), 256);
     L.off_carB = o; o = round_up(o + runs * sizeof(T), 256);
@@ -810,9 +810,9 @@ int run_linrec_runs(int64_t n, const void* a, const void* b, const void* ya, con
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return ADPAR_ERR_CUDA;
     if (!configured[dev]) {
         if (cudaFuncSetAttribute(linrec_runs_carry_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 2 * kRunArrBytes) != cudaSuccess ||
+                                 2 * Cf::ARR) != cudaSuccess ||
             cudaFuncSetAttribute(linrec_runs_vjp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 4 * kRunArrBytes) != cudaSuccess)
+                                 4 * Cf::ARR) != cudaSuccess)
             return ADPAR_ERR_CUDA;
         configured[dev] = true;
     }
@@ -820,9 +820,9 @@ int run_linrec_runs(int64_t n, const void* a, const void* b, const void* ya, con
     const int iblocks = (int)std::min<int64_t>((words + 255) / 256 + 1, 2048);
     scan_init_kernel<<<iblocks, 256, 0, stream>>>(R.hdr, reinterpret_cast<unsigned long long*>(w + L.off_slots),
                                                   words);
-    linrec_runs_carry_kernel<T><<<(unsigned)L.tiles, kRunNT, 2 * kRunArrBytes, stream>>>(tm[0], tm[1], R);
+    linrec_runs_carry_kernel<T><<<(unsigned)L.tiles, Cf::NT, 2 * Cf::ARR, stream>>>(tm[0], tm[1], R);
     scan_carry_kernel<RunPOp<T>><<<1, kCarryBlock, 0, stream>>>(R.tagg, R.tcar, L.tiles);
-    linrec_runs_vjp_kernel<T><<<(unsigned)L.tiles, kRunNT, 4 * kRunArrBytes, stream>>>(tm[0], tm[1], tm[2], tm[3],
+    linrec_runs_vjp_kernel<T><<<(unsigned)L.tiles, Cf::NT, 4 * Cf::ARR, stream>>>(tm[0], tm[1], tm[2], tm[3],
                                                                                        tm[4], tm[5], R);
     return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
 }

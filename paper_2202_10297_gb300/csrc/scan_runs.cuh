@@ -28,7 +28,7 @@
 //  That is 10 operations per element plus a share of the run scans, and
 //  (2 + 4 + 2) element sizes of HBM traffic per element plus 3 per run.
 //
-// A tile is kRunNT runs; each input array's tile (kRunNT runs of 128 bytes)
+// A tile is NT runs; each input array's tile (NT runs of 128 bytes)
 // comes into shared memory by one 3-D TMA copy with the 128-byte swizzle
 // (16-byte chunk c of 128-byte row r stored at chunk c ^ (r & 7)), so that a
 // thread reading its own run with 16-byte loads meets few bank conflicts.
@@ -44,16 +44,18 @@
 
 namespace adpar {
 
-constexpr int kRunNT = 128;                 // runs (threads) per tile
-constexpr int kRunNW = kRunNT / 32;         // warps per tile
-constexpr int kRunChunks = 8;               // 16-byte chunks per run
-constexpr int kRunArrBytes = kRunNT * 128;  // one array's tile (16 KB)
+constexpr int kRunChunks = 8;  // 16-byte chunks per run
 
 template <class T>
 struct RunCfg {
     static constexpr int V = 128 / (int)sizeof(T);   // elements per run
     static constexpr int EPC = 16 / (int)sizeof(T);  // elements per 16-byte chunk
-    static constexpr int TILE = V * kRunNT;          // elements per tile
+    // runs (threads) per tile (FP32 tiles of 64 runs were slower: 0.52 ->
+    // 0.59 ms at 2^26)
+    static constexpr int NT = 128;
+    static constexpr int NW = NT / 32;               // warps per tile
+    static constexpr int TILE = V * NT;              // elements per tile
+    static constexpr int ARR = NT * 128;             // one array's tile in bytes
 };
 
 template <class T>
@@ -95,9 +97,9 @@ struct RunArgs {
     WsHeader* hdr;
     unsigned long long* lbR_agg;
     unsigned long long* lbR_incl;
-    T* carA;        // [tiles * kRunNT] A before the run, from the tile's start
-    T* carB;        // [tiles * kRunNT] B before the run, from the tile's start
-    T* prod;        // [tiles * kRunNT] product of a over the run
+    T* carA;        // [tiles * NT] A before the run, from the tile's start
+    T* carB;        // [tiles * NT] B before the run, from the tile's start
+    T* prod;        // [tiles * NT] product of a over the run
     RunP<T>* tagg;  // [tiles] the tile's primal aggregate
     RunP<T>* tcar;  // [tiles] the primal state before the tile
 };
@@ -143,9 +145,9 @@ __device__ __forceinline__ void run_tile_load(unsigned char* const (&dst)[NA], c
         if (threadIdx.x == 0) {
             tc::mbar_init(bar, 1);
             tc::fence_mbar_init();
-            tc::mbar_arrive_expect_tx(bar, (uint32_t)(NA * kRunArrBytes));
+            tc::mbar_arrive_expect_tx(bar, (uint32_t)(NA * Cf::ARR));
 #pragma unroll
-            for (int q = 0; q < NA; ++q) tma_load_3d(dst[q], tm[q], (int)(tile * kRunNT), bar);
+            for (int q = 0; q < NA; ++q) tma_load_3d(dst[q], tm[q], (int)(tile * Cf::NT), bar);
         }
         __syncthreads();
         bool ok = false;
@@ -153,7 +155,7 @@ __device__ __forceinline__ void run_tile_load(unsigned char* const (&dst)[NA], c
         if (!ok) record_status(hdr, ADPAR_ERR_TIMEOUT);
     } else {
         const int64_t e0 = tile * Cf::TILE;
-        for (int i = threadIdx.x; i < kRunNT * kRunChunks; i += kRunNT) {
+        for (int i = threadIdx.x; i < Cf::NT * kRunChunks; i += Cf::NT) {
             const int t = i / kRunChunks, p = i % kRunChunks;
             const int64_t e = e0 + (int64_t)t * Cf::V + Cf::EPC * p;
             const int off = run_chunk_off(t, p);
@@ -171,16 +173,16 @@ __device__ __forceinline__ void run_tile_load(unsigned char* const (&dst)[NA], c
 
 // ---------------------------------------------------------------- pass C
 template <class T>
-__global__ void __launch_bounds__(kRunNT) linrec_runs_carry_kernel(const __grid_constant__ CUtensorMap tmA,
+__global__ void __launch_bounds__(RunCfg<T>::NT) linrec_runs_carry_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                    const __grid_constant__ CUtensorMap tmB,
                                                                    RunArgs<T> R) {
     using Cf = RunCfg<T>;
     using P = RunP<T>;
     extern __shared__ __align__(1024) unsigned char s_dyn[];
     unsigned char* sA = s_dyn;
-    unsigned char* sB = s_dyn + kRunArrBytes;
+    unsigned char* sB = s_dyn + Cf::ARR;
     __shared__ __align__(8) uint64_t s_bar;
-    __shared__ P s_tot[kRunNW];
+    __shared__ P s_tot[Cf::NW];
     const int64_t tile = blockIdx.x;
     const bool whole = (tile + 1) * Cf::TILE <= R.n;
     {
@@ -206,11 +208,11 @@ __global__ void __launch_bounds__(kRunNT) linrec_runs_carry_kernel(const __grid_
     auto comb = [](const P& l, const P& r) { return P{l.A * r.A, run_fma(r.A, l.B, r.B)}; };
     P wex[1];
     const P ident{T(1), T(0)};
-    const P total = block_scan_part1<P, false, 1, kRunNW>(agg, wex, s_tot, ident, comb);
+    const P total = block_scan_part1<P, false, 1, Cf::NW>(agg, wex, s_tot, ident, comb);
     if (threadIdx.x == 0) R.tagg[tile] = total;
     __syncthreads();
-    const P ex = block_scan_excl<P, false, 1, kRunNW>(0, wex, s_tot, ident, comb);
-    const int64_t run = tile * kRunNT + t;
+    const P ex = block_scan_excl<P, false, 1, Cf::NW>(0, wex, s_tot, ident, comb);
+    const int64_t run = tile * Cf::NT + t;
     R.carA[run] = ex.A;
     R.carB[run] = ex.B;
     R.prod[run] = A;
@@ -218,7 +220,7 @@ __global__ void __launch_bounds__(kRunNT) linrec_runs_carry_kernel(const __grid_
 
 // ---------------------------------------------------------------- pass R
 template <class T>
-__global__ void __launch_bounds__(kRunNT) linrec_runs_vjp_kernel(
+__global__ void __launch_bounds__(RunCfg<T>::NT) linrec_runs_vjp_kernel(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
     const __grid_constant__ CUtensorMap tmYA, const __grid_constant__ CUtensorMap tmYB,
     const __grid_constant__ CUtensorMap tmOA, const __grid_constant__ CUtensorMap tmOB, RunArgs<T> R) {
@@ -227,12 +229,12 @@ __global__ void __launch_bounds__(kRunNT) linrec_runs_vjp_kernel(
     constexpr int V = Cf::V, EPC = Cf::EPC;
     extern __shared__ __align__(1024) unsigned char s_dyn[];
     unsigned char* sA = s_dyn;
-    unsigned char* sB = s_dyn + kRunArrBytes;      // b, then B_{j-1}
-    unsigned char* sYA = s_dyn + 2 * kRunArrBytes;  // ybar_A, then abar
-    unsigned char* sYB = s_dyn + 3 * kRunArrBytes;  // ybar_B, then bbar
+    unsigned char* sB = s_dyn + Cf::ARR;      // b, then B_{j-1}
+    unsigned char* sYA = s_dyn + 2 * Cf::ARR;  // ybar_A, then abar
+    unsigned char* sYB = s_dyn + 3 * Cf::ARR;  // ybar_B, then bbar
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ uint32_t s_tile;
-    __shared__ L s_tot[kRunNW];
+    __shared__ L s_tot[Cf::NW];
     __shared__ L s_pre;
     if (threadIdx.x == 0) s_tile = atomicAdd(&R.hdr->ticket[1], 1u);
     __syncthreads();
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(kRunNT) linrec_runs_vjp_kernel(
     const int64_t tile = R.tiles - 1 - t_log;  // tiles are taken right to left
     const bool whole = (tile + 1) * Cf::TILE <= R.n;
     const int t = threadIdx.x;
-    const int64_t run = tile * kRunNT + t;
+    const int64_t run = tile * Cf::NT + t;
     // the run's carry (the state before the tile, then the run's local
     // carry within it) and product (pass C) load while the tile arrives
     const RunP<T> tc0 = R.tcar[tile];
@@ -298,14 +300,14 @@ __global__ void __launch_bounds__(kRunNT) linrec_runs_vjp_kernel(
     };
     const L ident{T(1), T(0), T(0)};
     L wex[1];
-    const L total = block_scan_part1<L, true, 1, kRunNW>(agg, wex, s_tot, ident, comb);
+    const L total = block_scan_part1<L, true, 1, Cf::NW>(agg, wex, s_tot, ident, comb);
     if ((threadIdx.x >> 5) == 0) {
         LookbackState<L> st{R.lbR_agg, R.lbR_incl};
         const L pre = lookback(t_log, st, total, ident, comb, R.hdr);
         if ((threadIdx.x & 31) == 0) s_pre = pre;
     }
     __syncthreads();
-    const L ex = block_scan_excl<L, true, 1, kRunNW>(0, wex, s_tot, s_pre, comb);
+    const L ex = block_scan_excl<L, true, 1, Cf::NW>(0, wex, s_tot, s_pre, comb);
 
     // 4. rs_bar right to left and the outputs, written over the cotangents;
     //    rs_bar_e = ybar_e + U_{e+1} with U_{e+1} = ex.d (a_up starts at 1)
@@ -337,8 +339,8 @@ __global__ void __launch_bounds__(kRunNT) linrec_runs_vjp_kernel(
         tc::fence_proxy_async();
         __syncthreads();
         if (threadIdx.x == 0) {
-            tma_store_3d(&tmOA, (int)(tile * kRunNT), sYA);
-            tma_store_3d(&tmOB, (int)(tile * kRunNT), sYB);
+            tma_store_3d(&tmOA, (int)(tile * Cf::NT), sYA);
+            tma_store_3d(&tmOB, (int)(tile * Cf::NT), sYB);
             bulk_commit_and_wait_read();
         }
         __syncthreads();

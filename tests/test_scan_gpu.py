@@ -240,6 +240,7 @@ def test_add_max_scan_full_size(A, oracle, op):
         np.testing.assert_array_equal(np.flatnonzero(got), np.flatnonzero(ref))
 
 
+# tiles of 128 runs: 2048 FP64 / 4096 FP32 elements
 RUN_SIZES = {np.float64: [1, 15, 16, 17, 2047, 2048, 2049, 3 * 2048 + 5, 100001, (1 << 20) + 3],
              np.float32: [1, 31, 32, 33, 4095, 4096, 4097, 3 * 4096 + 5, 100001, (1 << 20) + 3]}
 

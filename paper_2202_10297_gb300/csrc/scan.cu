@@ -94,18 +94,30 @@ __global__ void __launch_bounds__(kScanBlock) scan_tile_agg_kernel(ScanArgs A, t
     if (threadIdx.x == 0) agg[tile] = total;
 }
 
-// One block: carry[i] = agg[0] (.) ... (.) agg[i-1], in order.
+// carry[i] = agg[0] (.) ... (.) agg[i-1], in order, over segments of
+// kCarrySeg tiles: carry_local_kernel scans each segment (one block per
+// segment) and writes its total, carry_apply_kernel puts the fold of the
+// earlier segments' totals in front.  (One block over every tile left the
+// FP64 combines to one SM: 116 us for 32768 FP64 tiles.)  segtot holds one
+// state per segment.
 constexpr int kCarryBlock = 1024;
+constexpr int kCarryPer = 4;
+constexpr int kCarrySeg = kCarryBlock * kCarryPer;
+
 template <class Op>
-__global__ void __launch_bounds__(kCarryBlock) scan_carry_kernel(const typename Op::P* agg, typename Op::P* carry,
-                                                                 int64_t tiles) {
+__global__ void __launch_bounds__(kCarryBlock) carry_local_kernel(const typename Op::P* agg, typename Op::P* carry,
+                                                                  typename Op::P* segtot, int64_t tiles) {
     using P = typename Op::P;
     __shared__ P s_w[kCarryBlock / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t per = (tiles + kCarryBlock - 1) / kCarryBlock;
-    const int64_t lo = threadIdx.x * per, hi = lo + per < tiles ? lo + per : tiles;
+    const int64_t base = (int64_t)blockIdx.x * kCarrySeg + (int64_t)threadIdx.x * kCarryPer;
+    P v[kCarryPer];
     P run = Op::pid();
-    for (int64_t i = lo; i < hi; ++i) run = Op::pcomb(run, agg[i]);
+#pragma unroll
+    for (int j = 0; j < kCarryPer; ++j) {
+        v[j] = base + j < tiles ? agg[base + j] : Op::pid();
+        run = Op::pcomb(run, v[j]);
+    }
     P inc = run;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -115,22 +127,61 @@ __global__ void __launch_bounds__(kCarryBlock) scan_carry_kernel(const typename 
     if (lane == 31) s_w[warp] = inc;
     __syncthreads();
     if (warp == 0) {
-        P v = s_w[lane];
+        P w = s_w[lane];
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
-            const P o = shfl_up_s(v, off);
-            if (lane >= off) v = Op::pcomb(o, v);
+            const P o = shfl_up_s(w, off);
+            if (lane >= off) w = Op::pcomb(o, w);
         }
-        s_w[lane] = v;
+        s_w[lane] = w;
     }
     __syncthreads();
     P ex = shfl_up_s(inc, 1);
     if (lane == 0) ex = Op::pid();
     if (warp > 0) ex = Op::pcomb(s_w[warp - 1], ex);
-    for (int64_t i = lo; i < hi; ++i) {
-        carry[i] = ex;
-        ex = Op::pcomb(ex, agg[i]);
+#pragma unroll
+    for (int j = 0; j < kCarryPer; ++j) {
+        if (base + j < tiles) carry[base + j] = ex;
+        ex = Op::pcomb(ex, v[j]);
     }
+    if (threadIdx.x == 0) segtot[blockIdx.x] = s_w[kCarryBlock / 32 - 1];
+}
+
+template <class Op>
+__global__ void __launch_bounds__(256) carry_apply_kernel(typename Op::P* carry, const typename Op::P* segtot,
+                                                          int64_t tiles) {
+    using P = typename Op::P;
+    if (blockIdx.x == 0) return;
+    __shared__ P s_pre;
+    if (threadIdx.x < 32) {
+        // fold of segtot[0 .. blockIdx.x): contiguous pieces per lane, then
+        // a warp scan of the pieces in lane order
+        const int lane = threadIdx.x;
+        const int cnt = (int)blockIdx.x, per = (cnt + 31) / 32;
+        P r = Op::pid();
+        for (int i = lane * per; i < cnt && i < (lane + 1) * per; ++i) r = Op::pcomb(r, segtot[i]);
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const P o = shfl_up_s(r, off);
+            if (lane >= off) r = Op::pcomb(o, r);
+        }
+        if (lane == 31) s_pre = r;
+    }
+    __syncthreads();
+    const P pre = s_pre;
+    const int64_t lo = (int64_t)blockIdx.x * kCarrySeg;
+    const int64_t hi = lo + kCarrySeg < tiles ? lo + kCarrySeg : tiles;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) carry[i] = Op::pcomb(pre, carry[i]);
+}
+
+// the tile carries from the tile aggregates; segtot: room for one state per
+// kCarrySeg tiles
+template <class Op>
+void launch_carry_scan(const typename Op::P* agg, typename Op::P* carry, typename Op::P* segtot, int64_t tiles,
+                       cudaStream_t stream) {
+    const unsigned nseg = (unsigned)((tiles + kCarrySeg - 1) / kCarrySeg);
+    carry_local_kernel<Op><<<nseg, kCarryBlock, 0, stream>>>(agg, carry, segtot, tiles);
+    if (nseg > 1) carry_apply_kernel<Op><<<nseg, 256, 0, stream>>>(carry, segtot, tiles);
 }
 
 // MIN/MAX scans: the return sweep fused into the forward pass.  For these
@@ -821,7 +872,9 @@ int run_linrec_runs(int64_t n, const void* a, const void* b, const void* ya, con
     scan_init_kernel<<<iblocks, 256, 0, stream>>>(R.hdr, reinterpret_cast<unsigned long long*>(w + L.off_slots),
                                                   words);
     linrec_runs_carry_kernel<T><<<(unsigned)L.tiles, Cf::NT, 2 * Cf::ARR, stream>>>(tm[0], tm[1], R);
-    scan_carry_kernel<RunPOp<T>><<<1, kCarryBlock, 0, stream>>>(R.tagg, R.tcar, L.tiles);
+    // the segment totals take the second half of the tile aggregates' slots
+    static_assert(lb_words<RunP<T>>() * 8 >= 2 * sizeof(RunP<T>), "room after the aggregates");
+    launch_carry_scan<RunPOp<T>>(R.tagg, R.tcar, R.tagg + L.tiles, L.tiles, stream);
     linrec_runs_vjp_kernel<T><<<(unsigned)L.tiles, Cf::NT, 4 * Cf::ARR, stream>>>(tm[0], tm[1], tm[2], tm[3],
                                                                                        tm[4], tm[5], R);
     return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
@@ -1004,10 +1057,11 @@ int run_scan(int64_t n, const void* a, const void* b, const void* ya, const void
         if (need_primal) {
             // the tile aggregates take the primal aggregate slots, unused here
             using P = typename Op::P;
-            static_assert(lb_words<P>() * 8 >= sizeof(P), "an aggregate fits a slot");
+            // (and the segment totals of the carry scan their second half)
+            static_assert(lb_words<P>() * 8 >= 2 * sizeof(P), "an aggregate and a total fit a slot");
             P* agg = reinterpret_cast<P*>(A.lbP_agg);
             scan_tile_agg_kernel<Op, T><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A, agg);
-            scan_carry_kernel<Op><<<1, kCarryBlock, 0, stream>>>(agg, static_cast<P*>(A.carry), A.tiles);
+            launch_carry_scan<Op>(agg, static_cast<P*>(A.carry), agg + A.tiles, A.tiles, stream);
         }
         if (ys_a) scan_adjoint_kernel<Op, T, true><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);
         else scan_adjoint_kernel<Op, T, false><<<(unsigned)A.tiles, kScanBlock, 0, stream>>>(A);

@@ -284,3 +284,22 @@ def test_add_scan_shared_tile_path(A, oracle, dt, n, accumulate):
     A.adpar_vjp_scan("add", None, dev(y), abar=ab0, accumulate=accumulate, work=work)
     assert A.adpar_workspace_status(work) == A.OK
     assert rel_l2(ab0.cpu().numpy(), ref) < tol(dt, n)
+
+
+@pytest.mark.parametrize("path,dt,n", [("runs", np.float64, 2048 * 8193 + 5), ("runs", np.float32, 4096 * 4097 + 7),
+                                       ("minimal", np.float32, 4096 * 4097 + 9)])
+def test_tile_carry_segments(A, oracle, path, dt, n):
+    """More than 4096 tiles: the tile carries are scanned in segments of 4096
+    tiles (one block each) and the earlier segments' fold is applied after
+    (two and three segments, ragged last tile), on the runs path and on the
+    minimal-workspace path, against the oracle."""
+    f64 = dt == np.float64
+    a, b, ya, yb = synth.linrec(n, dt, seed=n % 1000 + 41)
+    rab, rbb, _, _ = oracle.scan_vjp("linrec", a, ya, b, yb)
+    flags = A.RULE_SCAN | (A.WS_MINIMAL if path == "minimal" else 0)
+    work = A.workspace(A.adpar_workspace_size(flags, A.OP_LINREC, A.F64 if f64 else A.F32, n))
+    ab, bb, _ = A.adpar_vjp_scan("linrec", dev(a), dev(ya), b=dev(b), ybar_b=dev(yb), work=work)
+    assert A.adpar_workspace_status(work) == A.OK
+    t = tol(dt, n)
+    assert rel_l2(ab.cpu().numpy(), rab) < t
+    assert rel_l2(bb.cpu().numpy(), rbb) < t

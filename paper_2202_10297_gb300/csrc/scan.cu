@@ -863,7 +863,7 @@ int run_linrec_runs(int64_t n, const void* a, const void* b, const void* ya, con
         if (cudaFuncSetAttribute(linrec_runs_carry_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  2 * Cf::ARR) != cudaSuccess ||
             cudaFuncSetAttribute(linrec_runs_vjp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 4 * Cf::ARR) != cudaSuccess)
+                                 3 * Cf::ARR) != cudaSuccess)
             return ADPAR_ERR_CUDA;
         configured[dev] = true;
     }
@@ -875,8 +875,7 @@ int run_linrec_runs(int64_t n, const void* a, const void* b, const void* ya, con
     // the segment totals take the second half of the tile aggregates' slots
     static_assert(lb_words<RunP<T>>() * 8 >= 2 * sizeof(RunP<T>), "room after the aggregates");
     launch_carry_scan<RunPOp<T>>(R.tagg, R.tcar, R.tagg + L.tiles, L.tiles, stream);
-    linrec_runs_vjp_kernel<T><<<(unsigned)L.tiles, Cf::NT, 4 * Cf::ARR, stream>>>(tm[0], tm[1], tm[2], tm[3],
-                                                                                       tm[4], tm[5], R);
+    linrec_runs_vjp_kernel<T><<<(unsigned)L.tiles, Cf::NT, 3 * Cf::ARR, stream>>>(tm[0], tm[2], tm[3], tm[4], tm[5], R);
     return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
 }
 

@@ -30,6 +30,7 @@
 //
 // A tile is NT runs; each input array's tile (NT runs of 128 bytes)
 // comes into shared memory by one 3-D TMA copy with the 128-byte swizzle
+// (in the reverse pass b instead goes straight into registers)
 // (16-byte chunk c of 128-byte row r stored at chunk c ^ (r & 7)), so that a
 // thread reading its own run with 16-byte loads meets few bank conflicts.
 // The outputs are written back into the cotangents' tiles and stored by TMA.
@@ -220,18 +221,17 @@ __global__ void __launch_bounds__(RunCfg<T>::NT) linrec_runs_carry_kernel(const 
 
 // ---------------------------------------------------------------- pass R
 template <class T>
-__global__ void __launch_bounds__(RunCfg<T>::NT) linrec_runs_vjp_kernel(
-    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-    const __grid_constant__ CUtensorMap tmYA, const __grid_constant__ CUtensorMap tmYB,
-    const __grid_constant__ CUtensorMap tmOA, const __grid_constant__ CUtensorMap tmOB, RunArgs<T> R) {
+__global__ void __launch_bounds__(RunCfg<T>::NT, 4) linrec_runs_vjp_kernel(
+    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmYA,
+    const __grid_constant__ CUtensorMap tmYB, const __grid_constant__ CUtensorMap tmOA,
+    const __grid_constant__ CUtensorMap tmOB, RunArgs<T> R) {
     using Cf = RunCfg<T>;
     using L = RunL<T>;
     constexpr int V = Cf::V, EPC = Cf::EPC;
     extern __shared__ __align__(1024) unsigned char s_dyn[];
     unsigned char* sA = s_dyn;
-    unsigned char* sB = s_dyn + Cf::ARR;      // b, then B_{j-1}
-    unsigned char* sYA = s_dyn + 2 * Cf::ARR;  // ybar_A, then abar
-    unsigned char* sYB = s_dyn + 3 * Cf::ARR;  // ybar_B, then bbar
+    unsigned char* sYA = s_dyn + Cf::ARR;      // ybar_A, then abar
+    unsigned char* sYB = s_dyn + 2 * Cf::ARR;  // ybar_B, then bbar
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ uint32_t s_tile;
     __shared__ L s_tot[Cf::NW];
@@ -248,15 +248,33 @@ __global__ void __launch_bounds__(RunCfg<T>::NT) linrec_runs_vjp_kernel(
     const RunP<T> tc0 = R.tcar[tile];
     const T lA = R.carA[run], lB = R.carB[run], cprod = R.prod[run];
     const T PA = tc0.A * lA, PB = run_fma(lA, tc0.B, lB);
+    // b is read once, by its own thread: straight from global memory into
+    // registers (its 128-byte row in eight 16-byte loads), so that the tile
+    // holds three arrays in shared memory and four tiles fit on an SM
+    T Bp[V];  // b_j, then B_{j-1}
     {
-        unsigned char* const dst[4] = {sA, sB, sYA, sYB};
-        const CUtensorMap* const tm[4] = {&tmA, &tmB, &tmYA, &tmYB};
-        const T* const src[4] = {R.a, R.b, R.ya, R.yb};
-        const T pad[4] = {T(1), T(0), T(0), T(0)};
-        run_tile_load<T, 4>(dst, tm, src, pad, whole, tile, R.n, &s_bar, R.hdr);
+        const int64_t e0 = tile * Cf::TILE + (int64_t)t * V;
+        if (whole) {
+#pragma unroll
+            for (int p = 0; p < kRunChunks; ++p) {
+                const RunVec<T> v = *reinterpret_cast<const RunVec<T>*>(R.b + e0 + EPC * p);
+#pragma unroll
+                for (int j = 0; j < EPC; ++j) Bp[EPC * p + j] = v.v[j];
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < V; ++j) Bp[j] = e0 + j < R.n ? R.b[e0 + j] : T(0);
+        }
+    }
+    {
+        unsigned char* const dst[3] = {sA, sYA, sYB};
+        const CUtensorMap* const tm[3] = {&tmA, &tmYA, &tmYB};
+        const T* const src[3] = {R.a, R.ya, R.yb};
+        const T pad[3] = {T(1), T(0), T(0)};
+        run_tile_load<T, 3>(dst, tm, src, pad, whole, tile, R.n, &s_bar, R.hdr);
     }
 
-    // 1. the primal from the carry: A_{j-1} in registers, B_{j-1} over b
+    // 1. the primal from the carry: A_{j-1} and B_{j-1} in registers
     T Aprev[V];
     {
         T A = PA, B = PB;
@@ -264,16 +282,14 @@ __global__ void __launch_bounds__(RunCfg<T>::NT) linrec_runs_vjp_kernel(
         for (int p = 0; p < kRunChunks; ++p) {
             const int off = run_chunk_off(t, p);
             const RunVec<T> x = run_ld<T>(sA, off);
-            const RunVec<T> y = run_ld<T>(sB, off);
-            RunVec<T> bp;
 #pragma unroll
             for (int j = 0; j < EPC; ++j) {
+                const T bj = Bp[EPC * p + j];
                 Aprev[EPC * p + j] = A;
-                bp.v[j] = B;
-                B = run_fma(x.v[j], B, y.v[j]);
+                Bp[EPC * p + j] = B;
+                B = run_fma(x.v[j], B, bj);
                 A *= x.v[j];
             }
-            run_st<T>(sB, off, bp);
         }
     }
     // 2. the run's reverse transfer: R_j = ybar_j + a_{j+1} R_{j+1}, from
@@ -320,13 +336,12 @@ __global__ void __launch_bounds__(RunCfg<T>::NT) linrec_runs_vjp_kernel(
             const RunVec<T> ya = run_ld<T>(sYA, off);
             const RunVec<T> yb = run_ld<T>(sYB, off);
             const RunVec<T> aa = run_ld<T>(sA, off);
-            const RunVec<T> bp = run_ld<T>(sB, off);  // B_{j-1}
             RunVec<T> oa, ob;
 #pragma unroll
             for (int j = EPC - 1; j >= 0; --j) {
                 rA = run_fma(a_up, rA, ya.v[j]);
                 rB = run_fma(a_up, rB, yb.v[j]);
-                oa.v[j] = run_fma(Aprev[EPC * p + j], rA, bp.v[j] * rB);
+                oa.v[j] = run_fma(Aprev[EPC * p + j], rA, Bp[EPC * p + j] * rB);
                 ob.v[j] = rB;
                 a_up = aa.v[j];
             }

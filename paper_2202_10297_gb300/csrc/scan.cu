@@ -654,6 +654,8 @@ __global__ void __launch_bounds__(kScanBlock) scan_forward_kernel(ScanArgs A) {
 // for the outputs.  Chunk k of a tile holds kScanBlock 16-byte vectors, one
 // per thread (the layout of the scan engine, conflict-free in shared memory).
 template <class T>
+// (tiles of 8 and 12 vectors per thread, and writing whole tiles back by
+// one bulk copy from shared memory, measured no faster at 2^28)
 struct AddSmemCfg {
     static constexpr int VEC = 16 / sizeof(T);
     static constexpr int K = 16;

@@ -510,6 +510,8 @@ __global__ void __launch_bounds__(KM_THREADS, 1)
                         if (A.argmin_out) A.argmin_out[row] = best;
                     }
                     if (want_grad) {
+                        // (a row at a time with lanes = its 32 coordinates,
+                        // conflict-free, measured slower: 0.225 -> 0.250 ms)
                         float* srow = s_sum + best * KM_SUM_LD + 8 * g;
                         atomicAdd(srow + 0, x0.x);
                         atomicAdd(srow + 1, x0.y);

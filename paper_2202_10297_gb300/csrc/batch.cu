@@ -237,22 +237,40 @@ __global__ void __launch_bounds__(256) batch_kernel(const char* plan, char* ws) 
     const int64_t nseg = H->nseg, total = H->total_items;
     __shared__ uint32_t s_item;
     __shared__ int s_stop;
+    __shared__ int64_t s_seg;
+    // thread 0's segment of the CTA's last item: tickets only grow, so the
+    // next item's segment is found from there (usually the same segment: no
+    // load at all; else a galloping search forward), instead of a binary
+    // search of 12 dependent loads per item
+    int64_t seg = 0, seg_next = nseg > 1 ? meta[1].item_base : INT64_MAX;
     while (true) {
         __syncthreads();  // consecutive items reuse the static shared memory
         if (threadIdx.x == 0) {
             s_item = atomicAdd(&hdr->ticket[0], 1u);
             s_stop = ((int64_t)s_item >= total) || gave_up(hdr);
+            const int64_t q = s_item;
+            if (!s_stop && q >= seg_next) {
+                // the last s with item_base <= q lies in (seg, nseg)
+                int64_t lo = seg + 1, step = 1;
+                while (lo + step < nseg && meta[lo + step].item_base <= q) {
+                    lo += step;
+                    step <<= 1;
+                }
+                int64_t hi = std::min<int64_t>(nseg - 1, lo + step - 1);
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi + 1) >> 1;
+                    if (meta[mid].item_base <= q) lo = mid;
+                    else hi = mid - 1;
+                }
+                seg = lo;
+                seg_next = seg + 1 < nseg ? meta[seg + 1].item_base : INT64_MAX;
+            }
+            s_seg = seg;
         }
         __syncthreads();
         if (s_stop) break;
         const int64_t q = s_item;
-        // segment of item q: last s with item_base <= q
-        int64_t lo = 0, hi = nseg - 1;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) >> 1;
-            if (meta[mid].item_base <= q) lo = mid;
-            else hi = mid - 1;
-        }
+        const int64_t lo = s_seg;
         const SegMeta m = meta[lo];
         const adpar_batch_segment sg = segs[lo];
         const StateLayout L = state_layout(sg.dtype, m.red_tiles, m.scan_tiles);

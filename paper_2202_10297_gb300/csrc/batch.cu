@@ -13,14 +13,17 @@
 // running, so the schedule cannot deadlock, and every wait is bounded.
 // Small segments are one tile of each kind; no look-back happens there.
 //
-// The scan tiles are the very device functions of the standalone scan
-// kernels (scan_tiles.cuh); the product tiles re-run the forward sweep as
-// a (zero count, lowest zero, scaled product) reduction per tile whose last
-// tile to finish combines the partials and raises the segment's flag.
+// The scan tiles run the linear recurrence on per-thread runs
+// (batch_runs.cuh: a forward tile stores its runs' carries, a reverse tile
+// re-forms the primal from them); the product tiles re-run the forward
+// sweep as a (zero count, lowest zero, scaled product) reduction per tile
+// whose last tile to finish combines the partials and raises the segment's
+// flag.
 #include <algorithm>
 #include <cstring>
 #include <vector>
 
+#include "batch_runs.cuh"
 #include "prod.cuh"
 #include "scan_tiles.cuh"
 
@@ -46,28 +49,26 @@ struct SegMeta {
     int32_t scan_tiles;
 };
 
-// tile shapes of the compiled variants: scan tile f32 = KF*256*EF,
-// f64 = KD*256*ED; reduce/map tile RT elements
+// reduce/map tile of the compiled variants (RT elements); the scan tiles
+// are brun_tile<T>() elements in every variant
 struct VariantShape {
-    int kf, ef, kd, ed, rt;
+    int rt;
 };
-constexpr VariantShape kVariants[] = {
-    {2, 4, 1, 8, 8192},    // 0: 2048-element scan tiles
-    {4, 4, 2, 8, 16384},   // 1: 4096-element scan tiles
-    {1, 4, 1, 4, 4096},    // 2: 1024-element scan tiles (many short segments)
-};
+constexpr VariantShape kVariants[] = {{8192}, {16384}, {4096}};
 constexpr int kNumVariants = 3;
 
 // per-segment state layout (bytes from state_off)
 struct StateLayout {
-    int64_t partials, counter, final_state, p_agg, p_incl, r_agg, r_incl, total;
+    int64_t partials, counter, final_state, p_agg, p_incl, r_agg, r_incl, done, carA, carB, prod, total;
 };
 
 __host__ __device__ inline int64_t al16(int64_t x) { return (x + 15) & ~int64_t(15); }
 
 __host__ __device__ inline StateLayout state_layout(int dtype, int red, int scan) {
     const int wp = dtype == ADPAR_F64 ? 4 : 2;  // 64-bit words of a primal (A, B) state
-    const int wr = dtype == ADPAR_F64 ? 6 : 3;  // of a lin_o (dA, dB, c) state
+    const int wr = dtype == ADPAR_F64 ? 6 : 3;  // of a lin_o (c, dA, dB) state
+    const int64_t es = dtype == ADPAR_F64 ? 8 : 4;
+    const int64_t runs = (int64_t)scan * kBNT;
     StateLayout L;
     int64_t o = 0;
     L.partials = o; o = al16(o + (int64_t)red * (int64_t)sizeof(ProdStateQ));
@@ -77,6 +78,10 @@ __host__ __device__ inline StateLayout state_layout(int dtype, int red, int scan
     L.p_incl = o; o = al16(o + (int64_t)scan * wp * 8);
     L.r_agg = o; o = al16(o + (int64_t)scan * wr * 8);
     L.r_incl = o; o = al16(o + (int64_t)scan * wr * 8);
+    L.done = o; o = al16(o + (int64_t)scan * 4);
+    L.carA = o; o = al16(o + runs * es);
+    L.carB = o; o = al16(o + runs * es);
+    L.prod = o; o = al16(o + runs * es);
     L.total = o;
     return L;
 }
@@ -199,26 +204,27 @@ __device__ void prod_map_tile(const adpar_batch_segment& sg, char* st, const Sta
     }
 }
 
-template <class T, int K, int E>
+// linear-recurrence tile j of a segment: forward (adjoint false, left to
+// right) or reverse (right to left), on per-thread runs
+template <class T>
 __device__ void linrec_tile(const adpar_batch_segment& sg, char* st, const StateLayout& L, int scan_tiles,
-                            int64_t t, bool adjoint, WsHeader* hdr) {
-    ScanArgs A{};
-    A.n = sg.len;
-    A.a = sg.a;
-    A.b = sg.b;
-    A.ya = sg.ybar_a;
-    A.yb = sg.ybar_b;
-    A.abar = sg.abar;
-    A.bbar = sg.bbar;
-    A.tiles = scan_tiles;
-    A.hdr = hdr;
-    A.carry = nullptr;  // carries come from the primal look-back slots
-    A.lbP_agg = reinterpret_cast<unsigned long long*>(st + L.p_agg);
-    A.lbP_incl = reinterpret_cast<unsigned long long*>(st + L.p_incl);
-    A.lbR_agg = reinterpret_cast<unsigned long long*>(st + L.r_agg);
-    A.lbR_incl = reinterpret_cast<unsigned long long*>(st + L.r_incl);
-    if (adjoint) scan_adjoint_tile<OpLinrec<T>, T, K, E, false>(A, t);
-    else scan_primal_tile<OpLinrec<T>, T, K, E>(A, t);
+                            int64_t j, bool adjoint, unsigned char* smem, WsHeader* hdr) {
+    BRunState S;
+    S.p_agg = reinterpret_cast<unsigned long long*>(st + L.p_agg);
+    S.p_incl = reinterpret_cast<unsigned long long*>(st + L.p_incl);
+    S.r_agg = reinterpret_cast<unsigned long long*>(st + L.r_agg);
+    S.r_incl = reinterpret_cast<unsigned long long*>(st + L.r_incl);
+    S.done = reinterpret_cast<uint32_t*>(st + L.done);
+    S.carA = st + L.carA;
+    S.carB = st + L.carB;
+    S.prod = st + L.prod;
+    const T* a = static_cast<const T*>(sg.a);
+    const T* b = static_cast<const T*>(sg.b);
+    if (adjoint)
+        brun_rev_tile<T>(a, b, static_cast<const T*>(sg.ybar_a), static_cast<const T*>(sg.ybar_b),
+                         static_cast<T*>(sg.abar), static_cast<T*>(sg.bbar), sg.len, S, scan_tiles, j, smem, hdr);
+    else
+        brun_fwd_tile<T>(a, b, sg.len, S, j, smem, hdr);
 }
 
 __global__ void batch_init_kernel(char* ws, int64_t bytes) {
@@ -228,8 +234,9 @@ __global__ void batch_init_kernel(char* ws, int64_t bytes) {
         reinterpret_cast<uint4*>(ws)[i] = make_uint4(0, 0, 0, 0);
 }
 
-template <int KF, int EF, int KD, int ED, int RT>
+template <int RT>
 __global__ void __launch_bounds__(256) batch_kernel(const char* plan, char* ws) {
+    extern __shared__ __align__(16) unsigned char s_dyn[];  // kBRunSmem: the scan tiles' arrays
     const BatchPlanHeader* H = reinterpret_cast<const BatchPlanHeader*>(plan);
     const adpar_batch_segment* segs = reinterpret_cast<const adpar_batch_segment*>(plan + H->seg_off);
     const SegMeta* meta = reinterpret_cast<const SegMeta*>(plan + H->meta_off);
@@ -284,14 +291,14 @@ __global__ void __launch_bounds__(256) batch_kernel(const char* plan, char* ws) 
         }
         j -= m.red_tiles;
         if (j < m.scan_tiles) {
-            if (f64) linrec_tile<double, KD, ED>(sg, st, L, m.scan_tiles, j, false, hdr);
-            else linrec_tile<float, KF, EF>(sg, st, L, m.scan_tiles, j, false, hdr);
+            if (f64) linrec_tile<double>(sg, st, L, m.scan_tiles, j, false, s_dyn, hdr);
+            else linrec_tile<float>(sg, st, L, m.scan_tiles, j, false, s_dyn, hdr);
             continue;
         }
         j -= m.scan_tiles;
         if (j < m.scan_tiles) {
-            if (f64) linrec_tile<double, KD, ED>(sg, st, L, m.scan_tiles, j, true, hdr);
-            else linrec_tile<float, KF, EF>(sg, st, L, m.scan_tiles, j, true, hdr);
+            if (f64) linrec_tile<double>(sg, st, L, m.scan_tiles, j, true, s_dyn, hdr);
+            else linrec_tile<float>(sg, st, L, m.scan_tiles, j, true, s_dyn, hdr);
             continue;
         }
         j -= m.scan_tiles;
@@ -303,9 +310,9 @@ __global__ void __launch_bounds__(256) batch_kernel(const char* plan, char* ws) 
 typedef void (*BatchKernel)(const char*, char*);
 BatchKernel kernel_of(int v) {
     switch (v) {
-    case 0: return batch_kernel<2, 4, 1, 8, 8192>;
-    case 1: return batch_kernel<4, 4, 2, 8, 16384>;
-    case 2: return batch_kernel<1, 4, 1, 4, 4096>;
+    case 0: return batch_kernel<8192>;
+    case 1: return batch_kernel<16384>;
+    case 2: return batch_kernel<4096>;
     }
     return nullptr;
 }
@@ -368,7 +375,7 @@ extern "C" int adpar_batch_plan(const adpar_batch_segment* segs, int nseg, const
     int64_t items = 0, state = (int64_t)sizeof(WsHeader);
     for (int q = 0; q < nseg; ++q) {
         const adpar_batch_segment& g = segs[order[q]];
-        const int st = g.dtype == ADPAR_F64 ? V.kd * 256 * V.ed : V.kf * 256 * V.ef;
+        const int st = g.dtype == ADPAR_F64 ? brun_tile<double>() : brun_tile<float>();
         const int64_t red = std::max<int64_t>(1, (g.len + V.rt - 1) / V.rt);
         const int64_t scan = std::max<int64_t>(1, (g.len + st - 1) / st);
         if (red > INT32_MAX || scan > INT32_MAX) return ADPAR_ERR_UNSUPPORTED;
@@ -402,8 +409,16 @@ extern "C" int adpar_vjp_batch(const void* plan_host, const void* plan_dev, void
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int ib = (int)std::max<int64_t>(1, std::min<int64_t>((H->ws_bytes / 16 + 255) / 256, (int64_t)sms * 4));
     batch_init_kernel<<<ib, 256, 0, s>>>(static_cast<char*>(work), H->ws_bytes);
+    static bool configured[64][kNumVariants] = {};
+    if (dev < 0 || dev >= 64) return ADPAR_ERR_CUDA;
+    if (!configured[dev][H->variant]) {
+        if (cudaFuncSetAttribute(kernel_of(H->variant), cudaFuncAttributeMaxDynamicSharedMemorySize, kBRunSmem) !=
+            cudaSuccess)
+            return ADPAR_ERR_CUDA;
+        configured[dev][H->variant] = true;
+    }
     const int64_t grid = std::min<int64_t>((int64_t)sms * H->ctas_per_sm, H->total_items);
-    kernel_of(H->variant)<<<(unsigned)std::max<int64_t>(1, grid), 256, 0, s>>>(static_cast<const char*>(plan_dev),
-                                                                           static_cast<char*>(work));
+    kernel_of(H->variant)<<<(unsigned)std::max<int64_t>(1, grid), 256, kBRunSmem, s>>>(
+        static_cast<const char*>(plan_dev), static_cast<char*>(work));
     return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
 }

@@ -196,8 +196,13 @@ __device__ void brun_rev_tile(const T* a, const T* b, const T* ya, const T* yb, 
         const RunVec<T> aa = run_ld<T>(sA, off);
 #pragma unroll
         for (int j = EPC - 1; j >= 0; --j) {
-            RA = run_fma(a_next, RA, y1.v[j]);
-            RB = run_fma(a_next, RB, y2.v[j]);
+            if (p == kRunChunks - 1 && j == EPC - 1) {  // R_e = ybar_e (no FMA)
+                RA = y1.v[j];
+                RB = y2.v[j];
+            } else {
+                RA = run_fma(a_next, RA, y1.v[j]);
+                RB = run_fma(a_next, RB, y2.v[j]);
+            }
             a_next = aa.v[j];
         }
     }

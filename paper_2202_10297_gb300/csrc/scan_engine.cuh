@@ -51,17 +51,21 @@ __device__ __forceinline__ S block_scan_part1(const S (&agg)[K], S (&wex)[K], S*
     __syncthreads();
     S total = ident;
     if (warp == 0) {
+        // with one total per lane (Q <= 32) the scan needs only the steps
+        // that span lanes 0..Q-1, and the tile total is lane Q-1's
+        constexpr int SPAN = R == 1 ? Q : 32;
         S v[R];
-        S run = ident;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int q = lane * R + r;
             v[r] = q < Q ? s_tot[q] : ident;
-            run = comb(run, v[r]);
         }
+        S run = v[0];
+#pragma unroll
+        for (int r = 1; r < R; ++r) run = comb(run, v[r]);
         S inc = run;
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
+        for (int off = 1; off < SPAN; off <<= 1) {
             S o = shfl_up_s(inc, off);
             if (lane >= off) inc = comb(o, inc);
         }
@@ -74,7 +78,7 @@ __device__ __forceinline__ S block_scan_part1(const S (&agg)[K], S (&wex)[K], S*
             if (q < Q) s_tot[q] = ex;
             ex = comb(ex, v[r]);
         }
-        total = shfl_idx_s(inc, 31);
+        total = shfl_idx_s(inc, SPAN - 1);
     }
     return total;
 }

@@ -305,8 +305,13 @@ __global__ void __launch_bounds__(RunCfg<T>::NT, 4) linrec_runs_vjp_kernel(
         const RunVec<T> aa = run_ld<T>(sA, off);
 #pragma unroll
         for (int j = EPC - 1; j >= 0; --j) {
-            RA = run_fma(a_next, RA, ya.v[j]);
-            RB = run_fma(a_next, RB, yb.v[j]);
+            if (p == kRunChunks - 1 && j == EPC - 1) {  // R_e = ybar_e (no FMA)
+                RA = ya.v[j];
+                RB = yb.v[j];
+            } else {
+                RA = run_fma(a_next, RA, ya.v[j]);
+                RB = run_fma(a_next, RB, yb.v[j]);
+            }
             a_next = aa.v[j];
         }
     }

@@ -86,7 +86,6 @@ __device__ void brun_fwd_tile(const T* a, const T* b, int64_t n, const BRunState
     using P = RunP<T>;
     constexpr int NW = kBNT / 32;
     __shared__ P s_totP[NW];
-    __shared__ P s_preP;
     unsigned char* sA = smem;
     unsigned char* sB = smem + kBArr;
     const int64_t e0 = tile * brun_tile<T>();
@@ -113,10 +112,10 @@ __device__ void brun_fwd_tile(const T* a, const T* b, int64_t n, const BRunState
     if ((threadIdx.x >> 5) == 0) {
         LookbackState<P> st{S.p_agg, S.p_incl};
         const P pre = lookback(tile, st, total, ident, comb, hdr);
-        if ((threadIdx.x & 31) == 0) s_preP = pre;
+        block_fold_prefix<P, 1, NW>(s_totP, pre, comb);
     }
     __syncthreads();
-    const P ex = block_scan_excl<P, false, 1, NW>(0, wex, s_totP, s_preP, comb);
+    const P ex = block_scan_excl_folded<P, false, 1, NW>(0, wex, s_totP, comb);
     const int64_t run = tile * kBNT + t;
     static_cast<T*>(S.carA)[run] = ex.A;
     static_cast<T*>(S.carB)[run] = ex.B;
@@ -133,7 +132,6 @@ __device__ void brun_rev_tile(const T* a, const T* b, const T* ya, const T* yb, 
     using L = RunL<T>;
     constexpr int V = RunCfg<T>::V, EPC = RunCfg<T>::EPC, NW = kBNT / 32;
     __shared__ L s_totL[NW];
-    __shared__ L s_preL;
     __shared__ int s_ok;
     unsigned char* sA = smem;
     unsigned char* sYA = smem + kBArr;      // ybar_A, then abar
@@ -216,10 +214,10 @@ __device__ void brun_rev_tile(const T* a, const T* b, const T* ya, const T* yb, 
     if ((threadIdx.x >> 5) == 0) {
         LookbackState<L> st{S.r_agg, S.r_incl};
         const L pre = lookback(t_log, st, total, ident, comb, hdr);
-        if ((threadIdx.x & 31) == 0) s_preL = pre;
+        block_fold_prefix<L, 1, NW>(s_totL, pre, comb);
     }
     __syncthreads();
-    const L ex = block_scan_excl<L, true, 1, NW>(0, wex, s_totL, s_preL, comb);
+    const L ex = block_scan_excl_folded<L, true, 1, NW>(0, wex, s_totL, comb);
     // rs_bar right to left and the outputs, over the cotangents' tiles
     {
         T rA = ex.dA, rB = ex.dB;

@@ -83,6 +83,25 @@ __device__ __forceinline__ S block_scan_part1(const S (&agg)[K], S (&wex)[K], S*
     return total;
 }
 
+// Part 2 when the tile's exclusive prefix is already folded into s_tot
+// (block_fold_prefix) or is the identity: one combine per thread.
+template <class S, bool REV, int K, int NW, class Comb>
+__device__ __forceinline__ S block_scan_excl_folded(int k, const S (&wex)[K], const S* s_tot, Comb comb) {
+    const int warp = threadIdx.x >> 5;
+    return comb(s_tot[chunk_warp_pos<REV, K, NW>(k, warp)], wex[k]);
+}
+
+// Called by warp 0 (every lane holding the tile's exclusive prefix `pre`)
+// after block_scan_part1 and before the barrier that precedes
+// block_scan_excl_folded: folds pre into the K*NW per-warp prefixes once,
+// instead of once per thread.
+template <class S, int K, int NW, class Comb>
+__device__ __forceinline__ void block_fold_prefix(S* s_tot, const S& pre, Comb comb) {
+    constexpr int Q = K * NW;
+    const int lane = threadIdx.x & 31;
+    for (int q = lane; q < Q; q += 32) s_tot[q] = comb(pre, s_tot[q]);
+}
+
 // Part 2: the thread's exclusive prefix for chunk k, given the exclusive
 // prefix of the whole tile (visible in shared memory after a sync).
 template <class S, bool REV, int K, int NW, class Comb>

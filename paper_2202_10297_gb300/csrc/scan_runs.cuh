@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(RunCfg<T>::NT) linrec_runs_carry_kernel(const 
     const P total = block_scan_part1<P, false, 1, Cf::NW>(agg, wex, s_tot, ident, comb);
     if (threadIdx.x == 0) R.tagg[tile] = total;
     __syncthreads();
-    const P ex = block_scan_excl<P, false, 1, Cf::NW>(0, wex, s_tot, ident, comb);
+    const P ex = block_scan_excl_folded<P, false, 1, Cf::NW>(0, wex, s_tot, comb);  // from the tile's start
     const int64_t run = tile * Cf::NT + t;
     R.carA[run] = ex.A;
     R.carB[run] = ex.B;
@@ -237,7 +237,6 @@ __global__ void __launch_bounds__(RunCfg<T>::NT, 4) linrec_runs_vjp_kernel(
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ uint32_t s_tile;
     __shared__ L s_tot[Cf::NW];
-    __shared__ L s_pre;
     if (threadIdx.x == 0) s_tile = atomicAdd(&R.hdr->ticket[1], 1u);
     __syncthreads();
     const int64_t t_log = s_tile;
@@ -327,10 +326,10 @@ __global__ void __launch_bounds__(RunCfg<T>::NT, 4) linrec_runs_vjp_kernel(
     if ((threadIdx.x >> 5) == 0) {
         LookbackState<L> st{R.lbR_agg, R.lbR_incl};
         const L pre = lookback(t_log, st, total, ident, comb, R.hdr);
-        if ((threadIdx.x & 31) == 0) s_pre = pre;
+        block_fold_prefix<L, 1, Cf::NW>(s_tot, pre, comb);
     }
     __syncthreads();
-    const L ex = block_scan_excl<L, true, 1, Cf::NW>(0, wex, s_tot, s_pre, comb);
+    const L ex = block_scan_excl_folded<L, true, 1, Cf::NW>(0, wex, s_tot, comb);
 
     // 4. rs_bar right to left and the outputs, written over the cotangents;
     //    rs_bar_e = ybar_e + U_{e+1} with U_{e+1} = ex.d (a_up starts at 1)

@@ -247,42 +247,32 @@ __device__ __forceinline__ float scale_pow2f(float x, int64_t e) {
     return __int_as_float((b & ~(0xff << 23)) | ((int)(ex + 100) << 23)) * 7.888609052210118e-31f;  // 2^-100
 }
 
-// k / m for mantissas with 0.25 <= |k| <= 1 and 0.5 <= |m| < 1: the FP32
-// reciprocal of |m| (relative error below 2^-22) gives q0 = k r0, and one
-// Newton correction of the quotient, q = q0 + (k - m q0) r0, squares that
-// error (below 2^-43 relative): one multiply and two FMAs in FP64.
-__device__ __forceinline__ double quot_mantissa(double k, double m) {
-    const long long bm = __double_as_longlong(m);
-    const long long sign = bm & (long long)0x8000000000000000ULL;
-    const float mf = __int_as_float(0x3F000000 | (int)((bm >> 29) & 0x7FFFFF));  // |m| truncated
-    const int br = __float_as_int(__frcp_rn(mf));
-    double r0 = __longlong_as_double(((long long)(((br >> 23) & 0xff) - 127 + 1023) << 52) |
-                                     ((long long)(br & 0x7FFFFF) << 29));
-    r0 = __longlong_as_double(__double_as_longlong(r0) | sign);  // 1/m carries m's sign
-    const double q0 = k * r0;
-    return fma(fma(-m, q0, k), r0, q0);
+// 1 / m for a mantissa with 0.5 <= |m| < 1 in integer arithmetic, so that
+// no FP64 instruction runs (GB300 issues FP64 at 1/64 of the FP32 rate):
+// the seed r0 is the FP32 reciprocal of |m| truncated to 24 bits (relative
+// error below 2^-22); one Newton step r1 = r0 (2 - |m| r0) in 64-bit fixed
+// point (r scaled by 2^62, |m| by 2^53, products by __umul64hi) squares the
+// error, below 2^-44 relative; r1 never exceeds 1/|m|, so it fits.  The sign
+// of m is put back at the end.
+__device__ __forceinline__ double recip_mantissa(double m) {
+    const unsigned long long bm = (unsigned long long)__double_as_longlong(m);
+    const unsigned long long sign = bm & 0x8000000000000000ULL;
+    const unsigned long long M = (bm & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);  // |m| * 2^53
+    const float mf = __int_as_float(0x3F000000 | (int)((bm >> 29) & 0x7FFFFF));  // |m| truncated, in [0.5, 1)
+    const unsigned br = __float_as_uint(__frcp_rn(mf));                          // in (1, 2]
+    const int ex = (int)((br >> 23) & 0xff) - 127;                               // 0, or 1 for r0 = 2
+    const unsigned long long R0 = (unsigned long long)((br & 0x7FFFFFu) | 0x800000u) << (39 + ex);  // r0 * 2^62
+    // |m| r0 * 2^62 = M R0 / 2^53 (M R0 < 2^116)
+    const unsigned long long mr = (__umul64hi(M, R0) << 11) | ((M * R0) >> 53);
+    const unsigned long long d = (2ULL << 62) - mr;  // (2 - |m| r0) * 2^62
+    const unsigned long long R1 = (__umul64hi(R0, d) << 2) | ((R0 * d) >> 62);  // r1 * 2^62, in [2^62, 2^63]
+    const int lz = __clzll((long long)R1);  // 0 only for r1 = 2
+    const unsigned long long mant = ((R1 << lz) >> 11) & 0xFFFFFFFFFFFFFULL;
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(1024 - lz) << 52) | mant));
 }
 
-// 1 / m for a mantissa with 0.5 <= |m| < 1, by Newton-Raphson on
-// f(r) = 1/r - |m|: the seed is the FP32 reciprocal of |m| truncated to 24
-// bits (relative error below 2^-22), and each step  r <- r + r (1 - |m| r)
-// squares the relative error, so two steps reach FP64 rounding (1-2 ulp).
-// The sign of m is put back at the end.
-__device__ __forceinline__ double recip_mantissa(double m) {
-    const long long bm = __double_as_longlong(m);
-    const long long sign = bm & (long long)0x8000000000000000ULL;
-    const double am = __longlong_as_double(bm ^ sign);
-    const float mf = __int_as_float(0x3F000000 | (int)((bm >> 29) & 0x7FFFFF));  // |m| truncated, in [0.5, 1)
-    const float rf = __frcp_rn(mf);                                             // in (1, 2]
-    const int br = __float_as_int(rf);
-    // widen the float (exponent 127 or 128) to a double without a conversion instruction
-    double r = __longlong_as_double(((long long)(((br >> 23) & 0xff) - 127 + 1023) << 52) |
-                                    ((long long)(br & 0x7FFFFF) << 29));
-    double e = fma(-am, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-am, r, 1.0);
-    r = fma(r, e, r);
-    return __longlong_as_double(__double_as_longlong(r) | sign);
-}
+// k / m for mantissas with 0.25 <= |k| <= 1 and 0.5 <= |m| < 1: k times the
+// integer reciprocal above (relative error below 2^-44), one FP64 multiply
+__device__ __forceinline__ double quot_mantissa(double k, double m) { return k * recip_mantissa(m); }
 
 }  // namespace adpar

@@ -1172,6 +1172,65 @@ int run_scan_jvp(int64_t n, const void* a, const void* b, const void* ad, const 
     return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
 }
 
+// the linear recurrence's forward mode on per-thread runs (scan_runs.cuh);
+// its tiles are the scan engine's, so the minimal workspace's dual-state
+// slots serve it
+template <class T>
+int run_linrec_runs_jvp(int64_t n, const void* a, const void* b, const void* ad, const void* bd, void* ys_a,
+                        void* ys_b, void* yd_a, void* yd_b, void* work, size_t work_bytes, cudaStream_t stream) {
+    using Cf = RunCfg<T>;
+    using Op = OpLinrec<T>;
+    static_assert(Cf::TILE == ScanCfg<Op, T>::TILE, "runs tiles are the engine's tiles");
+    static_assert(lb_words<RunD<T>>() == lb_words<DualState<Op>>(), "dual slots");
+    const ScanLayout L = scan_layout<Op, T>(n);
+    if (work == nullptr || work_bytes < L.total_min || (reinterpret_cast<uintptr_t>(work) & 255u))
+        return ADPAR_ERR_WORKSPACE;
+    if (n == 0) return ADPAR_OK;
+    char* w = static_cast<char*>(work);
+    RunJvpArgs<T> R{};
+    R.n = n;
+    R.tiles = (n + Cf::TILE - 1) / Cf::TILE;
+    R.a = static_cast<const T*>(a);
+    R.b = static_cast<const T*>(b);
+    R.ad = static_cast<const T*>(ad);
+    R.bd = static_cast<const T*>(bd);
+    R.ys_a = static_cast<T*>(ys_a);
+    R.ys_b = static_cast<T*>(ys_b);
+    R.yd_a = static_cast<T*>(yd_a);
+    R.yd_b = static_cast<T*>(yd_b);
+    R.hdr = reinterpret_cast<WsHeader*>(w);
+    // a dual state is twice a primal state: its aggregate slots span the
+    // primal aggregate and inclusive regions, its inclusive slots the
+    // adjoint ones (as for the engine's forward mode)
+    R.lb_agg = reinterpret_cast<unsigned long long*>(w + L.off_pA);
+    R.lb_incl = reinterpret_cast<unsigned long long*>(w + L.off_rA);
+    static_assert(lb_words<RunD<T>>() <= 2 * lb_words<RunL<T>>(), "inclusive slots fit the adjoint regions");
+    CUtensorMap tm[8];
+    memset(tm, 0, sizeof(tm));
+    if (n >= Cf::TILE) {
+        const T* ptr[8] = {R.a, R.b, R.ad, R.bd, R.ys_a, R.ys_b, R.yd_a, R.yd_b};
+        for (int i = 0; i < 8; ++i)
+            if (ptr[i] && !make_run_map<T>(&tm[i], ptr[i], n)) return ADPAR_ERR_CUDA;
+    }
+    static bool configured[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return ADPAR_ERR_CUDA;
+    if (!configured[dev]) {
+        if (cudaFuncSetAttribute(linrec_runs_jvp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 4 * Cf::ARR) != cudaSuccess)
+            return ADPAR_ERR_CUDA;
+        configured[dev] = true;
+    }
+    ScanArgs A{};
+    A.hdr = R.hdr;
+    A.tiles = R.tiles;
+    set_slots(A, w, L);
+    launch_init(A, w, L, stream);
+    linrec_runs_jvp_kernel<T><<<(unsigned)R.tiles, Cf::NT, 4 * Cf::ARR, stream>>>(tm[0], tm[1], tm[2], tm[3], tm[4],
+                                                                                   tm[5], tm[6], tm[7], R);
+    return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
+}
+
 template <class T>
 int dispatch_scan_jvp(int op, int64_t n, const void* a, const void* b, const void* ad, const void* bd, void* ys_a,
                       void* ys_b, void* yd_a, void* yd_b, void* work, size_t work_bytes, cudaStream_t s) {
@@ -1181,7 +1240,7 @@ int dispatch_scan_jvp(int op, int64_t n, const void* a, const void* b, const voi
     case ADPAR_OP_MIN: return run_scan_jvp<OpMin<T>, T>(n, a, b, ad, bd, ys_a, ys_b, yd_a, yd_b, work, work_bytes, s);
     case ADPAR_OP_MAX: return run_scan_jvp<OpMax<T>, T>(n, a, b, ad, bd, ys_a, ys_b, yd_a, yd_b, work, work_bytes, s);
     case ADPAR_OP_LINREC:
-        return run_scan_jvp<OpLinrec<T>, T>(n, a, b, ad, bd, ys_a, ys_b, yd_a, yd_b, work, work_bytes, s);
+        return run_linrec_runs_jvp<T>(n, a, b, ad, bd, ys_a, ys_b, yd_a, yd_b, work, work_bytes, s);
     }
     return ADPAR_ERR_INVALID;
 }

@@ -385,3 +385,159 @@ __global__ void __launch_bounds__(RunCfg<T>::NT, 4) linrec_runs_vjp_kernel(
 }
 
 }  // namespace adpar
+
+// ------------------------------------------------- forward mode (JVP)
+// The tangent of the linear-recurrence scan (Sec. 3's dual numbers through
+// the operator): one single-pass scan of dual states (A, B, dA, dB) on
+// per-thread runs.  A tile folds each run from the identity (6 operations
+// per element), scans the runs, looks back over the earlier tiles for its
+// exclusive prefix, then re-folds every run from its exclusive carry and
+// writes the inclusive tangents (and, when asked, the primal) over the
+// input tiles, which leave by TMA.
+namespace adpar {
+
+template <class T>
+struct RunD {  // dual primal state
+    T A, B, dA, dB;
+};
+
+// one element (x = a_j, y = b_j, dx, dy) folded into a dual state
+template <class T>
+__device__ __forceinline__ void rund_push(RunD<T>& s, T x, T y, T dx, T dy) {
+    s.dB = run_fma(dx, s.B, run_fma(x, s.dB, dy));  // d(x B + y)
+    s.B = run_fma(x, s.B, y);
+    s.dA = run_fma(dx, s.A, x * s.dA);  // d(x A)
+    s.A = x * s.A;
+}
+
+template <class T>
+struct RunJvpArgs {
+    int64_t n;
+    int64_t tiles;
+    const T* a;
+    const T* b;
+    const T* ad;
+    const T* bd;
+    T* ys_a;  // nullable
+    T* ys_b;
+    T* yd_a;
+    T* yd_b;
+    WsHeader* hdr;
+    unsigned long long* lb_agg;
+    unsigned long long* lb_incl;
+};
+
+template <class T>
+__global__ void __launch_bounds__(RunCfg<T>::NT) linrec_runs_jvp_kernel(
+    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+    const __grid_constant__ CUtensorMap tmAD, const __grid_constant__ CUtensorMap tmBD,
+    const __grid_constant__ CUtensorMap tmYA, const __grid_constant__ CUtensorMap tmYB,
+    const __grid_constant__ CUtensorMap tmDA, const __grid_constant__ CUtensorMap tmDB, RunJvpArgs<T> R) {
+    using Cf = RunCfg<T>;
+    using D = RunD<T>;
+    constexpr int EPC = Cf::EPC;
+    extern __shared__ __align__(1024) unsigned char s_dyn[];
+    unsigned char* sA = s_dyn;                 // a, then ys_a
+    unsigned char* sB = s_dyn + Cf::ARR;       // b, then ys_b
+    unsigned char* sAD = s_dyn + 2 * Cf::ARR;  // adot, then ysdot_a
+    unsigned char* sBD = s_dyn + 3 * Cf::ARR;  // bdot, then ysdot_b
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ uint32_t s_tile;
+    __shared__ D s_tot[Cf::NW];
+    if (threadIdx.x == 0) s_tile = atomicAdd(&R.hdr->ticket[0], 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const bool whole = (tile + 1) * Cf::TILE <= R.n;
+    const int t = threadIdx.x;
+    {
+        unsigned char* const dst[4] = {sA, sB, sAD, sBD};
+        const CUtensorMap* const tm[4] = {&tmA, &tmB, &tmAD, &tmBD};
+        const T* const src[4] = {R.a, R.b, R.ad, R.bd};
+        const T pad[4] = {T(1), T(0), T(0), T(0)};  // the identity element with a zero tangent
+        run_tile_load<T, 4>(dst, tm, src, pad, whole, tile, R.n, &s_bar, R.hdr);
+    }
+    const D ident{T(1), T(0), T(0), T(0)};
+    D run = ident;
+#pragma unroll
+    for (int p = 0; p < kRunChunks; ++p) {
+        const int off = run_chunk_off(t, p);
+        const RunVec<T> x = run_ld<T>(sA, off), y = run_ld<T>(sB, off);
+        const RunVec<T> dx = run_ld<T>(sAD, off), dy = run_ld<T>(sBD, off);
+#pragma unroll
+        for (int j = 0; j < EPC; ++j) rund_push(run, x.v[j], y.v[j], dx.v[j], dy.v[j]);
+    }
+    // l then r
+    auto comb = [](const D& l, const D& r) {
+        return D{r.A * l.A, run_fma(r.A, l.B, r.B), run_fma(r.dA, l.A, r.A * l.dA),
+                 run_fma(r.dA, l.B, run_fma(r.A, l.dB, r.dB))};
+    };
+    const D agg[1] = {run};
+    D wex[1];
+    const D total = block_scan_part1<D, false, 1, Cf::NW>(agg, wex, s_tot, ident, comb);
+    if ((threadIdx.x >> 5) == 0) {
+        LookbackState<D> st{R.lb_agg, R.lb_incl};
+        const D pre = lookback(tile, st, total, ident, comb, R.hdr);
+        block_fold_prefix<D, 1, Cf::NW>(s_tot, pre, comb);
+    }
+    __syncthreads();
+    D s = block_scan_excl_folded<D, false, 1, Cf::NW>(0, wex, s_tot, comb);
+    const bool want_ys = R.ys_a != nullptr;
+    // re-fold from the exclusive carry: the inclusive outputs over the inputs
+#pragma unroll
+    for (int p = 0; p < kRunChunks; ++p) {
+        const int off = run_chunk_off(t, p);
+        const RunVec<T> x = run_ld<T>(sA, off), y = run_ld<T>(sB, off);
+        const RunVec<T> dx = run_ld<T>(sAD, off), dy = run_ld<T>(sBD, off);
+        RunVec<T> oA, oB, oDA, oDB;
+#pragma unroll
+        for (int j = 0; j < EPC; ++j) {
+            rund_push(s, x.v[j], y.v[j], dx.v[j], dy.v[j]);
+            oA.v[j] = s.A;
+            oB.v[j] = s.B;
+            oDA.v[j] = s.dA;
+            oDB.v[j] = s.dB;
+        }
+        if (want_ys) {
+            run_st<T>(sA, off, oA);
+            run_st<T>(sB, off, oB);
+        }
+        run_st<T>(sAD, off, oDA);
+        run_st<T>(sBD, off, oDB);
+    }
+    if (whole) {
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tma_store_3d(&tmDA, (int)(tile * Cf::NT), sAD);
+            tma_store_3d(&tmDB, (int)(tile * Cf::NT), sBD);
+            if (want_ys) {
+                tma_store_3d(&tmYA, (int)(tile * Cf::NT), sA);
+                tma_store_3d(&tmYB, (int)(tile * Cf::NT), sB);
+            }
+            bulk_commit_and_wait_read();
+        }
+        __syncthreads();
+    } else {
+        const int64_t e0 = tile * Cf::TILE + (int64_t)t * Cf::V;
+#pragma unroll 2
+        for (int p = 0; p < kRunChunks; ++p) {
+            const int off = run_chunk_off(t, p);
+            const RunVec<T> oA = run_ld<T>(sA, off), oB = run_ld<T>(sB, off);
+            const RunVec<T> oDA = run_ld<T>(sAD, off), oDB = run_ld<T>(sBD, off);
+#pragma unroll
+            for (int j = 0; j < EPC; ++j) {
+                const int64_t e = e0 + EPC * p + j;
+                if (e < R.n) {
+                    R.yd_a[e] = oDA.v[j];
+                    R.yd_b[e] = oDB.v[j];
+                    if (want_ys) {
+                        R.ys_a[e] = oA.v[j];
+                        R.ys_b[e] = oB.v[j];
+                    }
+                }
+            }
+        }
+    }
+}
+
+}  // namespace adpar

@@ -271,7 +271,10 @@ int adpar_vjp_scan_wide(adpar_opdesc desc, int64_t n, const void *a, const void 
  * underflows beyond a few thousand factors and an FP64 one beyond about
  * 16000, and every adjoint then rounds to 0; use adpar_vjp_reduce for long
  * products); for MIN/MAX the lowest index of the extremum.  Two
- * single-pass kernels: the forward carries, then the reverse pass.
+ * single-pass kernels: the forward carries, then the reverse pass.  LINREC
+ * with the full workspace runs on per-thread runs (a carry pass storing
+ * run carries and products, then a reverse pass forming rA from the runs'
+ * products); with the ADPAR_WS_MINIMAL size, on the scan engine.
  * Arguments (as for adpar_vjp_scan; b, ybar_b, bbar, y_out_b for LINREC):
  *   n            number of elements (0 allowed: y = neutral element).
  *   a, b         [n] inputs.
@@ -279,7 +282,8 @@ int adpar_vjp_scan_wide(adpar_opdesc desc, int64_t n, const void *a, const void 
  *   abar, bbar   [n] output adjoints.
  *   y_out_a/_b   nullable device scalars: the recomputed y.
  * Flags: ADPAR_ACCUMULATE.
- * Workspace: adpar_workspace_size(ADPAR_RULE_REDUCE_GENERAL, desc, n, 0). */
+ * Workspace: adpar_workspace_size(ADPAR_RULE_REDUCE_GENERAL, desc, n, 0)
+ * (or with ADPAR_WS_MINIMAL: the smaller size, the engine's path). */
 int adpar_vjp_reduce_general(adpar_opdesc desc, int64_t n, const void *a, const void *b,
                              const void *ybar_a, const void *ybar_b, void *abar, void *bbar,
                              void *y_out_a, void *y_out_b, uint32_t flags, void *work,

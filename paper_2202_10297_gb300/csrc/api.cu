@@ -4,6 +4,7 @@
 
 namespace adpar {
 size_t scan_workspace_size(adpar_opdesc d, int64_t n, bool minimal);
+size_t reduce_general_workspace_size(adpar_opdesc d, int64_t n, bool minimal);
 size_t reduce_workspace_size(adpar_opdesc d);
 size_t hist_workspace_size(adpar_opdesc d, int64_t m);
 size_t kmeans_workspace_size(int64_t k);
@@ -36,7 +37,7 @@ extern "C" size_t adpar_workspace_size(int rule, adpar_opdesc d, int64_t n, int6
     rule &= ~ADPAR_WS_MINIMAL;
     switch (rule) {
     case ADPAR_RULE_SCAN: return adpar::scan_workspace_size(d, n, minimal);
-    case ADPAR_RULE_REDUCE_GENERAL: return adpar::scan_workspace_size(d, n, true);  // the scan's slots
+    case ADPAR_RULE_REDUCE_GENERAL: return adpar::reduce_general_workspace_size(d, n, minimal);
     case ADPAR_RULE_SCAN_VEC: return adpar::scan_vec_workspace_size(d, n, m);
     case ADPAR_RULE_HIST_GENERAL: return adpar::hist_general_workspace_size(d, n, m);
     case ADPAR_RULE_SCAN_WIDE: return adpar::scan_wide_workspace_size(d, n);

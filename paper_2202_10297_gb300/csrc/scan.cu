@@ -823,13 +823,16 @@ RunLayout run_layout(int64_t n) {
     return L;
 }
 
+// The runs path's common part: workspace pointers, tensor maps (a, b and
+// the outputs abar, bbar; ya, yb when given) and the carry pass with the
+// segmented carry scan.  Returns ADPAR_OK or an error before launching.
 template <class T>
-int run_linrec_runs(int64_t n, const void* a, const void* b, const void* ya, const void* yb, void* abar,
-                    void* bbar, uint32_t flags, void* work, cudaStream_t stream) {
+int runs_carry_pass(int64_t n, const void* a, const void* b, const void* ya, const void* yb, void* abar, void* bbar,
+                    uint32_t flags, void* work, RunArgs<T>& R, CUtensorMap (&tm)[6], cudaStream_t stream) {
     using Cf = RunCfg<T>;
     const RunLayout L = run_layout<T>(n);
     char* w = static_cast<char*>(work);
-    RunArgs<T> R{};
+    R = RunArgs<T>{};
     R.n = n;
     R.tiles = L.tiles;
     R.a = static_cast<const T*>(a);
@@ -849,14 +852,13 @@ int run_linrec_runs(int64_t n, const void* a, const void* b, const void* ya, con
     static_assert(lb_words<RunP<T>>() * 8 >= sizeof(RunP<T>), "a state fits a slot");
     R.tagg = reinterpret_cast<RunP<T>*>(w + L.off_pA);
     R.tcar = reinterpret_cast<RunP<T>*>(w + L.off_pI);
-    CUtensorMap tm[6];
     memset(tm, 0, sizeof(tm));
     if (n >= Cf::TILE) {
         // whole tiles exist: their copies go through TMA (the partial last
         // tile, and every tile when n < one tile, is copied element-wise)
         const T* ptr[6] = {R.a, R.b, R.ya, R.yb, R.abar, R.bbar};
         for (int i = 0; i < 6; ++i)
-            if (!make_run_map<T>(&tm[i], ptr[i], n)) return ADPAR_ERR_CUDA;
+            if (ptr[i] && !make_run_map<T>(&tm[i], ptr[i], n)) return ADPAR_ERR_CUDA;
     }
     static bool configured[64] = {};
     int dev = 0;
@@ -865,7 +867,9 @@ int run_linrec_runs(int64_t n, const void* a, const void* b, const void* ya, con
         if (cudaFuncSetAttribute(linrec_runs_carry_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  2 * Cf::ARR) != cudaSuccess ||
             cudaFuncSetAttribute(linrec_runs_vjp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 3 * Cf::ARR) != cudaSuccess)
+                                 3 * Cf::ARR) != cudaSuccess ||
+            cudaFuncSetAttribute(linrec_runs_reduce_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 2 * Cf::ARR) != cudaSuccess)
             return ADPAR_ERR_CUDA;
         configured[dev] = true;
     }
@@ -877,7 +881,36 @@ int run_linrec_runs(int64_t n, const void* a, const void* b, const void* ya, con
     // the segment totals take the second half of the tile aggregates' slots
     static_assert(lb_words<RunP<T>>() * 8 >= 2 * sizeof(RunP<T>), "room after the aggregates");
     launch_carry_scan<RunPOp<T>>(R.tagg, R.tcar, R.tagg + L.tiles, L.tiles, stream);
-    linrec_runs_vjp_kernel<T><<<(unsigned)L.tiles, Cf::NT, 3 * Cf::ARR, stream>>>(tm[0], tm[2], tm[3], tm[4], tm[5], R);
+    return ADPAR_OK;
+}
+
+// the scan VJP on per-thread runs
+template <class T>
+int run_linrec_runs(int64_t n, const void* a, const void* b, const void* ya, const void* yb, void* abar,
+                    void* bbar, uint32_t flags, void* work, cudaStream_t stream) {
+    using Cf = RunCfg<T>;
+    RunArgs<T> R;
+    CUtensorMap tm[6];
+    const int st = runs_carry_pass<T>(n, a, b, ya, yb, abar, bbar, flags, work, R, tm, stream);
+    if (st != ADPAR_OK) return st;
+    linrec_runs_vjp_kernel<T><<<(unsigned)R.tiles, Cf::NT, 3 * Cf::ARR, stream>>>(tm[0], tm[2], tm[3], tm[4], tm[5], R);
+    return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
+}
+
+// the reduce VJP by the general rule on per-thread runs (ybar_a, ybar_b:
+// device scalars; y_a, y_b nullable device scalars for the reduction)
+template <class T>
+int run_linrec_runs_reduce(int64_t n, const void* a, const void* b, const void* ybar_a, const void* ybar_b,
+                           void* abar, void* bbar, void* y_a, void* y_b, uint32_t flags, void* work,
+                           cudaStream_t stream) {
+    using Cf = RunCfg<T>;
+    RunArgs<T> R;
+    CUtensorMap tm[6];
+    const int st = runs_carry_pass<T>(n, a, b, nullptr, nullptr, abar, bbar, flags, work, R, tm, stream);
+    if (st != ADPAR_OK) return st;
+    linrec_runs_reduce_kernel<T><<<(unsigned)R.tiles, Cf::NT, 2 * Cf::ARR, stream>>>(
+        tm[0], tm[1], tm[4], tm[5], R, static_cast<const T*>(ybar_a), static_cast<const T*>(ybar_b),
+        static_cast<T*>(y_a), static_cast<T*>(y_b));
     return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
 }
 
@@ -1375,6 +1408,11 @@ int run_reduce_general(int64_t n, const void* a, const void* b, const void* ybar
         if (y_a) reduce_neutral_kernel<Op, T><<<1, 1, 0, stream>>>(static_cast<T*>(y_a), static_cast<T*>(y_b));
         return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
     }
+    if constexpr (std::is_same<Op, OpLinrec<T>>::value) {
+        // per-thread runs, when the workspace holds the runs' carries
+        if (work_bytes >= run_layout<T>(n).total)
+            return run_linrec_runs_reduce<T>(n, a, b, ybar_a, ybar_b, abar, bbar, y_a, y_b, flags, work, stream);
+    }
     char* w = static_cast<char*>(work);
     ScanArgs A{};
     A.n = n;
@@ -1424,6 +1462,15 @@ size_t scan_workspace_size(adpar_opdesc d, int64_t n, bool minimal) {
     else if (d.dtype == ADPAR_F64) L = scan_layout_of<double>(d.op, n, ok);
     if (!ok) return (size_t)-1;
     return minimal ? L.total_min : L.total;
+}
+
+// the general reduce rule: the scan's slots, and for the linear recurrence
+// (unless minimal) room for the runs path's carries
+size_t reduce_general_workspace_size(adpar_opdesc d, int64_t n, bool minimal) {
+    const size_t base = scan_workspace_size(d, n, true);
+    if (base == (size_t)-1 || minimal || d.op != ADPAR_OP_LINREC) return base;
+    const size_t runs = d.dtype == ADPAR_F32 ? run_layout<float>(n).total : run_layout<double>(n).total;
+    return std::max(base, runs);
 }
 
 }  // namespace adpar

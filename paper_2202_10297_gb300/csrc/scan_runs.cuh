@@ -541,3 +541,132 @@ __global__ void __launch_bounds__(RunCfg<T>::NT) linrec_runs_jvp_kernel(
 }
 
 }  // namespace adpar
+
+// --------------------------------------- reduce VJP, general rule (LINREC)
+// The VJP of y = reduce (.) as for the linear recurrence by the general rule
+// of Sec. 5.1: with l_i the composite of the elements before i and r_i of
+// those after it, y = l_i (.) as_i (.) r_i, so abar_i = A(r_i) (ybar_A A(l_i)
+// + ybar_B B(l_i)) and bbar_i = A(r_i) ybar_B, where A(r_i) is the product of
+// the a after i.  After the carry pass (run carries and products, tile
+// carries), a reverse pass per tile re-forms l from the run's carry (2
+// operations per element, plus 2 for ybar_A A + ybar_B B), scans the runs'
+// products of a right to left with a look-back over the later tiles for
+// A(r), and forms the outputs (3 per element): 7 per element here and 2 in
+// the carry pass.
+namespace adpar {
+
+template <class T>
+struct RunS {  // a product of a (scalar look-back state)
+    T c;
+};
+
+template <class T>
+__global__ void __launch_bounds__(RunCfg<T>::NT, 4) linrec_runs_reduce_kernel(
+    const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+    const __grid_constant__ CUtensorMap tmOA, const __grid_constant__ CUtensorMap tmOB, RunArgs<T> R,
+    const T* ybar_a, const T* ybar_b, T* y_a, T* y_b) {
+    using Cf = RunCfg<T>;
+    using S = RunS<T>;
+    constexpr int V = Cf::V, EPC = Cf::EPC;
+    extern __shared__ __align__(1024) unsigned char s_dyn[];
+    unsigned char* sA = s_dyn;            // a, then abar
+    unsigned char* sB = s_dyn + Cf::ARR;  // b, then bbar
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ uint32_t s_tile;
+    __shared__ S s_tot[Cf::NW];
+    if (threadIdx.x == 0) s_tile = atomicAdd(&R.hdr->ticket[1], 1u);
+    __syncthreads();
+    const int64_t t_log = s_tile;
+    const int64_t tile = R.tiles - 1 - t_log;  // tiles are taken right to left
+    const bool whole = (tile + 1) * Cf::TILE <= R.n;
+    const int t = threadIdx.x;
+    const int64_t run = tile * Cf::NT + t;
+    const RunP<T> tc0 = R.tcar[tile];
+    const T lA = R.carA[run], lB = R.carB[run], cprod = R.prod[run];
+    const T PA = tc0.A * lA, PB = run_fma(lA, tc0.B, lB);
+    const T yA = *ybar_a, yB = *ybar_b;
+    if (y_a && t_log == 0 && threadIdx.x == 0) {  // y: the state before the last tile, then the tile
+        const RunP<T> ag = R.tagg[tile];
+        *y_a = tc0.A * ag.A;
+        *y_b = run_fma(ag.A, tc0.B, ag.B);
+    }
+    {
+        unsigned char* const dst[2] = {sA, sB};
+        const CUtensorMap* const tm[2] = {&tmA, &tmB};
+        const T* const src[2] = {R.a, R.b};
+        const T pad[2] = {T(1), T(0)};
+        run_tile_load<T, 2>(dst, tm, src, pad, whole, tile, R.n, &s_bar, R.hdr);
+    }
+    // the product of a after each run: reverse scan of the runs' products,
+    // look-back over the later tiles
+    auto mul = [](const S& x, const S& y) { return S{x.c * y.c}; };
+    const S ident{T(1)};
+    const S agg[1] = {S{cprod}};
+    S wex[1];
+    const S total = block_scan_part1<S, true, 1, Cf::NW>(agg, wex, s_tot, ident, mul);
+    if ((threadIdx.x >> 5) == 0) {
+        LookbackState<S> st{R.lbR_agg, R.lbR_incl};
+        const S pre = lookback(t_log, st, total, ident, mul, R.hdr);
+        block_fold_prefix<S, 1, Cf::NW>(s_tot, pre, mul);
+    }
+    // l re-formed from the run's carry: t_j = ybar_A A_{j-1} + ybar_B B_{j-1}
+    T tj[V];
+    {
+        T A = PA, B = PB;
+#pragma unroll
+        for (int p = 0; p < kRunChunks; ++p) {
+            const int off = run_chunk_off(t, p);
+            const RunVec<T> x = run_ld<T>(sA, off), y = run_ld<T>(sB, off);
+#pragma unroll
+            for (int j = 0; j < EPC; ++j) {
+                tj[EPC * p + j] = run_fma(A, yA, B * yB);
+                B = run_fma(x.v[j], B, y.v[j]);
+                A *= x.v[j];
+            }
+        }
+    }
+    __syncthreads();
+    T rA = block_scan_excl_folded<S, true, 1, Cf::NW>(0, wex, s_tot, mul).c;  // product of a after the run
+    // right to left: the outputs, then fold a_j into the product
+#pragma unroll
+    for (int p = kRunChunks - 1; p >= 0; --p) {
+        const int off = run_chunk_off(t, p);
+        const RunVec<T> x = run_ld<T>(sA, off);
+        RunVec<T> oa, ob;
+#pragma unroll
+        for (int j = EPC - 1; j >= 0; --j) {
+            oa.v[j] = rA * tj[EPC * p + j];
+            ob.v[j] = rA * yB;
+            rA *= x.v[j];
+        }
+        run_st<T>(sA, off, oa);
+        run_st<T>(sB, off, ob);
+    }
+    if (whole && !R.accumulate) {
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tma_store_3d(&tmOA, (int)(tile * Cf::NT), sA);
+            tma_store_3d(&tmOB, (int)(tile * Cf::NT), sB);
+            bulk_commit_and_wait_read();
+        }
+        __syncthreads();
+    } else {
+        const int64_t e0 = tile * Cf::TILE + (int64_t)t * V;
+#pragma unroll 2
+        for (int p = 0; p < kRunChunks; ++p) {
+            const int off = run_chunk_off(t, p);
+            const RunVec<T> oa = run_ld<T>(sA, off), ob = run_ld<T>(sB, off);
+#pragma unroll
+            for (int j = 0; j < EPC; ++j) {
+                const int64_t e = e0 + EPC * p + j;
+                if (e < R.n) {
+                    R.abar[e] = R.accumulate ? R.abar[e] + oa.v[j] : oa.v[j];
+                    R.bbar[e] = R.accumulate ? R.bbar[e] + ob.v[j] : ob.v[j];
+                }
+            }
+        }
+    }
+}
+
+}  // namespace adpar

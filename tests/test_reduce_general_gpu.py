@@ -123,3 +123,24 @@ def test_reduce_general_linrec_full_size(A, oracle):
     ry, rab, rbb = oracle.reduce_general_vjp("linrec", a, 0.5, b=b, ybar_b=1.0)
     assert rel_l2(ab.cpu().numpy(), rab) < 1e-3
     assert rel_l2(bb.cpu().numpy(), rbb) < 1e-3
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+@pytest.mark.parametrize("n", [1, 31, 33, 2049, 4097, 3 * 4096 + 5, 100001, (1 << 20) + 3])
+@pytest.mark.parametrize("minimal", [False, True])
+def test_reduce_general_linrec_both_workspaces(A, oracle, dt, n, minimal):
+    """LINREC by the general rule on per-thread runs (full workspace: run
+    carries and products, the product of the later a from a reverse scan of
+    the runs' products) and on the scan engine (the minimal size), ragged
+    sizes around run and tile edges, against the oracle."""
+    a, b = inputs("linrec", n, dt, seed=n * 7 + 3)
+    ya, yb = -0.5, 1.75
+    code = A.F64 if dt == np.float64 else A.F32
+    flags = A.RULE_REDUCE_GENERAL | (A.WS_MINIMAL if minimal else 0)
+    work = A.workspace(A.adpar_workspace_size(flags, A.OP_LINREC, code, n))
+    ab, bb, y = A.adpar_vjp_reduce_general("linrec", dev(a), ya, b=dev(b), ybar_b=yb, work=work)
+    assert A.adpar_workspace_status(work) == A.OK
+    ry, rab, rbb = oracle.reduce_general_vjp("linrec", a, ya, b=b, ybar_b=yb)
+    assert rel_l2(ab.cpu().numpy(), rab) < tol(dt)
+    assert rel_l2(bb.cpu().numpy(), rbb) < tol(dt)
+    assert rel_l2(y.cpu().numpy(), np.array(ry)) < tol(dt)

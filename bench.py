@@ -548,7 +548,7 @@ def row_prod(args):
 
 
 def row_reduce_general(args):
-    """Reduce VJP by the general rule (Sec. 5.1.1: two exclusive scans, then a
+    """Reduce VJP by the general rule (Sec. 5.1: two exclusive scans, then a
     map): the linear recurrence (no special rule) at 2^26 pairs FP32/FP64, and
     the general vs the special rules for +, max and * at 2^28 FP32."""
     import torch

@@ -1278,7 +1278,7 @@ int dispatch_scan_jvp(int op, int64_t n, const void* a, const void* b, const voi
     return ADPAR_ERR_INVALID;
 }
 
-// ------------------------------------------- reduce, general rule (Sec. 5.1.1)
+// --------------------------------------------- reduce, general rule (Sec. 5.1)
 // y = a_0 (.) ... (.) a_{n-1} for any operator above, and
 //   a_bar_i (+)= d(l_i (.) a_i (.) r_i)/d a_i ^T y_bar
 // with l_i = a_0 (.) ... (.) a_{i-1} (forward exclusive scan) and

@@ -643,121 +643,159 @@ __global__ void __launch_bounds__(kScanBlock) scan_forward_kernel(ScanArgs A) {
     scan_forward_tile<Op, T, Cfg::K, Cfg::E>(A, (int64_t)s_tile);
 }
 
-// --------------------------------------------- + scan, tile in shared memory
+// ---------------------------------------------------- + scan on per-thread runs
 // The return sweep of the + scan is the reverse suffix sum
-// as_bar_i = sum_{j >= i} ys_bar_j.  Every block takes one 64 KB tile,
-// brought into shared memory by one bulk copy (cp.async.bulk completing on
-// an mbarrier), so its registers hold only per-chunk sums and many blocks
-// (with their tiles' loads) stay resident per SM while look-backs run.  The
-// tile is read from shared memory twice: for the per-thread chunk sums,
-// and, once the look-back has given the sum of everything to the right,
-// for the outputs.  Chunk k of a tile holds kScanBlock 16-byte vectors, one
-// per thread (the layout of the scan engine, conflict-free in shared memory).
+// as_bar_i = sum_{j >= i} ys_bar_j.  One block per tile, tiles taken right to
+// left by a ticket.  A tile is kAddRB row blocks of kAddNT rows of 128 bytes
+// (runs of V elements), every thread owning one row in each row block.  Each
+// row block comes into shared memory by one 3-D TMA copy with the 128-byte
+// swizzle of the runs layout (a thread reads its own row without bank
+// conflicts); each thread sums its rows, one reverse block scan over the rows
+// and the look-back give every row the sum of everything to its right, the
+// rows' suffix sums are written back in place and the row blocks leave by
+// TMA stores.  A block holds its tile in shared memory from its load to its
+// stores, so the loads in flight per SM are bounded by the tiles resident
+// there; to keep HBM busy beyond that, each block also asks L2 to prefetch
+// the tile kAddAhead tickets later, which a block launched about a wave
+// later then finds in L2.
+constexpr int kAddNT = 256;     // threads, and rows per row block
+constexpr int kAddRB = 2;       // row blocks per tile
+constexpr int kAddAhead = 152;  // tickets between a tile and the one its block prefetches
+
 template <class T>
-// (tiles of 8 and 12 vectors per thread, and writing whole tiles back by
-// one bulk copy from shared memory, measured no faster at 2^28)
-struct AddSmemCfg {
-    static constexpr int VEC = 16 / sizeof(T);
-    static constexpr int K = 16;
-    static constexpr int TILE = K * kScanBlock * VEC;  // 64 KB
-    static constexpr size_t kSmem = (size_t)TILE * sizeof(T);
+struct AddRunCfg {
+    static constexpr int V = RunCfg<T>::V;
+    static constexpr int TILE = kAddRB * kAddNT * V;  // elements per tile (64 KB)
+    static constexpr int RBB = kAddNT * 128;          // bytes per row block
+    static constexpr int kSmem = kAddRB * RBB;
 };
 
 template <class T>
-__global__ void __launch_bounds__(kScanBlock) scan_add_smem_kernel(ScanArgs A) {
-    using C = AddSmemCfg<T>;
-    constexpr int K = C::K, VEC = C::VEC, TILE = C::TILE, NW = kScanBlock / 32;
-    extern __shared__ __align__(128) unsigned char s_dyn[];
-    T* tile_s = reinterpret_cast<T*>(s_dyn);
+__global__ void __launch_bounds__(kAddNT) scan_add_runs_kernel(const __grid_constant__ CUtensorMap tmY,
+                                                              const __grid_constant__ CUtensorMap tmO, ScanArgs A) {
+    using C = AddRunCfg<T>;
+    constexpr int V = C::V, EPC = RunCfg<T>::EPC, NW = kAddNT / 32, RB = kAddRB, TILE = C::TILE, RBB = C::RBB;
+    extern __shared__ __align__(1024) unsigned char s_dyn[];
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ uint32_t s_tile;
-    __shared__ T s_tot[K * NW];
-    __shared__ T s_pref;
-
+    __shared__ T s_tot[RB * NW];
     if (threadIdx.x == 0) s_tile = atomicAdd(&A.hdr->ticket[1], 1u);
     __syncthreads();
     const int64_t t_log = s_tile;
-    const int64_t tile = A.tiles - 1 - t_log;  // tiles are taken right to left
-    const int64_t base = tile * TILE;
-    const bool full = base + TILE <= A.n;
+    const int64_t tile = A.tiles - 1 - t_log;  // right to left
+    const int64_t row0 = tile * (RB * kAddNT);
+    const int64_t e0 = tile * TILE;
+    const bool whole = e0 + TILE <= A.n;
     const T* ya = static_cast<const T*>(A.ya);
-    if (full) {
-        if (threadIdx.x == 0) {
+    T* abar = static_cast<T*>(A.abar);
+    const int t = threadIdx.x;
+    if (whole) {
+        if (t == 0) {
             tc::mbar_init(&s_bar, 1);
             tc::fence_mbar_init();
             tc::mbar_arrive_expect_tx(&s_bar, (uint32_t)C::kSmem);
-            tc::bulk_load(tile_s, ya + base, (uint32_t)C::kSmem, &s_bar);
+#pragma unroll
+            for (int k = 0; k < RB; ++k) tma_load_3d(s_dyn + k * RBB, &tmY, (int)(row0 + k * kAddNT), &s_bar);
+            // a tile to the left of a whole tile is whole
+            if (tile >= kAddAhead) tc::prefetch_l2(ya + (tile - kAddAhead) * TILE, (uint32_t)(TILE * sizeof(T)));
         }
         __syncthreads();
         bool ok = false;
         for (uint32_t w = 0; w < (1u << 20) && !ok; ++w) ok = tc::mbar_try_wait(&s_bar, 0u);
         if (!ok) record_status(A.hdr, ADPAR_ERR_TIMEOUT);
     } else {
-        for (int64_t i = threadIdx.x; i < TILE; i += kScanBlock) tile_s[i] = base + i < A.n ? ya[base + i] : T(0);
+        // element by element in the same layout, zero past the end (row q of
+        // the tile is row q % kAddNT of row block q / kAddNT)
+        for (int i = t; i < RB * kAddNT * kRunChunks; i += kAddNT) {
+            const int q = i / kRunChunks, p = i % kRunChunks;
+            const int64_t e = e0 + (int64_t)q * V + EPC * p;
+            RunVec<T> v;
+#pragma unroll
+            for (int j = 0; j < EPC; ++j) v.v[j] = e + j < A.n ? ya[e + j] : T(0);
+            run_st<T>(s_dyn + (q / kAddNT) * RBB, run_chunk_off(q % kAddNT, p), v);
+        }
         __syncthreads();
     }
 
-    // per-thread sums of its K vectors, reverse block scan, look-back
+    // the sums of the thread's rows, reverse block scan over the rows, look-back
     auto add = [](const T& x, const T& y) { return x + y; };
-    T agg[K];
+    T agg[RB];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        T v[VEC];
-        load_chunk_smem<VEC>(tile_s, ((int64_t)k * kScanBlock + threadIdx.x) * VEC, v);
-        T sum = v[0];
+    for (int k = 0; k < RB; ++k) {
+        const unsigned char* base = s_dyn + k * RBB;
+        T part[kRunChunks];
 #pragma unroll
-        for (int j = 1; j < VEC; ++j) sum += v[j];
-        agg[k] = sum;
+        for (int p = 0; p < kRunChunks; ++p) {
+            const RunVec<T> x = run_ld<T>(base, run_chunk_off(t, p));
+            T c = x.v[0];
+#pragma unroll
+            for (int j = 1; j < EPC; ++j) c += x.v[j];
+            part[p] = c;
+        }
+#pragma unroll
+        for (int h = kRunChunks / 2; h > 0; h /= 2)
+#pragma unroll
+            for (int p = 0; p < h; ++p) part[p] += part[p + h];
+        agg[k] = part[0];
     }
-    T wex[K];
-    const T total = block_scan_part1<T, true, K, NW>(agg, wex, s_tot, T(0), add);
-    if ((threadIdx.x >> 5) == 0) {
+    T wex[RB];
+    const T total = block_scan_part1<T, true, RB, NW>(agg, wex, s_tot, T(0), add);
+    if ((t >> 5) == 0) {
         LookbackState<T> st{A.lbR_agg, A.lbR_incl};
         const T pre = lookback(t_log, st, total, T(0), add, A.hdr);
-        if ((threadIdx.x & 31) == 0) s_pref = pre;
+        block_fold_prefix<T, RB, NW>(s_tot, pre, add);
     }
     __syncthreads();
 
-    // outputs: the vector's suffix sums plus everything to its right
-    T* abar = static_cast<T*>(A.abar);
+    // each row's suffix sums plus everything to its right, in place
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int64_t off = ((int64_t)k * kScanBlock + threadIdx.x) * VEC;
-        const int64_t e = base + off;
-        if (e >= A.n) continue;
-        T v[VEC];
-        load_chunk_smem<VEC>(tile_s, off, v);
-        T run = block_scan_excl<T, true, K, NW>(k, wex, s_tot, s_pref, add);
+    for (int k = 0; k < RB; ++k) {
+        unsigned char* base = s_dyn + k * RBB;
+        T run = block_scan_excl_folded<T, true, RB, NW>(k, wex, s_tot, add);
 #pragma unroll
-        for (int j = VEC - 1; j >= 0; --j) {
-            run += v[j];
-            v[j] = run;
+        for (int p = kRunChunks - 1; p >= 0; --p) {
+            const int off = run_chunk_off(t, p);
+            RunVec<T> x = run_ld<T>(base, off);
+#pragma unroll
+            for (int j = EPC - 1; j >= 0; --j) {
+                run += x.v[j];
+                x.v[j] = run;
+            }
+            run_st<T>(base, off, x);
         }
-        if (A.accumulate) {
-            T old[VEC];
-            load_chunk_keep(static_cast<const T*>(A.abar), e, A.n, T(0), old);
-#pragma unroll
-            for (int j = 0; j < VEC; ++j) v[j] += old[j];
-        }
-        store_chunk(abar, e, A.n, v);
     }
-}
 
-template <class T>
-int launch_add_smem(ScanArgs A, cudaStream_t stream) {
-    using C = AddSmemCfg<T>;
-    static bool configured[64] = {};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return ADPAR_ERR_CUDA;
-    if (!configured[dev]) {
-        if (cudaFuncSetAttribute(scan_add_smem_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)C::kSmem) != cudaSuccess)
-            return ADPAR_ERR_CUDA;
-        configured[dev] = true;
+    if (whole && !A.accumulate) {
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (t == 0) {
+#pragma unroll
+            for (int k = 0; k < RB; ++k) tma_store_3d(&tmO, (int)(row0 + k * kAddNT), s_dyn + k * RBB);
+            bulk_commit_and_wait_read();
+        }
+    } else {
+        __syncthreads();
+        // coalesced: consecutive threads take consecutive 16-byte chunks
+        for (int i = t; i < RB * kAddNT * kRunChunks; i += kAddNT) {
+            const int q = i / kRunChunks, p = i % kRunChunks;
+            const int64_t e = e0 + (int64_t)q * V + EPC * p;
+            if (e >= A.n) continue;
+            RunVec<T> v = run_ld<T>(s_dyn + (q / kAddNT) * RBB, run_chunk_off(q % kAddNT, p));
+            if (e + EPC <= A.n) {
+                RunVec<T>* dst = reinterpret_cast<RunVec<T>*>(abar + e);
+                if (A.accumulate) {
+                    const RunVec<T> o = *dst;
+#pragma unroll
+                    for (int j = 0; j < EPC; ++j) v.v[j] += o.v[j];
+                }
+                *dst = v;
+            } else {
+#pragma unroll
+                for (int j = 0; j < EPC; ++j)
+                    if (e + j < A.n) abar[e + j] = A.accumulate ? abar[e + j] + v.v[j] : v.v[j];
+            }
+        }
     }
-    A.tiles = (A.n + C::TILE - 1) / C::TILE;
-    scan_add_smem_kernel<T><<<(unsigned)A.tiles, kScanBlock, C::kSmem, stream>>>(A);
-    return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
 }
 
 // ------------------------------------------ linear recurrence, per-thread runs
@@ -794,6 +832,48 @@ bool make_run_map(CUtensorMap* m, const T* ptr, int64_t n) {
     return f(m, dt, 3, const_cast<T*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// An array of n elements as [n / V rows][1][V], box of kAddNT rows, 128-byte
+// swizzle: one row block per copy.
+template <class T>
+bool make_add_map(CUtensorMap* m, const T* ptr, int64_t n) {
+    EncodeTiledFn f = encode_tiled();
+    if (!f) return false;
+    constexpr int V = RunCfg<T>::V;
+    cuuint64_t dims[3] = {(cuuint64_t)V, 1, (cuuint64_t)(n / V)};
+    cuuint64_t strides[2] = {128, 128};
+    cuuint32_t box[3] = {(cuuint32_t)V, 1, (cuuint32_t)kAddNT};
+    cuuint32_t es[3] = {1, 1, 1};
+    const CUtensorMapDataType dt = sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    return f(m, dt, 3, const_cast<T*>(ptr), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <class T>
+int launch_add_runs(ScanArgs A, cudaStream_t stream) {
+    using C = AddRunCfg<T>;
+    static bool configured[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return ADPAR_ERR_CUDA;
+    if (!configured[dev]) {
+        if (cudaFuncSetAttribute(scan_add_runs_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem) !=
+            cudaSuccess)
+            return ADPAR_ERR_CUDA;
+        configured[dev] = true;
+    }
+    A.tiles = (A.n + C::TILE - 1) / C::TILE;
+    if (A.tiles == 0) return ADPAR_OK;
+    CUtensorMap tm[2];
+    memset(tm, 0, sizeof(tm));
+    if (A.n >= C::TILE) {  // whole tiles exist: they move by TMA
+        if (!make_add_map<T>(&tm[0], static_cast<const T*>(A.ya), A.n) ||
+            !make_add_map<T>(&tm[1], static_cast<const T*>(A.abar), A.n))
+            return ADPAR_ERR_CUDA;
+    }
+    scan_add_runs_kernel<T><<<(unsigned)A.tiles, kAddNT, C::kSmem, stream>>>(tm[0], tm[1], A);
+    return cudaGetLastError() == cudaSuccess ? ADPAR_OK : ADPAR_ERR_CUDA;
 }
 
 struct RunLayout {
@@ -1085,8 +1165,8 @@ int run_scan(int64_t n, const void* a, const void* b, const void* ya, const void
         if constexpr (std::is_same<Op, OpAdd<T>>::value) {
             // the tile in shared memory needs fewer look-back slots than the
             // register tile the layout is sized for (its tiles are larger)
-            static_assert(AddSmemCfg<T>::TILE >= ScanCfg<Op, T>::TILE, "no more tiles than slots");
-            if (!ys_a) return launch_add_smem<T>(A, stream);
+            static_assert(AddRunCfg<T>::TILE >= ScanCfg<Op, T>::TILE, "no more tiles than slots");
+            if (!ys_a) return launch_add_runs<T>(A, stream);
         }
         if (need_primal) {
             // the tile aggregates take the primal aggregate slots, unused here

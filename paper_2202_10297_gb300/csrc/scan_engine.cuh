@@ -19,6 +19,14 @@ __device__ __forceinline__ int chunk_warp_pos(int k, int w) {
     return REV ? (K - 1 - k) * NW + (NW - 1 - w) : k * NW + w;
 }
 
+// The barrier of a block scan: the whole block (BAR = 0) or, in a kernel
+// with warps outside the scan, named barrier BAR over the NW scanning warps.
+template <int BAR, int NW>
+__device__ __forceinline__ void scan_bar() {
+    if constexpr (BAR == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(NW * 32) : "memory");
+}
+
 // Part 1 of a block scan.  agg[k] is the thread's aggregate of its V
 // elements of chunk k (in scan order).  On return:
 //   wex[k]        the warp-exclusive prefix of the thread for chunk k,
@@ -26,8 +34,8 @@ __device__ __forceinline__ int chunk_warp_pos(int k, int w) {
 //   return value  (in warp 0) the aggregate of the whole tile.
 // Warp 0 scans the K*NW per-warp totals with R = ceil(K*NW/32) of them per
 // lane.  Warp 0 writes s_tot after the internal barrier, so callers must
-// __syncthreads() before block_scan_excl reads it.
-template <class S, bool REV, int K, int NW, class Comb>
+// pass the same barrier again before block_scan_excl reads it.
+template <class S, bool REV, int K, int NW, int BAR = 0, class Comb>
 __device__ __forceinline__ S block_scan_part1(const S (&agg)[K], S (&wex)[K], S* s_tot,
                                               const S& ident, Comb comb) {
     constexpr int Q = K * NW;
@@ -48,7 +56,7 @@ __device__ __forceinline__ S block_scan_part1(const S (&agg)[K], S (&wex)[K], S*
         wex[k] = ex;
         if (REV ? lane == 0 : lane == 31) s_tot[chunk_warp_pos<REV, K, NW>(k, warp)] = inc;
     }
-    __syncthreads();
+    scan_bar<BAR, NW>();
     S total = ident;
     if (warp == 0) {
         // with one total per lane (Q <= 32) the scan needs only the steps

@@ -71,6 +71,11 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
         "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
         : "memory");
 }
+// Asks L2 to fetch `bytes` from global memory (16-byte aligned, a multiple
+// of 16 bytes) without waiting: a later copy of the same bytes then hits L2.
+__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 // Orders this thread's earlier shared-memory accesses before later bulk
 // (async-proxy) copies into the same memory.
 __device__ __forceinline__ void fence_proxy_async() {

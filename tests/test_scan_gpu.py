@@ -269,12 +269,15 @@ def test_linrec_runs_path(A, oracle, dt, n, accumulate):
 
 
 @pytest.mark.parametrize("dt", [np.float32, np.float64])
-@pytest.mark.parametrize("n", [1, 3, 4, 5, 8191, 8192, 8193, 16383, 16384, 16385, 3 * 16384 + 7, 1000003])
+@pytest.mark.parametrize("n", [1, 3, 4, 5, 8191, 8192, 8193, 16383, 16384, 16385, 3 * 16384 + 7, 1000003,
+                               1000 * 16384 + 5])
 @pytest.mark.parametrize("accumulate", [False, True])
-def test_add_scan_shared_tile_path(A, oracle, dt, n, accumulate):
-    """The + scan VJP without the recomputed ys takes whole 64 KB tiles
-    through one bulk copy into shared memory (the last tile element by
-    element): sizes around its tile edges (16384 FP32 / 8192 FP64 elements),
+def test_add_scan_runs_path(A, oracle, dt, n, accumulate):
+    """The + scan VJP without the recomputed ys runs on 128-byte rows in
+    tiles of 512 rows (16384 FP32 / 8192 FP64 elements) moved by TMA through
+    a ring of tiles per block, with the carries formed from the tile sums of
+    lower tickets (the last tile element by element): sizes around row and
+    tile edges, a size with several tiles per block (the ring wraps),
     overwrite and accumulation, against the oracle."""
     y = synth.normal(n, dt, seed=n + 31)
     base = synth.normal(n, dt, seed=32) if accumulate else np.zeros(n, dt)

@@ -91,9 +91,9 @@ LINREC_FLOP_PER_PAIR = 10
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes per call of the FP64 linear-recurrence VJP (carry pass + reverse
 # pass of the runs path), from an ncu capture at n = 2^24 (carry: 268.5 MB
-# read + 18.5 MB written; reverse: 563.4 + 244.8 MB) scaled by 4 to 2^26
+# read + 18.3 MB written; reverse: 563.6 + 245.0 MB) scaled by 4 to 2^26
 # (traffic grows in proportion to n)
-LINREC_F64_TRAFFIC_PER_CALL = 4 * (268450816 + 18455040 + 563448064 + 244848128)
+LINREC_F64_TRAFFIC_PER_CALL = 4 * (268452096 + 18297344 + 563612928 + 244971008)
 
 WORKLOAD = ("scan VJPs: linear-recurrence n=2^26 pairs FP32 and FP64 (a~U[0.9,1], b,ybar~N(0,1)); "
             "+ scan and max scan n=2^28 FP32 N(0,1)")

@@ -1096,7 +1096,7 @@ ROWS = {"prod": row_prod, "hist": row_hist, "hist_general": row_hist_general, "s
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=400)  # a timed region of about 1.2 s
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="adpar", choices=["adpar", "reference"])
     ap.add_argument("--workload", default="scan",

@@ -89,6 +89,21 @@ def test_noalloc_matches_workspace_entry_two_calls(A):
     assert rel_l2(ab3.cpu().numpy(), ab_ref.cpu().numpy()) < 1e-12
     assert rel_l2(bb3.cpu().numpy(), bb_ref.cpu().numpy()) < 1e-12
 
+    # call 4: + scan VJP in FP32 over many TMA tiles of 16384 elements and a
+    # ragged one, overwriting, then accumulating
+    n4 = 200 * 16384 + 9
+    y4 = synth.normal(n4, np.float32, seed=36)
+    ref4, _, _ = A.adpar_vjp_scan("add", None, dev(y4))
+    out4 = torch.empty(n4, dtype=torch.float32, device="cuda")
+    A.adpar_vjp_scan_noalloc("add", None, dev(y4), abar=out4)
+    torch.cuda.synchronize()
+    assert A.adpar_noalloc_status() == A.OK
+    assert rel_l2(out4.cpu().numpy(), ref4.cpu().numpy()) < 1e-5
+    A.adpar_vjp_scan_noalloc("add", None, dev(y4), abar=out4, accumulate=True)
+    torch.cuda.synchronize()
+    assert A.adpar_noalloc_status() == A.OK
+    assert rel_l2(out4.cpu().numpy(), 2 * ref4.cpu().numpy()) < 1e-5
+
 
 def test_noalloc_call_takes_no_device_memory(A):
     # inputs and outputs first; one warm-up call loads every kernel the call uses

@@ -114,6 +114,7 @@ __device__ void prod_reduce_tile(const adpar_batch_segment& sg, char* st, const 
     __shared__ int s_last;
     const T* x = static_cast<const T*>(sg.x);
     const int64_t lo = (int64_t)r * RT, hi = std::min<int64_t>(sg.len, lo + RT);
+    range_prefetch_l2(x, lo, hi);
     ProdStateQ ps = ProdStateQ::id();  // fixed-point products: no FP64 per element
     constexpr int V = Vec16<T>::N;
     for (int64_t i = lo + threadIdx.x * V; i < hi; i += 256 * V) {
@@ -165,15 +166,16 @@ __device__ void prod_map_tile(const adpar_batch_segment& sg, char* st, const Sta
                               WsHeader* hdr) {
     __shared__ ProdState s_fin;
     unsigned int* counter = reinterpret_cast<unsigned int*>(st + L.counter);
+    range_prefetch_l2(static_cast<const T*>(sg.x), (int64_t)r * RT, std::min<int64_t>(sg.len, (int64_t)r * RT + RT));
     if (threadIdx.x == 0) {
         if (wait_flag(counter + 1, hdr) != 0u) s_fin = ld_cg(reinterpret_cast<const ProdState*>(st + L.final_state));
         else s_fin = ProdState::id();
     }
     __syncthreads();
-    const ProdState f = s_fin;
     const T* x = static_cast<const T*>(sg.x);
     T* xb = static_cast<T*>(sg.xbar);
     const int64_t lo = (int64_t)r * RT, hi = std::min<int64_t>(sg.len, lo + RT);
+    const ProdState f = s_fin;
     const double yb = sg.ybar_prod;
     double ym = 0.0;
     int64_t ye = 0;

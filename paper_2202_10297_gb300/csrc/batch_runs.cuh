@@ -29,6 +29,16 @@ constexpr int brun_tile() {
     return kBNT * RunCfg<T>::V;  // elements per tile: 4096 FP64, 8192 FP32
 }
 
+// Thread 0 asks L2 for elements [lo, hi) of p (the whole 16-byte units):
+// L2 fetches the whole range at once, so the block's own loads that follow
+// wait for about one memory latency instead of one per batch of loads in
+// flight.  p + lo must be 16-byte aligned.
+template <class T>
+__device__ __forceinline__ void range_prefetch_l2(const T* p, int64_t lo, int64_t hi) {
+    const uint32_t bytes = (uint32_t)(((hi - lo) * (int64_t)sizeof(T)) & ~(int64_t)15);
+    if (threadIdx.x == 0 && hi > lo && bytes > 0) tc::prefetch_l2(p + lo, bytes);
+}
+
 // a segment's runs state in the workspace
 struct BRunState {
     unsigned long long* p_agg;   // forward look-back slots (RunP)
@@ -89,6 +99,9 @@ __device__ void brun_fwd_tile(const T* a, const T* b, int64_t n, const BRunState
     unsigned char* sA = smem;
     unsigned char* sB = smem + kBArr;
     const int64_t e0 = tile * brun_tile<T>();
+    const int64_t e1 = min(n, e0 + (int64_t)brun_tile<T>());
+    range_prefetch_l2(a, e0, e1);
+    range_prefetch_l2(b, e0, e1);
     brun_load<T>(sA, a, e0, n, T(1));  // (1, 0) is the neutral element
     brun_load<T>(sB, b, e0, n, T(0));
     __syncthreads();
@@ -139,6 +152,11 @@ __device__ void brun_rev_tile(const T* a, const T* b, const T* ya, const T* yb, 
     const int64_t tile = tiles - 1 - t_log;  // right to left
     const int64_t e0 = tile * brun_tile<T>();
     const int t = threadIdx.x;
+    const int64_t e1 = min(n, e0 + (int64_t)brun_tile<T>());
+    range_prefetch_l2(a, e0, e1);
+    range_prefetch_l2(ya, e0, e1);
+    range_prefetch_l2(yb, e0, e1);
+    range_prefetch_l2(b, e0, e1);
     // the cotangents and a need no carry: their tiles load first
     brun_load<T>(sA, a, e0, n, T(1));
     brun_load<T>(sYA, ya, e0, n, T(0));
